@@ -1,0 +1,261 @@
+/*
+ * fe.h -- C ABI of a GB300 (sm_103a) library for finite-element numerical
+ * integration with first-order elements: per-element stiffness matrices A^e and
+ * load vectors b^e for linear tetrahedra and linear 6-node prisms.
+ *
+ * The operation is the one of Banas, Kruzel, Bielanski, arXiv 1504.01023:
+ *   (A^e)^{rs} = int_{Omega_e} ( c^{i;j} phi^r_{,i} phi^s_{,j} + c^{i;0} phi^r_{,i} phi^s
+ *                               + c^{0;i} phi^r phi^s_{,i} + c^{0;0} phi^r phi^s ) dOmega
+ *   (b^e)^{r}  = int_{Omega_e} ( d^i phi^r_{,i} + d^0 phi^r ) dOmega
+ * (Sec. 2.2, Eqs. sm_local and lv_local), evaluated through the reference element
+ * (Eq. change_of_variables) with Gaussian quadrature (Eq. quadrature), following
+ * the generic procedure of Algorithm 1 and its QSS orderings (Algorithms 2, 3).
+ * Boundary terms are not computed (Sec. 2.1 neglects them).
+ *
+ * Conventions used by every entry point
+ *  - No exception crosses the ABI; every call returns an fe_status.
+ *  - Pointers marked "device" are CUDA device pointers of the context's device,
+ *    owned by the caller unless stated otherwise. Pointers marked "host" are plain
+ *    host memory (pinned memory makes the copies asynchronous).
+ *  - A `stream` argument is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is enqueued on it; the call returns after the enqueue.
+ *    Asynchronous device errors are reported by fe_ctx_sync, fe_serve_poll or the
+ *    next call on the context.
+ *  - Index 0 of the coefficient arrays means the function value, 1..3 the x,y,z
+ *    derivatives: C[a][b] (a,b = 0..3) holds c^{a;b}, D[a] holds d^a. Row r of A^e
+ *    is the test function, column s the trial function.
+ *  - Reference elements and node order: tetrahedron {xi,eta,zeta >= 0,
+ *    xi+eta+zeta <= 1} with shape functions 1-xi-eta-zeta, xi, eta, zeta for
+ *    vertices 0..3; prism = triangle {xi,eta >= 0, xi+eta <= 1} x zeta in [-1,1],
+ *    vertices 0..2 the bottom triangle (zeta = -1) and 3..5 the top one, vertex
+ *    k+3 above vertex k.
+ *  - A context is used by one host thread at a time, except fe_serve_submit,
+ *    fe_serve_poll and fe_serve_release, which may be called from any thread.
+ */
+#ifndef FE_H_
+#define FE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FE_ABI_VERSION 1
+
+typedef enum fe_status {
+    FE_OK = 0,
+    FE_NOT_READY = 1,          /* serving: the request has not finished yet */
+    FE_ERR_INVALID_ARG = -1,   /* a pointer, size, enum or layout is not valid */
+    FE_ERR_OOM = -2,           /* a device or host allocation failed */
+    FE_ERR_BUDGET = -3,        /* serving: the request can never fit the HBM budget */
+    FE_ERR_CUDA = -4,          /* a CUDA runtime call failed (text in fe_last_error) */
+    FE_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
+    FE_ERR_UNSUPPORTED = -6    /* valid but not implemented combination */
+} fe_status;
+
+typedef enum fe_elem_type { FE_TET = 0, FE_PRISM = 1 } fe_elem_type;
+
+/* Sec. 4.1: "Poisson" = Laplace operator (c^{i;j} = delta_ij, no other c),
+   d^0 per integration point; "conv-diff" (here FE_GENERIC) = all 16 c and 4 d. */
+typedef enum fe_problem { FE_POISSON = 0, FE_GENERIC = 1 } fe_problem;
+
+/* FE_FP64: all arithmetic in double, inputs and outputs double.
+   FE_FP32_MIXED: coordinates stay double in memory; edge vectors are formed
+   exactly enough in single precision, the coefficient and shape-derivative
+   arithmetic and accumulation run in float, coefficients and outputs are float.
+   Elements that fail a mean-ratio shape test (quality < 0.1) get their Jacobian,
+   determinant and inverse in double (flag bit 0). */
+typedef enum fe_precision { FE_FP64 = 0, FE_FP32_MIXED = 1 } fe_precision;
+
+/* Gaussian rules (Sec. 2.3; the paper names no points, these are the readings):
+   TET1   centroid, weight 1/6 (degree 1);
+   TET4   barycentric permutations of (b,a,a,a), a=(5-sqrt5)/20, b=(5+3sqrt5)/20,
+          weights 1/24 (degree 2);
+   PRISM6 triangle {(1/6,1/6),(2/3,1/6),(1/6,2/3)} weights 1/6 x Gauss-Legendre
+          zeta = -+1/sqrt3 weights 1. */
+typedef enum fe_quad { FE_QUAD_TET1 = 0, FE_QUAD_TET4 = 1, FE_QUAD_PRISM6 = 2 } fe_quad;
+
+/* Sec. 3.3 takes coefficients constant per element; per integration point is the
+   input mode of the prism workload with varying coefficients. */
+typedef enum fe_coef_mode { FE_COEF_PER_ELEMENT = 0, FE_COEF_PER_QPOINT = 1 } fe_coef_mode;
+
+/* Sec. 4.2 (Figs. 1, 2): SOA = one plane per scalar, elements contiguous inside a
+   plane ("coalesced" order); AOS = the "natural" order, all scalars of one
+   element contiguous. */
+typedef enum fe_layout { FE_LAYOUT_SOA = 0, FE_LAYOUT_AOS = 1 } fe_layout;
+
+typedef enum fe_memory { FE_MEM_DEVICE = 0, FE_MEM_HOST = 1 } fe_memory;
+
+typedef struct fe_ctx fe_ctx;
+
+typedef struct fe_ctx_config {
+    int device;                    /* CUDA device ordinal */
+    uint64_t hbm_budget_bytes;     /* serving admission budget; 0 = 120e9 bytes */
+    int serve_slots;               /* serving launches in flight at once; 0 = 4 */
+    int autotune;                  /* 1: time the candidate launch shapes of a key on
+                                      its first use and keep the fastest */
+    const char *tuning_cache_path; /* text file holding tuned shapes; NULL = none */
+} fe_ctx_config;
+
+/*
+ * Inputs of one element set of a single type (Sec. 2.3, input list): geometry
+ * degrees of freedom (vertex coordinates), the coefficients, the rule.
+ *
+ * coords (double, always): NS = 4 (tet) or 6 (prism) vertices x 3 coordinates.
+ *   SOA: scalar j = 3*v + d lives at coords[j*coords_stride + e].
+ *   AOS: coords[(e*NS + v)*3 + d].
+ * coefs (double for FE_FP64, float for FE_FP32_MIXED), NC scalars per element:
+ *   FE_GENERIC: 20 per point (C[4][4] row-major, then D[4]); FE_POISSON: 1 per
+ *   point (d^0). NC = that count times NQ for FE_COEF_PER_QPOINT (point-major:
+ *   scalar j = q*per_point + k), times 1 for FE_COEF_PER_ELEMENT.
+ *   SOA: scalar j at coefs[j*coefs_stride + e]; AOS: coefs[e*NC + j].
+ * A stride of 0 means n_elem. SOA strides are counted in elements.
+ */
+typedef struct fe_elem_args {
+    int64_t n_elem;
+    const double *coords;
+    fe_layout coords_layout;
+    int64_t coords_stride;
+    fe_problem kind;
+    fe_quad quad;
+    fe_coef_mode coef_mode;
+    const void *coefs;
+    fe_layout coefs_layout;
+    int64_t coefs_stride;
+    fe_precision prec;
+    fe_memory memory;              /* where coords and coefs live */
+} fe_elem_args;
+
+/*
+ * Outputs (Sec. 4.2, Fig. 2): A^e full NS x NS (not symmetric-packed), row-major
+ * entry k = r*NS + s; b^e NS entries. Element type: double (FE_FP64) or float.
+ *   SOA ("coalesced"): A[k*stride + e], b[r*stride + e].
+ *   AOS (element-contiguous): A[e*NS*NS + k], b[e*NS + r].
+ * flags (optional, may be NULL): one byte per element, bit 0 = the double
+ * Jacobian path was used, bit 1 = det J < 0 somewhere (|det J| is integrated),
+ * bit 2 = degenerate (|det J| <= 1e-300 in double): A^e = 0 and b^e = 0.
+ */
+typedef struct fe_out {
+    void *A;
+    void *b;
+    fe_layout layout;
+    int64_t stride;
+    uint8_t *flags;
+    fe_memory memory;              /* where A, b and flags live */
+} fe_out;
+
+/* Create a context on cfg->device (NULL cfg = device 0, defaults). Allocates the
+   context's scratch (fix-up lists, status words) and streams. */
+fe_status fe_ctx_create(const fe_ctx_config *cfg, fe_ctx **out);
+/* Stop serving, free every resident mesh, output and scratch buffer. */
+fe_status fe_ctx_destroy(fe_ctx *ctx);
+/* Wait for all work of the context and report the first asynchronous error. */
+fe_status fe_ctx_sync(fe_ctx *ctx);
+/* Text of the last error on this context (thread-local when ctx is NULL). */
+const char *fe_last_error(fe_ctx *ctx);
+
+/*
+ * Integrate n_elem tetrahedra (Algorithm 3, QSS_geo_linear: the Jacobian terms
+ * are formed once per element) / n_elem prisms (Algorithm 2, QSS_geo_generic:
+ * the Jacobian terms are formed at each integration point).
+ * Quadrature: tet FE_QUAD_TET1 or FE_QUAD_TET4; prism FE_QUAD_PRISM6.
+ * With memory = FE_MEM_HOST (inputs) and/or FE_MEM_HOST (outputs) the call copies
+ * through device staging buffers of the context in chunks, overlapping the copies
+ * with the kernels, and returns once the outputs are in host memory.
+ * Errors: FE_ERR_INVALID_ARG (null or misaligned pointer, stride < n_elem, quad
+ * not valid for the type), FE_ERR_OOM (staging or scratch growth failed),
+ * FE_ERR_CUDA. n_elem = 0 is valid and does nothing.
+ */
+fe_status fe_integrate_tet(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream);
+fe_status fe_integrate_prism(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream);
+
+/* Host-only argument validation used by the calls above (no CUDA call). */
+fe_status fe_check_args(fe_elem_type type, const fe_elem_args *args, const fe_out *out);
+
+/* Algorithmic bytes moved per element (inputs read once, outputs written once):
+   8*3*NS for coordinates + coefficient bytes + (NS*NS + NS) output scalars; the
+   double-precision cases of Table 3 give 288, 528, 416, 640. -1 if invalid. */
+int64_t fe_bytes_per_element(fe_elem_type type, fe_problem kind, fe_quad quad, fe_coef_mode mode,
+                             fe_precision prec);
+
+/*
+ * Resident meshes (Sec. 3.1: element data kept in the memory of the processor
+ * doing the integration). Copies geometry (host or device source, any layout) into
+ * a context-owned SOA buffer and returns its id. Counted against the HBM budget.
+ */
+fe_status fe_mesh_register(fe_ctx *ctx, fe_elem_type type, int64_t n_elem, const double *coords,
+                           fe_layout layout, fe_memory memory, int64_t *mesh_id);
+fe_status fe_mesh_release(fe_ctx *ctx, int64_t mesh_id);
+
+/*
+ * Batched integration: many element sets of uneven size and mixed type/kind in
+ * one persistent kernel launched from a captured CUDA graph (not in the paper,
+ * which launches one homogeneous set per kernel, Sec. 3.2). Items must be
+ * FE_FP32_MIXED with SOA inputs and outputs in device memory. The graph for a
+ * given item list is captured on first submission and replayed afterwards.
+ */
+typedef struct fe_batch_item {
+    fe_elem_type type;
+    fe_elem_args args;
+    fe_out out;
+} fe_batch_item;
+fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, void *stream);
+
+/*
+ * Serving: requests on resident meshes arrive at any time; a scheduler thread
+ * admits them under the HBM budget (outputs are context-owned until released),
+ * merges waiting requests into one batched launch and keeps up to serve_slots
+ * launches in flight, so requests that arrive while others run overlap with them
+ * on the device. coefs is a device pointer in SOA layout with stride n_elem.
+ */
+typedef struct fe_request {
+    int64_t mesh_id;
+    fe_problem kind;
+    fe_quad quad;
+    fe_coef_mode coef_mode;
+    const void *coefs;
+    fe_precision prec;             /* FE_FP32_MIXED (batched) or FE_FP64 (own launch) */
+} fe_request;
+
+typedef struct fe_result {
+    fe_status status;
+    fe_elem_type type;
+    int64_t n_elem;
+    void *A;                       /* device, SOA with stride n_elem, context-owned */
+    void *b;
+    uint8_t *flags;
+    double t_submit_us;            /* host clock, microseconds */
+    double t_launch_us;
+    double t_done_us;
+} fe_result;
+
+/* Queue a request; FE_ERR_BUDGET if it could never fit. Thread-safe. */
+fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket);
+/* FE_NOT_READY while running; FE_OK with res filled when done. Thread-safe. */
+fe_status fe_serve_poll(fe_ctx *ctx, uint64_t ticket, fe_result *res);
+/* Free a finished request's outputs and return its bytes to the budget. */
+fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket);
+
+/* Number of kernels this library has launched in this process (graph replays
+   count the kernels in the graph). */
+uint64_t fe_launch_count(void);
+
+/* Profiling: when on, the integration calls record CUDA events around their main
+   kernel on the launching stream; fe_ctx_kernel_time returns the summed device
+   time in ms and the launch count since the last reset (it synchronises). */
+fe_status fe_ctx_set_profiling(fe_ctx *ctx, int on);
+fe_status fe_ctx_kernel_time(fe_ctx *ctx, double *ms, int64_t *launches, int reset);
+
+/* Autotuner: time every candidate launch shape for the key of (type, args, out)
+   now, on these buffers, and keep the fastest. Writes the tuning cache if set. */
+fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
+                  void *stream);
+/* The launch shape that the next call with this key would use. */
+fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
+                       int *block_threads, int *elems_per_thread);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H_ */
