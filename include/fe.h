@@ -251,9 +251,11 @@ fe_status fe_ctx_kernel_time(fe_ctx *ctx, double *ms, int64_t *launches, int res
    now, on these buffers, and keep the fastest. Writes the tuning cache if set. */
 fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                   void *stream);
-/* The launch shape that the next call with this key would use. */
+/* The launch shape that the next call with this key would use: threads (=
+   elements) per block, and whether the grid is persistent (one wave of resident
+   blocks striding over tiles) or one block per tile. */
 fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
-                       int *block_threads, int *elems_per_thread);
+                       int *block_threads, int *persistent);
 
 #ifdef __cplusplus
 }

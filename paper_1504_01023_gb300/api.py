@@ -1,0 +1,330 @@
+"""Thin Python binding of the C ABI in include/fe.h (argument marshalling only).
+
+Every step of the integration runs in ``libfe.so``; this module only converts
+torch tensors (device memory and streams come from PyTorch) into pointers,
+strides and enums. It raises if the library has not been built: there is no
+Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+# enums (values as in include/fe.h)
+FE_OK, FE_NOT_READY = 0, 1
+TET, PRISM = 0, 1
+POISSON, GENERIC = 0, 1
+FP64, FP32_MIXED = 0, 1
+QUAD_TET1, QUAD_TET4, QUAD_PRISM6 = 0, 1, 2
+PER_ELEMENT, PER_QPOINT = 0, 1
+SOA, AOS = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+NS = {TET: 4, PRISM: 6}
+NQ = {QUAD_TET1: 1, QUAD_TET4: 4, QUAD_PRISM6: 6}
+
+_STATUS = {0: "FE_OK", 1: "FE_NOT_READY", -1: "FE_ERR_INVALID_ARG", -2: "FE_ERR_OOM", -3: "FE_ERR_BUDGET",
+           -4: "FE_ERR_CUDA", -5: "FE_ERR_TIMEOUT", -6: "FE_ERR_UNSUPPORTED"}
+
+
+class FeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CtxConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_uint64), ("serve_slots", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("tuning_cache_path", ctypes.c_char_p)]
+
+
+class ElemArgs(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("coords", ctypes.c_void_p), ("coords_layout", ctypes.c_int),
+                ("coords_stride", ctypes.c_int64), ("kind", ctypes.c_int), ("quad", ctypes.c_int),
+                ("coef_mode", ctypes.c_int), ("coefs", ctypes.c_void_p), ("coefs_layout", ctypes.c_int),
+                ("coefs_stride", ctypes.c_int64), ("prec", ctypes.c_int), ("memory", ctypes.c_int)]
+
+
+class Out(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("layout", ctypes.c_int), ("stride", ctypes.c_int64),
+                ("flags", ctypes.c_void_p), ("memory", ctypes.c_int)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("args", ElemArgs), ("out", Out)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("mesh_id", ctypes.c_int64), ("kind", ctypes.c_int), ("quad", ctypes.c_int), ("coef_mode", ctypes.c_int),
+                ("coefs", ctypes.c_void_p), ("prec", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("type", ctypes.c_int), ("n_elem", ctypes.c_int64), ("A", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("t_submit_us", ctypes.c_double),
+                ("t_launch_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+# (name, restype, argtypes) of every exported entry point
+_P = ctypes.c_void_p
+_SIGS = [
+    ("fe_ctx_create", ctypes.c_int, [ctypes.POINTER(CtxConfig), ctypes.POINTER(_P)]),
+    ("fe_ctx_destroy", ctypes.c_int, [_P]),
+    ("fe_ctx_sync", ctypes.c_int, [_P]),
+    ("fe_last_error", ctypes.c_char_p, [_P]),
+    ("fe_integrate_tet", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
+    ("fe_integrate_prism", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
+    ("fe_check_args", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out)]),
+    ("fe_bytes_per_element", ctypes.c_int64, [ctypes.c_int] * 5),
+    ("fe_mesh_register", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    ("fe_mesh_release", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("fe_batch_submit", ctypes.c_int, [_P, ctypes.POINTER(BatchItem), ctypes.c_int, _P]),
+    ("fe_serve_submit", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("fe_serve_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
+    ("fe_serve_release", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("fe_launch_count", ctypes.c_uint64, []),
+    ("fe_ctx_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
+    ("fe_ctx_kernel_time", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+    ("fe_tune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
+    ("fe_get_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libfe.so (it must have been built by ``build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"{_build.LIB} is missing: build it with __graft_entry__.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, res, args in _SIGS:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, ctx_handle=None):
+    if st != FE_OK:
+        msg = load().fe_last_error(ctx_handle)
+        raise FeError(st, msg.decode() if msg else "")
+    return st
+
+
+def bytes_per_element(elem_type, kind, quad, coef_mode, prec) -> int:
+    return int(load().fe_bytes_per_element(elem_type, kind, quad, coef_mode, prec))
+
+
+def launch_count() -> int:
+    return int(load().fe_launch_count())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _mem(t):
+    return MEM_DEVICE if t.is_cuda else MEM_HOST
+
+
+def n_coefs(kind, quad, coef_mode):
+    return (1 if kind == POISSON else 20) * (NQ[quad] if coef_mode == PER_QPOINT else 1)
+
+
+def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout):
+    """ElemArgs for torch tensors. SOA: coords (3*NS, E) and coefs (NC, E), unit
+    stride along elements, any plane stride. AOS: coords (E, NS, 3), coefs (E, ...)."""
+    a = ElemArgs()
+    if layout == SOA:
+        assert coords.dim() == 2 and coords.shape[0] == 3 * NS[elem_type]
+        n = coords.shape[1]
+        cf = coefs.reshape(-1, n) if coefs.dim() == 1 else coefs
+        # size-1 dimensions may report any stride: only a real element axis must be unit-stride
+        assert n <= 1 or (coords.stride(1) == 1 and cf.stride(-1) == 1)
+        a.coords_stride = coords.stride(0) if n > 1 else 0
+        # a single plane has no plane stride (size-1 dimensions may report any stride)
+        a.coefs_stride = cf.stride(0) if cf.shape[0] > 1 else 0
+    else:
+        assert coords.is_contiguous() and coefs.is_contiguous()
+        n = coords.shape[0]
+        a.coords_stride = 0
+        a.coefs_stride = 0
+    assert coords.dtype == torch.float64
+    want = torch.float64 if prec == FP64 else torch.float32
+    assert coefs.dtype == want, f"coefficients must be {want}"
+    a.n_elem = n
+    a.coords = coords.data_ptr()
+    a.coords_layout = layout
+    a.kind, a.quad, a.coef_mode, a.prec = kind, quad, coef_mode, prec
+    a.coefs = coefs.data_ptr()
+    a.coefs_layout = layout
+    a.memory = _mem(coords)
+    return a
+
+
+def alloc_out(elem_type, n, prec, out_layout, device, with_flags=True, pin=False):
+    ns = NS[elem_type]
+    dt = torch.float64 if prec == FP64 else torch.float32
+    kw = dict(dtype=dt, device=device)
+    if out_layout == SOA:
+        # A and b share one plane stride: one (NS*NS + NS, n) buffer
+        buf = torch.empty((ns * ns + ns, n), **kw, pin_memory=pin) if pin else torch.empty((ns * ns + ns, n), **kw)
+        A, b = buf[: ns * ns], buf[ns * ns:]
+    else:
+        A = torch.empty((n, ns, ns), **kw, pin_memory=pin) if pin else torch.empty((n, ns, ns), **kw)
+        b = torch.empty((n, ns), **kw, pin_memory=pin) if pin else torch.empty((n, ns), **kw)
+    flags = None
+    if with_flags:
+        flags = (torch.empty(n, dtype=torch.uint8, device=device, pin_memory=pin) if pin
+                 else torch.empty(n, dtype=torch.uint8, device=device))
+    return A, b, flags
+
+
+def make_out(A, b, flags, out_layout):
+    o = Out()
+    o.A, o.b = A.data_ptr(), b.data_ptr()
+    o.layout = out_layout
+    if out_layout == SOA:
+        n = A.shape[1]
+        assert n <= 1 or (A.stride(0) == b.stride(0) and A.stride(1) == 1 and b.stride(1) == 1)
+        o.stride = A.stride(0) if n > 1 else 0
+    o.flags = flags.data_ptr() if flags is not None else None
+    o.memory = _mem(A)
+    return o
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, autotune: bool = False, tuning_cache: str | None = None,
+                 hbm_budget: int = 0, serve_slots: int = 0):
+        lib = load()
+        cfg = CtxConfig(device, hbm_budget, serve_slots, int(autotune),
+                        tuning_cache.encode() if tuning_cache else None)
+        h = ctypes.c_void_p()
+        _check(lib.fe_ctx_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self.device = device
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            load().fe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sync(self):
+        _check(load().fe_ctx_sync(self.h), self.h)
+
+    def _stream(self, stream, on_device):
+        if stream is not None:
+            return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        if on_device:
+            return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        return ctypes.c_void_p(0)
+
+    def integrate(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
+                  out_layout=SOA, out=None, with_flags=True, stream=None):
+        """Integrate one element set; returns (A, b, flags) tensors (allocated if
+        ``out`` is None, on the device of ``coords``; pinned host memory for host inputs)."""
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+        if out is None:
+            on_host = not coords.is_cuda
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, with_flags, pin=on_host)
+        A, b, flags = out
+        o = make_out(A, b, flags, out_layout)
+        fn = load().fe_integrate_tet if elem_type == TET else load().fe_integrate_prism
+        _check(fn(self.h, ctypes.byref(args), ctypes.byref(o), self._stream(stream, coords.is_cuda)), self.h)
+        return A, b, flags
+
+    def tune(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
+             out_layout=SOA, out=None, stream=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+        if out is None:
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
+        o = make_out(*out, out_layout)
+        _check(load().fe_tune(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), self._stream(stream, True)), self.h)
+        return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out)
+
+    def shape(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
+              out_layout=SOA, out=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+        if out is None:
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
+        o = make_out(*out, out_layout)
+        blk, pers = ctypes.c_int(), ctypes.c_int()
+        _check(load().fe_get_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), ctypes.byref(blk),
+                                   ctypes.byref(pers)), self.h)
+        return blk.value, pers.value
+
+    def set_profiling(self, on: bool):
+        _check(load().fe_ctx_set_profiling(self.h, int(on)), self.h)
+
+    def kernel_time(self, reset: bool = True):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(load().fe_ctx_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n), int(reset)), self.h)
+        return ms.value, n.value
+
+    # -- resident meshes, batching, serving ---------------------------------
+    def mesh_register(self, elem_type, coords, layout=AOS) -> int:
+        mid = ctypes.c_int64()
+        n = coords.shape[0] if layout == AOS else coords.shape[1]
+        _check(load().fe_mesh_register(self.h, elem_type, n, _ptr(coords), layout, _mem(coords), ctypes.byref(mid)),
+               self.h)
+        return mid.value
+
+    def mesh_release(self, mesh_id: int):
+        _check(load().fe_mesh_release(self.h, mesh_id), self.h)
+
+    def batch_submit(self, items, stream=None):
+        """items: list of (elem_type, ElemArgs, Out)."""
+        arr = (BatchItem * len(items))()
+        for i, (t, a, o) in enumerate(items):
+            arr[i].type, arr[i].args, arr[i].out = t, a, o
+        _check(load().fe_batch_submit(self.h, arr, len(items), self._stream(stream, True)), self.h)
+
+    def serve_submit(self, mesh_id, kind, quad, coef_mode, coefs, prec=FP32_MIXED) -> int:
+        req = Request(mesh_id, kind, quad, coef_mode, coefs.data_ptr(), prec)
+        t = ctypes.c_uint64()
+        _check(load().fe_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t)), self.h)
+        self._keep[t.value] = coefs
+        return t.value
+
+    def serve_poll(self, ticket):
+        """None while running, else the Result structure."""
+        res = Result()
+        st = load().fe_serve_poll(self.h, ticket, ctypes.byref(res))
+        if st == FE_NOT_READY:
+            return None
+        _check(st, self.h)
+        return res
+
+    def serve_release(self, ticket):
+        self._keep.pop(ticket, None)
+        _check(load().fe_serve_release(self.h, ticket), self.h)

@@ -1,0 +1,503 @@
+// Device-side building blocks of the integration kernels: reference rules,
+// memory helpers, exact-enough edge vectors from double coordinates, and the
+// per-element arithmetic of Sec. 2.2-2.3 (Eqs. sm_local, lv_local,
+// change_of_variables, quadrature; Algorithms 2 and 3).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "fe_internal.h"
+
+namespace fe {
+
+// ---------------------------------------------------------------------------
+// Reference rules (Eq. quadrature). The paper only says "Gaussian"; the point
+// sets are the readings documented in include/fe.h.
+// ---------------------------------------------------------------------------
+constexpr double kTet4A = 0.13819660112501051517954131656343618822796908201942;  // (5 - sqrt 5) / 20
+constexpr double kTet4B = 0.58541019662496845446137605030969143531609275394172;  // (5 + 3 sqrt 5) / 20
+constexpr double kInvSqrt3 = 0.57735026918962576450914878050195745564760175127013;
+
+template <int QUAD> struct Rule;
+
+template <> struct Rule<Q_TET1> {
+    static constexpr int NQ = 1;
+    __host__ __device__ static constexpr double w(int) { return 1.0 / 6.0; }
+    // shape value phi_r at point q (shape functions = barycentric coordinates)
+    __host__ __device__ static constexpr double phi(int, int) { return 0.25; }
+};
+
+template <> struct Rule<Q_TET4> {
+    static constexpr int NQ = 4;
+    __host__ __device__ static constexpr double w(int) { return 1.0 / 24.0; }
+    // point q: barycentric weight B on vertex q, A on the other three
+    __host__ __device__ static constexpr double phi(int q, int r) { return q == r ? kTet4B : kTet4A; }
+};
+
+template <> struct Rule<Q_PRISM6> {
+    static constexpr int NQ = 6;  // q = 3*l + t: zeta level l, triangle point t
+    __host__ __device__ static constexpr double w(int) { return 1.0 / 6.0; }
+    // triangle point t: barycentric 2/3 on vertex t, 1/6 on the others
+    __host__ __device__ static constexpr double lam(int t, int k) { return t == k ? 2.0 / 3.0 : 1.0 / 6.0; }
+    // zeta = -1/sqrt3 (l = 0) or +1/sqrt3 (l = 1); zb = (1 - zeta)/2, zt = (1 + zeta)/2
+    __host__ __device__ static constexpr double zb(int l) { return 0.5 * (1.0 + (l ? -kInvSqrt3 : kInvSqrt3)); }
+    __host__ __device__ static constexpr double zt(int l) { return 0.5 * (1.0 + (l ? kInvSqrt3 : -kInvSqrt3)); }
+    __host__ __device__ static constexpr double phi(int q, int r) {
+        return r < 3 ? lam(q % 3, r) * zb(q / 3) : lam(q % 3, r - 3) * zt(q / 3);
+    }
+};
+
+// Quadrature sums that do not depend on the element (Sec. 4.4 counts loop-invariant
+// motion of such terms): W = sum w_q, m_r = sum w_q phi_r(q), M2_rs = sum w_q phi_r phi_s.
+struct TetSums {
+    double W, m[4], M2[4][4];
+};
+template <int QUAD> __host__ __device__ constexpr TetSums tet_sums() {
+    TetSums s{};
+    for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
+        s.W += Rule<QUAD>::w(q);
+        for (int r = 0; r < 4; ++r) {
+            s.m[r] += Rule<QUAD>::w(q) * Rule<QUAD>::phi(q, r);
+            for (int c = 0; c < 4; ++c) s.M2[r][c] += Rule<QUAD>::w(q) * Rule<QUAD>::phi(q, r) * Rule<QUAD>::phi(q, c);
+        }
+    }
+    return s;
+}
+
+// Mean-ratio shape test constants. q = 3 |det T|^{2/3} / ||T||_F^2 with T = J S^{-1},
+// S the reference-to-ideal map; q < 0.1 <=> K det_J^2 / f^3 < 1e-3 with f = ||T||_F^2
+// and K = 27 det(S^{-1})^2: tetrahedron det S^{-1} = sqrt 2 (K = 54), prism
+// det S^{-1} = 4/sqrt 3 (K = 144).
+constexpr float kQualityQ3 = 1.0e-3f;  // 0.1^3
+constexpr float kTetQK = 54.0f;
+constexpr float kPrismQK = 144.0f;
+
+// ---------------------------------------------------------------------------
+// Small vectors
+// ---------------------------------------------------------------------------
+template <class T> struct V3 {
+    T x, y, z;
+};
+template <class T> __device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T> __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T> __device__ __forceinline__ V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class T> __device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// ---------------------------------------------------------------------------
+// Memory helpers
+// ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+template <class T> __device__ __forceinline__ void st_stream(T *p, T v) { __stcs(p, v); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// mbarrier + bulk copy (cp.async.bulk, the 1-D TMA path) for staging element
+// blocks of the "natural" element-contiguous layout through shared memory
+// (Sec. 4.2, Fig. 1 a: coalesced reading through shared memory).
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bounded wait on an mbarrier phase. Returns false (and sets the status bit) if
+// the copy has not landed after ~2^22 polls with back-off (seconds); callers
+// then skip their work for this block instead of spinning forever.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, int *status) {
+    for (unsigned it = 0; it < (1u << 22); ++it) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (it > 64) __nanosleep(256);
+    }
+    if (status) atomicOr(status, ST_TMA_TIMEOUT);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Double -> (hi, lo) float pair with integer operations only. The product needs
+// edge vectors x_k - x_0 with float relative accuracy although x_k are absolute
+// coordinates in double; rounding each coordinate to float first would lose
+// ~|x|/h ulps. hi = x truncated to 24 significant bits, lo = x - hi (exact up to
+// the last 6 of 53 bits). The double pipe of this GPU runs at 1/64 of the float
+// rate, so no double instruction is used. Coordinates with |x| outside
+// [2^-74, 2^128) (other than 0) give NaN, which fails the shape test and sends
+// the element down the double-precision path.
+// ---------------------------------------------------------------------------
+struct HiLo {
+    float hi, lo;
+};
+__device__ __forceinline__ HiLo split_double(double x) {
+    const uint32_t h = static_cast<uint32_t>(__double2hiint(x));
+    const uint32_t l = static_cast<uint32_t>(__double2loint(x));
+    const uint32_t sign = h & 0x80000000u;
+    const uint32_t e = (h >> 20) & 0x7FFu;                       // biased double exponent
+    const uint32_t frac23 = ((h & 0xFFFFFu) << 3) | (l >> 29);    // top 23 fraction bits
+    const uint32_t ehi = (e - 896u) << 23;                        // float exponent field of hi
+    const uint32_t elo = (e - 919u) << 23;                        // float exponent of 2^(E-23)
+    const float p = __uint_as_float(elo);
+    // 2^(E-23) * (1 + next23 / 2^23) - 2^(E-23): exact by Sterbenz
+    const float lo_mag = __uint_as_float(elo | ((l >> 6) & 0x7FFFFFu)) - p;
+    const bool in_range = (e - 949u) <= (1150u - 949u);
+    const bool zero = ((h & 0x7FFFFFFFu) | l) == 0u;
+    HiLo r;
+    r.hi = in_range ? __uint_as_float(sign | ehi | frac23) : (zero ? 0.0f : __uint_as_float(0x7FC00000u));
+    r.lo = in_range ? __uint_as_float(__float_as_uint(lo_mag) | sign) : 0.0f;
+    return r;
+}
+__device__ __forceinline__ float diff_hilo(HiLo a, HiLo b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+// ---------------------------------------------------------------------------
+// Accessors for the per-element inputs. SOA: global planes (coalesced across
+// the warp). AOS: the element's contiguous record staged in shared memory.
+// ---------------------------------------------------------------------------
+template <int LAYOUT, class T> struct Src {
+    const T *base;   // SOA: global array; AOS: this element's record in shared memory
+    int64_t stride;  // SOA plane stride
+    __device__ __forceinline__ T operator()(int j) const {
+        if (LAYOUT == SOA) return ld_stream(base + j * stride);
+        return base[j];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Tetrahedron (Algorithm 3, QSS_geo_linear): Jacobian terms once per element.
+// J = [e1 e2 e3] (columns x_k - x_0). Rows of J^{-1} are a_m / det with
+// a_1 = e2 x e3, a_2 = e3 x e1, a_3 = e1 x e2, det = e1 . a_1; the global
+// gradient of phi_m (m = 1..3) is row m of J^{-1} and grad phi_0 = -sum.
+// ---------------------------------------------------------------------------
+template <class T> struct TetGeo {
+    V3<T> a[3];
+    T det;
+};
+template <class T> __device__ __forceinline__ TetGeo<T> tet_geometry(V3<T> e1, V3<T> e2, V3<T> e3) {
+    TetGeo<T> g;
+    g.a[0] = cross(e2, e3);
+    g.a[1] = cross(e3, e1);
+    g.a[2] = cross(e1, e2);
+    g.det = dot(e1, g.a[0]);
+    return g;
+}
+
+// Shape test on float edges: true if the mean ratio is below 0.1 (or not finite).
+// ||T||_F^2 = |e1|^2 + |2 e2 - e1|^2 / 3 + |3 e3 - e1 - e2|^2 / 6 for the
+// equilateral ideal; q^3 = 54 det^2 / f^3.
+__device__ __forceinline__ bool tet_poor(V3<float> e1, V3<float> e2, V3<float> e3, float det) {
+    const V3<float> t1 = 2.0f * e2 - e1;
+    const V3<float> t2 = 3.0f * e3 - e1 - e2;
+    const float f = dot(e1, e1) + dot(t1, t1) * (1.0f / 3.0f) + dot(t2, t2) * (1.0f / 6.0f);
+    const float r = rsqrtf(f);
+    const float x = det * r * r * r;
+    return !(kTetQK * x * x >= kQualityQ3);
+}
+
+// Coefficient products and accumulation for a tetrahedron, given the global
+// gradients g[0..3] and V = |det J|. Per-element coefficients fold the Q loop
+// into the reference sums W, m, M2 (loop-invariant motion, Sec. 3.3 end); per-point
+// coefficients accumulate their weighted sums over Q first.
+//   A_rs = V ( g_r . Cbar g_s + P_s . g_r + R_r . g_s + M_rs )
+//   b_r  = V ( dbar . g_r + e_r )
+// with Cbar = sum_q w c^{ij}, P_s = sum_q w phi_s c^{i0}, R_r = sum_q w phi_r c^{0i},
+// M_rs = sum_q w c^{00} phi_r phi_s, dbar = sum_q w d^i, e_r = sum_q w d^0 phi_r.
+template <class T, int QUAD, int CPQ, class CS>
+__device__ __forceinline__ void tet_generic_products(const V3<T> g[4], T V, const CS &c, T A[16], T b[4]) {
+    constexpr TetSums S = tet_sums<QUAD>();
+    constexpr int NQ = Rule<QUAD>::NQ;
+    V3<T> Cg[4];                 // Cbar g_s
+    T conv[4][4];                // P_s . g_r + R_r . g_s
+    T M[4][4];
+    V3<T> db;
+    T eb[4];
+    if (!CPQ) {
+        // P_s = m_s c^{i;0}, R_r = m_r c^{0;i}: conv_rs = m_s (c^{i0} . g_r) + m_r (c^{0i} . g_s)
+        const V3<T> ci0 = {c(4), c(8), c(12)};
+        const V3<T> c0i = {c(1), c(2), c(3)};
+        T cr[4], cs[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cr[k] = dot(ci0, g[k]);
+            cs[k] = dot(c0i, g[k]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) conv[r][s] = T(S.m[s]) * cr[r] + T(S.m[r]) * cs[s];
+        const T Wt = T(S.W);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            Cg[s].x = Wt * (c(5) * g[s].x + c(6) * g[s].y + c(7) * g[s].z);
+            Cg[s].y = Wt * (c(9) * g[s].x + c(10) * g[s].y + c(11) * g[s].z);
+            Cg[s].z = Wt * (c(13) * g[s].x + c(14) * g[s].y + c(15) * g[s].z);
+        }
+        const T c00 = c(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) M[r][s] = c00 * T(S.M2[r][s]);
+        db = {Wt * c(17), Wt * c(18), Wt * c(19)};
+        const T d0 = c(16);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) eb[r] = d0 * T(S.m[r]);
+    } else {
+        T Cb[3][3];
+        V3<T> P[4], R[4];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Cb[i][j] = T(0);
+        db = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            eb[r] = T(0);
+            P[r] = R[r] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int s = 0; s < 4; ++s) M[r][s] = T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int o = 20 * q;
+            const T w = T(Rule<QUAD>::w(q));
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) Cb[i][j] += w * c(o + 4 * (i + 1) + (j + 1));
+            const V3<T> ci0 = {w * c(o + 4), w * c(o + 8), w * c(o + 12)};
+            const V3<T> c0i = {w * c(o + 1), w * c(o + 2), w * c(o + 3)};
+            db = db + w * V3<T>{c(o + 17), c(o + 18), c(o + 19)};
+            const T c00 = w * c(o);
+            const T d0 = w * c(o + 16);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const T ph = T(Rule<QUAD>::phi(q, r));
+                P[r] = P[r] + ph * ci0;
+                R[r] = R[r] + ph * c0i;
+                eb[r] += ph * d0;
+#pragma unroll
+                for (int s = 0; s < 4; ++s) M[r][s] += c00 * T(Rule<QUAD>::phi(q, r) * Rule<QUAD>::phi(q, s));
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            Cg[s].x = Cb[0][0] * g[s].x + Cb[0][1] * g[s].y + Cb[0][2] * g[s].z;
+            Cg[s].y = Cb[1][0] * g[s].x + Cb[1][1] * g[s].y + Cb[1][2] * g[s].z;
+            Cg[s].z = Cb[2][0] * g[s].x + Cb[2][1] * g[s].y + Cb[2][2] * g[s].z;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) conv[r][s] = dot(P[s], g[r]) + dot(R[r], g[s]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) A[4 * r + s] = V * (dot(g[r], Cg[s]) + conv[r][s] + M[r][s]);
+        b[r] = V * (dot(db, g[r]) + eb[r]);
+    }
+}
+
+// Poisson tetrahedron: A_rs = W / |det| (a_r . a_s) for r,s = 1..3; row and column 0
+// from the vanishing row sums (sum_k grad phi_k = 0); b_r = |det| sum_q w d0_q phi_r(q).
+template <class T, int QUAD, int CPQ, class CS>
+__device__ __forceinline__ void tet_poisson_products(const TetGeo<T> &geo, T invabs, T V, const CS &c, T A[16], T b[4]) {
+    constexpr TetSums S = tet_sums<QUAD>();
+    const T k = T(S.W) * invabs;
+    T G[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int s = r; s < 3; ++s) {
+            G[r][s] = k * dot(geo.a[r], geo.a[s]);
+            G[s][r] = G[r][s];
+        }
+    T row0[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) row0[s] = -(G[0][s] + G[1][s] + G[2][s]);
+    const T a00 = -(row0[0] + row0[1] + row0[2]);
+    A[0] = a00;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        A[1 + s] = row0[s];
+        A[4 * (1 + s)] = row0[s];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int s = 0; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = G[r][s];
+    if (!CPQ) {
+        const T vd = V * c(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] = vd * T(S.m[r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] = T(0);
+#pragma unroll
+        for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
+            const T wd = T(Rule<QUAD>::w(q)) * c(q);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] += wd * T(Rule<QUAD>::phi(q, r));
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] *= V;
+    }
+}
+
+// Poisson tetrahedron from gradients (used by the double-Jacobian fix-up).
+template <class T, int QUAD, int CPQ, class CS>
+__device__ __forceinline__ void tet_poisson_from_grads(const V3<T> g[4], T V, const CS &c, T A[16], T b[4]) {
+    constexpr TetSums S = tet_sums<QUAD>();
+    const T k = T(S.W) * V;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = r; s < 4; ++s) {
+            const T v = k * dot(g[r], g[s]);
+            A[4 * r + s] = v;
+            A[4 * s + r] = v;
+        }
+    if (!CPQ) {
+        const T vd = V * c(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] = vd * T(S.m[r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] = T(0);
+#pragma unroll
+        for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
+            const T wd = T(Rule<QUAD>::w(q)) * c(q);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] += wd * T(Rule<QUAD>::phi(q, r));
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] *= V;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Prism (Algorithm 2, QSS_geo_generic): Jacobian terms at every point.
+// With r_k = x_k - x_0, the columns of J at (xi, eta, zeta) are
+//   d x / d xi   = zb (r1 - r0) + zt (r4 - r3)
+//   d x / d eta  = zb (r2 - r0) + zt (r5 - r3)
+//   d x / d zeta = 1/2 sum_k lambda_k (r_{k+3} - r_k)
+// (the derivatives of phi_k = lambda_k zb, phi_{k+3} = lambda_k zt). Rows of
+// J^{-1}: rho_1 = (cy x cz)/det, rho_2 = (cz x cx)/det, rho_3 = (cx x cy)/det.
+// grad phi_k = zb P_k - lambda_k/2 rho_3, grad phi_{k+3} = zt P_k + lambda_k/2 rho_3
+// with P_0 = -(rho_1 + rho_2), P_1 = rho_1, P_2 = rho_2.
+// ---------------------------------------------------------------------------
+template <class T> struct PrismFrame {
+    V3<T> ub, ut, vb, vt, w0, w1, w2;
+};
+template <class T> __device__ __forceinline__ PrismFrame<T> prism_frame(const V3<T> r[6]) {
+    PrismFrame<T> f;
+    f.ub = r[1] - r[0];
+    f.ut = r[4] - r[3];
+    f.vb = r[2] - r[0];
+    f.vt = r[5] - r[3];
+    f.w0 = r[3] - r[0];
+    f.w1 = r[4] - r[1];
+    f.w2 = r[5] - r[2];
+    return f;
+}
+
+// Global gradients and vol at point (l, t) of PRISM6. Returns det J.
+template <class T>
+__device__ __forceinline__ T prism_point(const PrismFrame<T> &f, V3<T> cx, V3<T> cy, V3<T> a3, int l, int t, V3<T> g[6],
+                                         V3<T> &cz_out) {
+    using R = Rule<Q_PRISM6>;
+    const T h0 = T(0.5 * R::lam(t, 0)), h1 = T(0.5 * R::lam(t, 1)), h2 = T(0.5 * R::lam(t, 2));
+    const V3<T> cz = h0 * f.w0 + h1 * f.w1 + h2 * f.w2;
+    const V3<T> a1 = cross(cy, cz);
+    const V3<T> a2 = cross(cz, cx);
+    const T det = dot(cx, a1);
+    const T inv = T(1) / det;
+    const V3<T> r1 = inv * a1, r2 = inv * a2, r3 = inv * a3;
+    const V3<T> P[3] = {T(-1) * (r1 + r2), r1, r2};
+    const T zb = T(R::zb(l)), zt = T(R::zt(l));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T hl = T(0.5 * R::lam(t, k));
+        g[k] = zb * P[k] - hl * r3;
+        g[k + 3] = zt * P[k] + hl * r3;
+    }
+    cz_out = cz;
+    return det;
+}
+
+// Shape test at a prism point: ideal = unit-edge equilateral triangle x unit height;
+// ||T||_F^2 = |cx|^2 + |2 cy - cx|^2 / 3 + 4 |cz|^2; q^3 = 144 det^2 / f^3.
+__device__ __forceinline__ bool prism_poor(float fxy, V3<float> cz, float det) {
+    const float f = fxy + 4.0f * dot(cz, cz);
+    const float r = rsqrtf(f);
+    const float x = det * r * r * r;
+    return !(kPrismQK * x * x >= kQualityQ3);
+}
+
+// Generic coefficient products at one prism point (the S x S x (N_D+1)^2 update of
+// Algorithm 2): T_as = sum_b vol c_ab Phi_bs, A_rs += sum_a Phi_ar T_as;
+// b_r += sum_a vol d_a Phi_ar. Phi_0s = phi_s(q), Phi_is = (grad phi_s)_i.
+template <class T, int Q, class CS>
+__device__ __forceinline__ void prism_generic_update(const V3<T> g[6], T vol, const CS &c, int o, T A[36], T b[6]) {
+    T C[4][4], d[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) C[a][bb] = vol * c(o + 4 * a + bb);
+        d[a] = vol * c(o + 16 + a);
+    }
+    T Tm[4][6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const T ph = T(Rule<Q_PRISM6>::phi(Q, s));
+#pragma unroll
+        for (int a = 0; a < 4; ++a) Tm[a][s] = C[a][0] * ph + C[a][1] * g[s].x + C[a][2] * g[s].y + C[a][3] * g[s].z;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const T ph = T(Rule<Q_PRISM6>::phi(Q, r));
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+            A[6 * r + s] += ph * Tm[0][s] + g[r].x * Tm[1][s] + g[r].y * Tm[2][s] + g[r].z * Tm[3][s];
+        b[r] += d[0] * ph + d[1] * g[r].x + d[2] * g[r].y + d[3] * g[r].z;
+    }
+}
+
+// Poisson products at one prism point: A_rs += vol grad phi_r . grad phi_s,
+// b_r += vol d0_q phi_r(q) (upper triangle accumulated; mirrored at the end).
+template <class T, int Q>
+__device__ __forceinline__ void prism_poisson_update(const V3<T> g[6], T vol, T d0, T A[36], T b[6]) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const V3<T> gr = vol * g[r];
+#pragma unroll
+        for (int s = r; s < 6; ++s) A[6 * r + s] += dot(gr, g[s]);
+        b[r] += (vol * d0) * T(Rule<Q_PRISM6>::phi(Q, r));
+    }
+}
+
+}  // namespace fe

@@ -1,0 +1,19 @@
+// Explicit kernel tables: every (kind, coefficient mode, input layout, output
+// layout) combination of one element type, precision and rule.
+#pragma once
+#include "fe_kernels.cuh"
+
+#define FE_ELEM_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                  \
+    if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
+        return reinterpret_cast<const void *>(&fe::elem_kernel<ET, KD, PREC, QUAD, CP, IL, OL>);
+#define FE_FIX_CASE(ET, QUAD, KD, CP, IL, OL)                                         \
+    if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
+        return reinterpret_cast<const void *>(&fe::fixup_kernel<ET, KD, QUAD, CP, IL, OL>);
+
+#define FE_ALL16(M, ...)                                                              \
+    M(__VA_ARGS__, 0, 0, 0, 0) M(__VA_ARGS__, 0, 0, 0, 1) M(__VA_ARGS__, 0, 0, 1, 0)  \
+    M(__VA_ARGS__, 0, 0, 1, 1) M(__VA_ARGS__, 0, 1, 0, 0) M(__VA_ARGS__, 0, 1, 0, 1)  \
+    M(__VA_ARGS__, 0, 1, 1, 0) M(__VA_ARGS__, 0, 1, 1, 1) M(__VA_ARGS__, 1, 0, 0, 0)  \
+    M(__VA_ARGS__, 1, 0, 0, 1) M(__VA_ARGS__, 1, 0, 1, 0) M(__VA_ARGS__, 1, 0, 1, 1)  \
+    M(__VA_ARGS__, 1, 1, 0, 0) M(__VA_ARGS__, 1, 1, 0, 1) M(__VA_ARGS__, 1, 1, 1, 0)  \
+    M(__VA_ARGS__, 1, 1, 1, 1)

@@ -1,0 +1,70 @@
+// Internal interface between the runtime (fe_runtime.cu) and the kernel
+// translation units. Plain C++ types only; no CUDA headers needed by users.
+#pragma once
+#include <cstdint>
+
+namespace fe {
+
+enum ElemType { TET = 0, PRISM = 1 };
+enum Kind { POISSON = 0, GENERIC = 1 };
+enum Prec { FP64 = 0, MIXED = 1 };
+enum Quad { Q_TET1 = 0, Q_TET4 = 1, Q_PRISM6 = 2 };
+enum Layout { SOA = 0, AOS = 1 };
+
+// Bits of the device status word (one per context, read at sync).
+enum StatusBits : int {
+    ST_TMA_TIMEOUT = 1,       // a bounded wait on a bulk copy ran out
+    ST_FIXUP_OVERFLOW = 2,    // the fix-up list was too short (never with capacity = n)
+    ST_BAD_TILE = 4           // a batch tile descriptor was out of range
+};
+
+// One homogeneous element set as the kernels see it (device pointers).
+struct ElemParams {
+    int64_t n;                     // elements
+    const double *X;               // coordinates
+    int64_t xs;                    // SOA plane stride (elements)
+    const void *C;                 // coefficients (double or float)
+    int64_t cs;                    // SOA plane stride
+    void *A;                       // outputs (double or float)
+    void *B;
+    int64_t os;                    // SOA plane stride of A and B
+    uint8_t *flags;                // may be null
+    unsigned long long *fix_list;  // mixed precision: flagged elements (item << 40 | element)
+    unsigned int *fix_count;
+    unsigned int fix_cap;
+    unsigned int item;             // batch item id (0 for a plain call)
+    int *status;                   // device status word
+};
+
+// Compile-time configuration of one element kernel.
+struct KernelKey {
+    int type, kind, prec, quad, cpq, in_layout, out_layout;
+};
+
+// Kernel pointer for a key, or nullptr if that combination is not built.
+// Implemented in the instantiation units.
+const void *kernel_tet_fp64(int kind, int quad, int cpq, int inl, int outl);
+const void *kernel_tet_mixed(int kind, int quad, int cpq, int inl, int outl);
+const void *kernel_prism_fp64(int kind, int cpq, int inl, int outl);
+const void *kernel_prism_mixed(int kind, int cpq, int inl, int outl);
+
+// Fix-up kernels (mixed precision, flagged elements in double); they read the
+// list written by the main kernel.
+const void *kernel_fixup_tet(int kind, int quad, int cpq, int inl, int outl);
+const void *kernel_fixup_prism(int kind, int cpq, int inl, int outl);
+
+// Batched persistent kernel (see fe_batch.cu).
+struct BatchTile {
+    unsigned int item;        // index into the item table
+    unsigned int count;       // elements in this tile
+    long long first;          // first element of the tile within the item
+};
+struct BatchItem {
+    ElemParams p;             // SOA inputs/outputs, mixed precision
+    int type, kind, quad, cpq;
+};
+const void *kernel_batch();
+const void *kernel_batch_fixup();
+int batch_tile_elems();       // elements per tile (= threads per block)
+
+}  // namespace fe

@@ -1,0 +1,514 @@
+// Integration kernels: one element per thread (the element-loop parallelisation
+// of Sec. 3.2), QSS loop order (Algorithms 2 and 3), inputs in "coalesced"
+// plane order or in the "natural" element-contiguous order staged through shared
+// memory by bulk copies (Sec. 4.2, Fig. 1), outputs in either order (Fig. 2).
+#pragma once
+#include <type_traits>
+
+#include "fe_device.cuh"
+
+namespace fe {
+
+template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct ElemCfg {
+    static constexpr int NS = ET == TET ? 4 : 6;
+    static constexpr int NX = 3 * NS;
+    static constexpr int NA = NS * NS;
+    static constexpr int NQ = Rule<QUAD>::NQ;
+    static constexpr int NC = (KIND == POISSON ? 1 : 20) * (CPQ ? NQ : 1);
+    using CT = typename std::conditional<PREC == FP64, double, float>::type;
+};
+
+__device__ __forceinline__ V3<float> to_f(V3<double> v) {
+    return {static_cast<float>(v.x), static_cast<float>(v.y), static_cast<float>(v.z)};
+}
+
+// ---------------------------------------------------------------------------
+// One element: inputs through accessors, outputs into registers.
+// Returns the flag byte; `poor` is set when the mixed-precision shape test fails.
+// ---------------------------------------------------------------------------
+template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct ElemMath;
+
+// Tetrahedron, FP64 (Algorithm 3 in double).
+template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CPQ> {
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[16], double b[4], bool &poor) {
+        poor = false;
+        const V3<double> x0 = {x(0), x(1), x(2)};
+        const V3<double> e1 = V3<double>{x(3), x(4), x(5)} - x0;
+        const V3<double> e2 = V3<double>{x(6), x(7), x(8)} - x0;
+        const V3<double> e3 = V3<double>{x(9), x(10), x(11)} - x0;
+        const TetGeo<double> geo = tet_geometry(e1, e2, e3);
+        if (!(fabs(geo.det) > 1e-300)) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) A[k] = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = 0.0;
+            return 4;
+        }
+        const double V = fabs(geo.det);
+        if (KIND == POISSON) {
+            tet_poisson_products<double, QUAD, CPQ>(geo, 1.0 / V, V, c, A, b);
+        } else {
+            const double inv = 1.0 / geo.det;
+            V3<double> g[4];
+            g[1] = inv * geo.a[0];
+            g[2] = inv * geo.a[1];
+            g[3] = inv * geo.a[2];
+            g[0] = -1.0 * (g[1] + g[2] + g[3]);
+            tet_generic_products<double, QUAD, CPQ>(g, V, c, A, b);
+        }
+        return geo.det < 0.0 ? 2 : 0;
+    }
+};
+
+// Tetrahedron, mixed: float arithmetic from hi/lo edge vectors; shape test.
+template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, MIXED, QUAD, CPQ> {
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, float A[16], float b[4], bool &poor) {
+        HiLo h[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) h[j] = split_double(x(j));
+        V3<float> e[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            e[k] = {diff_hilo(h[3 * (k + 1)], h[0]), diff_hilo(h[3 * (k + 1) + 1], h[1]), diff_hilo(h[3 * (k + 1) + 2], h[2])};
+        const TetGeo<float> geo = tet_geometry(e[0], e[1], e[2]);
+        poor = tet_poor(e[0], e[1], e[2], geo.det);
+        const float V = fabsf(geo.det);
+        const float inv = 1.0f / geo.det;
+        if (KIND == POISSON) {
+            tet_poisson_products<float, QUAD, CPQ>(geo, fabsf(inv), V, c, A, b);
+        } else {
+            V3<float> g[4];
+            g[1] = inv * geo.a[0];
+            g[2] = inv * geo.a[1];
+            g[3] = inv * geo.a[2];
+            g[0] = -1.0f * (g[1] + g[2] + g[3]);
+            tet_generic_products<float, QUAD, CPQ>(g, V, c, A, b);
+        }
+        return geo.det < 0.0f ? 2 : 0;
+    }
+    // Double-precision Jacobian for a flagged element: det, inverse and gradients
+    // in double, narrowed to float, the rest in float.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t fixup(const XS &x, const CS &c, float A[16], float b[4]) {
+        const V3<double> x0 = {x(0), x(1), x(2)};
+        const V3<double> e1 = V3<double>{x(3), x(4), x(5)} - x0;
+        const V3<double> e2 = V3<double>{x(6), x(7), x(8)} - x0;
+        const V3<double> e3 = V3<double>{x(9), x(10), x(11)} - x0;
+        const TetGeo<double> geo = tet_geometry(e1, e2, e3);
+        if (!(fabs(geo.det) > 1e-300)) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) A[k] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = 0.0f;
+            return 1 | 4;
+        }
+        const double inv = 1.0 / geo.det;
+        V3<double> gd[4];
+        gd[1] = inv * geo.a[0];
+        gd[2] = inv * geo.a[1];
+        gd[3] = inv * geo.a[2];
+        gd[0] = -1.0 * (gd[1] + gd[2] + gd[3]);
+        V3<float> g[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[k] = to_f(gd[k]);
+        const float V = static_cast<float>(fabs(geo.det));
+        if (KIND == POISSON)
+            tet_poisson_from_grads<float, QUAD, CPQ>(g, V, c, A, b);
+        else
+            tet_generic_products<float, QUAD, CPQ>(g, V, c, A, b);
+        return 1 | (geo.det < 0.0 ? 2 : 0);
+    }
+};
+
+// Prism (Algorithm 2): T = double or float arithmetic after the edge vectors.
+template <int KIND, int PREC, int CPQ> struct PrismMath {
+    using T = typename std::conditional<PREC == FP64, double, float>::type;
+
+    // Q loop on relative coordinates r[0..5] (r[0] = 0). Returns bit1/bit2 flags.
+    template <class CS>
+    __device__ __forceinline__ static uint8_t qloop(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor) {
+        const PrismFrame<T> f = prism_frame(r);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) A[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) b[k] = T(0);
+        bool neg = false, degenerate = false;
+        poor = false;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const T zb = T(Rule<Q_PRISM6>::zb(l)), zt = T(Rule<Q_PRISM6>::zt(l));
+            const V3<T> cx = zb * f.ub + zt * f.ut;
+            const V3<T> cy = zb * f.vb + zt * f.vt;
+            const V3<T> a3 = cross(cx, cy);
+            T fxy = T(0);
+            if (PREC == MIXED) {
+                const V3<T> t1 = T(2) * cy - cx;
+                fxy = dot(cx, cx) + dot(t1, t1) * T(1.0 / 3.0);
+            }
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                V3<T> g[6], cz;
+                const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
+                if (PREC == MIXED) poor |= prism_poor(static_cast<float>(fxy), to_float(cz), static_cast<float>(det));
+                if (PREC == FP64) degenerate |= !(fabs(static_cast<double>(det)) > 1e-300);
+                neg |= det < T(0);
+                const T vol = abs_t(det) * T(Rule<Q_PRISM6>::w(3 * l + t));
+                update_point(3 * l + t, g, vol, c, A, b);
+            }
+        }
+        if (KIND == POISSON) mirror(A);
+        if (degenerate) {
+#pragma unroll
+            for (int k = 0; k < 36; ++k) A[k] = T(0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) b[k] = T(0);
+            return 4;
+        }
+        return neg ? 2 : 0;
+    }
+
+    __device__ __forceinline__ static V3<float> to_float(V3<T> v) {
+        return {static_cast<float>(v.x), static_cast<float>(v.y), static_cast<float>(v.z)};
+    }
+    __device__ __forceinline__ static T abs_t(T v) { return v < T(0) ? -v : v; }
+    __device__ __forceinline__ static void mirror(T A[36]) {
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int s = 0; s < r; ++s) A[6 * r + s] = A[6 * s + r];
+    }
+
+    template <class CS>
+    __device__ __forceinline__ static void update_point(int q, const V3<T> g[6], T vol, const CS &c, T A[36], T b[6]) {
+        // q is a compile-time constant after unrolling; dispatch to the templated update
+        switch (q) {
+            case 0: upd<0>(g, vol, c, A, b); break;
+            case 1: upd<1>(g, vol, c, A, b); break;
+            case 2: upd<2>(g, vol, c, A, b); break;
+            case 3: upd<3>(g, vol, c, A, b); break;
+            case 4: upd<4>(g, vol, c, A, b); break;
+            default: upd<5>(g, vol, c, A, b); break;
+        }
+    }
+    template <int Q, class CS>
+    __device__ __forceinline__ static void upd(const V3<T> g[6], T vol, const CS &c, T A[36], T b[6]) {
+        if (KIND == POISSON)
+            prism_poisson_update<T, Q>(g, vol, c(CPQ ? Q : 0), A, b);
+        else
+            prism_generic_update<T, Q>(g, vol, c, CPQ ? 20 * Q : 0, A, b);
+    }
+};
+
+template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, FP64, Q_PRISM6, CPQ> {
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[36], double b[6], bool &poor) {
+        V3<double> r[6];
+        const V3<double> x0 = {x(0), x(1), x(2)};
+        r[0] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 1; k < 6; ++k) r[k] = V3<double>{x(3 * k), x(3 * k + 1), x(3 * k + 2)} - x0;
+        return PrismMath<KIND, FP64, CPQ>::qloop(r, c, A, b, poor);
+    }
+};
+
+template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> {
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, float A[36], float b[6], bool &poor) {
+        HiLo h[18];
+#pragma unroll
+        for (int j = 0; j < 18; ++j) h[j] = split_double(x(j));
+        V3<float> r[6];
+        r[0] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int k = 1; k < 6; ++k)
+            r[k] = {diff_hilo(h[3 * k], h[0]), diff_hilo(h[3 * k + 1], h[1]), diff_hilo(h[3 * k + 2], h[2])};
+        return PrismMath<KIND, MIXED, CPQ>::qloop(r, c, A, b, poor);
+    }
+    // Flagged element: Jacobian terms in double at every point, narrowed to float.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t fixup(const XS &x, const CS &c, float A[36], float b[6]) {
+        V3<double> r[6];
+        const V3<double> x0 = {x(0), x(1), x(2)};
+        r[0] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 1; k < 6; ++k) r[k] = V3<double>{x(3 * k), x(3 * k + 1), x(3 * k + 2)} - x0;
+        const PrismFrame<double> f = prism_frame(r);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) A[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) b[k] = 0.0f;
+        bool neg = false, degenerate = false;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const double zb = Rule<Q_PRISM6>::zb(l), zt = Rule<Q_PRISM6>::zt(l);
+            const V3<double> cx = zb * f.ub + zt * f.ut;
+            const V3<double> cy = zb * f.vb + zt * f.vt;
+            const V3<double> a3 = cross(cx, cy);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                V3<double> gd[6], cz;
+                const double det = prism_point(f, cx, cy, a3, l, t, gd, cz);
+                degenerate |= !(fabs(det) > 1e-300);
+                neg |= det < 0.0;
+                V3<float> g[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) g[k] = to_f(gd[k]);
+                const float vol = static_cast<float>(fabs(det) * Rule<Q_PRISM6>::w(3 * l + t));
+                PrismMath<KIND, MIXED, CPQ>::update_point(3 * l + t, g, vol, c, A, b);
+            }
+        }
+        if (KIND == POISSON) PrismMath<KIND, MIXED, CPQ>::mirror(A);
+        if (degenerate) {
+#pragma unroll
+            for (int k = 0; k < 36; ++k) A[k] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) b[k] = 0.0f;
+            return 1 | 4;
+        }
+        return 1 | (neg ? 2 : 0);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of one block: inputs and outputs of the tile's elements.
+// AOS regions hold element records back to back; SOA regions hold one row of B
+// scalars per plane. Every region starts on a 16-byte boundary.
+// ---------------------------------------------------------------------------
+template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct BlockSmem {
+    using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
+    using CT = typename CF::CT;
+    __host__ __device__ static constexpr int64_t r16(int64_t v) { return (v + 15) / 16 * 16; }
+    __host__ __device__ static constexpr int64_t x_bytes(int B) { return int64_t(B) * CF::NX * 8; }
+    __host__ __device__ static constexpr int64_t c_bytes(int B) { return r16(int64_t(B) * CF::NC * int64_t(sizeof(CT))); }
+    __host__ __device__ static constexpr int64_t a_bytes(int B) { return r16(int64_t(B) * CF::NA * int64_t(sizeof(CT))); }
+    __host__ __device__ static constexpr int64_t b_bytes(int B) { return r16(int64_t(B) * CF::NS * int64_t(sizeof(CT))); }
+    __host__ __device__ static constexpr int64_t total(int B) { return x_bytes(B) + c_bytes(B) + a_bytes(B) + b_bytes(B); }
+};
+
+__device__ __forceinline__ bool aligned16(const void *p, uint64_t bytes) {
+    return ((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) == 0;
+}
+
+// Shared-memory accessor: element record (stride 1) or plane rows (stride B).
+template <class T> struct SmemSrc {
+    const T *base;
+    int stride;
+    __device__ __forceinline__ T operator()(int j) const { return base[j * stride]; }
+};
+
+// Append flagged elements of this warp to the fix-up list (one atomic per warp).
+__device__ __forceinline__ void append_fixup(const ElemParams &p, bool poor, int64_t e) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, poor);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(p.fix_count, static_cast<unsigned>(__popc(m)));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (poor) {
+        const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < p.fix_cap)
+            p.fix_list[slot] = (static_cast<unsigned long long>(p.item) << 40) | static_cast<unsigned long long>(e);
+        else
+            atomicOr(p.status, ST_FIXUP_OVERFLOW);
+    }
+}
+
+// Copy `rows` rows of `bytes` from global rows (pitch gpitch elements) into
+// shared rows (pitch spitch elements). Bulk copies issued by the lanes of warp 0
+// when `bulk`; otherwise every thread of the block copies element by element.
+template <class T>
+__device__ __forceinline__ void stage_rows_in(T *s, int64_t spitch, const T *g, int64_t gpitch, int rows, int count,
+                                              bool bulk, uint64_t *bar) {
+    if (bulk) {
+        if (threadIdx.x < 32)
+            for (int r = threadIdx.x; r < rows; r += 32)
+                bulk_g2s(s + r * spitch, g + r * gpitch, static_cast<unsigned>(count * sizeof(T)), bar);
+    } else {
+        for (int r = 0; r < rows; ++r)
+            for (int i = threadIdx.x; i < count; i += blockDim.x) s[r * spitch + i] = g[r * gpitch + i];
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void stage_rows_out(T *g, int64_t gpitch, const T *s, int64_t spitch, int rows, int count,
+                                               bool bulk) {
+    if (bulk) {
+        if (threadIdx.x < 32) {
+            for (int r = threadIdx.x; r < rows; r += 32)
+                bulk_s2g(g + r * gpitch, s + r * spitch, static_cast<unsigned>(count * sizeof(T)));
+        }
+    } else {
+        for (int r = 0; r < rows; ++r)
+            for (int i = threadIdx.x; i < count; i += blockDim.x) st_stream(g + r * gpitch + i, s[r * spitch + i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Main kernel: tiles of blockDim.x elements, grid-stride over tiles. Each tile's
+// inputs are staged into shared memory by bulk copies (cp.async.bulk, completion
+// on an mbarrier), computed one element per thread, and written back by bulk
+// copies from shared memory.
+// ---------------------------------------------------------------------------
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
+__global__ void __launch_bounds__(ET == TET ? 512 : 256)
+    elem_kernel(const ElemParams p) {
+    using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
+    using CT = typename CF::CT;
+    using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ>;
+    constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+
+    const int B = blockDim.x;
+    const int tid = threadIdx.x;
+    double *sX = reinterpret_cast<double *>(smem);
+    CT *sC = reinterpret_cast<CT *>(smem + SM::x_bytes(B));
+    CT *sA = reinterpret_cast<CT *>(smem + SM::x_bytes(B) + SM::c_bytes(B));
+    CT *sB = reinterpret_cast<CT *>(smem + SM::x_bytes(B) + SM::c_bytes(B) + SM::a_bytes(B));
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    const double *X = p.X;
+    const CT *C = static_cast<const CT *>(p.C);
+    CT *Aout = static_cast<CT *>(p.A);
+    CT *Bout = static_cast<CT *>(p.B);
+    // alignment that does not depend on the tile: bases, and SOA plane pitches
+    const bool x_ok = aligned16(X, INL == SOA ? uint64_t(p.xs) * 8 : 0);
+    const bool c_ok = aligned16(C, INL == SOA ? uint64_t(p.cs) * sizeof(CT) : 0);
+    const bool a_ok = aligned16(Aout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
+    const bool b_ok = aligned16(Bout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
+    const int64_t ntiles = (p.n + B - 1) / B;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t e0 = tile * B;
+        const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
+        const int64_t e = e0 + tid;
+        const bool active = tid < nb;
+
+        // ---- stage inputs ----
+        {
+            const bool tX = x_ok && ((uint64_t(nb) * (INL == SOA ? 8 : NX * 8)) % 16 == 0);
+            const bool tC = c_ok && ((uint64_t(nb) * (INL == SOA ? 1 : NC) * sizeof(CT)) % 16 == 0);
+            const unsigned tx = (tX ? unsigned(nb) * NX * 8u : 0u) + (tC ? unsigned(nb) * NC * unsigned(sizeof(CT)) : 0u);
+            if (tid == 0 && tx) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(&bar, tx);
+            }
+            if (tx) __syncwarp();
+            if (INL == SOA) {
+                stage_rows_in(sX, B, X + e0, p.xs, NX, nb, tX, &bar);
+                stage_rows_in(sC, B, C + e0, p.cs, NC, nb, tC, &bar);
+            } else {
+                stage_rows_in(sX, 0, X + e0 * NX, 0, 1, nb * NX, tX, &bar);
+                stage_rows_in(sC, 0, C + e0 * NC, 0, 1, nb * NC, tC, &bar);
+            }
+            bool ok = true;
+            if (tx) {
+                ok = mbar_wait_bounded(&bar, phase, p.status);
+                phase ^= 1u;
+            }
+            if (__syncthreads_or(!ok)) {
+                // a copy did not land: wait once more (bounded) so nothing is in flight, then stop
+                if (tx) mbar_wait_bounded(&bar, phase ^ 1u, nullptr);
+                return;
+            }
+        }
+
+        // ---- compute ----
+        CT A[NA], b[NS];
+        bool poor = false;
+        if (active) {
+            const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
+            const SmemSrc<CT> cs{INL == SOA ? sC + tid : sC + tid * NC, INL == SOA ? B : 1};
+            uint8_t fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
+            if (PREC == MIXED && poor) fl |= 1;
+            if (p.flags) p.flags[e] = fl;
+            if (OUTL == SOA) {
+#pragma unroll
+                for (int k = 0; k < NA; ++k) sA[k * B + tid] = A[k];
+#pragma unroll
+                for (int k = 0; k < NS; ++k) sB[k * B + tid] = b[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < NA; ++k) sA[tid * NA + k] = A[k];
+#pragma unroll
+                for (int k = 0; k < NS; ++k) sB[tid * NS + k] = b[k];
+            }
+        }
+        if (PREC == MIXED) append_fixup(p, active && poor, e);
+
+        // ---- store outputs ----
+        fence_proxy_async_smem();
+        __syncthreads();
+        {
+            const bool tA = a_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NA) * sizeof(CT)) % 16 == 0);
+            const bool tB = b_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NS) * sizeof(CT)) % 16 == 0);
+            if (OUTL == SOA) {
+                stage_rows_out(Aout + e0, p.os, sA, B, NA, nb, tA);
+                stage_rows_out(Bout + e0, p.os, sB, B, NS, nb, tB);
+            } else {
+                stage_rows_out(Aout + e0 * NA, 0, sA, 0, 1, nb * NA, tA);
+                stage_rows_out(Bout + e0 * NS, 0, sB, 0, 1, nb * NS, tB);
+            }
+            if ((tA || tB) && tid < 32) {
+                bulk_commit();
+                bulk_wait_read0();
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Fix-up kernel (mixed precision): flagged elements of one call, read straight
+// from global memory, Jacobian terms in double, results overwrite the float ones.
+// ---------------------------------------------------------------------------
+template <int ET, int KIND, int QUAD, int CPQ, int INL, int OUTL>
+__global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p) {
+    using CF = ElemCfg<ET, KIND, MIXED, QUAD, CPQ>;
+    constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
+    const unsigned cnt = *p.fix_count;
+    const unsigned n = cnt < p.fix_cap ? cnt : p.fix_cap;
+    const float *C = static_cast<const float *>(p.C);
+    float *Aout = static_cast<float *>(p.A);
+    float *Bout = static_cast<float *>(p.B);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int64_t e = static_cast<int64_t>(p.fix_list[i] & ((1ull << 40) - 1));
+        if (e >= p.n) {
+            atomicOr(p.status, ST_BAD_TILE);
+            continue;
+        }
+        float A[NA], b[NS];
+        uint8_t fl;
+        if (INL == SOA) {
+            const Src<SOA, double> xs{p.X + e, p.xs};
+            const Src<SOA, float> cs{C + e, p.cs};
+            fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
+        } else {
+            const Src<AOS, double> xs{p.X + e * NX, 0};
+            const Src<AOS, float> cs{C + e * NC, 0};
+            fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
+        }
+        if (OUTL == SOA) {
+#pragma unroll
+            for (int k = 0; k < NA; ++k) Aout[k * p.os + e] = A[k];
+#pragma unroll
+            for (int k = 0; k < NS; ++k) Bout[k * p.os + e] = b[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < NA; ++k) Aout[e * NA + k] = A[k];
+#pragma unroll
+            for (int k = 0; k < NS; ++k) Bout[e * NS + k] = b[k];
+        }
+        if (p.flags) p.flags[e] = fl;
+    }
+}
+
+}  // namespace fe

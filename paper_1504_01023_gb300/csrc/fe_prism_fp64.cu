@@ -1,0 +1,8 @@
+// Prism kernels, FP64 form.
+#include "fe_inst.cuh"
+namespace fe {
+const void *kernel_prism_fp64(int kind, int cpq, int inl, int outl) {
+    FE_ALL16(FE_ELEM_CASE, PRISM, FP64, Q_PRISM6)
+    return nullptr;
+}
+}  // namespace fe

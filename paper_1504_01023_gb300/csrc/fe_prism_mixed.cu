@@ -1,0 +1,12 @@
+// Prism kernels, mixed form (float arithmetic, double Jacobian fix-up).
+#include "fe_inst.cuh"
+namespace fe {
+const void *kernel_prism_mixed(int kind, int cpq, int inl, int outl) {
+    FE_ALL16(FE_ELEM_CASE, PRISM, MIXED, Q_PRISM6)
+    return nullptr;
+}
+const void *kernel_fixup_prism(int kind, int cpq, int inl, int outl) {
+    FE_ALL16(FE_FIX_CASE, PRISM, Q_PRISM6)
+    return nullptr;
+}
+}  // namespace fe

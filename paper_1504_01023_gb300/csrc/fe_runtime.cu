@@ -1,0 +1,643 @@
+// C ABI of the integration library: context, argument validation, launch shapes
+// and the autotuner, profiling, and the chunked host-buffer pipeline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+
+#include "fe_runtime.h"
+
+namespace fe {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string t_last_error;
+
+fe_status set_error(fe_ctx *ctx, fe_status st, const std::string &msg) {
+    t_last_error = msg;
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
+        ctx->last_error = msg;
+    }
+    return st;
+}
+
+fe_status cuda_check(fe_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return FE_OK;
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return set_error(ctx, e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA, msg);
+}
+
+int ns_of(fe_elem_type t) { return t == FE_TET ? 4 : 6; }
+int nq_of(fe_quad q) { return q == FE_QUAD_TET1 ? 1 : (q == FE_QUAD_TET4 ? 4 : 6); }
+int nc_of(const fe_elem_args *a) {
+    return (a->kind == FE_POISSON ? 1 : 20) * (a->coef_mode == FE_COEF_PER_QPOINT ? nq_of(a->quad) : 1);
+}
+static int csize(fe_precision p) { return p == FE_FP64 ? 8 : 4; }
+
+fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n) {
+    if (!s.fix_count) {
+        fe_status st = cuda_check(ctx, cudaMalloc(&s.fix_count, 64), "cudaMalloc(fix_count)");
+        if (st != FE_OK) return st;
+        st = cuda_check(ctx, cudaMalloc(&s.status, 64), "cudaMalloc(status)");
+        if (st != FE_OK) return st;
+        cudaMemset(s.fix_count, 0, 64);
+        cudaMemset(s.status, 0, 64);
+    }
+    if (n > 0xFFFFFFFFull) return set_error(ctx, FE_ERR_INVALID_ARG, "more than 2^32-1 elements in one call");
+    if (n > s.fix_cap) {
+        if (s.fix_list) cudaFree(s.fix_list);
+        s.fix_list = nullptr;
+        s.fix_cap = 0;
+        uint64_t cap = std::max<uint64_t>(n, 1024);
+        fe_status st = cuda_check(ctx, cudaMalloc(&s.fix_list, cap * sizeof(unsigned long long)), "cudaMalloc(fix_list)");
+        if (st != FE_OK) return st;
+        s.fix_cap = static_cast<unsigned>(cap);
+    }
+    return FE_OK;
+}
+
+void free_scratch(Scratch &s) {
+    if (s.fix_list) cudaFree(s.fix_list);
+    if (s.fix_count) cudaFree(s.fix_count);
+    if (s.status) cudaFree(s.status);
+    s = Scratch{};
+}
+
+static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
+    const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
+    if (type == FE_TET) {
+        return a->prec == FE_FP64 ? kernel_tet_fp64(a->kind, a->quad, cpq, a->coords_layout, outl)
+                                  : kernel_tet_mixed(a->kind, a->quad, cpq, a->coords_layout, outl);
+    }
+    return a->prec == FE_FP64 ? kernel_prism_fp64(a->kind, cpq, a->coords_layout, outl)
+                              : kernel_prism_mixed(a->kind, cpq, a->coords_layout, outl);
+}
+
+static const void *fix_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
+    const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
+    return type == FE_TET ? kernel_fixup_tet(a->kind, a->quad, cpq, a->coords_layout, outl)
+                          : kernel_fixup_prism(a->kind, cpq, a->coords_layout, outl);
+}
+
+// Dynamic shared memory of one block: the tile's inputs and outputs, each region
+// rounded to 16 bytes exactly as BlockSmem in fe_kernels.cuh lays them out.
+static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, int B) {
+    (void)outl;
+    const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
+    auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
+    return int64_t(B) * 3 * ns * 8 + r16(int64_t(B) * nc * cs) + r16(int64_t(B) * ns * ns * cs) + r16(int64_t(B) * ns * cs);
+}
+
+// Static shared memory of the kernels (the mbarrier), kept out of the dynamic budget.
+static constexpr int64_t kStaticSmem = 1024;
+
+static fe_status set_smem_attr(fe_ctx *ctx, const void *k, int64_t smem) {
+    static std::mutex mu;
+    static std::map<const void *, int64_t> done;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(k);
+    if (it != done.end() && it->second >= smem) return FE_OK;
+    fe_status e = cuda_check(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                             "cudaFuncSetAttribute");
+    if (e == FE_OK) done[k] = smem;
+    return e;
+}
+
+static std::string shape_key(fe_elem_type type, const fe_elem_args *a, const fe_out *o) {
+    int bucket = 0;
+    for (int64_t n = a->n_elem; n > 1; n >>= 2) ++bucket;  // size class: floor(log4 n)
+    std::ostringstream k;
+    k << "t" << type << "k" << a->kind << "p" << a->prec << "q" << a->quad << "c" << a->coef_mode << "i"
+      << a->coords_layout << "o" << o->layout << "n" << bucket;
+    return k.str();
+}
+
+static Shape default_shape(fe_elem_type type) { return Shape{type == FE_TET ? 256 : 128, 0}; }
+
+static int max_block(fe_elem_type type) { return type == FE_TET ? 512 : 256; }
+
+static cudaEvent_t pool_event(fe_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, Scratch &s, cudaStream_t st,
+                     const Shape *force) {
+    if (a->n_elem == 0) return FE_OK;
+    const int outl = o->layout;
+    const void *k = main_kernel(type, a, outl);
+    if (!k) return set_error(ctx, FE_ERR_UNSUPPORTED, "no kernel for this combination");
+    Shape sh = default_shape(type);
+    if (force) {
+        sh = *force;
+    } else {
+        auto it = ctx->shapes.find(shape_key(type, a, o));
+        if (it != ctx->shapes.end()) sh = it->second;
+    }
+    const int64_t smem = smem_bytes(type, a, outl, sh.block);
+    if (smem + kStaticSmem > ctx->max_smem_optin)
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
+    {
+        fe_status e = set_smem_attr(ctx, k, smem);
+        if (e != FE_OK) return e;
+    }
+    const int64_t ntiles = (a->n_elem + sh.block - 1) / sh.block;
+    int64_t grid = ntiles;
+    if (sh.persistent) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, sh.block, size_t(smem));
+        grid = std::min<int64_t>(ntiles, int64_t(std::max(per_sm, 1)) * ctx->sms);
+    }
+    grid = std::min<int64_t>(grid, 0x7FFFFFFF);
+
+    ElemParams p{};
+    p.n = a->n_elem;
+    p.X = a->coords;
+    p.xs = a->coords_stride ? a->coords_stride : a->n_elem;
+    p.C = a->coefs;
+    p.cs = a->coefs_stride ? a->coefs_stride : a->n_elem;
+    p.A = o->A;
+    p.B = o->b;
+    p.os = o->stride ? o->stride : a->n_elem;
+    p.flags = o->flags;
+    p.item = 0;
+    const bool mixed = a->prec == FE_FP32_MIXED;
+    if (mixed) {
+        fe_status e = ensure_scratch(ctx, s, uint64_t(a->n_elem));
+        if (e != FE_OK) return e;
+        p.fix_list = s.fix_list;
+        p.fix_count = s.fix_count;
+        p.fix_cap = s.fix_cap;
+        cudaError_t ce = cudaMemsetAsync(s.fix_count, 0, sizeof(unsigned), st);
+        if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaMemsetAsync");
+    } else if (!s.status) {
+        fe_status e = ensure_scratch(ctx, s, 0);
+        if (e != FE_OK) return e;
+    }
+    p.status = s.status;
+
+    void *args[] = {&p};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (ctx->profiling) {
+        ev0 = pool_event(ctx);
+        ev1 = pool_event(ctx);
+        cudaEventRecord(ev0, st);
+    }
+    cudaError_t ce = cudaLaunchKernel(k, dim3(unsigned(grid)), dim3(unsigned(sh.block)), args, size_t(smem), st);
+    if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaLaunchKernel(elem)");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (ctx->profiling) {
+        cudaEventRecord(ev1, st);
+        ctx->prof_events.emplace_back(ev0, ev1);
+    }
+    if (mixed) {
+        const void *fk = fix_kernel(type, a, outl);
+        const int64_t fgrid = std::min<int64_t>((a->n_elem + 255) / 256, int64_t(ctx->sms) * 4);
+        ce = cudaLaunchKernel(fk, dim3(unsigned(std::max<int64_t>(fgrid, 1))), dim3(256), args, 0, st);
+        if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaLaunchKernel(fixup)");
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    return FE_OK;
+}
+
+// Chunked pipeline for host buffers: copy-in, kernels and copy-out of
+// consecutive chunks overlap on three streams (double-buffered staging).
+static fe_status ensure_stage(fe_ctx *ctx, int slot, int idx, uint64_t bytes) {
+    if (ctx->stage[slot][idx] && ctx->stage_bytes[slot][idx] >= bytes) return FE_OK;
+    if (ctx->stage[slot][idx]) cudaFree(ctx->stage[slot][idx]);
+    ctx->stage[slot][idx] = nullptr;
+    ctx->stage_bytes[slot][idx] = 0;
+    bytes = std::max<uint64_t>(bytes, 256);
+    fe_status st = cuda_check(ctx, cudaMalloc(&ctx->stage[slot][idx], bytes), "cudaMalloc(stage)");
+    if (st == FE_OK) ctx->stage_bytes[slot][idx] = bytes;
+    return st;
+}
+
+static fe_status host_pipeline(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, cudaStream_t user) {
+    const int64_t n = a->n_elem;
+    const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
+    const int nx = 3 * ns, na = ns * ns;
+    const int64_t K = std::min<int64_t>(n, int64_t(1) << 20);
+    const bool in_host = a->memory == FE_MEM_HOST, out_host = o->memory == FE_MEM_HOST;
+    const uint64_t need[5] = {uint64_t(K) * nx * 8, uint64_t(K) * nc * cs, uint64_t(K) * na * cs, uint64_t(K) * ns * cs,
+                              uint64_t(K)};
+    for (int slot = 0; slot < 2; ++slot)
+        for (int i = 0; i < 5; ++i) {
+            if ((i < 2 && !in_host) || (i >= 2 && !out_host)) continue;
+            fe_status st = ensure_stage(ctx, slot, i, need[i]);
+            if (st != FE_OK) return st;
+        }
+    if (!ctx->s_in) {
+        cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking);
+    }
+    cudaEvent_t start, in_done[2], comp_done[2], out_done[2];
+    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventCreateWithFlags(&in_done[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&comp_done[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&out_done[i], cudaEventDisableTiming);
+    }
+    cudaEventRecord(start, user);
+    cudaStreamWaitEvent(ctx->s_in, start, 0);
+    cudaStreamWaitEvent(ctx->s_comp, start, 0);
+    cudaStreamWaitEvent(ctx->s_out, start, 0);
+    const int64_t xs = a->coords_stride ? a->coords_stride : n;
+    const int64_t cst = a->coefs_stride ? a->coefs_stride : n;
+    const int64_t os = o->stride ? o->stride : n;
+    const char *X = reinterpret_cast<const char *>(a->coords);
+    const char *C = static_cast<const char *>(a->coefs);
+    char *A = static_cast<char *>(o->A);
+    char *B = static_cast<char *>(o->b);
+    fe_status result = FE_OK;
+    int64_t chunk = 0;
+    for (int64_t c0 = 0; c0 < n && result == FE_OK; c0 += K, ++chunk) {
+        const int slot = int(chunk & 1);
+        const int64_t m = std::min(K, n - c0);
+        if (chunk >= 2) {
+            cudaStreamWaitEvent(ctx->s_in, out_done[slot], 0);
+            cudaStreamWaitEvent(ctx->s_comp, out_done[slot], 0);
+        }
+        fe_elem_args ca = *a;
+        fe_out co = *o;
+        ca.n_elem = m;
+        ca.memory = FE_MEM_DEVICE;
+        co.memory = FE_MEM_DEVICE;
+        // inputs
+        if (in_host) {
+            char *dX = static_cast<char *>(ctx->stage[slot][0]);
+            char *dC = static_cast<char *>(ctx->stage[slot][1]);
+            if (a->coords_layout == FE_LAYOUT_SOA) {
+                cudaMemcpy2DAsync(dX, size_t(K) * 8, X + c0 * 8, size_t(xs) * 8, size_t(m) * 8, nx, cudaMemcpyHostToDevice,
+                                  ctx->s_in);
+                cudaMemcpy2DAsync(dC, size_t(K) * cs, C + c0 * cs, size_t(cst) * cs, size_t(m) * cs, nc,
+                                  cudaMemcpyHostToDevice, ctx->s_in);
+                ca.coords_stride = K;
+                ca.coefs_stride = K;
+            } else {
+                cudaMemcpyAsync(dX, X + c0 * nx * 8, size_t(m) * nx * 8, cudaMemcpyHostToDevice, ctx->s_in);
+                cudaMemcpyAsync(dC, C + c0 * nc * cs, size_t(m) * nc * cs, cudaMemcpyHostToDevice, ctx->s_in);
+            }
+            ca.coords = reinterpret_cast<const double *>(dX);
+            ca.coefs = dC;
+            cudaEventRecord(in_done[slot], ctx->s_in);
+            cudaStreamWaitEvent(ctx->s_comp, in_done[slot], 0);
+        } else {
+            if (a->coords_layout == FE_LAYOUT_SOA) {
+                ca.coords = reinterpret_cast<const double *>(X + c0 * 8);
+                ca.coefs = C + c0 * cs;
+                ca.coords_stride = xs;
+                ca.coefs_stride = cst;
+            } else {
+                ca.coords = reinterpret_cast<const double *>(X + c0 * nx * 8);
+                ca.coefs = C + c0 * nc * cs;
+            }
+        }
+        // outputs
+        if (out_host) {
+            co.A = ctx->stage[slot][2];
+            co.b = ctx->stage[slot][3];
+            co.flags = o->flags ? static_cast<uint8_t *>(ctx->stage[slot][4]) : nullptr;
+            co.stride = K;
+        } else {
+            if (o->layout == FE_LAYOUT_SOA) {
+                co.A = A + c0 * cs;
+                co.b = B + c0 * cs;
+                co.stride = os;
+            } else {
+                co.A = A + c0 * na * cs;
+                co.b = B + c0 * ns * cs;
+            }
+            co.flags = o->flags ? o->flags + c0 : nullptr;
+        }
+        if (co.layout == FE_LAYOUT_SOA && out_host) co.stride = K;
+        result = launch_set(ctx, type, &ca, &co, ctx->scratch, ctx->s_comp);
+        cudaEventRecord(comp_done[slot], ctx->s_comp);
+        if (out_host) {
+            cudaStreamWaitEvent(ctx->s_out, comp_done[slot], 0);
+            if (o->layout == FE_LAYOUT_SOA) {
+                cudaMemcpy2DAsync(A + c0 * cs, size_t(os) * cs, co.A, size_t(K) * cs, size_t(m) * cs, na,
+                                  cudaMemcpyDeviceToHost, ctx->s_out);
+                cudaMemcpy2DAsync(B + c0 * cs, size_t(os) * cs, co.b, size_t(K) * cs, size_t(m) * cs, ns,
+                                  cudaMemcpyDeviceToHost, ctx->s_out);
+            } else {
+                cudaMemcpyAsync(A + c0 * na * cs, co.A, size_t(m) * na * cs, cudaMemcpyDeviceToHost, ctx->s_out);
+                cudaMemcpyAsync(B + c0 * ns * cs, co.b, size_t(m) * ns * cs, cudaMemcpyDeviceToHost, ctx->s_out);
+            }
+            if (o->flags) cudaMemcpyAsync(o->flags + c0, co.flags, size_t(m), cudaMemcpyDeviceToHost, ctx->s_out);
+            cudaEventRecord(out_done[slot], ctx->s_out);
+        } else {
+            cudaEventRecord(out_done[slot], ctx->s_comp);
+        }
+    }
+    cudaError_t e1 = cudaStreamSynchronize(ctx->s_in);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->s_comp);
+    cudaError_t e3 = cudaStreamSynchronize(ctx->s_out);
+    cudaEventDestroy(start);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventDestroy(in_done[i]);
+        cudaEventDestroy(comp_done[i]);
+        cudaEventDestroy(out_done[i]);
+    }
+    if (result != FE_OK) return result;
+    fe_status st = cuda_check(ctx, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "host pipeline");
+    return st;
+}
+
+static fe_status integrate(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, void *stream) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    fe_status st = fe_check_args(type, a, o);
+    if (st != FE_OK) {
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
+        ctx->last_error = t_last_error;
+        return st;
+    }
+    if (a->n_elem == 0) return FE_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (a->memory == FE_MEM_HOST || o->memory == FE_MEM_HOST) return host_pipeline(ctx, type, a, o, s);
+    if (ctx->autotune && !ctx->shapes.count(shape_key(type, a, o))) {
+        st = fe_tune(ctx, type, a, o, stream);
+        if (st != FE_OK) return st;
+    }
+    return launch_set(ctx, type, a, o, ctx->scratch, s);
+}
+
+static void load_tuning_cache(fe_ctx *ctx) {
+    if (ctx->tuning_cache_path.empty()) return;
+    std::ifstream f(ctx->tuning_cache_path);
+    std::string dev, key;
+    int block, pers;
+    while (f >> dev >> key >> block >> pers) {
+        if (dev == ctx->device_name) ctx->shapes[key] = Shape{block, pers};
+    }
+}
+
+static void save_tuning_cache(fe_ctx *ctx) {
+    if (ctx->tuning_cache_path.empty()) return;
+    std::ofstream f(ctx->tuning_cache_path, std::ios::trunc);
+    for (auto &kv : ctx->shapes) f << ctx->device_name << " " << kv.first << " " << kv.second.block << " " << kv.second.persistent << "\n";
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *o) {
+    if (type != FE_TET && type != FE_PRISM) return set_error(nullptr, FE_ERR_INVALID_ARG, "bad element type");
+    if (!a || !o) return set_error(nullptr, FE_ERR_INVALID_ARG, "null args or out");
+    if (a->n_elem < 0) return set_error(nullptr, FE_ERR_INVALID_ARG, "n_elem < 0");
+    if (a->kind != FE_POISSON && a->kind != FE_GENERIC) return set_error(nullptr, FE_ERR_INVALID_ARG, "bad problem kind");
+    if (a->prec != FE_FP64 && a->prec != FE_FP32_MIXED) return set_error(nullptr, FE_ERR_INVALID_ARG, "bad precision");
+    if (a->coef_mode != FE_COEF_PER_ELEMENT && a->coef_mode != FE_COEF_PER_QPOINT)
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "bad coefficient mode");
+    if (type == FE_TET && a->quad != FE_QUAD_TET1 && a->quad != FE_QUAD_TET4)
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "tetrahedra take FE_QUAD_TET1 or FE_QUAD_TET4");
+    if (type == FE_PRISM && a->quad != FE_QUAD_PRISM6)
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "prisms take FE_QUAD_PRISM6");
+    if ((a->coords_layout != FE_LAYOUT_SOA && a->coords_layout != FE_LAYOUT_AOS) ||
+        (o->layout != FE_LAYOUT_SOA && o->layout != FE_LAYOUT_AOS))
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "bad layout");
+    if (a->coefs_layout != a->coords_layout)
+        return set_error(nullptr, FE_ERR_UNSUPPORTED, "coefficients must use the layout of the coordinates");
+    if ((a->memory != FE_MEM_DEVICE && a->memory != FE_MEM_HOST) || (o->memory != FE_MEM_DEVICE && o->memory != FE_MEM_HOST))
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "bad memory kind");
+    if (a->n_elem == 0) return FE_OK;
+    if (!a->coords || !a->coefs || !o->A || !o->b) return set_error(nullptr, FE_ERR_INVALID_ARG, "null data pointer");
+    const int64_t n = a->n_elem;
+    if (a->coords_layout == FE_LAYOUT_SOA) {
+        if ((a->coords_stride != 0 && a->coords_stride < n) || (a->coefs_stride != 0 && a->coefs_stride < n))
+            return set_error(nullptr, FE_ERR_INVALID_ARG, "SOA input stride smaller than n_elem");
+    }
+    if (o->layout == FE_LAYOUT_SOA && o->stride != 0 && o->stride < n)
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "SOA output stride smaller than n_elem");
+    const unsigned cs = a->prec == FE_FP64 ? 8 : 4;
+    if ((reinterpret_cast<uintptr_t>(a->coords) & 7) || (reinterpret_cast<uintptr_t>(a->coefs) & (cs - 1)) ||
+        (reinterpret_cast<uintptr_t>(o->A) & (cs - 1)) || (reinterpret_cast<uintptr_t>(o->b) & (cs - 1)))
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "misaligned data pointer");
+    if (n > 0xFFFFFFFFLL) return set_error(nullptr, FE_ERR_INVALID_ARG, "more than 2^32-1 elements in one call");
+    return FE_OK;
+}
+
+int64_t fe_bytes_per_element(fe_elem_type type, fe_problem kind, fe_quad quad, fe_coef_mode mode, fe_precision prec) {
+    if (type != FE_TET && type != FE_PRISM) return -1;
+    if (kind != FE_POISSON && kind != FE_GENERIC) return -1;
+    if (prec != FE_FP64 && prec != FE_FP32_MIXED) return -1;
+    if (type == FE_TET && quad != FE_QUAD_TET1 && quad != FE_QUAD_TET4) return -1;
+    if (type == FE_PRISM && quad != FE_QUAD_PRISM6) return -1;
+    if (mode != FE_COEF_PER_ELEMENT && mode != FE_COEF_PER_QPOINT) return -1;
+    fe_elem_args a{};
+    a.kind = kind;
+    a.quad = quad;
+    a.coef_mode = mode;
+    const int ns = ns_of(type), cs = prec == FE_FP64 ? 8 : 4;
+    return int64_t(3 * ns) * 8 + int64_t(nc_of(&a)) * cs + int64_t(ns * ns + ns) * cs;
+}
+
+fe_status fe_ctx_create(const fe_ctx_config *cfg, fe_ctx **out) {
+    if (!out) return set_error(nullptr, FE_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    fe_ctx_config c{};
+    if (cfg) c = *cfg;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return set_error(nullptr, FE_ERR_CUDA, "no CUDA device available");
+    if (c.device < 0 || c.device >= ndev) return set_error(nullptr, FE_ERR_INVALID_ARG, "bad device ordinal");
+    e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return cuda_check(nullptr, e, "cudaSetDevice");
+    fe_ctx *ctx = new fe_ctx();
+    ctx->device = c.device;
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, c.device);
+    ctx->sms = prop.multiProcessorCount;
+    ctx->max_smem_optin = int(prop.sharedMemPerBlockOptin);
+    ctx->device_name = prop.name;
+    for (auto &ch : ctx->device_name)
+        if (ch == ' ') ch = '_';
+    ctx->autotune = c.autotune;
+    ctx->hbm_budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : 120000000000ull;
+    ctx->serve_slots = c.serve_slots > 0 ? c.serve_slots : 4;
+    if (c.tuning_cache_path) ctx->tuning_cache_path = c.tuning_cache_path;
+    load_tuning_cache(ctx);
+    fe_status st = ensure_scratch(ctx, ctx->scratch, 0);
+    if (st != FE_OK) {
+        delete ctx;
+        return st;
+    }
+    cudaMallocHost(&ctx->h_status, sizeof(int));
+    *out = ctx;
+    return FE_OK;
+}
+
+fe_status fe_ctx_destroy(fe_ctx *ctx) {
+    if (!ctx) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    serve_destroy(ctx);
+    batch_destroy(ctx);
+    cudaDeviceSynchronize();
+    free_scratch(ctx->scratch);
+    for (auto &kv : ctx->meshes) cudaFree(kv.second.coords);
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < 5; ++i)
+            if (ctx->stage[s][i]) cudaFree(ctx->stage[s][i]);
+    if (ctx->s_in) {
+        cudaStreamDestroy(ctx->s_in);
+        cudaStreamDestroy(ctx->s_comp);
+        cudaStreamDestroy(ctx->s_out);
+    }
+    for (auto &pr : ctx->prof_events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto ev : ctx->event_pool) cudaEventDestroy(ev);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    delete ctx;
+    return FE_OK;
+}
+
+fe_status fe_ctx_sync(fe_ctx *ctx) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_check(ctx, e, "device synchronize");
+    if (ctx->scratch.status) {
+        cudaMemcpy(ctx->h_status, ctx->scratch.status, sizeof(int), cudaMemcpyDeviceToHost);
+        const int s = *ctx->h_status;
+        if (s) {
+            cudaMemset(ctx->scratch.status, 0, sizeof(int));
+            if (s & ST_TMA_TIMEOUT) return set_error(ctx, FE_ERR_TIMEOUT, "a bulk copy wait ran out");
+            return set_error(ctx, FE_ERR_CUDA, "device status word " + std::to_string(s));
+        }
+    }
+    if (ctx->async_error != FE_OK) {
+        fe_status st = ctx->async_error;
+        ctx->async_error = FE_OK;
+        return st;
+    }
+    return FE_OK;
+}
+
+const char *fe_last_error(fe_ctx *ctx) {
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
+        t_last_error = ctx->last_error;
+    }
+    return t_last_error.c_str();
+}
+
+fe_status fe_integrate_tet(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream) {
+    return integrate(ctx, FE_TET, args, out, stream);
+}
+
+fe_status fe_integrate_prism(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream) {
+    return integrate(ctx, FE_PRISM, args, out, stream);
+}
+
+uint64_t fe_launch_count(void) { return g_launches.load(); }
+
+fe_status fe_ctx_set_profiling(fe_ctx *ctx, int on) {
+    if (!ctx) return FE_ERR_INVALID_ARG;
+    ctx->profiling = on != 0;
+    return FE_OK;
+}
+
+fe_status fe_ctx_kernel_time(fe_ctx *ctx, double *ms, int64_t *launches, int reset) {
+    if (!ctx || !ms || !launches) return set_error(ctx, FE_ERR_INVALID_ARG, "null argument");
+    cudaSetDevice(ctx->device);
+    double total = 0.0;
+    for (auto &pr : ctx->prof_events) {
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "cudaEventSynchronize");
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, pr.first, pr.second);
+        total += t;
+    }
+    *ms = total;
+    *launches = int64_t(ctx->prof_events.size());
+    if (reset) {
+        for (auto &pr : ctx->prof_events) {
+            ctx->event_pool.push_back(pr.first);
+            ctx->event_pool.push_back(pr.second);
+        }
+        ctx->prof_events.clear();
+    }
+    return FE_OK;
+}
+
+fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out, int *block_threads,
+                       int *persistent) {
+    if (!ctx || !block_threads || !persistent) return set_error(ctx, FE_ERR_INVALID_ARG, "null argument");
+    fe_status st = fe_check_args(type, args, out);
+    if (st != FE_OK) return st;
+    Shape sh = default_shape(type);
+    auto it = ctx->shapes.find(shape_key(type, args, out));
+    if (it != ctx->shapes.end()) sh = it->second;
+    *block_threads = sh.block;
+    *persistent = sh.persistent;
+    return FE_OK;
+}
+
+fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, void *stream) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    fe_status st = fe_check_args(type, a, o);
+    if (st != FE_OK) return st;
+    if (a->memory != FE_MEM_DEVICE || o->memory != FE_MEM_DEVICE)
+        return set_error(ctx, FE_ERR_INVALID_ARG, "tuning needs device buffers");
+    if (a->n_elem == 0) return FE_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool was_prof = ctx->profiling;
+    ctx->profiling = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Shape best_shape = default_shape(type);
+    for (int B = 64; B <= max_block(type); B *= 2) {
+        for (int pers = 0; pers < 2; ++pers) {
+            Shape sh{B, pers};
+            if (smem_bytes(type, a, o->layout, B) + kStaticSmem > ctx->max_smem_optin) continue;
+            st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);  // warm-up
+            if (st != FE_OK) break;
+            cudaEventRecord(e0, s);
+            const int reps = 3;
+            for (int r = 0; r < reps && st == FE_OK; ++r) st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);
+            cudaEventRecord(e1, s);
+            if (st != FE_OK) break;
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) {
+                st = cuda_check(ctx, ce, "tuning");
+                break;
+            }
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t < best) {
+                best = t;
+                best_shape = sh;
+            }
+        }
+        if (st != FE_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->profiling = was_prof;
+    if (st != FE_OK) return st;
+    ctx->shapes[shape_key(type, a, o)] = best_shape;
+    save_tuning_cache(ctx);
+    return FE_OK;
+}
+
+}  // extern "C"

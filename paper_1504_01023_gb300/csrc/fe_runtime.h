@@ -1,0 +1,100 @@
+// Runtime internals shared by fe_runtime.cu, fe_batch.cu and fe_serve.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fe.h"
+#include "fe_internal.h"
+
+namespace fe {
+
+extern std::atomic<uint64_t> g_launches;
+
+// Device scratch of one launch sequence (fix-up list, its counter, status word).
+struct Scratch {
+    unsigned long long *fix_list = nullptr;
+    unsigned int fix_cap = 0;
+    unsigned int *fix_count = nullptr;
+    int *status = nullptr;
+};
+
+struct Shape {
+    int block = 0;          // threads per block = elements per tile
+    int persistent = 0;     // 1: grid = SMs x resident blocks, tiles strided
+};
+
+struct ServeState;          // fe_serve.cu
+struct BatchCache;          // fe_batch.cu
+
+struct MeshRec {
+    fe_elem_type type;
+    int64_t n_elem;
+    double *coords;         // SOA planes, stride n_elem, context-owned
+    uint64_t bytes;
+};
+
+}  // namespace fe
+
+struct fe_ctx {
+    int device = 0;
+    int sms = 0;
+    int max_smem_optin = 0;
+    std::string device_name;
+    std::string last_error;
+    std::mutex err_mu;
+    fe_status async_error = FE_OK;
+
+    fe::Scratch scratch;            // plain calls
+    int *h_status = nullptr;        // pinned mirror for status reads
+
+    // profiling
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    std::vector<cudaEvent_t> event_pool;
+
+    // autotuner
+    int autotune = 0;
+    std::string tuning_cache_path;
+    std::map<std::string, fe::Shape> shapes;
+
+    // host-buffer pipeline
+    cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+    void *stage[2][5] = {{nullptr}};
+    uint64_t stage_bytes[2][5] = {{0}};
+
+    // resident meshes
+    std::mutex mesh_mu;
+    std::unordered_map<int64_t, fe::MeshRec> meshes;
+    int64_t next_mesh = 1;
+    uint64_t hbm_budget = 0;
+    std::atomic<uint64_t> hbm_used{0};
+
+    fe::BatchCache *batch = nullptr;
+    fe::ServeState *serve = nullptr;
+    int serve_slots = 4;
+};
+
+namespace fe {
+fe_status set_error(fe_ctx *ctx, fe_status st, const std::string &msg);
+fe_status cuda_check(fe_ctx *ctx, cudaError_t e, const char *what);
+fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n);
+void free_scratch(Scratch &s);
+// Launch main + fix-up kernels of one homogeneous set (device pointers).
+fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, Scratch &s,
+                     cudaStream_t st, const Shape *force = nullptr);
+int ns_of(fe_elem_type t);
+int nq_of(fe_quad q);
+int nc_of(const fe_elem_args *a);
+void batch_destroy(fe_ctx *ctx);
+void serve_destroy(fe_ctx *ctx);
+}  // namespace fe

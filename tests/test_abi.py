@@ -1,0 +1,96 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/fe.h, and validates arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1504_01023_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fe_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return api.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding declares a signature for each of them
+    assert set(names) <= {s[0] for s in api._SIGS}
+
+
+def test_bytes_per_element_matches_table3(lib):
+    """Table 3 (Sec. 4.1): DP words per element 36, 66, 52, 80 (Poisson tet and
+    prism with d^0 per point, conv-diff tet and prism with 20 per-element
+    coefficients) -> 288, 528, 416, 640 bytes."""
+    b = api.bytes_per_element
+    assert b(api.TET, api.POISSON, api.QUAD_TET4, api.PER_QPOINT, api.FP64) == 288
+    assert b(api.PRISM, api.POISSON, api.QUAD_PRISM6, api.PER_QPOINT, api.FP64) == 528
+    assert b(api.TET, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP64) == 416
+    assert b(api.PRISM, api.GENERIC, api.QUAD_PRISM6, api.PER_ELEMENT, api.FP64) == 640
+    # the workloads of this library
+    assert b(api.TET, api.POISSON, api.QUAD_TET1, api.PER_ELEMENT, api.FP64) == 264
+    assert b(api.TET, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP32_MIXED) == 256
+    assert b(api.PRISM, api.GENERIC, api.QUAD_PRISM6, api.PER_QPOINT, api.FP32_MIXED) == 792
+    assert b(api.TET, 7, api.QUAD_TET4, 0, 0) == -1
+
+
+def _args(n=10, et=api.TET, quad=api.QUAD_TET4, prec=api.FP32_MIXED):
+    a = api.ElemArgs()
+    a.n_elem = n
+    a.coords = 4096
+    a.coefs = 8192
+    a.kind, a.quad, a.coef_mode, a.prec = api.GENERIC, quad, api.PER_ELEMENT, prec
+    o = api.Out()
+    o.A, o.b = 16384, 32768
+    return a, o
+
+
+def _chk(lib, et, a, o):
+    return lib.fe_check_args(et, ctypes.byref(a), ctypes.byref(o))
+
+
+def test_argument_validation(lib):
+    a, o = _args()
+    assert _chk(lib, api.TET, a, o) == 0
+    bad = []
+    a2, o2 = _args(); a2.n_elem = -1; bad.append((api.TET, a2, o2))
+    a2, o2 = _args(); a2.quad = api.QUAD_PRISM6; bad.append((api.TET, a2, o2))
+    a2, o2 = _args(); bad.append((api.PRISM, a2, o2))                       # tet rule on a prism
+    a2, o2 = _args(); a2.coords = 0; bad.append((api.TET, a2, o2))
+    a2, o2 = _args(); a2.coords = 4100; bad.append((api.TET, a2, o2))        # misaligned double
+    a2, o2 = _args(); a2.coords_stride = 5; bad.append((api.TET, a2, o2))    # SOA stride < n
+    a2, o2 = _args(); o2.stride = 3; bad.append((api.TET, a2, o2))
+    a2, o2 = _args(); a2.kind = 9; bad.append((api.TET, a2, o2))
+    a2, o2 = _args(); a2.prec = 5; bad.append((api.TET, a2, o2))
+    a2, o2 = _args(); o2.layout = 4; bad.append((api.TET, a2, o2))
+    a2, o2 = _args(); a2.memory = 3; bad.append((api.TET, a2, o2))
+    for et, a2, o2 in bad:
+        assert _chk(lib, et, a2, o2) == -1, (a2.n_elem, a2.quad)
+    assert lib.fe_check_args(api.TET, None, ctypes.byref(o)) == -1
+    # coefficient layout must follow the coordinate layout
+    a2, o2 = _args(); a2.coefs_layout = api.AOS
+    assert _chk(lib, api.TET, a2, o2) == -6
+    # zero elements is valid even with null pointers
+    a2, o2 = _args(0); a2.coords = 0; a2.coefs = 0; o2.A = 0; o2.b = 0
+    assert _chk(lib, api.TET, a2, o2) == 0
+    assert lib.fe_last_error(None)
+
+
+def test_null_context_rejected(lib):
+    a, o = _args()
+    assert lib.fe_integrate_tet(None, ctypes.byref(a), ctypes.byref(o), None) == -1
+    assert lib.fe_ctx_sync(None) == -1

@@ -1,0 +1,174 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative Frobenius per element, A and b separately): 1e-12 for the
+FP64 form, 2e-5 for the mixed form. Inputs span several tiles with a ragged tail.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TOL, make_inputs, max_errors, run_gpu, run_oracle
+from paper_1504_01023_gb300 import api, meshgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1504_01023_gb300 import build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+TET_CASES = list(itertools.product([api.POISSON, api.GENERIC], [api.QUAD_TET1, api.QUAD_TET4], [0, 1],
+                                   [api.FP64, api.FP32_MIXED], [api.SOA, api.AOS], [api.SOA, api.AOS]))
+PRISM_CASES = list(itertools.product([api.POISSON, api.GENERIC], [api.QUAD_PRISM6], [0, 1],
+                                     [api.FP64, api.FP32_MIXED], [api.SOA, api.AOS], [api.SOA, api.AOS]))
+
+
+def _ids(cases):
+    return ["k%d-q%d-c%d-p%d-i%d-o%d" % c for c in cases]
+
+
+@pytest.mark.parametrize("kind,quad,cpq,prec,lay,olay", TET_CASES, ids=_ids(TET_CASES))
+def test_tet_parity(ctx, kind, quad, cpq, prec, lay, olay):
+    mesh, c = make_inputs(api.TET, kind, quad, cpq, n=2999, seed=11)
+    An, bn, fn, cu = run_gpu(ctx, api.TET, kind, quad, cpq, prec, lay, olay, mesh, c)
+    Ar, br, fr = run_oracle(api.TET, kind, quad, cpq, mesh, cu)
+    ea, eb = max_errors(An, bn, Ar, br)
+    assert ea <= TOL[prec] and eb <= TOL[prec], (ea, eb)
+    assert (fn == fr).all()      # no element here is poor, inverted or degenerate
+
+
+@pytest.mark.parametrize("kind,quad,cpq,prec,lay,olay", PRISM_CASES, ids=_ids(PRISM_CASES))
+def test_prism_parity(ctx, kind, quad, cpq, prec, lay, olay):
+    mesh, c = make_inputs(api.PRISM, kind, quad, cpq, n=1999, seed=13)
+    An, bn, fn, cu = run_gpu(ctx, api.PRISM, kind, quad, cpq, prec, lay, olay, mesh, c)
+    Ar, br, fr = run_oracle(api.PRISM, kind, quad, cpq, mesh, cu)
+    ea, eb = max_errors(An, bn, Ar, br)
+    assert ea <= TOL[prec] and eb <= TOL[prec], (ea, eb)
+    assert (fn == fr).all()
+
+
+@pytest.mark.parametrize("prec", [api.FP64, api.FP32_MIXED])
+def test_thin_prisms_far_from_origin(ctx, prec):
+    """h = 1e-3 elements at coordinates up to 1: the mixed form must form its edge
+    vectors without the cancellation of rounding absolute coordinates."""
+    full = meshgen.prism_slab_mesh(1000, seed=meshgen.SEED_BASE + 3, n_elem=1_999_000)
+    mesh = full[-3001:].copy()        # elements near (1, 1)
+    _, c = make_inputs(api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, mesh=mesh, seed=17)
+    An, bn, fn, cu = run_gpu(ctx, api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, prec, api.SOA, api.SOA, mesh, c)
+    Ar, br, _ = run_oracle(api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, mesh, cu)
+    ea, eb = max_errors(An, bn, Ar, br)
+    assert ea <= TOL[prec] and eb <= TOL[prec], (ea, eb)
+
+
+@pytest.mark.parametrize("et", [api.TET, api.PRISM])
+def test_small_and_ragged_sizes(ctx, et):
+    quad = api.QUAD_TET4 if et == api.TET else api.QUAD_PRISM6
+    for n in [1, 2, 31, 33, 255, 257, 513]:
+        mesh, c = make_inputs(et, api.GENERIC, quad, 0, n=n, seed=n)
+        for prec in (api.FP64, api.FP32_MIXED):
+            for lay, olay in [(api.SOA, api.SOA), (api.AOS, api.AOS)]:
+                An, bn, fn, cu = run_gpu(ctx, et, api.GENERIC, quad, 0, prec, lay, olay, mesh, c)
+                Ar, br, _ = run_oracle(et, api.GENERIC, quad, 0, mesh, cu)
+                ea, eb = max_errors(An, bn, Ar, br)
+                assert ea <= TOL[prec] and eb <= TOL[prec], (n, prec, lay, ea, eb)
+
+
+def test_zero_elements(ctx):
+    X = torch.empty((12, 0), dtype=torch.float64, device="cuda")
+    C = torch.empty((20, 0), dtype=torch.float32, device="cuda")
+    A, b, f = ctx.integrate(api.TET, X, C, api.GENERIC, api.QUAD_TET4)
+    ctx.sync()
+    assert A.numel() == 0
+
+
+def test_inverted_and_degenerate_elements(ctx):
+    mesh, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, n=300, seed=3)
+    mesh = mesh.copy()
+    inv = np.arange(0, 300, 7)
+    mesh[inv] = mesh[inv][:, [0, 2, 1, 3]]                 # inverted
+    deg = np.arange(3, 300, 11)
+    mesh[deg, 3] = mesh[deg, 0]                            # vertex 3 on vertex 0: zero volume
+    for prec in (api.FP64, api.FP32_MIXED):
+        An, bn, fn, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, prec, api.SOA, api.SOA, mesh, c)
+        Ar, br, fr = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh, cu)
+        ea, eb = max_errors(An, bn, Ar, br)
+        assert ea <= TOL[prec] and eb <= TOL[prec]
+        assert ((fn & 6) == fr).all()                      # bits 1, 2 agree with the oracle
+        assert (fn[deg] & 4).all() and not An[deg].any()
+        if prec == api.FP32_MIXED:
+            assert (fn[deg] & 1).all()                     # degenerate -> double path
+
+
+def test_nan_coordinates_do_not_fault(ctx):
+    mesh, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, n=200, seed=4)
+    mesh = mesh.copy()
+    mesh[5, 2, 1] = np.nan
+    mesh[9, 0, 0] = np.inf
+    for prec in (api.FP64, api.FP32_MIXED):
+        An, bn, fn, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, prec, api.SOA, api.SOA, mesh, c)
+        ok = np.ones(200, bool)
+        ok[[5, 9]] = False
+        Ar, br, _ = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh[ok], cu[ok])
+        ea, eb = max_errors(An[ok], bn[ok], Ar, br)
+        assert ea <= TOL[prec] and eb <= TOL[prec]
+
+
+@pytest.mark.parametrize("fraction", [0.01, 0.1])
+def test_sliver_stress_mixed(ctx, fraction):
+    """Poorly shaped elements (mean ratio < 0.1) take the double-precision Jacobian
+    path; the flag decision is the float mean ratio, compared with the oracle's
+    float quality away from the threshold."""
+    mesh = meshgen.tet_cube_mesh(12, seed=meshgen.SEED_BASE + 2)
+    sl = meshgen.make_slivers(mesh, fraction, seed=meshgen.SEED_BASE + 20)
+    _, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh=mesh, seed=5)
+    An, bn, fn, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, api.FP32_MIXED, api.SOA, api.SOA, mesh, c)
+    Ar, br, _ = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh, cu)
+    ea, eb = max_errors(An, bn, Ar, br)
+    assert ea <= 2e-5 and eb <= 2e-5, (ea, eb)
+    q = oracle.quality(oracle.TET, mesh, n_threads=8)
+    flagged = (fn & 1).astype(bool)
+    clear = np.abs(q - 0.1) > 1e-3 * 0.1
+    assert (flagged[clear] == (q[clear] < 0.1)).all()
+    assert flagged.sum() >= 0.5 * len(sl)
+
+
+def test_host_buffers_match_device_path(ctx):
+    mesh, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, n=5000, seed=8)
+    Ad, bd, fd, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, api.FP32_MIXED, api.SOA, api.SOA, mesh, c)
+    Ah, bh, fh, _ = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, api.FP32_MIXED, api.SOA, api.SOA, mesh, c,
+                            device=None)
+    assert np.array_equal(Ad, Ah) and np.array_equal(bd, bh) and np.array_equal(fd, fh)
+
+
+def test_autotune_keeps_results(ctx):
+    mesh, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, n=20000, seed=9)
+    from helpers import to_device_inputs, gpu_outputs_to_numpy
+    X, C, cu = to_device_inputs(api.TET, mesh, c, api.FP32_MIXED, api.SOA)
+    r0 = gpu_outputs_to_numpy(api.TET, *ctx.integrate(api.TET, X, C, api.GENERIC, api.QUAD_TET4), api.SOA)
+    shape = ctx.tune(api.TET, X, C, api.GENERIC, api.QUAD_TET4)
+    assert shape[0] in (64, 128, 256, 512)
+    r1 = gpu_outputs_to_numpy(api.TET, *ctx.integrate(api.TET, X, C, api.GENERIC, api.QUAD_TET4), api.SOA)
+    ctx.sync()
+    assert np.array_equal(r0[0], r1[0]) and np.array_equal(r0[1], r1[1])
+
+
+def test_profiling_records_kernel_time(ctx):
+    mesh, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, n=10000, seed=10)
+    from helpers import to_device_inputs
+    X, C, _ = to_device_inputs(api.TET, mesh, c, api.FP32_MIXED, api.SOA)
+    ctx.set_profiling(True)
+    n0 = api.launch_count()
+    for _ in range(3):
+        ctx.integrate(api.TET, X, C, api.GENERIC, api.QUAD_TET4)
+    ms, k = ctx.kernel_time()
+    ctx.set_profiling(False)
+    assert k == 3 and ms > 0
+    assert api.launch_count() - n0 == 6          # main + fix-up per call
