@@ -1,0 +1,393 @@
+"""Benchmark: finite-element integration throughput on GB300.
+
+A step is one pass of the whole hot path over one batch: the mixed-precision
+integration of 6,000,000 generic convection-diffusion-reaction tetrahedra
+(100^3 cubes x 6, nodes jittered by +-0.2 h, 4-point rule, 20 coefficients per
+element): coordinate split and edge vectors, Jacobian terms, shape test, global
+derivatives, coefficient products, accumulation and stores (main kernel), then
+the double-Jacobian fix-up of flagged elements (fix-up kernel).
+
+Prints one JSON line (rank 0). Under torchrun every rank integrates its own
+seeded mesh of that size on its own GPU (weak scaling, no data-path
+collective; the barrier and the max over ranks are timing only).
+
+--impl reference times the FP64 CPU oracle (Algorithm 1 as written) on the host
+cores instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Melements/s & % of HBM roofline, FP32 vs FP64 form; served p50/p99 latency"
+WORKLOAD = ("generic conv-diff-reaction tetrahedra: unit cube 100^3 x 6 Kuhn = 6,000,000 elements, "
+            "jitter +-0.2h, TET4 rule, per-element coefficients (c^{ij} SPD eig U[0.1,10], c^{i0},c^{0i} "
+            "U[-1,1]^3, c^{00} U[0,1], d U[-1,1]), mixed FP32 with FP64 Jacobian for mean ratio < 0.1, "
+            "element-contiguous (natural) input and output order")
+N_ELEM = 6_000_000
+SEED = 1504010230 + 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--n-cubes", type=int, default=100,
+                    help="cubes per axis of the tetrahedral mesh (6 n^3 elements); smaller only for profiling")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank: int, n_cubes: int = 100):
+    from paper_1504_01023_gb300 import meshgen
+    mesh = meshgen.tet_cube_mesh(n_cubes, jitter=0.2, seed=SEED + 1000 * rank)
+    coefs = meshgen.generic_coefs(len(mesh), 1, seed=SEED + 1000 * rank)
+    return mesh, coefs
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of the GPU's clocks and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((t, parts))
+        inside = [r for r in rows if self.t0 is not None and self.t0 - 0.2 <= r[0] <= (self.t1 or 1e30) + 0.2]
+        use = inside or rows[-3:]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(p[1]) for _, p in use if p[1].replace(".", "").isdigit()]
+        smax = [float(p[2]) for _, p in use if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, p in use for i in range(4) if p[5 + i].lower() == "active"})
+        pw = [float(p[3]) for _, p in use if re.match(r"^[0-9.]+$", p[3])]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(use), "samples_in_region": len(inside),
+                "power_w_max": max(pw) if pw else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1504_01023_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_tag: str):
+    """DRAM bytes per launch of a kernel from profiles/traffic.md, if its record was
+    taken on the current kernel sources (otherwise None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel_tag and cells[1] == cur:
+            try:
+                return float(cells[3])
+            except ValueError:
+                return None
+    return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(mesh, coefs, target_s=10.0, max_elems=None):
+    """The FP64 oracle as it stands, on all host cores, over the first S elements
+    of the workload (S calibrated for ~target_s of CPU work)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    c = coefs.astype(np.float32).astype(np.float64)
+    probe = min(len(mesh), 50_000)
+    t = time.perf_counter()
+    oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:probe], c[:probe], n_threads=cores)
+    dt = time.perf_counter() - t
+    s = int(min(len(mesh), max(probe, probe * target_s / max(dt, 1e-6))))
+    if max_elems:
+        s = min(s, max_elems)
+    t = time.perf_counter()
+    oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:s], c[:s], n_threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": s / dt / 1e6, "unit": "Melem/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {s:,} of {N_ELEM:,} elements of the workload, one pass, FP64, OpenMP over elements",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    mesh, coefs = workload(0)
+    cores = os.cpu_count() or 1
+    c = coefs.astype(np.float32).astype(np.float64)
+    # size each step for ~1.5 s, so that warmup + steps stay within a few minutes
+    per_step = min(1.5, 150.0 / max(args.steps + args.warmup, 1))
+    probe = 20_000
+    t = time.perf_counter()
+    oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:probe], c[:probe], n_threads=cores)
+    rate = probe / max(time.perf_counter() - t, 1e-6)
+    s = int(min(len(mesh), max(1000, rate * per_step)))
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        o = int(rng.integers(0, len(mesh) - s + 1))
+        oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[o:o + s], c[o:o + s], n_threads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o = int(rng.integers(0, len(mesh) - s + 1))
+        oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[o:o + s], c[o:o + s], n_threads=cores)
+    dt = time.perf_counter() - t
+    value = s * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_elem": N_ELEM, "step": f"{s:,} elements of the workload"},
+            "cpu_baseline": {"value": value, "unit": "Melem/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{s:,}-element contiguous slices of the {N_ELEM:,}-element workload per step"},
+            "e2e": {"value": value, "unit": "Melem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def aggregate(ms_total, n_per_rank, steps, world, dist=None, device=None):
+    """Max of the timed region over ranks (each rank did n_per_rank elements per
+    step); returns (ms per step, whole-job Melem/s)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_step = ms_total / steps
+    return ms_step, world * n_per_rank / (ms_step * 1e-3) / 1e6
+
+
+# ---------------------------------------------------------------------------
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1504_01023_gb300 import api
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    ctx = api.Context(dev.index)
+    mesh, coefs = workload(rank, args.n_cubes)
+    n = len(mesh)
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)                       # [E,4,3] f64
+    C = torch.from_numpy(coefs.astype(np.float32)).to(dev)                         # [E,20] f32
+    out = api.alloc_out(api.TET, n, api.FP32_MIXED, api.AOS, dev, with_flags=True)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(kind=api.GENERIC, quad=api.QUAD_TET4, coef_mode=api.PER_ELEMENT, prec=api.FP32_MIXED,
+              layout=api.AOS, out_layout=api.AOS)
+    shape = ctx.tune(api.TET, X, C, out=out, **kw)                                 # autotuner (untimed)
+    step = lambda: ctx.integrate(api.TET, X, C, out=out, **kw)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    bpe = api.bytes_per_element(api.TET, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP32_MIXED)
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.5)
+    ctx.set_profiling(True)
+    ctx.kernel_time(reset=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = api.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark(0)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark(1)
+    launches = api.launch_count() - l0
+    ms_total = e0.elapsed_time(e1)
+    kms, kn = ctx.kernel_time(reset=True)
+    ctx.set_profiling(False)
+    clocks.stop()
+    ms_step, value = aggregate(ms_total, n, args.steps, world, dist if world > 1 else None, dev)
+    k_ms = kms / max(kn, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = n * bpe / (k_ms * 1e-3) / 1e9
+    traffic = ncu_traffic("tet_generic_mixed_aos_6M")
+
+    result = {"metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": WORKLOAD, "n_elem_per_gpu": n, "bytes_per_element": bpe,
+                         "launch_shape": {"block": shape[0], "persistent": shape[1]},
+                         "l2": "inputs larger than L2: %.2f GB read+written per step per GPU" % (n * bpe / 1e9),
+                         "parallelism": f"weak: {world} independent mesh(es), one per GPU"},
+              "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "traffic": traffic,
+                           "kernel": "elem_kernel<TET,GENERIC,MIXED,TET4,per-element,AOS,AOS>",
+                           "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                           "kernel_ms": k_ms, "algorithmic_bytes_per_launch": n * bpe},
+              "gpu_launches": int(launches), "clocks": clocks.summary()}
+
+    if rank == 0 and world == 1:
+        if not args.no_fp64:
+            result["fp64_form"] = fp64_form(ctx, dev, api, mesh, args)
+        if not args.no_e2e:
+            result["e2e"] = e2e(ctx, api, mesh, coefs, args)
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(mesh, coefs)
+    elif rank == 0:
+        result["e2e"] = {"value": None, "unit": "Melem/s", "note": "measured at N=1 only"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def fp64_form(ctx, dev, api, mesh, args):
+    """FP64 plain form: Poisson tetrahedra, 1-point rule, d^0 = 1 per element, on the
+    same 6M-element mesh (the 48,000-element Poisson mesh scaled to 100^3 x 6)."""
+    import torch
+    n = len(mesh)
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)
+    C = torch.ones((n, 1), dtype=torch.float64, device=dev)
+    out = api.alloc_out(api.TET, n, api.FP64, api.AOS, dev, with_flags=True)
+    kw = dict(kind=api.POISSON, quad=api.QUAD_TET1, coef_mode=api.PER_ELEMENT, prec=api.FP64, layout=api.AOS,
+              out_layout=api.AOS)
+    ctx.tune(api.TET, X, C, out=out, **kw)
+    for _ in range(3):
+        ctx.integrate(api.TET, X, C, out=out, **kw)
+    torch.cuda.synchronize(dev)
+    reps = max(20, min(200, args.steps // 10))
+    ctx.set_profiling(True)
+    ctx.kernel_time(reset=True)
+    for _ in range(reps):
+        ctx.integrate(api.TET, X, C, out=out, **kw)
+    kms, kn = ctx.kernel_time(reset=True)
+    ctx.set_profiling(False)
+    bpe = api.bytes_per_element(api.TET, api.POISSON, api.QUAD_TET1, api.PER_ELEMENT, api.FP64)
+    k_ms = kms / kn
+    peak, _ = measured_peaks()
+    gbs = n * bpe / (k_ms * 1e-3) / 1e9
+    del X, C, out
+    torch.cuda.empty_cache()
+    return {"workload": "Poisson tetrahedra, 6,000,000 elements (100^3 x 6, jitter +-0.2h), TET1, d^0 = 1 per "
+                        "element, all arithmetic FP64, element-contiguous order", "value": n / k_ms / 1e3,
+            "unit": "Melem/s", "bytes_per_element": bpe, "achieved_gbs": gbs, "hbm_frac": gbs / peak,
+            "bound": "alu (FP64 pipe)", "dtype": "f64"}
+
+
+def e2e(ctx, api, mesh, coefs, args):
+    """Same metric through the C ABI with pinned HOST buffers: host->device copies
+    of the inputs, the kernels and device->host copies of the outputs are inside the
+    timed call (chunked and overlapped by the library)."""
+    import torch
+    n = len(mesh)
+    Xh = torch.from_numpy(np.ascontiguousarray(mesh)).pin_memory()
+    Ch = torch.from_numpy(coefs.astype(np.float32)).pin_memory()
+    out = api.alloc_out(api.TET, n, api.FP32_MIXED, api.AOS, "cpu", with_flags=True, pin=True)
+    kw = dict(kind=api.GENERIC, quad=api.QUAD_TET4, coef_mode=api.PER_ELEMENT, prec=api.FP32_MIXED,
+              layout=api.AOS, out_layout=api.AOS)
+    for _ in range(2):
+        ctx.integrate(api.TET, Xh, Ch, out=out, **kw)
+    reps = max(3, min(20, args.steps // 100))
+    t = time.perf_counter()
+    for _ in range(reps):
+        ctx.integrate(api.TET, Xh, Ch, out=out, **kw)
+    dt = (time.perf_counter() - t) / reps
+    bi = Xh.numel() * 8 + Ch.numel() * 4
+    bo = out[0].numel() * 4 + out[1].numel() * 4 + out[2].numel()
+    return {"value": n / dt / 1e6, "unit": "Melem/s", "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+            "ms_per_step": dt * 1e3, "steps": reps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()
