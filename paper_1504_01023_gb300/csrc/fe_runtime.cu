@@ -194,7 +194,15 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
         cudaEventRecord(ev0, st);
     }
     cudaError_t ce = cudaLaunchKernel(k, dim3(unsigned(grid)), dim3(unsigned(sh.block)), args, size_t(smem), st);
-    if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaLaunchKernel(elem)");
+    if (ce != cudaSuccess) {
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, k);
+        std::ostringstream m;
+        m << "cudaLaunchKernel(elem) grid " << grid << " block " << sh.block << " smem " << smem
+          << " (func: max threads " << fa.maxThreadsPerBlock << ", max dyn smem " << fa.maxDynamicSharedSizeBytes
+          << ", static smem " << fa.sharedSizeBytes << ", regs " << fa.numRegs << ")";
+        return cuda_check(ctx, ce, m.str().c_str());
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (ctx->profiling) {
         cudaEventRecord(ev1, st);
