@@ -257,6 +257,29 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, cons
 fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                        int *block_threads, int *persistent);
 
+/*
+ * Mixed-precision tetrahedron integration that allocates nothing (the paper has
+ * no counterpart; it is a service to callers that cannot call cudaMalloc, such
+ * as code running inside a device-memory arena owned by a host application,
+ * real-time loops that forbid allocator calls, or plugins that may not create a
+ * context of this library).
+ * Same inputs, outputs, layouts and results as fe_integrate_tet with
+ * prec = FE_FP32_MIXED and device buffers; no context. Its scratch (the list of
+ * elements sent to the double-precision Jacobian pass, a counter and a status
+ * word) is a fixed 4 MiB array in the library's device image, which every GPU
+ * that loads the library holds until the process exits. Hence at most 524,256
+ * elements per call; larger n_elem is rejected with FE_ERR_INVALID_ARG before any
+ * GPU work. Runs on the calling thread's current device. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. Every call clears the counter and the
+ * status word, launches its two kernels on `stream` and returns after they
+ * finish, reporting FE_ERR_TIMEOUT if a bulk-copy wait ran out. All calls share
+ * the array: calls that overlap on the GPU (other streams or threads at the same
+ * time) race and must not be made. Calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ */
+fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe_out *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

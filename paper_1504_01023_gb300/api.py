@@ -93,6 +93,7 @@ _SIGS = [
     ("fe_tune", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
     ("fe_get_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("fe_integrate_tet_noalloc", ctypes.c_int, [ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
 ]
 
 _lock = threading.Lock()
@@ -206,6 +207,22 @@ def make_out(A, b, flags, out_layout):
     o.flags = flags.data_ptr() if flags is not None else None
     o.memory = _mem(A)
     return o
+
+
+# Largest n_elem fe_integrate_tet_noalloc accepts (its static scratch holds one
+# list entry per element).
+NOALLOC_MAX_ELEMS = (4 << 20) // 8 - 32
+
+
+def integrate_tet_noalloc(coords, coefs, kind, quad, coef_mode, layout, out_layout, out, stream=None):
+    """Mixed-precision tetrahedra through fe_integrate_tet_noalloc: the caller
+    provides every buffer (``out`` = (A, b, flags)); the library allocates nothing.
+    Returns after the kernels finish."""
+    args = make_args(TET, coords, coefs, kind, quad, coef_mode, FP32_MIXED, layout)
+    o = make_out(*out, out_layout)
+    s = ctypes.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    _check(load().fe_integrate_tet_noalloc(ctypes.byref(args), ctypes.byref(o), s))
+    return out
 
 
 class Context:
