@@ -181,19 +181,27 @@ int64_t fe_bytes_per_element(fe_elem_type type, fe_problem kind, fe_quad quad, f
 
 /*
  * Resident meshes (Sec. 3.1: element data kept in the memory of the processor
- * doing the integration). Copies geometry (host or device source, any layout) into
- * a context-owned SOA buffer and returns its id. Counted against the HBM budget.
+ * doing the integration). Copies geometry (host or device source, SOA planes of
+ * stride n_elem or AOS records) into a context-owned element-contiguous (AOS)
+ * device buffer and returns its id. Counted against the HBM budget
+ * (FE_ERR_BUDGET if it does not fit). Releasing waits for the device.
  */
 fe_status fe_mesh_register(fe_ctx *ctx, fe_elem_type type, int64_t n_elem, const double *coords,
                            fe_layout layout, fe_memory memory, int64_t *mesh_id);
 fe_status fe_mesh_release(fe_ctx *ctx, int64_t mesh_id);
 
 /*
- * Batched integration: many element sets of uneven size and mixed type/kind in
- * one persistent kernel launched from a captured CUDA graph (not in the paper,
- * which launches one homogeneous set per kernel, Sec. 3.2). Items must be
- * FE_FP32_MIXED with SOA inputs and outputs in device memory. The graph for a
- * given item list is captured on first submission and replayed afterwards.
+ * Batched integration: many element sets of uneven size and mixed type, kind,
+ * rule and coefficient mode in one persistent kernel (not in the paper, which
+ * runs one homogeneous set per kernel, Sec. 3.2). Blocks take tiles of
+ * consecutive elements from a global counter; tiles are ordered by decreasing
+ * cost. The launch sequence {counter reset, persistent kernel, fix-up kernel} is
+ * captured into a CUDA graph on the first submission of an item list (same items
+ * byte for byte, i.e. same pointers and sizes) and replayed on later ones; the
+ * last 8 lists are kept. With autotune on, the first submission times tiles of
+ * 64, 128 and 256 elements and keeps the fastest.
+ * Items must be FE_FP32_MIXED, device memory, element-contiguous (AOS) inputs
+ * and outputs (FE_ERR_UNSUPPORTED otherwise). At most 2^23 items.
  */
 typedef struct fe_batch_item {
     fe_elem_type type;
@@ -203,11 +211,16 @@ typedef struct fe_batch_item {
 fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, void *stream);
 
 /*
- * Serving: requests on resident meshes arrive at any time; a scheduler thread
- * admits them under the HBM budget (outputs are context-owned until released),
- * merges waiting requests into one batched launch and keeps up to serve_slots
- * launches in flight, so requests that arrive while others run overlap with them
- * on the device. coefs is a device pointer in SOA layout with stride n_elem.
+ * Serving: integration requests on resident meshes arrive at any time. A
+ * scheduler thread admits them in arrival order while the resident meshes plus
+ * the outputs of admitted, unreleased requests fit the HBM budget, merges every
+ * admitted mixed-precision request into one batched launch (continuous
+ * batching), runs FE_FP64 requests as their own launches, and keeps up to
+ * serve_slots launches in flight on separate streams, so requests that arrive
+ * while others run overlap with them on the device. coefs is a device pointer,
+ * element-contiguous (AOS), float for FE_FP32_MIXED and double for FE_FP64. The
+ * outputs are context-owned element-contiguous device buffers, valid until
+ * fe_serve_release.
  */
 typedef struct fe_request {
     int64_t mesh_id;
@@ -215,26 +228,27 @@ typedef struct fe_request {
     fe_quad quad;
     fe_coef_mode coef_mode;
     const void *coefs;
-    fe_precision prec;             /* FE_FP32_MIXED (batched) or FE_FP64 (own launch) */
+    fe_precision prec;
 } fe_request;
 
 typedef struct fe_result {
     fe_status status;
     fe_elem_type type;
     int64_t n_elem;
-    void *A;                       /* device, SOA with stride n_elem, context-owned */
-    void *b;
-    uint8_t *flags;
-    double t_submit_us;            /* host clock, microseconds */
-    double t_launch_us;
-    double t_done_us;
+    void *A;                       /* device, AOS [n_elem][NS][NS], context-owned */
+    void *b;                       /* device, AOS [n_elem][NS] */
+    uint8_t *flags;                /* device, [n_elem] */
+    double t_submit_us;            /* host steady clock, microseconds */
+    double t_launch_us;            /* when the scheduler enqueued its launch */
+    double t_done_us;              /* stamped by a host callback when its stream finished */
 } fe_result;
 
-/* Queue a request; FE_ERR_BUDGET if it could never fit. Thread-safe. */
+/* Queue a request; FE_ERR_BUDGET if its outputs could never fit. Thread-safe. */
 fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket);
-/* FE_NOT_READY while running; FE_OK with res filled when done. Thread-safe. */
+/* FE_NOT_READY while waiting or running; FE_OK with res filled when done.
+   Thread-safe. */
 fe_status fe_serve_poll(fe_ctx *ctx, uint64_t ticket, fe_result *res);
-/* Free a finished request's outputs and return its bytes to the budget. */
+/* Free a finished request's outputs and return their bytes to the budget. */
 fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket);
 
 /* Number of kernels this library has launched in this process (graph replays

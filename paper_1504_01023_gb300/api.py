@@ -225,6 +225,20 @@ def integrate_tet_noalloc(coords, coefs, kind, quad, coef_mode, layout, out_layo
     return out
 
 
+class _DeviceArray:
+    """__cuda_array_interface__ view of a device pointer owned by the library."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape), "typestr": typestr,
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr, shape, dtype, device=0):
+    """Zero-copy torch view of library-owned device memory (e.g. served outputs)."""
+    typestr = {torch.float32: "<f4", torch.float64: "<f8", torch.uint8: "|u1"}[dtype]
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=f"cuda:{device}")
+
+
 class Context:
     """One library context on one CUDA device."""
 
@@ -330,8 +344,16 @@ class Context:
         req = Request(mesh_id, kind, quad, coef_mode, coefs.data_ptr(), prec)
         t = ctypes.c_uint64()
         _check(load().fe_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t)), self.h)
-        self._keep[t.value] = coefs
+        self._keep[t.value] = (coefs, prec)
         return t.value
+
+    def serve_result_tensors(self, ticket, res):
+        """(A [n,NS,NS], b [n,NS], flags [n]) views of a finished request's outputs."""
+        prec = self._keep[ticket][1]
+        dt = torch.float64 if prec == FP64 else torch.float32
+        ns, n = NS[res.type], res.n_elem
+        return (device_view(res.A, (n, ns, ns), dt, self.device), device_view(res.b, (n, ns), dt, self.device),
+                device_view(res.flags, (n,), torch.uint8, self.device))
 
     def serve_poll(self, ticket):
         """None while running, else the Result structure."""

@@ -1,18 +1,432 @@
-// Batched integration (persistent kernel, captured graph) and resident meshes.
+// Resident meshes and batched integration (host side): tile plans, the
+// autotuner of the batched launch, and CUDA-graph capture of
+// {counter reset, persistent kernel, fix-up kernel}.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <functional>
+#include <list>
+#include <string>
+
 #include "fe_runtime.h"
 
 namespace fe {
-struct BatchCache {};
-void batch_destroy(fe_ctx *ctx) { (void)ctx; }
+
+// ---------------------------------------------------------------------------
+// Element-contiguous copy of plane-major coordinates (resident meshes).
+// ---------------------------------------------------------------------------
+__global__ void soa_to_aos_kernel(const double *__restrict__ in, int64_t stride, int nx, int64_t n,
+                                  double *__restrict__ out) {
+    const int64_t total = n * nx;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t e = i / nx;
+        const int j = int(i - e * nx);
+        out[i] = in[j * stride + e];
+    }
+}
+
+struct BatchPlan {
+    size_t key = 0;
+    std::vector<unsigned char> items_bytes;
+    BatchItemDev *d_items = nullptr;
+    BatchTile *d_tiles = nullptr;
+    unsigned n_items = 0, n_tiles = 0;
+    unsigned *d_counter = nullptr;
+    Scratch scratch;
+    int block = 128;
+    int grid = 0;
+    int64_t smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct BatchCache {
+    std::list<BatchPlan *> plans;  // most recent first
+    cudaStream_t capture_stream = nullptr;
+};
+
+static void free_plan(BatchPlan *pl) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->d_items) cudaFree(pl->d_items);
+    if (pl->d_tiles) cudaFree(pl->d_tiles);
+    if (pl->d_counter) cudaFree(pl->d_counter);
+    free_scratch(pl->scratch);
+    delete pl;
+}
+
+void batch_destroy(fe_ctx *ctx) {
+    if (!ctx->batch) return;
+    for (auto *pl : ctx->batch->plans) free_plan(pl);
+    if (ctx->batch->capture_stream) cudaStreamDestroy(ctx->batch->capture_stream);
+    delete ctx->batch;
+    ctx->batch = nullptr;
+}
+
+// Relative cost of one element of a combination (bytes moved plus arithmetic),
+// used only to order tiles longest-first.
+static double combo_cost(int combo) {
+    static const double cost[12] = {1.0, 1.0, 1.1, 1.2, 1.4, 1.5, 1.5, 1.8, 2.5, 2.6, 6.0, 8.0};
+    return combo >= 0 && combo < 12 ? cost[combo] : 1.0;
+}
+
+static std::vector<BatchTile> make_tiles(const std::vector<BatchItemDev> &items, int B) {
+    std::vector<std::pair<double, BatchTile>> t;
+    for (unsigned i = 0; i < items.size(); ++i) {
+        const int64_t n = items[i].p.n;
+        for (int64_t e0 = 0; e0 < n; e0 += B) {
+            BatchTile tl;
+            tl.item = i;
+            tl.first = e0;
+            tl.count = unsigned(std::min<int64_t>(B, n - e0));
+            t.push_back({combo_cost(items[i].combo) * tl.count, tl});
+        }
+    }
+    std::stable_sort(t.begin(), t.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<BatchTile> out;
+    out.reserve(t.size());
+    for (auto &x : t) out.push_back(x.second);
+    return out;
+}
+
+static fe_status upload_tiles(fe_ctx *ctx, BatchPlan *pl, const std::vector<BatchItemDev> &items, int B) {
+    std::vector<BatchTile> tiles = make_tiles(items, B);
+    if (pl->d_tiles) cudaFree(pl->d_tiles);
+    pl->d_tiles = nullptr;
+    pl->n_tiles = unsigned(tiles.size());
+    fe_status st = cuda_check(ctx, cudaMalloc(&pl->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(BatchTile)),
+                              "cudaMalloc(tiles)");
+    if (st != FE_OK) return st;
+    st = cuda_check(ctx, cudaMemcpy(pl->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice),
+                    "cudaMemcpy(tiles)");
+    if (st != FE_OK) return st;
+    int64_t smem = 0;
+    for (auto &it : items) smem = std::max<int64_t>(smem, batch_smem_bytes(it.combo, B));
+    pl->smem = smem;
+    pl->block = B;
+    st = cuda_check(ctx, cudaFuncSetAttribute(kernel_batch(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                    "cudaFuncSetAttribute(batch)");
+    if (st != FE_OK) return st;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_batch(), B, size_t(smem));
+    pl->grid = std::max(1, per_sm) * ctx->sms;
+    return FE_OK;
+}
+
+// Enqueue {counter reset, batch kernel, fix-up kernel} on a stream.
+static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch.fix_count, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemsetAsync(batch)");
+    int *status = ctx->scratch.status;
+    void *args[] = {&pl->d_items, &pl->n_items, &pl->d_tiles, &pl->n_tiles, &pl->d_counter, &status};
+    e = cudaLaunchKernel(kernel_batch(), dim3(pl->grid), dim3(pl->block), args, size_t(pl->smem), st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
+    unsigned long long *list = pl->scratch.fix_list;
+    unsigned *count = pl->scratch.fix_count;
+    unsigned cap = pl->scratch.fix_cap;
+    void *fargs[] = {&pl->d_items, &pl->n_items, &list, &count, &cap, &status};
+    e = cudaLaunchKernel(kernel_batch_fixup(), dim3(ctx->sms * 4), dim3(256), fargs, 0, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch fix-up)");
+    return FE_OK;
+}
+
+static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size_t key, BatchPlan *&out) {
+    auto *pl = new BatchPlan();
+    pl->key = key;
+    pl->items_bytes.assign(reinterpret_cast<const unsigned char *>(items),
+                           reinterpret_cast<const unsigned char *>(items) + sizeof(fe_batch_item) * n);
+    std::vector<BatchItemDev> dev(n);
+    uint64_t total = 0;
+    for (int i = 0; i < n; ++i) total += uint64_t(items[i].args.n_elem);
+    fe_status st = ensure_scratch(ctx, pl->scratch, total);
+    if (st == FE_OK) st = cuda_check(ctx, cudaMalloc(&pl->d_counter, 256), "cudaMalloc(counter)");
+    for (int i = 0; i < n && st == FE_OK; ++i) {
+        const fe_elem_args &a = items[i].args;
+        const fe_out &o = items[i].out;
+        BatchItemDev &d = dev[i];
+        memset(&d, 0, sizeof d);
+        d.p.n = a.n_elem;
+        d.p.X = a.coords;
+        d.p.xs = a.n_elem;
+        d.p.C = a.coefs;
+        d.p.cs = a.n_elem;
+        d.p.A = o.A;
+        d.p.B = o.b;
+        d.p.os = a.n_elem;
+        d.p.flags = o.flags;
+        d.p.fix_list = pl->scratch.fix_list;
+        d.p.fix_count = pl->scratch.fix_count;
+        d.p.fix_cap = pl->scratch.fix_cap;
+        d.p.item = unsigned(i);
+        d.p.status = ctx->scratch.status;
+        d.combo = batch_combo(items[i].type, a.kind, a.quad, a.coef_mode == FE_COEF_PER_QPOINT);
+    }
+    if (st == FE_OK) {
+        pl->n_items = unsigned(n);
+        st = cuda_check(ctx, cudaMalloc(&pl->d_items, sizeof(BatchItemDev) * n), "cudaMalloc(items)");
+    }
+    if (st == FE_OK)
+        st = cuda_check(ctx, cudaMemcpy(pl->d_items, dev.data(), sizeof(BatchItemDev) * n, cudaMemcpyHostToDevice),
+                        "cudaMemcpy(items)");
+    if (!ctx->batch->capture_stream) cudaStreamCreateWithFlags(&ctx->batch->capture_stream, cudaStreamNonBlocking);
+    cudaStream_t cs = ctx->batch->capture_stream;
+    // launch shape: the tuned elements per tile for this plan, or 128
+    int bestB = 128;
+    if (st == FE_OK && ctx->autotune) {
+        float best = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int B : {64, 128, 256}) {
+            st = upload_tiles(ctx, pl, dev, B);
+            if (st != FE_OK) break;
+            if (pl->smem + 1024 > ctx->max_smem_optin) continue;
+            st = enqueue_batch(ctx, pl, cs);  // warm-up
+            cudaEventRecord(e0, cs);
+            for (int r = 0; r < 3 && st == FE_OK; ++r) st = enqueue_batch(ctx, pl, cs);
+            cudaEventRecord(e1, cs);
+            if (st != FE_OK) break;
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) {
+                st = cuda_check(ctx, ce, "batch tuning");
+                break;
+            }
+            float t;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t < best) {
+                best = t;
+                bestB = B;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (st == FE_OK) st = upload_tiles(ctx, pl, dev, bestB);
+    if (st == FE_OK && pl->smem + 1024 > ctx->max_smem_optin)
+        st = set_error(ctx, FE_ERR_UNSUPPORTED, "batched tile does not fit in shared memory");
+    // capture the launch sequence once; later submissions replay it
+    if (st == FE_OK) {
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = cuda_check(ctx, e, "cudaStreamBeginCapture");
+        if (st == FE_OK) {
+            fe_status est = enqueue_batch(ctx, pl, cs);
+            e = cudaStreamEndCapture(cs, &pl->graph);
+            if (est != FE_OK) st = est;
+            else if (e != cudaSuccess) st = cuda_check(ctx, e, "cudaStreamEndCapture");
+        }
+        if (st == FE_OK) st = cuda_check(ctx, cudaGraphInstantiate(&pl->exec, pl->graph, 0), "cudaGraphInstantiate");
+    }
+    if (st != FE_OK) {
+        free_plan(pl);
+        return st;
+    }
+    out = pl;
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Dynamically built batch (serving).
+// ---------------------------------------------------------------------------
+void dyn_batch_free(DynBatch &db) {
+    if (db.d_items) cudaFree(db.d_items);
+    if (db.d_tiles) cudaFree(db.d_tiles);
+    if (db.h_items) cudaFreeHost(db.h_items);
+    if (db.h_tiles) cudaFreeHost(db.h_tiles);
+    if (db.d_counter) cudaFree(db.d_counter);
+    free_scratch(db.scratch);
+    db = DynBatch{};
+}
+
+static fe_status grow(fe_ctx *ctx, void **d, void **h, size_t &cap, size_t need, size_t elem) {
+    if (need <= cap) return FE_OK;
+    size_t c = std::max<size_t>(need, cap * 2);
+    if (*d) cudaFree(*d);
+    if (*h) cudaFreeHost(*h);
+    *d = *h = nullptr;
+    cap = 0;
+    fe_status st = cuda_check(ctx, cudaMalloc(d, c * elem), "cudaMalloc(batch table)");
+    if (st == FE_OK) st = cuda_check(ctx, cudaMallocHost(h, c * elem), "cudaMallocHost(batch table)");
+    if (st == FE_OK) cap = c;
+    return st;
+}
+
+// The caller guarantees that the previous launch on this DynBatch has finished
+// (its pinned staging and device tables are reused).
+fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> &items, cudaStream_t st) {
+    const int B = 128;
+    uint64_t total = 0;
+    for (auto &it : items) total += uint64_t(it.p.n);
+    fe_status r = ensure_scratch(ctx, db.scratch, total);
+    if (r != FE_OK) return r;
+    if (!db.d_counter) {
+        r = cuda_check(ctx, cudaMalloc(&db.d_counter, 256), "cudaMalloc(counter)");
+        if (r != FE_OK) return r;
+    }
+    for (auto &it : items) {
+        it.p.fix_list = db.scratch.fix_list;
+        it.p.fix_count = db.scratch.fix_count;
+        it.p.fix_cap = db.scratch.fix_cap;
+        it.p.status = ctx->scratch.status;
+    }
+    std::vector<BatchTile> tiles = make_tiles(items, B);
+    r = grow(ctx, reinterpret_cast<void **>(&db.d_items), reinterpret_cast<void **>(&db.h_items), db.cap_items,
+             items.size(), sizeof(BatchItemDev));
+    if (r == FE_OK)
+        r = grow(ctx, reinterpret_cast<void **>(&db.d_tiles), reinterpret_cast<void **>(&db.h_tiles), db.cap_tiles,
+                 std::max<size_t>(tiles.size(), 1), sizeof(BatchTile));
+    if (r != FE_OK) return r;
+    memcpy(db.h_items, items.data(), items.size() * sizeof(BatchItemDev));
+    memcpy(db.h_tiles, tiles.data(), tiles.size() * sizeof(BatchTile));
+    cudaError_t e = cudaMemcpyAsync(db.d_items, db.h_items, items.size() * sizeof(BatchItemDev), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(db.d_tiles, db.h_tiles, tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemcpyAsync(batch tables)");
+    BatchPlan pl;
+    pl.d_items = db.d_items;
+    pl.d_tiles = db.d_tiles;
+    pl.n_items = unsigned(items.size());
+    pl.n_tiles = unsigned(tiles.size());
+    pl.d_counter = db.d_counter;
+    pl.scratch = db.scratch;
+    pl.block = B;
+    int64_t smem = 0;
+    for (auto &it : items) smem = std::max<int64_t>(smem, batch_smem_bytes(it.combo, B));
+    pl.smem = smem;
+    static std::mutex mu;
+    static int64_t attr_set = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > attr_set) {
+            r = cuda_check(ctx, cudaFuncSetAttribute(kernel_batch(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                           "cudaFuncSetAttribute(batch)");
+            if (r != FE_OK) return r;
+            attr_set = smem;
+        }
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_batch(), B, size_t(smem));
+    pl.grid = int(std::min<int64_t>(int64_t(std::max(1, per_sm)) * ctx->sms, std::max<int64_t>(1, tiles.size())));
+    r = enqueue_batch(ctx, &pl, st);
+    // the plan only borrowed the tables
+    pl.d_items = nullptr;
+    pl.d_tiles = nullptr;
+    pl.d_counter = nullptr;
+    pl.scratch = Scratch{};
+    if (r == FE_OK) g_launches.fetch_add(2);
+    return r;
+}
+
 }  // namespace fe
 
 using namespace fe;
+
 extern "C" {
-fe_status fe_mesh_register(fe_ctx *ctx, fe_elem_type, int64_t, const double *, fe_layout, fe_memory, int64_t *) {
-    return set_error(ctx, FE_ERR_UNSUPPORTED, "not built yet");
+
+fe_status fe_mesh_register(fe_ctx *ctx, fe_elem_type type, int64_t n_elem, const double *coords, fe_layout layout,
+                           fe_memory memory, int64_t *mesh_id) {
+    if (!ctx || !mesh_id) return set_error(ctx, FE_ERR_INVALID_ARG, "null argument");
+    if ((type != FE_TET && type != FE_PRISM) || n_elem <= 0 || !coords)
+        return set_error(ctx, FE_ERR_INVALID_ARG, "bad mesh description");
+    if ((layout != FE_LAYOUT_SOA && layout != FE_LAYOUT_AOS) || (memory != FE_MEM_DEVICE && memory != FE_MEM_HOST))
+        return set_error(ctx, FE_ERR_INVALID_ARG, "bad layout or memory kind");
+    cudaSetDevice(ctx->device);
+    const int nx = 3 * ns_of(type);
+    const uint64_t bytes = uint64_t(n_elem) * nx * 8;
+    if (ctx->hbm_used.load() + bytes > ctx->hbm_budget)
+        return set_error(ctx, FE_ERR_BUDGET, "resident mesh does not fit the HBM budget");
+    double *d = nullptr;
+    fe_status st = cuda_check(ctx, cudaMalloc(&d, bytes), "cudaMalloc(mesh)");
+    if (st != FE_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (layout == FE_LAYOUT_AOS) {
+        e = cudaMemcpy(d, coords, bytes, memory == FE_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
+    } else {
+        const double *src = coords;
+        double *tmp = nullptr;
+        if (memory == FE_MEM_HOST) {
+            e = cudaMalloc(&tmp, bytes);
+            if (e == cudaSuccess) e = cudaMemcpy(tmp, coords, bytes, cudaMemcpyHostToDevice);
+            src = tmp;
+        }
+        if (e == cudaSuccess) {
+            const int64_t total = n_elem * nx;
+            const int grid = int(std::min<int64_t>((total + 255) / 256, int64_t(ctx->sms) * 8));
+            soa_to_aos_kernel<<<grid, 256>>>(src, n_elem, nx, n_elem, d);
+            g_launches.fetch_add(1);
+            e = cudaDeviceSynchronize();
+        }
+        if (tmp) cudaFree(tmp);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_check(ctx, e, "mesh upload");
+    }
+    std::lock_guard<std::mutex> lk(ctx->mesh_mu);
+    const int64_t id = ctx->next_mesh++;
+    ctx->meshes[id] = MeshRec{type, n_elem, d, bytes};
+    ctx->hbm_used += bytes;
+    *mesh_id = id;
+    return FE_OK;
 }
-fe_status fe_mesh_release(fe_ctx *ctx, int64_t) { return set_error(ctx, FE_ERR_UNSUPPORTED, "not built yet"); }
-fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *, int, void *) {
-    return set_error(ctx, FE_ERR_UNSUPPORTED, "not built yet");
+
+fe_status fe_mesh_release(fe_ctx *ctx, int64_t mesh_id) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    std::lock_guard<std::mutex> lk(ctx->mesh_mu);
+    auto it = ctx->meshes.find(mesh_id);
+    if (it == ctx->meshes.end()) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown mesh id");
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(it->second.coords);
+    ctx->hbm_used -= it->second.bytes;
+    ctx->meshes.erase(it);
+    return FE_OK;
 }
+
+fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, void *stream) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    if (!items || n_items <= 0) return set_error(ctx, FE_ERR_INVALID_ARG, "empty batch");
+    if (n_items > (1 << 23)) return set_error(ctx, FE_ERR_INVALID_ARG, "too many batch items");
+    for (int i = 0; i < n_items; ++i) {
+        const fe_batch_item &it = items[i];
+        fe_status st = fe_check_args(it.type, &it.args, &it.out);
+        if (st != FE_OK) return set_error(ctx, st, "batch item " + std::to_string(i) + ": " + fe_last_error(nullptr));
+        if (it.args.prec != FE_FP32_MIXED || it.args.memory != FE_MEM_DEVICE || it.out.memory != FE_MEM_DEVICE ||
+            it.args.coords_layout != FE_LAYOUT_AOS || it.out.layout != FE_LAYOUT_AOS)
+            return set_error(ctx, FE_ERR_UNSUPPORTED,
+                             "batch items must be FE_FP32_MIXED, device memory, element-contiguous (AOS) in and out");
+        if (it.args.n_elem >= (int64_t(1) << 40)) return set_error(ctx, FE_ERR_INVALID_ARG, "batch item too large");
+    }
+    cudaSetDevice(ctx->device);
+    if (!ctx->batch) ctx->batch = new BatchCache();
+    const size_t key = std::hash<std::string>()(
+        std::string(reinterpret_cast<const char *>(items), sizeof(fe_batch_item) * size_t(n_items)));
+    BatchPlan *pl = nullptr;
+    for (auto it = ctx->batch->plans.begin(); it != ctx->batch->plans.end(); ++it) {
+        if ((*it)->key == key && (*it)->items_bytes.size() == sizeof(fe_batch_item) * size_t(n_items) &&
+            memcmp((*it)->items_bytes.data(), items, (*it)->items_bytes.size()) == 0) {
+            pl = *it;
+            ctx->batch->plans.erase(it);
+            ctx->batch->plans.push_front(pl);
+            break;
+        }
+    }
+    if (!pl) {
+        fe_status st = build_plan(ctx, items, n_items, key, pl);
+        if (st != FE_OK) return st;
+        ctx->batch->plans.push_front(pl);
+        while (ctx->batch->plans.size() > 8) {
+            cudaDeviceSynchronize();
+            free_plan(ctx->batch->plans.back());
+            ctx->batch->plans.pop_back();
+        }
+    }
+    cudaError_t e = cudaGraphLaunch(pl->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaGraphLaunch(batch)");
+    g_launches.fetch_add(2);
+    return FE_OK;
 }
+
+}  // extern "C"

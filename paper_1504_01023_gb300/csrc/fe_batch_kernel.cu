@@ -1,0 +1,147 @@
+// Batched persistent kernel: many element sets of uneven size and mixed
+// type/kind in one launch. Each block repeatedly takes the next tile from a
+// global counter (tiles are ordered by decreasing cost on the host) and runs
+// the same tile code as the single-set kernels; nothing waits on another block.
+#include "fe_kernels.cuh"
+
+namespace fe {
+
+template <int COMBO> struct ComboCfg;
+#define FE_COMBO(ID, ET, KD, Q, CP)                                    \
+    template <> struct ComboCfg<ID> {                                  \
+        static constexpr int et = ET, kind = KD, quad = Q, cpq = CP;   \
+    };
+FE_COMBO(0, TET, POISSON, Q_TET1, 0)
+FE_COMBO(1, TET, POISSON, Q_TET1, 1)
+FE_COMBO(2, TET, POISSON, Q_TET4, 0)
+FE_COMBO(3, TET, POISSON, Q_TET4, 1)
+FE_COMBO(4, TET, GENERIC, Q_TET1, 0)
+FE_COMBO(5, TET, GENERIC, Q_TET1, 1)
+FE_COMBO(6, TET, GENERIC, Q_TET4, 0)
+FE_COMBO(7, TET, GENERIC, Q_TET4, 1)
+FE_COMBO(8, PRISM, POISSON, Q_PRISM6, 0)
+FE_COMBO(9, PRISM, POISSON, Q_PRISM6, 1)
+FE_COMBO(10, PRISM, GENERIC, Q_PRISM6, 0)
+FE_COMBO(11, PRISM, GENERIC, Q_PRISM6, 1)
+#undef FE_COMBO
+
+template <int ID>
+__device__ __forceinline__ bool tile_combo(const ElemParams &p, int64_t e0, int nb, unsigned char *smem, uint64_t *bar,
+                                           unsigned &phase) {
+    using K = ComboCfg<ID>;
+    return process_tile<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, e0, nb, smem, bar, phase);
+}
+
+template <int ID> __device__ __forceinline__ void fix_combo(const ElemParams &p, int64_t e) {
+    using K = ComboCfg<ID>;
+    fixup_element<K::et, K::kind, K::quad, K::cpq, AOS, AOS>(p, e);
+}
+
+__global__ void __launch_bounds__(256) batch_kernel(const BatchItemDev *__restrict__ items, unsigned n_items,
+                                                    const BatchTile *__restrict__ tiles, unsigned n_tiles,
+                                                    unsigned *tile_counter, int *status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ unsigned s_tile;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const unsigned t = s_tile;
+        __syncthreads();
+        if (t >= n_tiles) break;
+        const BatchTile tl = tiles[t];
+        if (tl.item >= n_items || tl.count > blockDim.x) {
+            if (threadIdx.x == 0) atomicOr(status, ST_BAD_TILE);
+            continue;
+        }
+        const ElemParams p = items[tl.item].p;
+        const int combo = items[tl.item].combo;
+        bool ok = true;
+        switch (combo) {
+            case 0: ok = tile_combo<0>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 1: ok = tile_combo<1>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 2: ok = tile_combo<2>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 3: ok = tile_combo<3>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 4: ok = tile_combo<4>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 5: ok = tile_combo<5>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 6: ok = tile_combo<6>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 7: ok = tile_combo<7>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 8: ok = tile_combo<8>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 9: ok = tile_combo<9>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 10: ok = tile_combo<10>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            case 11: ok = tile_combo<11>(p, tl.first, int(tl.count), smem, &bar, phase); break;
+            default:
+                if (threadIdx.x == 0) atomicOr(status, ST_BAD_TILE);
+                break;
+        }
+        if (!ok) return;
+    }
+    if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Fix-up of every flagged element of the batch (list entries: item << 40 | element).
+__global__ void __launch_bounds__(256) batch_fixup_kernel(const BatchItemDev *__restrict__ items, unsigned n_items,
+                                                          const unsigned long long *__restrict__ list,
+                                                          const unsigned *count, unsigned cap, int *status) {
+    const unsigned c = *count;
+    const unsigned n = c < cap ? c : cap;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long ent = list[i];
+        const unsigned item = static_cast<unsigned>(ent >> 40);
+        const int64_t e = static_cast<int64_t>(ent & ((1ull << 40) - 1));
+        if (item >= n_items || e >= items[item].p.n) {
+            atomicOr(status, ST_BAD_TILE);
+            continue;
+        }
+        const ElemParams p = items[item].p;
+        switch (items[item].combo) {
+            case 0: fix_combo<0>(p, e); break;
+            case 1: fix_combo<1>(p, e); break;
+            case 2: fix_combo<2>(p, e); break;
+            case 3: fix_combo<3>(p, e); break;
+            case 4: fix_combo<4>(p, e); break;
+            case 5: fix_combo<5>(p, e); break;
+            case 6: fix_combo<6>(p, e); break;
+            case 7: fix_combo<7>(p, e); break;
+            case 8: fix_combo<8>(p, e); break;
+            case 9: fix_combo<9>(p, e); break;
+            case 10: fix_combo<10>(p, e); break;
+            case 11: fix_combo<11>(p, e); break;
+            default: atomicOr(status, ST_BAD_TILE); break;
+        }
+    }
+}
+
+template <int ID> static long long smem_of(int B) {
+    using K = ComboCfg<ID>;
+    return BlockSmem<K::et, K::kind, MIXED, K::quad, K::cpq>::total(B);
+}
+
+long long batch_smem_bytes(int combo, int B) {
+    switch (combo) {
+        case 0: return smem_of<0>(B);
+        case 1: return smem_of<1>(B);
+        case 2: return smem_of<2>(B);
+        case 3: return smem_of<3>(B);
+        case 4: return smem_of<4>(B);
+        case 5: return smem_of<5>(B);
+        case 6: return smem_of<6>(B);
+        case 7: return smem_of<7>(B);
+        case 8: return smem_of<8>(B);
+        case 9: return smem_of<9>(B);
+        case 10: return smem_of<10>(B);
+        case 11: return smem_of<11>(B);
+    }
+    return -1;
+}
+
+const void *kernel_batch() { return reinterpret_cast<const void *>(&batch_kernel); }
+const void *kernel_batch_fixup() { return reinterpret_cast<const void *>(&batch_fixup_kernel); }
+
+}  // namespace fe

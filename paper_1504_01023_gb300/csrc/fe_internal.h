@@ -53,18 +53,28 @@ const void *kernel_prism_mixed(int kind, int cpq, int inl, int outl);
 const void *kernel_fixup_tet(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_fixup_prism(int kind, int cpq, int inl, int outl);
 
-// Batched persistent kernel (see fe_batch.cu).
+// Batched persistent kernel (fe_batch.cu): one descriptor per element set and
+// one per tile of consecutive elements of a set.
+struct BatchItemDev {
+    ElemParams p;             // element-contiguous inputs and outputs, mixed precision
+    int combo;                // (type, kind, rule, coefficient mode), see batch_combo()
+    int pad;
+};
 struct BatchTile {
     unsigned int item;        // index into the item table
     unsigned int count;       // elements in this tile
     long long first;          // first element of the tile within the item
 };
-struct BatchItem {
-    ElemParams p;             // SOA inputs/outputs, mixed precision
-    int type, kind, quad, cpq;
-};
+// Dense index of the 12 (type, kind, rule, coefficient mode) combinations of the
+// batched kernel, or -1.
+inline int batch_combo(int type, int kind, int quad, int cpq) {
+    if (type == TET && (quad == Q_TET1 || quad == Q_TET4)) return ((kind * 2 + (quad == Q_TET4)) * 2 + cpq);
+    if (type == PRISM && quad == Q_PRISM6) return 8 + kind * 2 + cpq;
+    return -1;
+}
 const void *kernel_batch();
 const void *kernel_batch_fixup();
-int batch_tile_elems();       // elements per tile (= threads per block)
+// Dynamic shared memory of one block of the batched kernel for a combination.
+long long batch_smem_bytes(int combo, int block);
 
 }  // namespace fe

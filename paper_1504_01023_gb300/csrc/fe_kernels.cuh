@@ -347,167 +347,183 @@ __device__ __forceinline__ void stage_rows_out(T *g, int64_t gpitch, const T *s,
 }
 
 // ---------------------------------------------------------------------------
-// Main kernel: tiles of blockDim.x elements, grid-stride over tiles. Each tile's
-// inputs are staged into shared memory by bulk copies (cp.async.bulk, completion
-// on an mbarrier), computed one element per thread, and written back by bulk
-// copies from shared memory.
+// One tile of nb <= blockDim.x elements starting at e0, for every thread of the
+// block: inputs staged into shared memory by bulk copies (cp.async.bulk,
+// completion on the block's mbarrier), computed one element per thread, written
+// back by bulk copies from shared memory. Returns false (for the whole block) if
+// a bounded wait on a copy ran out; the caller must then stop.
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
-__global__ void __launch_bounds__(ET == TET ? 512 : 256)
-    elem_kernel(const ElemParams p) {
+__device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, int nb, unsigned char *smem, uint64_t *bar,
+                                             unsigned &phase) {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
     using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ>;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar;
-
     const int B = blockDim.x;
     const int tid = threadIdx.x;
     double *sX = reinterpret_cast<double *>(smem);
     CT *sC = reinterpret_cast<CT *>(smem + SM::x_bytes(B));
     CT *sA = reinterpret_cast<CT *>(smem + SM::x_bytes(B) + SM::c_bytes(B));
     CT *sB = reinterpret_cast<CT *>(smem + SM::x_bytes(B) + SM::c_bytes(B) + SM::a_bytes(B));
-    if (tid == 0) {
+    const double *X = p.X;
+    const CT *C = static_cast<const CT *>(p.C);
+    CT *Aout = static_cast<CT *>(p.A);
+    CT *Bout = static_cast<CT *>(p.B);
+    const int64_t e = e0 + tid;
+    const bool active = tid < nb;
+
+    // ---- stage inputs ----
+    {
+        // alignment of bases and SOA plane pitches, then of this tile's byte counts
+        const bool x_ok = aligned16(X, INL == SOA ? uint64_t(p.xs) * 8 : 0);
+        const bool c_ok = aligned16(C, INL == SOA ? uint64_t(p.cs) * sizeof(CT) : 0);
+        const bool tX = x_ok && ((uint64_t(nb) * (INL == SOA ? 8 : NX * 8)) % 16 == 0);
+        const bool tC = c_ok && ((uint64_t(nb) * (INL == SOA ? 1 : NC) * sizeof(CT)) % 16 == 0);
+        const unsigned tx = (tX ? unsigned(nb) * NX * 8u : 0u) + (tC ? unsigned(nb) * NC * unsigned(sizeof(CT)) : 0u);
+        if (tid == 0 && tx) {
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, tx);
+        }
+        if (tx) __syncwarp();
+        if (INL == SOA) {
+            stage_rows_in(sX, B, X + e0, p.xs, NX, nb, tX, bar);
+            stage_rows_in(sC, B, C + e0, p.cs, NC, nb, tC, bar);
+        } else {
+            stage_rows_in(sX, 0, X + e0 * NX, 0, 1, nb * NX, tX, bar);
+            stage_rows_in(sC, 0, C + e0 * NC, 0, 1, nb * NC, tC, bar);
+        }
+        bool ok = true;
+        if (tx) {
+            ok = mbar_wait_bounded(bar, phase, p.status);
+            phase ^= 1u;
+        }
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land: wait once more (bounded) so nothing is in flight
+            if (tx) mbar_wait_bounded(bar, phase ^ 1u, nullptr);
+            return false;
+        }
+    }
+
+    // ---- compute ----
+    CT A[NA], b[NS];
+    bool poor = false;
+    if (active) {
+        const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
+        const SmemSrc<CT> cs{INL == SOA ? sC + tid : sC + tid * NC, INL == SOA ? B : 1};
+        uint8_t fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
+        if (PREC == MIXED && poor) fl |= 1;
+        if (p.flags) p.flags[e] = fl;
+        if (OUTL == SOA) {
+#pragma unroll
+            for (int k = 0; k < NA; ++k) sA[k * B + tid] = A[k];
+#pragma unroll
+            for (int k = 0; k < NS; ++k) sB[k * B + tid] = b[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < NA; ++k) sA[tid * NA + k] = A[k];
+#pragma unroll
+            for (int k = 0; k < NS; ++k) sB[tid * NS + k] = b[k];
+        }
+    }
+    if (PREC == MIXED) append_fixup(p, active && poor, e);
+
+    // ---- store outputs ----
+    fence_proxy_async_smem();
+    __syncthreads();
+    {
+        const bool a_ok = aligned16(Aout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
+        const bool b_ok = aligned16(Bout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
+        const bool tA = a_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NA) * sizeof(CT)) % 16 == 0);
+        const bool tB = b_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NS) * sizeof(CT)) % 16 == 0);
+        if (OUTL == SOA) {
+            stage_rows_out(Aout + e0, p.os, sA, B, NA, nb, tA);
+            stage_rows_out(Bout + e0, p.os, sB, B, NS, nb, tB);
+        } else {
+            stage_rows_out(Aout + e0 * NA, 0, sA, 0, 1, nb * NA, tA);
+            stage_rows_out(Bout + e0 * NS, 0, sB, 0, 1, nb * NS, tB);
+        }
+        if ((tA || tB) && tid < 32) {
+            bulk_commit();
+            bulk_wait_read0();
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Main kernel: tiles of blockDim.x elements, grid-stride over tiles.
+// ---------------------------------------------------------------------------
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
+__global__ void __launch_bounds__(ET == TET ? 512 : 256)
+    elem_kernel(const ElemParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     unsigned phase = 0;
-    const double *X = p.X;
-    const CT *C = static_cast<const CT *>(p.C);
-    CT *Aout = static_cast<CT *>(p.A);
-    CT *Bout = static_cast<CT *>(p.B);
-    // alignment that does not depend on the tile: bases, and SOA plane pitches
-    const bool x_ok = aligned16(X, INL == SOA ? uint64_t(p.xs) * 8 : 0);
-    const bool c_ok = aligned16(C, INL == SOA ? uint64_t(p.cs) * sizeof(CT) : 0);
-    const bool a_ok = aligned16(Aout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
-    const bool b_ok = aligned16(Bout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
+    const int B = blockDim.x;
     const int64_t ntiles = (p.n + B - 1) / B;
-
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
-        const int64_t e = e0 + tid;
-        const bool active = tid < nb;
-
-        // ---- stage inputs ----
-        {
-            const bool tX = x_ok && ((uint64_t(nb) * (INL == SOA ? 8 : NX * 8)) % 16 == 0);
-            const bool tC = c_ok && ((uint64_t(nb) * (INL == SOA ? 1 : NC) * sizeof(CT)) % 16 == 0);
-            const unsigned tx = (tX ? unsigned(nb) * NX * 8u : 0u) + (tC ? unsigned(nb) * NC * unsigned(sizeof(CT)) : 0u);
-            if (tid == 0 && tx) {
-                fence_proxy_async_smem();
-                mbar_expect_tx(&bar, tx);
-            }
-            if (tx) __syncwarp();
-            if (INL == SOA) {
-                stage_rows_in(sX, B, X + e0, p.xs, NX, nb, tX, &bar);
-                stage_rows_in(sC, B, C + e0, p.cs, NC, nb, tC, &bar);
-            } else {
-                stage_rows_in(sX, 0, X + e0 * NX, 0, 1, nb * NX, tX, &bar);
-                stage_rows_in(sC, 0, C + e0 * NC, 0, 1, nb * NC, tC, &bar);
-            }
-            bool ok = true;
-            if (tx) {
-                ok = mbar_wait_bounded(&bar, phase, p.status);
-                phase ^= 1u;
-            }
-            if (__syncthreads_or(!ok)) {
-                // a copy did not land: wait once more (bounded) so nothing is in flight, then stop
-                if (tx) mbar_wait_bounded(&bar, phase ^ 1u, nullptr);
-                return;
-            }
-        }
-
-        // ---- compute ----
-        CT A[NA], b[NS];
-        bool poor = false;
-        if (active) {
-            const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
-            const SmemSrc<CT> cs{INL == SOA ? sC + tid : sC + tid * NC, INL == SOA ? B : 1};
-            uint8_t fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
-            if (PREC == MIXED && poor) fl |= 1;
-            if (p.flags) p.flags[e] = fl;
-            if (OUTL == SOA) {
-#pragma unroll
-                for (int k = 0; k < NA; ++k) sA[k * B + tid] = A[k];
-#pragma unroll
-                for (int k = 0; k < NS; ++k) sB[k * B + tid] = b[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < NA; ++k) sA[tid * NA + k] = A[k];
-#pragma unroll
-                for (int k = 0; k < NS; ++k) sB[tid * NS + k] = b[k];
-            }
-        }
-        if (PREC == MIXED) append_fixup(p, active && poor, e);
-
-        // ---- store outputs ----
-        fence_proxy_async_smem();
-        __syncthreads();
-        {
-            const bool tA = a_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NA) * sizeof(CT)) % 16 == 0);
-            const bool tB = b_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NS) * sizeof(CT)) % 16 == 0);
-            if (OUTL == SOA) {
-                stage_rows_out(Aout + e0, p.os, sA, B, NA, nb, tA);
-                stage_rows_out(Bout + e0, p.os, sB, B, NS, nb, tB);
-            } else {
-                stage_rows_out(Aout + e0 * NA, 0, sA, 0, 1, nb * NA, tA);
-                stage_rows_out(Bout + e0 * NS, 0, sB, 0, 1, nb * NS, tB);
-            }
-            if ((tA || tB) && tid < 32) {
-                bulk_commit();
-                bulk_wait_read0();
-            }
-        }
-        __syncthreads();
+        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase)) return;
     }
-    if (tid < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
-// Fix-up kernel (mixed precision): flagged elements of one call, read straight
-// from global memory, Jacobian terms in double, results overwrite the float ones.
+// Fix-up of one flagged element (mixed precision): read straight from global
+// memory, Jacobian terms in double, results overwrite the float ones.
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int QUAD, int CPQ, int INL, int OUTL>
-__global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p) {
+__device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
     using CF = ElemCfg<ET, KIND, MIXED, QUAD, CPQ>;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
-    const unsigned cnt = *p.fix_count;
-    const unsigned n = cnt < p.fix_cap ? cnt : p.fix_cap;
     const float *C = static_cast<const float *>(p.C);
     float *Aout = static_cast<float *>(p.A);
     float *Bout = static_cast<float *>(p.B);
+    float A[NA], b[NS];
+    uint8_t fl;
+    if (INL == SOA) {
+        const Src<SOA, double> xs{p.X + e, p.xs};
+        const Src<SOA, float> cs{C + e, p.cs};
+        fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
+    } else {
+        const Src<AOS, double> xs{p.X + e * NX, 0};
+        const Src<AOS, float> cs{C + e * NC, 0};
+        fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
+    }
+    if (OUTL == SOA) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) Aout[k * p.os + e] = A[k];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) Bout[k * p.os + e] = b[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) Aout[e * NA + k] = A[k];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) Bout[e * NS + k] = b[k];
+    }
+    if (p.flags) p.flags[e] = fl;
+}
+
+// Fix-up kernel of one call: grid-stride over the list written by the main kernel.
+template <int ET, int KIND, int QUAD, int CPQ, int INL, int OUTL>
+__global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p) {
+    const unsigned cnt = *p.fix_count;
+    const unsigned n = cnt < p.fix_cap ? cnt : p.fix_cap;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int64_t e = static_cast<int64_t>(p.fix_list[i] & ((1ull << 40) - 1));
         if (e >= p.n) {
             atomicOr(p.status, ST_BAD_TILE);
             continue;
         }
-        float A[NA], b[NS];
-        uint8_t fl;
-        if (INL == SOA) {
-            const Src<SOA, double> xs{p.X + e, p.xs};
-            const Src<SOA, float> cs{C + e, p.cs};
-            fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
-        } else {
-            const Src<AOS, double> xs{p.X + e * NX, 0};
-            const Src<AOS, float> cs{C + e * NC, 0};
-            fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
-        }
-        if (OUTL == SOA) {
-#pragma unroll
-            for (int k = 0; k < NA; ++k) Aout[k * p.os + e] = A[k];
-#pragma unroll
-            for (int k = 0; k < NS; ++k) Bout[k * p.os + e] = b[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < NA; ++k) Aout[e * NA + k] = A[k];
-#pragma unroll
-            for (int k = 0; k < NS; ++k) Bout[e * NS + k] = b[k];
-        }
-        if (p.flags) p.flags[e] = fl;
+        fixup_element<ET, KIND, QUAD, CPQ, INL, OUTL>(p, e);
     }
 }
 

@@ -116,7 +116,7 @@ static std::string shape_key(fe_elem_type type, const fe_elem_args *a, const fe_
     return k.str();
 }
 
-static Shape default_shape(fe_elem_type type) { return Shape{type == FE_TET ? 256 : 128, 0}; }
+Shape default_shape(fe_elem_type type) { return Shape{type == FE_TET ? 256 : 128, 0}; }
 
 static int max_block(fe_elem_type type) { return type == FE_TET ? 512 : 256; }
 
@@ -188,7 +188,8 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
 
     void *args[] = {&p};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (ctx->profiling) {
+    const bool profile = ctx->profiling && !force;
+    if (profile) {
         ev0 = pool_event(ctx);
         ev1 = pool_event(ctx);
         cudaEventRecord(ev0, st);
@@ -204,7 +205,7 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
         return cuda_check(ctx, ce, m.str().c_str());
     }
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (ctx->profiling) {
+    if (profile) {
         cudaEventRecord(ev1, st);
         ctx->prof_events.emplace_back(ev0, ev1);
     }

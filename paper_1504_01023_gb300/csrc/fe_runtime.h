@@ -13,7 +13,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/fe.h"
+#include "fe.h"
 #include "fe_internal.h"
 
 namespace fe {
@@ -35,6 +35,8 @@ struct Shape {
 
 struct ServeState;          // fe_serve.cu
 struct BatchCache;          // fe_batch.cu
+struct BatchItemDev;
+struct BatchTile;
 
 struct MeshRec {
     fe_elem_type type;
@@ -90,8 +92,22 @@ fe_status cuda_check(fe_ctx *ctx, cudaError_t e, const char *what);
 fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n);
 void free_scratch(Scratch &s);
 // Launch main + fix-up kernels of one homogeneous set (device pointers).
+// With `force`, that launch shape is used and the context's tuned shapes and
+// profiling events are not touched (safe from the serving thread).
 fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, Scratch &s,
                      cudaStream_t st, const Shape *force = nullptr);
+Shape default_shape(fe_elem_type type);
+// Dynamically built batch (serving): device tables grown on demand, uploaded
+// from pinned staging with stream-ordered copies, launched without a graph.
+struct DynBatch {
+    BatchItemDev *d_items = nullptr, *h_items = nullptr;
+    BatchTile *d_tiles = nullptr, *h_tiles = nullptr;
+    size_t cap_items = 0, cap_tiles = 0;
+    unsigned *d_counter = nullptr;
+    Scratch scratch;
+};
+fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> &items, cudaStream_t st);
+void dyn_batch_free(DynBatch &db);
 int ns_of(fe_elem_type t);
 int nq_of(fe_quad q);
 int nc_of(const fe_elem_args *a);

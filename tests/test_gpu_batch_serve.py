@@ -1,0 +1,216 @@
+"""Batched and served integration through the C ABI: the persistent kernel and
+the serving loop must give each element set the results of its own call (and of
+the FP64 oracle), alone and in the mix."""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import ORACLE_RULE, TOL, make_inputs, max_errors
+from paper_1504_01023_gb300 import api, meshgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1504_01023_gb300 import build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+# (type, kind, quad, per-point coefficients, elements, sliver fraction)
+MIX = [
+    (api.TET, api.POISSON, api.QUAD_TET1, 0, 1, 0.0),
+    (api.TET, api.POISSON, api.QUAD_TET4, 1, 5000, 0.0),
+    (api.TET, api.GENERIC, api.QUAD_TET4, 0, 12345, 0.05),
+    (api.TET, api.GENERIC, api.QUAD_TET1, 1, 33, 0.0),
+    (api.TET, api.GENERIC, api.QUAD_TET4, 1, 2000, 0.1),
+    (api.PRISM, api.POISSON, api.QUAD_PRISM6, 0, 777, 0.0),
+    (api.PRISM, api.POISSON, api.QUAD_PRISM6, 1, 4096, 0.0),
+    (api.PRISM, api.GENERIC, api.QUAD_PRISM6, 0, 3001, 0.0),
+    (api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, 6000, 0.0),
+    (api.TET, api.GENERIC, api.QUAD_TET4, 0, 129, 0.0),
+]
+
+
+def _set(i, et, kind, quad, cpq, n, frac):
+    mesh = (meshgen.tet_cube_mesh(14, seed=40 + i) if et == api.TET else meshgen.prism_slab_mesh(60, seed=40 + i))[:n].copy()
+    if frac and et == api.TET:
+        meshgen.make_slivers(mesh, frac, seed=90 + i)
+    _, c = make_inputs(et, kind, quad, cpq, mesh=mesh, seed=60 + i)
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).cuda()
+    C = torch.from_numpy(np.ascontiguousarray(c.astype(np.float32).reshape(n, -1))).cuda()
+    return mesh, c.astype(np.float32).astype(np.float64), X, C
+
+
+@pytest.fixture(scope="module")
+def mix():
+    return [_set(i, *m) for i, m in enumerate(MIX)]
+
+
+def _items(mix, outs):
+    items = []
+    for (et, kind, quad, cpq, n, _), (mesh, c, X, C), out in zip(MIX, mix, outs):
+        a = api.make_args(et, X, C, kind, quad, api.PER_QPOINT if cpq else api.PER_ELEMENT, api.FP32_MIXED, api.AOS)
+        o = api.make_out(*out, api.AOS)
+        items.append((et, a, o))
+    return items
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_matches_single_calls_and_oracle(ctx, mix, autotune):
+    bctx = api.Context(0, autotune=autotune) if autotune else ctx
+    outs = [api.alloc_out(et, n, api.FP32_MIXED, api.AOS, "cuda") for (et, kind, quad, cpq, n, _) in MIX]
+    items = _items(mix, outs)
+    for rep in range(2):                       # first submission captures the graph, second replays it
+        for o in outs:
+            for t in o:
+                t.zero_()
+        bctx.batch_submit(items)
+        bctx.sync()
+        for (et, kind, quad, cpq, n, _), (mesh, c, X, C), out in zip(MIX, mix, outs):
+            ref = ctx.integrate(et, X, C, kind, quad, api.PER_QPOINT if cpq else api.PER_ELEMENT, api.FP32_MIXED,
+                                api.AOS, api.AOS)
+            ctx.sync()
+            An, bn, fn = (t.double().cpu().numpy() if t.dtype != torch.uint8 else t.cpu().numpy() for t in out)
+            Ar, br, fr = (t.double().cpu().numpy() if t.dtype != torch.uint8 else t.cpu().numpy() for t in ref)
+            assert np.array_equal(fn, fr)
+            assert oracle.rel_frobenius(An, Ar).max() <= 1e-6
+            assert oracle.rel_frobenius(bn, br).max() <= 1e-6
+            Ao, bo, _ = oracle.integrate(et, kind, ORACLE_RULE[quad], mesh, c, coef_per_q=bool(cpq), n_threads=8)
+            ea, eb = max_errors(An, bn, Ao, bo)
+            assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED], (et, kind, quad, cpq, ea, eb)
+    if autotune:
+        bctx.close()
+
+
+def test_batch_rejects_unsupported_items(ctx, mix):
+    (et, kind, quad, cpq, n, _), (mesh, c, X, C) = MIX[2], mix[2]
+    out = api.alloc_out(et, n, api.FP32_MIXED, api.SOA, "cuda")
+    a = api.make_args(et, X, C, kind, quad, api.PER_ELEMENT, api.FP32_MIXED, api.AOS)
+    o = api.make_out(*out, api.SOA)
+    with pytest.raises(api.FeError) as e:
+        ctx.batch_submit([(et, a, o)])
+    assert e.value.status == -6
+
+
+def _register(ctx, et, mesh, how):
+    if how == "aos-host":
+        return ctx.mesh_register(et, torch.from_numpy(np.ascontiguousarray(mesh)), api.AOS)
+    if how == "aos-dev":
+        return ctx.mesh_register(et, torch.from_numpy(np.ascontiguousarray(mesh)).cuda(), api.AOS)
+    if how == "soa-host":
+        return ctx.mesh_register(et, torch.from_numpy(meshgen.soa(mesh)), api.SOA)
+    return ctx.mesh_register(et, torch.from_numpy(meshgen.soa(mesh)).cuda(), api.SOA)
+
+
+def _wait(ctx, tk, timeout=30.0):
+    t0 = time.time()
+    while True:
+        r = ctx.serve_poll(tk)
+        if r is not None:
+            return r
+        assert time.time() - t0 < timeout, "request did not finish"
+        time.sleep(0.0005)
+
+
+def test_serve_alone_and_in_the_mix(ctx, mix):
+    hows = ["aos-host", "aos-dev", "soa-host", "soa-dev"]
+    reqs = []
+    for i, ((et, kind, quad, cpq, n, _), (mesh, c, X, C)) in enumerate(zip(MIX, mix)):
+        mid = _register(ctx, et, mesh, hows[i % 4])
+        reqs.append((mid, et, kind, quad, api.PER_QPOINT if cpq else api.PER_ELEMENT, C, mesh, c))
+    # alone: one request at a time
+    alone = []
+    for mid, et, kind, quad, cm, C, mesh, c in reqs:
+        tk = ctx.serve_submit(mid, kind, quad, cm, C)
+        r = _wait(ctx, tk)
+        assert r.status == 0 and r.t_submit_us <= r.t_launch_us <= r.t_done_us
+        A, b, f = ctx.serve_result_tensors(tk, r)
+        alone.append((A.double().cpu().numpy(), b.double().cpu().numpy(), f.cpu().numpy()))
+        ctx.serve_release(tk)
+    # the oracle for each set
+    for (mid, et, kind, quad, cm, C, mesh, c), (An, bn, fn) in zip(reqs, alone):
+        Ao, bo, _ = oracle.integrate(et, kind, ORACLE_RULE[quad], mesh, c, coef_per_q=cm == api.PER_QPOINT, n_threads=8)
+        ea, eb = max_errors(An, bn, Ao, bo)
+        assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED]
+    # in the mix: every request three times, submitted from two threads while others run
+    tickets = []
+    lock = threading.Lock()
+
+    def client(order):
+        for j in order:
+            mid, et, kind, quad, cm, C, mesh, c = reqs[j]
+            tk = ctx.serve_submit(mid, kind, quad, cm, C)
+            with lock:
+                tickets.append((j, tk))
+            time.sleep(0.0002)
+
+    idx = list(range(len(reqs))) * 3
+    th = [threading.Thread(target=client, args=(idx[k::2],)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    overlapped = 0
+    results = []
+    for j, tk in tickets:
+        r = _wait(ctx, tk)
+        assert r.status == 0
+        results.append((r.t_launch_us, r.t_done_us))
+        A, b, f = ctx.serve_result_tensors(tk, r)
+        An, bn, fn = A.double().cpu().numpy(), b.double().cpu().numpy(), f.cpu().numpy()
+        assert np.array_equal(fn, alone[j][2])
+        assert oracle.rel_frobenius(An, alone[j][0]).max() <= 1e-6
+        assert oracle.rel_frobenius(bn, alone[j][1]).max() <= 1e-6
+        ctx.serve_release(tk)
+    # some requests ran while others were on the device
+    results.sort()
+    for (l0, d0), (l1, d1) in zip(results, results[1:]):
+        if l1 < d0:
+            overlapped += 1
+    assert overlapped > 0
+    for mid, *_ in reqs:
+        ctx.mesh_release(mid)
+
+
+def test_serve_fp64_request(ctx, mix):
+    (et, kind, quad, cpq, n, _), (mesh, c, X, C) = MIX[7], mix[7]
+    mid = _register(ctx, et, mesh, "aos-dev")
+    C64 = torch.from_numpy(np.ascontiguousarray(c.reshape(n, -1))).cuda()
+    tk = ctx.serve_submit(mid, kind, quad, api.PER_ELEMENT, C64, prec=api.FP64)
+    r = _wait(ctx, tk)
+    A, b, f = ctx.serve_result_tensors(tk, r)
+    Ao, bo, _ = oracle.integrate(et, kind, ORACLE_RULE[quad], mesh, c, n_threads=8)
+    ea, eb = max_errors(A.cpu().numpy(), b.cpu().numpy(), Ao, bo)
+    assert ea <= TOL[api.FP64] and eb <= TOL[api.FP64]
+    ctx.serve_release(tk)
+    ctx.mesh_release(mid)
+
+
+def test_serve_budget(mix):
+    (et, kind, quad, cpq, n, _), (mesh, c, X, C) = MIX[2], mix[2]
+    mesh_bytes = n * 12 * 8
+    out_bytes = 3 * 256 + n * (16 + 4) * 4 + n
+    with api.Context(0, hbm_budget=mesh_bytes + out_bytes + 4096) as small:
+        mid = small.mesh_register(et, torch.from_numpy(np.ascontiguousarray(mesh)), api.AOS)
+        t1 = small.serve_submit(mid, kind, quad, api.PER_ELEMENT, C)
+        t2 = small.serve_submit(mid, kind, quad, api.PER_ELEMENT, C)   # waits for t1's release
+        r1 = _wait(small, t1)
+        time.sleep(0.05)
+        assert small.serve_poll(t2) is None                          # not admitted yet
+        small.serve_release(t1)
+        r2 = _wait(small, t2)
+        assert r2.status == 0 and r2.t_launch_us >= r1.t_done_us
+        small.serve_release(t2)
+        # a mesh that can never fit
+        with pytest.raises(api.FeError) as e:
+            small.mesh_register(et, torch.from_numpy(np.ascontiguousarray(meshgen.tet_cube_mesh(30))), api.AOS)
+        assert e.value.status == -3
+        small.mesh_release(mid)
