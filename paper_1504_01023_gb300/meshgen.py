@@ -201,6 +201,45 @@ def mesh_for_size(elem_type: int, n_elem: int, seed: int):
     return prism_slab_mesh(n, None, 0.1, seed=seed, n_elem=n_elem)
 
 
+class MixPool:
+    """Seeded base data for workloads of many meshes of uneven size: one
+    tetrahedral and one prism base mesh of at least `max_elems` elements, a pool of
+    independent generic coefficient draws and of Poisson right-hand sides. A mesh
+    of n elements is a window of n consecutive elements of its base mesh at a
+    seeded offset; its per-element or per-point coefficients are consecutive pool
+    entries from a seeded offset (cyclically)."""
+
+    def __init__(self, max_elems: int, seed: int, pool_size: int = 1 << 22):
+        n = max(1, int(np.ceil((max_elems / 6.0) ** (1.0 / 3.0))))
+        while 6 * n ** 3 < max_elems:
+            n += 1
+        self.tet = tet_cube_mesh(n, 0.2, seed=seed)
+        m = max(1, int(np.ceil(np.sqrt(max_elems / 2.0))))
+        while 2 * m * m < max_elems:
+            m += 1
+        self.prism = prism_slab_mesh(m, None, 0.1, seed=seed + 1)
+        self.generic = generic_coefs(pool_size, 1, seed=seed + 2)
+        self.poisson = np.random.default_rng(seed + 3).uniform(-1.0, 1.0, size=pool_size)
+        self.rng = np.random.default_rng(seed + 4)
+
+    def window(self, elem_type: int, n: int):
+        base = self.tet if elem_type == 0 else self.prism
+        off = int(self.rng.integers(0, len(base) - n + 1))
+        return off
+
+    def coef_offset(self):
+        return int(self.rng.integers(0, len(self.poisson)))
+
+
+def mix_spec(elem_type: int, kind: int):
+    """Rule and coefficient mode of each (type, kind) in the mixed workloads:
+    tetrahedra Poisson TET1 with d^0 per element, generic TET4 per element;
+    prisms PRISM6 with d^0 per point (Poisson) or 20 coefficients per point."""
+    if elem_type == 0:
+        return (0, 0) if kind == 0 else (1, 0)       # (quad, per-point)
+    return (2, 1)
+
+
 def soa(a: np.ndarray) -> np.ndarray:
     """[E, ...] -> [K, E] planes (structure of arrays), contiguous."""
     return np.ascontiguousarray(a.reshape(a.shape[0], -1).T)

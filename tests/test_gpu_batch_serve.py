@@ -126,6 +126,12 @@ def test_serve_alone_and_in_the_mix(ctx, mix):
     for i, ((et, kind, quad, cpq, n, _), (mesh, c, X, C)) in enumerate(zip(MIX, mix)):
         mid = _register(ctx, et, mesh, hows[i % 4])
         reqs.append((mid, et, kind, quad, api.PER_QPOINT if cpq else api.PER_ELEMENT, C, mesh, c))
+    # one large set (generic prisms, per-point coefficients) keeps the device busy in the mix
+    big_mesh = meshgen.prism_slab_mesh(800, seed=77)                        # 1,280,000 prisms
+    _, big_c = make_inputs(api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, mesh=big_mesh, seed=78)
+    big_C = torch.from_numpy(big_c.astype(np.float32).reshape(len(big_mesh), -1)).cuda()
+    big_id = _register(ctx, api.PRISM, big_mesh, "aos-host")
+    reqs.append((big_id, api.PRISM, api.GENERIC, api.QUAD_PRISM6, api.PER_QPOINT, big_C, None, None))
     # alone: one request at a time
     alone = []
     for mid, et, kind, quad, cm, C, mesh, c in reqs:
@@ -135,13 +141,15 @@ def test_serve_alone_and_in_the_mix(ctx, mix):
         A, b, f = ctx.serve_result_tensors(tk, r)
         alone.append((A.double().cpu().numpy(), b.double().cpu().numpy(), f.cpu().numpy()))
         ctx.serve_release(tk)
-    # the oracle for each set
-    for (mid, et, kind, quad, cm, C, mesh, c), (An, bn, fn) in zip(reqs, alone):
+    # the oracle for each small set
+    for (mid, et, kind, quad, cm, C, mesh, c), (An, bn, fn) in zip(reqs[:-1], alone):
         Ao, bo, _ = oracle.integrate(et, kind, ORACLE_RULE[quad], mesh, c, coef_per_q=cm == api.PER_QPOINT, n_threads=8)
         ea, eb = max_errors(An, bn, Ao, bo)
         assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED]
-    # in the mix: every request three times, submitted from two threads while others run
-    tickets = []
+    # in the mix: the large request first, then every small one three times from two
+    # threads while it runs
+    big = len(reqs) - 1
+    tickets = [(big, ctx.serve_submit(*(reqs[big][:1] + reqs[big][2:6])))]
     lock = threading.Lock()
 
     def client(order):
@@ -150,31 +158,27 @@ def test_serve_alone_and_in_the_mix(ctx, mix):
             tk = ctx.serve_submit(mid, kind, quad, cm, C)
             with lock:
                 tickets.append((j, tk))
-            time.sleep(0.0002)
 
-    idx = list(range(len(reqs))) * 3
+    idx = list(range(big)) * 3
     th = [threading.Thread(target=client, args=(idx[k::2],)) for k in range(2)]
     for t in th:
         t.start()
     for t in th:
         t.join()
-    overlapped = 0
-    results = []
+    spans = {}
     for j, tk in tickets:
         r = _wait(ctx, tk)
         assert r.status == 0
-        results.append((r.t_launch_us, r.t_done_us))
+        spans[tk] = (j, r.t_launch_us, r.t_done_us)
         A, b, f = ctx.serve_result_tensors(tk, r)
         An, bn, fn = A.double().cpu().numpy(), b.double().cpu().numpy(), f.cpu().numpy()
         assert np.array_equal(fn, alone[j][2])
         assert oracle.rel_frobenius(An, alone[j][0]).max() <= 1e-6
         assert oracle.rel_frobenius(bn, alone[j][1]).max() <= 1e-6
         ctx.serve_release(tk)
-    # some requests ran while others were on the device
-    results.sort()
-    for (l0, d0), (l1, d1) in zip(results, results[1:]):
-        if l1 < d0:
-            overlapped += 1
+    # requests that arrived while the large one ran were launched before it finished
+    _, bl, bd = spans[tickets[0][1]]
+    overlapped = sum(1 for tk, (j, l, d) in spans.items() if j != big and l < bd)
     assert overlapped > 0
     for mid, *_ in reqs:
         ctx.mesh_release(mid)
