@@ -39,6 +39,10 @@ WORKLOAD = ("generic conv-diff-reaction tetrahedra: unit cube 100^3 x 6 Kuhn = 6
             "element-contiguous (natural) input and output order")
 N_ELEM = 6_000_000
 SEED = 1504010230 + 2
+PRISM_WORKLOAD = ("generic conv-diff-reaction prisms: [0,1]^2 in 1000 x 1000 squares x 2 triangles, one layer "
+                  "h = 1e-3 with z-jitter +-0.1h = 2,000,000 elements, PRISM6 rule (3 triangle x 2 line), 20 "
+                  "coefficients per integration point, mixed FP32 with FP64 Jacobian for mean ratio < 0.1, "
+                  "element-contiguous order")
 
 
 def parse():
@@ -55,6 +59,13 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--no-prism", action="store_true")
+    ap.add_argument("--workload", default="tet", choices=["tet", "prism"],
+                    help="tet: the 6M generic tetrahedra (default); prism: the 2M generic prisms")
+    ap.add_argument("--shape", default=None, help="BLOCK,PERSISTENT: pin the main kernel's launch shape instead of "
+                                                  "autotuning it (profiling)")
+    ap.add_argument("--n-slab", type=int, default=1000,
+                    help="squares per axis of the prism slab (2 n^2 elements); smaller only for profiling")
     return ap.parse_args()
 
 
@@ -254,20 +265,32 @@ def run_native(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     ctx = api.Context(dev.index)
-    mesh, coefs = workload(rank, args.n_cubes)
+    if args.workload == "tet":
+        et, mesh, coefs = api.TET, *workload(rank, args.n_cubes)
+        kw = dict(kind=api.GENERIC, quad=api.QUAD_TET4, coef_mode=api.PER_ELEMENT, prec=api.FP32_MIXED,
+                  layout=api.AOS, out_layout=api.AOS)
+        wl_name, kernel_name, tag = WORKLOAD, "elem_kernel<TET,GENERIC,MIXED,TET4,per-element,AOS,AOS>", "tet_generic_mixed_aos_6M"
+    else:
+        et, mesh, coefs = api.PRISM, *prism_workload(rank, args.n_slab)
+        kw = dict(kind=api.GENERIC, quad=api.QUAD_PRISM6, coef_mode=api.PER_QPOINT, prec=api.FP32_MIXED,
+                  layout=api.AOS, out_layout=api.AOS)
+        wl_name, kernel_name, tag = PRISM_WORKLOAD, "elem_kernel<PRISM,GENERIC,MIXED,PRISM6,per-point,AOS,AOS>", "prism_generic_mixed_aos_2M"
     n = len(mesh)
-    X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)                       # [E,4,3] f64
-    C = torch.from_numpy(coefs.astype(np.float32)).to(dev)                         # [E,20] f32
-    out = api.alloc_out(api.TET, n, api.FP32_MIXED, api.AOS, dev, with_flags=True)
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)                       # [E,NS,3] f64
+    C = torch.from_numpy(np.ascontiguousarray(coefs.reshape(n, -1).astype(np.float32))).to(dev)
+    out = api.alloc_out(et, n, api.FP32_MIXED, api.AOS, dev, with_flags=True)
     stream = torch.cuda.current_stream(dev)
-    kw = dict(kind=api.GENERIC, quad=api.QUAD_TET4, coef_mode=api.PER_ELEMENT, prec=api.FP32_MIXED,
-              layout=api.AOS, out_layout=api.AOS)
-    shape = ctx.tune(api.TET, X, C, out=out, **kw)                                 # autotuner (untimed)
-    step = lambda: ctx.integrate(api.TET, X, C, out=out, **kw)
+    if args.shape:
+        blk, pers = (int(v) for v in args.shape.split(","))
+        ctx.set_shape(blk, pers, et, X, C, out=out, **kw)
+        shape = (blk, pers)
+    else:
+        shape = ctx.tune(et, X, C, out=out, **kw)                                  # autotuner (untimed)
+    step = lambda: ctx.integrate(et, X, C, out=out, **kw)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize(dev)
-    bpe = api.bytes_per_element(api.TET, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP32_MIXED)
+    bpe = api.bytes_per_element(et, kw["kind"], kw["quad"], kw["coef_mode"], api.FP32_MIXED)
 
     clocks = ClockSampler(dev.index)
     clocks.start()
@@ -295,23 +318,25 @@ def run_native(args):
     k_ms = kms / max(kn, 1)
     peak, peak_kind = measured_peaks()
     achieved = n * bpe / (k_ms * 1e-3) / 1e9
-    traffic = ncu_traffic("tet_generic_mixed_aos_6M")
+    traffic = ncu_traffic(tag)
 
     result = {"metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-              "config": {"workload": WORKLOAD, "n_elem_per_gpu": n, "bytes_per_element": bpe,
+              "config": {"workload": wl_name, "n_elem_per_gpu": n, "bytes_per_element": bpe,
                          "launch_shape": {"block": shape[0], "persistent": shape[1]},
                          "l2": "inputs larger than L2: %.2f GB read+written per step per GPU" % (n * bpe / 1e9),
                          "parallelism": f"weak: {world} independent mesh(es), one per GPU"},
               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak, "traffic": traffic,
-                           "kernel": "elem_kernel<TET,GENERIC,MIXED,TET4,per-element,AOS,AOS>",
+                           "kernel": kernel_name,
                            "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                            "kernel_ms": k_ms, "algorithmic_bytes_per_launch": n * bpe},
               "gpu_launches": int(launches), "clocks": clocks.summary()}
 
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.workload == "tet":
+        if not args.no_prism:
+            result["prism_form"] = prism_form(ctx, dev, api, args)
         if not args.no_fp64:
             result["fp64_form"] = fp64_form(ctx, dev, api, mesh, args)
         if not args.no_batch:
@@ -329,6 +354,50 @@ def run_native(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def prism_workload(rank: int, n_slab: int = 1000):
+    from paper_1504_01023_gb300 import meshgen
+    mesh = meshgen.prism_slab_mesh(n_slab, None, 0.1, seed=meshgen.SEED_BASE + 3 + 1000 * rank)
+    coefs = meshgen.generic_coefs(len(mesh), 6, seed=meshgen.SEED_BASE + 3 + 1000 * rank)
+    return mesh, coefs
+
+
+def prism_form(ctx, dev, api, args):
+    """The 2,000,000 generic prisms (per-point coefficients), mixed form, timed
+    with CUDA events around the main kernel."""
+    import torch
+    mesh, coefs = prism_workload(0, args.n_slab)
+    n = len(mesh)
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)
+    C = torch.from_numpy(np.ascontiguousarray(coefs.reshape(n, -1).astype(np.float32))).to(dev)
+    out = api.alloc_out(api.PRISM, n, api.FP32_MIXED, api.AOS, dev, with_flags=True)
+    kw = dict(kind=api.GENERIC, quad=api.QUAD_PRISM6, coef_mode=api.PER_QPOINT, prec=api.FP32_MIXED,
+              layout=api.AOS, out_layout=api.AOS)
+    shape = ctx.tune(api.PRISM, X, C, out=out, **kw)
+    for _ in range(3):
+        ctx.integrate(api.PRISM, X, C, out=out, **kw)
+    torch.cuda.synchronize(dev)
+    reps = max(20, min(200, args.steps // 20))
+    ctx.set_profiling(True)
+    ctx.kernel_time(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.integrate(api.PRISM, X, C, out=out, **kw)
+    e1.record()
+    kms, kn = ctx.kernel_time(reset=True)
+    ctx.set_profiling(False)
+    step_ms = e0.elapsed_time(e1) / reps
+    bpe = api.bytes_per_element(api.PRISM, api.GENERIC, api.QUAD_PRISM6, api.PER_QPOINT, api.FP32_MIXED)
+    k_ms = kms / kn
+    peak, _ = measured_peaks()
+    gbs = n * bpe / (k_ms * 1e-3) / 1e9
+    del X, C, out
+    torch.cuda.empty_cache()
+    return {"workload": PRISM_WORKLOAD, "value": n / step_ms / 1e3, "unit": "Melem/s", "ms_per_step": step_ms,
+            "kernel_ms": k_ms, "bytes_per_element": bpe, "achieved_gbs": gbs, "hbm_frac": gbs / peak,
+            "launch_shape": {"block": shape[0], "persistent": shape[1]}, "dtype": "f32"}
 
 
 def fp64_form(ctx, dev, api, mesh, args):

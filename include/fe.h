@@ -265,6 +265,11 @@ fe_status fe_ctx_kernel_time(fe_ctx *ctx, double *ms, int64_t *launches, int res
    now, on these buffers, and keep the fastest. Writes the tuning cache if set. */
 fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                   void *stream);
+/* Pin the launch shape of a key (threads = elements per block: 32..512 for
+   tetrahedra, 32..256 for prisms, a multiple of 32; persistent 0 or 1), as the
+   autotuner would; FE_ERR_UNSUPPORTED if its shared memory does not fit. */
+fe_status fe_set_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
+                       int block_threads, int persistent);
 /* The launch shape that the next call with this key would use: threads (=
    elements) per block, and whether the grid is persistent (one wave of resident
    blocks striding over tiles) or one block per tile. */

@@ -94,6 +94,8 @@ _SIGS = [
     ("fe_get_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("fe_integrate_tet_noalloc", ctypes.c_int, [ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
+    ("fe_set_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), ctypes.c_int,
+                                    ctypes.c_int]),
 ]
 
 _lock = threading.Lock()
@@ -302,6 +304,14 @@ class Context:
         o = make_out(*out, out_layout)
         _check(load().fe_tune(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), self._stream(stream, True)), self.h)
         return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out)
+
+    def set_shape(self, block, persistent, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT,
+                  prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+        if out is None:
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
+        o = make_out(*out, out_layout)
+        _check(load().fe_set_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), block, persistent), self.h)
 
     def shape(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
               out_layout=SOA, out=None):

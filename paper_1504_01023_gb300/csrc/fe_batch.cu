@@ -27,17 +27,25 @@ __global__ void soa_to_aos_kernel(const double *__restrict__ in, int64_t stride,
     }
 }
 
+// One persistent launch per combination present: its tiles are a contiguous
+// segment of the plan's tile array, with its own counter.
+struct ClassLaunch {
+    int combo = 0;
+    unsigned tile_off = 0, n_tiles = 0;
+    int grid = 0;
+    int64_t smem = 0;
+};
+
 struct BatchPlan {
     size_t key = 0;
     std::vector<unsigned char> items_bytes;
     BatchItemDev *d_items = nullptr;
     BatchTile *d_tiles = nullptr;
     unsigned n_items = 0, n_tiles = 0;
-    unsigned *d_counter = nullptr;
+    unsigned *d_counter = nullptr;   // kCombos counters
     Scratch scratch;
     int block = 128;
-    int grid = 0;
-    int64_t smem = 0;
+    std::vector<ClassLaunch> classes;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -72,27 +80,68 @@ static double combo_cost(int combo) {
     return combo >= 0 && combo < 12 ? cost[combo] : 1.0;
 }
 
-static std::vector<BatchTile> make_tiles(const std::vector<BatchItemDev> &items, int B) {
-    std::vector<std::pair<double, BatchTile>> t;
+// Tiles of B consecutive elements, grouped by combination (heaviest
+// combination first) and, within one, ordered by decreasing size.
+static std::vector<BatchTile> make_tiles(const std::vector<BatchItemDev> &items, int B, std::vector<ClassLaunch> &classes) {
+    std::vector<std::vector<std::pair<double, BatchTile>>> per(kCombos);
     for (unsigned i = 0; i < items.size(); ++i) {
         const int64_t n = items[i].p.n;
+        const int c = items[i].combo;
+        if (c < 0 || c >= kCombos) continue;
         for (int64_t e0 = 0; e0 < n; e0 += B) {
             BatchTile tl;
             tl.item = i;
             tl.first = e0;
             tl.count = unsigned(std::min<int64_t>(B, n - e0));
-            t.push_back({combo_cost(items[i].combo) * tl.count, tl});
+            per[c].push_back({double(tl.count), tl});
         }
     }
-    std::stable_sort(t.begin(), t.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<int> order(kCombos);
+    for (int c = 0; c < kCombos; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [](int a, int b) { return combo_cost(a) > combo_cost(b); });
     std::vector<BatchTile> out;
-    out.reserve(t.size());
-    for (auto &x : t) out.push_back(x.second);
+    classes.clear();
+    for (int c : order) {
+        if (per[c].empty()) continue;
+        std::stable_sort(per[c].begin(), per[c].end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+        ClassLaunch cl;
+        cl.combo = c;
+        cl.tile_off = unsigned(out.size());
+        cl.n_tiles = unsigned(per[c].size());
+        for (auto &x : per[c]) out.push_back(x.second);
+        classes.push_back(cl);
+    }
     return out;
 }
 
+static std::mutex g_attr_mu;
+static int64_t g_attr_set[kCombos] = {0};
+
+// Shared memory attribute and grid (SMs x resident blocks) of each class launch.
+static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes, int B) {
+    for (auto &cl : classes) {
+        const void *k = kernel_batch(cl.combo);
+        cl.smem = batch_smem_bytes(cl.combo, B);
+        if (cl.smem + 1024 > ctx->max_smem_optin)
+            return set_error(ctx, FE_ERR_UNSUPPORTED, "batched tile does not fit in shared memory");
+        {
+            std::lock_guard<std::mutex> lk(g_attr_mu);
+            if (cl.smem > g_attr_set[cl.combo]) {
+                fe_status st = cuda_check(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cl.smem)),
+                                          "cudaFuncSetAttribute(batch)");
+                if (st != FE_OK) return st;
+                g_attr_set[cl.combo] = cl.smem;
+            }
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, B, size_t(cl.smem));
+        cl.grid = int(std::min<int64_t>(int64_t(std::max(1, per_sm)) * ctx->sms, cl.n_tiles));
+    }
+    return FE_OK;
+}
+
 static fe_status upload_tiles(fe_ctx *ctx, BatchPlan *pl, const std::vector<BatchItemDev> &items, int B) {
-    std::vector<BatchTile> tiles = make_tiles(items, B);
+    std::vector<BatchTile> tiles = make_tiles(items, B, pl->classes);
     if (pl->d_tiles) cudaFree(pl->d_tiles);
     pl->d_tiles = nullptr;
     pl->n_tiles = unsigned(tiles.size());
@@ -102,28 +151,24 @@ static fe_status upload_tiles(fe_ctx *ctx, BatchPlan *pl, const std::vector<Batc
     st = cuda_check(ctx, cudaMemcpy(pl->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice),
                     "cudaMemcpy(tiles)");
     if (st != FE_OK) return st;
-    int64_t smem = 0;
-    for (auto &it : items) smem = std::max<int64_t>(smem, batch_smem_bytes(it.combo, B));
-    pl->smem = smem;
     pl->block = B;
-    st = cuda_check(ctx, cudaFuncSetAttribute(kernel_batch(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
-                    "cudaFuncSetAttribute(batch)");
-    if (st != FE_OK) return st;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_batch(), B, size_t(smem));
-    pl->grid = std::max(1, per_sm) * ctx->sms;
-    return FE_OK;
+    return size_classes(ctx, pl->classes, B);
 }
 
-// Enqueue {counter reset, batch kernel, fix-up kernel} on a stream.
+// Enqueue {counter reset, one persistent kernel per combination, fix-up kernel}.
 static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, kCombos * sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch.fix_count, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemsetAsync(batch)");
     int *status = ctx->scratch.status;
-    void *args[] = {&pl->d_items, &pl->n_items, &pl->d_tiles, &pl->n_tiles, &pl->d_counter, &status};
-    e = cudaLaunchKernel(kernel_batch(), dim3(pl->grid), dim3(pl->block), args, size_t(pl->smem), st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
+    for (const auto &cl : pl->classes) {
+        const BatchTile *tiles = pl->d_tiles + cl.tile_off;
+        unsigned n_tiles = cl.n_tiles;
+        unsigned *counter = pl->d_counter + cl.combo;
+        void *args[] = {&pl->d_items, &pl->n_items, &tiles, &n_tiles, &counter, &status};
+        e = cudaLaunchKernel(kernel_batch(cl.combo), dim3(cl.grid), dim3(pl->block), args, size_t(cl.smem), st);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
+    }
     unsigned long long *list = pl->scratch.fix_list;
     unsigned *count = pl->scratch.fix_count;
     unsigned cap = pl->scratch.fix_cap;
@@ -132,6 +177,8 @@ static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch fix-up)");
     return FE_OK;
 }
+
+static int plan_launches(const BatchPlan *pl) { return int(pl->classes.size()) + 1; }
 
 static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size_t key, BatchPlan *&out) {
     auto *pl = new BatchPlan();
@@ -182,8 +229,11 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
         cudaEventCreate(&e1);
         for (int B : {64, 128, 256}) {
             st = upload_tiles(ctx, pl, dev, B);
+            if (st == FE_ERR_UNSUPPORTED) {   // tile too large for shared memory at this size
+                st = FE_OK;
+                continue;
+            }
             if (st != FE_OK) break;
-            if (pl->smem + 1024 > ctx->max_smem_optin) continue;
             st = enqueue_batch(ctx, pl, cs);  // warm-up
             cudaEventRecord(e0, cs);
             for (int r = 0; r < 3 && st == FE_OK; ++r) st = enqueue_batch(ctx, pl, cs);
@@ -205,8 +255,6 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
         cudaEventDestroy(e1);
     }
     if (st == FE_OK) st = upload_tiles(ctx, pl, dev, bestB);
-    if (st == FE_OK && pl->smem + 1024 > ctx->max_smem_optin)
-        st = set_error(ctx, FE_ERR_UNSUPPORTED, "batched tile does not fit in shared memory");
     // capture the launch sequence once; later submissions replay it
     if (st == FE_OK) {
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -271,7 +319,8 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
         it.p.fix_cap = db.scratch.fix_cap;
         it.p.status = ctx->scratch.status;
     }
-    std::vector<BatchTile> tiles = make_tiles(items, B);
+    std::vector<ClassLaunch> classes;
+    std::vector<BatchTile> tiles = make_tiles(items, B, classes);
     r = grow(ctx, reinterpret_cast<void **>(&db.d_items), reinterpret_cast<void **>(&db.h_items), db.cap_items,
              items.size(), sizeof(BatchItemDev));
     if (r == FE_OK)
@@ -284,6 +333,8 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(db.d_tiles, db.h_tiles, tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemcpyAsync(batch tables)");
+    r = size_classes(ctx, classes, B);
+    if (r != FE_OK) return r;
     BatchPlan pl;
     pl.d_items = db.d_items;
     pl.d_tiles = db.d_tiles;
@@ -292,30 +343,14 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     pl.d_counter = db.d_counter;
     pl.scratch = db.scratch;
     pl.block = B;
-    int64_t smem = 0;
-    for (auto &it : items) smem = std::max<int64_t>(smem, batch_smem_bytes(it.combo, B));
-    pl.smem = smem;
-    static std::mutex mu;
-    static int64_t attr_set = 0;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (smem > attr_set) {
-            r = cuda_check(ctx, cudaFuncSetAttribute(kernel_batch(), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
-                           "cudaFuncSetAttribute(batch)");
-            if (r != FE_OK) return r;
-            attr_set = smem;
-        }
-    }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_batch(), B, size_t(smem));
-    pl.grid = int(std::min<int64_t>(int64_t(std::max(1, per_sm)) * ctx->sms, std::max<int64_t>(1, tiles.size())));
+    pl.classes = classes;
     r = enqueue_batch(ctx, &pl, st);
     // the plan only borrowed the tables
     pl.d_items = nullptr;
     pl.d_tiles = nullptr;
     pl.d_counter = nullptr;
     pl.scratch = Scratch{};
-    if (r == FE_OK) g_launches.fetch_add(2);
+    if (r == FE_OK) g_launches.fetch_add(uint64_t(plan_launches(&pl)));
     return r;
 }
 
@@ -425,7 +460,7 @@ fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
     }
     cudaError_t e = cudaGraphLaunch(pl->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_check(ctx, e, "cudaGraphLaunch(batch)");
-    g_launches.fetch_add(2);
+    g_launches.fetch_add(uint64_t(plan_launches(pl)));
     return FE_OK;
 }
 

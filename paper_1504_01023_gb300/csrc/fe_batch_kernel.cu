@@ -1,7 +1,7 @@
-// Batched persistent kernel: many element sets of uneven size and mixed
-// type/kind in one launch. Each block repeatedly takes the next tile from a
-// global counter (tiles are ordered by decreasing cost on the host) and runs
-// the same tile code as the single-set kernels; nothing waits on another block.
+// Batched persistent kernels: many element sets of uneven size and mixed
+// type/kind. Each block repeatedly takes the next tile of its combination from a
+// global counter (tiles are ordered by decreasing cost on the host) and runs the
+// same tile code as the single-set kernels; nothing waits on another block.
 #include "fe_kernels.cuh"
 
 namespace fe {
@@ -26,10 +26,12 @@ FE_COMBO(11, PRISM, GENERIC, Q_PRISM6, 1)
 #undef FE_COMBO
 
 template <int ID>
-__device__ __forceinline__ bool tile_combo(const ElemParams &p, int64_t e0, int nb, unsigned char *smem, uint64_t *bar,
-                                           unsigned &phase) {
+__device__ __forceinline__ bool tile_combo(const BatchItemDev *item, const BatchTile *tile, unsigned char *smem,
+                                           uint64_t *bar, unsigned *phase) {
     using K = ComboCfg<ID>;
-    return process_tile<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, e0, nb, smem, bar, phase);
+    const ElemParams p = item->p;
+    return process_tile<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, tile->first, int(tile->count), smem, bar,
+                                                                          *phase);
 }
 
 template <int ID> __device__ __forceinline__ void fix_combo(const ElemParams &p, int64_t e) {
@@ -37,6 +39,10 @@ template <int ID> __device__ __forceinline__ void fix_combo(const ElemParams &p,
     fixup_element<K::et, K::kind, K::quad, K::cpq, AOS, AOS>(p, e);
 }
 
+// Persistent kernel of one combination: blocks take the next tile of this
+// combination from its counter until none is left. A batch launches one such
+// kernel per combination present (one register allocation per combination).
+template <int ID>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchItemDev *__restrict__ items, unsigned n_items,
                                                     const BatchTile *__restrict__ tiles, unsigned n_tiles,
                                                     unsigned *tile_counter, int *status) {
@@ -55,32 +61,12 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchItemDev *__restri
         const unsigned t = s_tile;
         __syncthreads();
         if (t >= n_tiles) break;
-        const BatchTile tl = tiles[t];
-        if (tl.item >= n_items || tl.count > blockDim.x) {
+        const BatchTile *tp = tiles + t;
+        if (tp->item >= n_items || tp->count > blockDim.x || items[tp->item].combo != ID) {
             if (threadIdx.x == 0) atomicOr(status, ST_BAD_TILE);
             continue;
         }
-        const ElemParams p = items[tl.item].p;
-        const int combo = items[tl.item].combo;
-        bool ok = true;
-        switch (combo) {
-            case 0: ok = tile_combo<0>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 1: ok = tile_combo<1>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 2: ok = tile_combo<2>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 3: ok = tile_combo<3>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 4: ok = tile_combo<4>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 5: ok = tile_combo<5>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 6: ok = tile_combo<6>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 7: ok = tile_combo<7>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 8: ok = tile_combo<8>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 9: ok = tile_combo<9>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 10: ok = tile_combo<10>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            case 11: ok = tile_combo<11>(p, tl.first, int(tl.count), smem, &bar, phase); break;
-            default:
-                if (threadIdx.x == 0) atomicOr(status, ST_BAD_TILE);
-                break;
-        }
-        if (!ok) return;
+        if (!tile_combo<ID>(items + tp->item, tp, smem, &bar, &phase)) return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
@@ -141,7 +127,23 @@ long long batch_smem_bytes(int combo, int B) {
     return -1;
 }
 
-const void *kernel_batch() { return reinterpret_cast<const void *>(&batch_kernel); }
+const void *kernel_batch(int combo) {
+    switch (combo) {
+        case 0: return reinterpret_cast<const void *>(&batch_kernel<0>);
+        case 1: return reinterpret_cast<const void *>(&batch_kernel<1>);
+        case 2: return reinterpret_cast<const void *>(&batch_kernel<2>);
+        case 3: return reinterpret_cast<const void *>(&batch_kernel<3>);
+        case 4: return reinterpret_cast<const void *>(&batch_kernel<4>);
+        case 5: return reinterpret_cast<const void *>(&batch_kernel<5>);
+        case 6: return reinterpret_cast<const void *>(&batch_kernel<6>);
+        case 7: return reinterpret_cast<const void *>(&batch_kernel<7>);
+        case 8: return reinterpret_cast<const void *>(&batch_kernel<8>);
+        case 9: return reinterpret_cast<const void *>(&batch_kernel<9>);
+        case 10: return reinterpret_cast<const void *>(&batch_kernel<10>);
+        case 11: return reinterpret_cast<const void *>(&batch_kernel<11>);
+    }
+    return nullptr;
+}
 const void *kernel_batch_fixup() { return reinterpret_cast<const void *>(&batch_fixup_kernel); }
 
 }  // namespace fe

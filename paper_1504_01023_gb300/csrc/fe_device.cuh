@@ -487,6 +487,43 @@ __device__ __forceinline__ void prism_generic_update(const V3<T> g[6], T vol, co
     }
 }
 
+// The same update with the point's shape values passed in registers (the point
+// loop then needs no unrolling: one copy of the code serves all six points).
+template <class T, class CS>
+__device__ __forceinline__ void prism_generic_update_rt(const V3<T> g[6], T vol, const CS &c, int o, const T ph[6],
+                                                        T A[36], T b[6]) {
+    // one row a of the coefficient matrix at a time: T_as = sum_b vol c_ab Phi_bs,
+    // then A_rs += Phi_ar T_as and b_r += vol d_a Phi_ar (same products as the
+    // full rank-4 update, fewer values live at once)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const T c0 = vol * c(o + 4 * a), c1 = vol * c(o + 4 * a + 1), c2 = vol * c(o + 4 * a + 2),
+                c3 = vol * c(o + 4 * a + 3);
+        const T da = vol * c(o + 16 + a);
+        T Ta[6];
+#pragma unroll
+        for (int s = 0; s < 6; ++s) Ta[s] = c0 * ph[s] + c1 * g[s].x + c2 * g[s].y + c3 * g[s].z;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const T phi = a == 0 ? ph[r] : (a == 1 ? g[r].x : (a == 2 ? g[r].y : g[r].z));
+#pragma unroll
+            for (int s = 0; s < 6; ++s) A[6 * r + s] += phi * Ta[s];
+            b[r] += da * phi;
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void prism_poisson_update_rt(const V3<T> g[6], T vol, T d0, const T ph[6], T A[36], T b[6]) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        const V3<T> gr = vol * g[r];
+#pragma unroll
+        for (int s = r; s < 6; ++s) A[6 * r + s] += dot(gr, g[s]);
+        b[r] += (vol * d0) * ph[r];
+    }
+}
+
 // Poisson products at one prism point: A_rs += vol grad phi_r . grad phi_s,
 // b_r += vol d0_q phi_r(q) (upper triangle accumulated; mirrored at the end).
 template <class T, int Q>

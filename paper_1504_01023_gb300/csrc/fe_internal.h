@@ -72,8 +72,9 @@ inline int batch_combo(int type, int kind, int quad, int cpq) {
     if (type == PRISM && quad == Q_PRISM6) return 8 + kind * 2 + cpq;
     return -1;
 }
-const void *kernel_batch();
+const void *kernel_batch(int combo);   // persistent kernel of one combination
 const void *kernel_batch_fixup();
+constexpr int kCombos = 12;
 // Dynamic shared memory of one block of the batched kernel for a combination.
 long long batch_smem_bytes(int combo, int block);
 

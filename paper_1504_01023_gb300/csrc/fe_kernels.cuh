@@ -127,8 +127,18 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     using T = typename std::conditional<PREC == FP64, double, float>::type;
 
     // Q loop on relative coordinates r[0..5] (r[0] = 0). Returns bit1/bit2 flags.
+    // Generic coefficients: the three points of a zeta level run in a rolled loop
+    // (shape values computed per point), which keeps the large body in the
+    // instruction cache; the lighter Poisson body is fully unrolled.
     template <class CS>
     __device__ __forceinline__ static uint8_t qloop(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor) {
+        if (KIND == POISSON) return qloop_unrolled(r, c, A, b, poor);
+        return qloop_rolled(r, c, A, b, poor);
+    }
+
+    template <class CS>
+    __device__ __forceinline__ static uint8_t qloop_unrolled(const V3<T> r[6], const CS &c, T A[36], T b[6],
+                                                             bool &poor) {
         const PrismFrame<T> f = prism_frame(r);
 #pragma unroll
         for (int k = 0; k < 36; ++k) A[k] = T(0);
@@ -156,6 +166,60 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
                 neg |= det < T(0);
                 const T vol = abs_t(det) * T(Rule<Q_PRISM6>::w(3 * l + t));
                 update_point(3 * l + t, g, vol, c, A, b);
+            }
+        }
+        if (KIND == POISSON) mirror(A);
+        if (degenerate) {
+#pragma unroll
+            for (int k = 0; k < 36; ++k) A[k] = T(0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) b[k] = T(0);
+            return 4;
+        }
+        return neg ? 2 : 0;
+    }
+
+    template <class CS>
+    __device__ __forceinline__ static uint8_t qloop_rolled(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor) {
+        using R = Rule<Q_PRISM6>;
+        const PrismFrame<T> f = prism_frame(r);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) A[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) b[k] = T(0);
+        bool neg = false, degenerate = false;
+        poor = false;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const T zb = T(R::zb(l)), zt = T(R::zt(l));
+            const V3<T> cx = zb * f.ub + zt * f.ut;
+            const V3<T> cy = zb * f.vb + zt * f.vt;
+            const V3<T> a3 = cross(cx, cy);
+            T fxy = T(0);
+            if (PREC == MIXED) {
+                const V3<T> t1 = T(2) * cy - cx;
+                fxy = dot(cx, cx) + dot(t1, t1) * T(1.0 / 3.0);
+            }
+#pragma unroll 1
+            for (int t = 0; t < 3; ++t) {
+                const int q = 3 * l + t;
+                T ph[6];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const T lam = t == k ? T(2.0 / 3.0) : T(1.0 / 6.0);
+                    ph[k] = lam * zb;
+                    ph[k + 3] = lam * zt;
+                }
+                V3<T> g[6], cz;
+                const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
+                if (PREC == MIXED) poor |= prism_poor(static_cast<float>(fxy), to_float(cz), static_cast<float>(det));
+                if (PREC == FP64) degenerate |= !(fabs(static_cast<double>(det)) > 1e-300);
+                neg |= det < T(0);
+                const T vol = abs_t(det) * T(R::w(0));
+                if (KIND == POISSON)
+                    prism_poisson_update_rt<T>(g, vol, c(CPQ ? q : 0), ph, A, b);
+                else
+                    prism_generic_update_rt<T>(g, vol, c, CPQ ? 20 * q : 0, ph, A, b);
             }
         }
         if (KIND == POISSON) mirror(A);
@@ -284,7 +348,9 @@ template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct BlockSmem {
     __host__ __device__ static constexpr int64_t c_bytes(int B) { return r16(int64_t(B) * CF::NC * int64_t(sizeof(CT))); }
     __host__ __device__ static constexpr int64_t a_bytes(int B) { return r16(int64_t(B) * CF::NA * int64_t(sizeof(CT))); }
     __host__ __device__ static constexpr int64_t b_bytes(int B) { return r16(int64_t(B) * CF::NS * int64_t(sizeof(CT))); }
-    __host__ __device__ static constexpr int64_t total(int B) { return x_bytes(B) + c_bytes(B) + a_bytes(B) + b_bytes(B); }
+    __host__ __device__ static constexpr int64_t in_bytes(int B) { return x_bytes(B) + c_bytes(B); }
+    __host__ __device__ static constexpr int64_t out_bytes(int B) { return a_bytes(B) + b_bytes(B); }
+    __host__ __device__ static constexpr int64_t total(int B) { return in_bytes(B) > out_bytes(B) ? in_bytes(B) : out_bytes(B); }
 };
 
 __device__ __forceinline__ bool aligned16(const void *p, uint64_t bytes) {
@@ -364,8 +430,8 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     const int tid = threadIdx.x;
     double *sX = reinterpret_cast<double *>(smem);
     CT *sC = reinterpret_cast<CT *>(smem + SM::x_bytes(B));
-    CT *sA = reinterpret_cast<CT *>(smem + SM::x_bytes(B) + SM::c_bytes(B));
-    CT *sB = reinterpret_cast<CT *>(smem + SM::x_bytes(B) + SM::c_bytes(B) + SM::a_bytes(B));
+    CT *sA = reinterpret_cast<CT *>(smem);
+    CT *sB = reinterpret_cast<CT *>(smem + SM::a_bytes(B));
     const double *X = p.X;
     const CT *C = static_cast<const CT *>(p.C);
     CT *Aout = static_cast<CT *>(p.A);
@@ -414,6 +480,9 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         uint8_t fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
         if (PREC == MIXED && poor) fl |= 1;
         if (p.flags) p.flags[e] = fl;
+    }
+    __syncthreads();   // every input read: the output records reuse the same shared memory
+    if (active) {
         if (OUTL == SOA) {
 #pragma unroll
             for (int k = 0; k < NA; ++k) sA[k * B + tid] = A[k];

@@ -91,7 +91,8 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
     const int B = 128;
     const int nc = nc_of(args);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
-    const int64_t smem = int64_t(B) * 12 * 8 + r16(int64_t(B) * nc * 4) + r16(int64_t(B) * 16 * 4) + r16(int64_t(B) * 4 * 4);
+    const int64_t smem_in = int64_t(B) * 12 * 8 + r16(int64_t(B) * nc * 4), smem_out = r16(int64_t(B) * 16 * 4) + r16(int64_t(B) * 4 * 4);
+    const int64_t smem = smem_in > smem_out ? smem_in : smem_out;
     // raise the kernel's dynamic shared-memory limit if needed, never lower it
     // (other entry points of the library launch the same kernel with larger tiles)
     cudaFuncAttributes fa{};

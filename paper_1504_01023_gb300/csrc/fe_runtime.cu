@@ -89,7 +89,8 @@ static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, in
     (void)outl;
     const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
-    return int64_t(B) * 3 * ns * 8 + r16(int64_t(B) * nc * cs) + r16(int64_t(B) * ns * ns * cs) + r16(int64_t(B) * ns * cs);
+    const int64_t in = int64_t(B) * 3 * ns * 8 + r16(int64_t(B) * nc * cs), out = r16(int64_t(B) * ns * ns * cs) + r16(int64_t(B) * ns * cs);
+    return in > out ? in : out;
 }
 
 // Static shared memory of the kernels (the mbarrier), kept out of the dynamic budget.
@@ -596,6 +597,20 @@ fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
     if (it != ctx->shapes.end()) sh = it->second;
     *block_threads = sh.block;
     *persistent = sh.persistent;
+    return FE_OK;
+}
+
+fe_status fe_set_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out, int block_threads,
+                       int persistent) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    fe_status st = fe_check_args(type, args, out);
+    if (st != FE_OK) return st;
+    if (block_threads < 32 || block_threads > max_block(type) || block_threads % 32 || (persistent != 0 && persistent != 1))
+        return set_error(ctx, FE_ERR_INVALID_ARG, "bad launch shape");
+    if (smem_bytes(type, args, out->layout, block_threads) + kStaticSmem > ctx->max_smem_optin)
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
+    ctx->shapes[shape_key(type, args, out)] = Shape{block_threads, persistent};
+    save_tuning_cache(ctx);
     return FE_OK;
 }
 
