@@ -425,17 +425,26 @@ template <class T> __device__ __forceinline__ PrismFrame<T> prism_frame(const V3
     return f;
 }
 
-// Global gradients and vol at point (l, t) of PRISM6. Returns det J.
-template <class T>
+// 1/v: IEEE division in double; in float the hardware reciprocal (within 2 ulp),
+// ample for the float form's tolerance and far cheaper than a correctly rounded
+// division.
+__device__ __forceinline__ double recip_fast(double v) { return 1.0 / v; }
+__device__ __forceinline__ float recip_fast(float v) { return __fdividef(1.0f, v); }
+
+// Global gradients at point (l, t) of PRISM6. Returns det J. With SQRTVOL the
+// gradients come out multiplied by sqrt(vol), vol = |det J| w (then the Laplace
+// products g_r . g_s carry the volume factor without further multiplies).
+template <class T, bool SQRTVOL = false>
 __device__ __forceinline__ T prism_point(const PrismFrame<T> &f, V3<T> cx, V3<T> cy, V3<T> a3, int l, int t, V3<T> g[6],
-                                         V3<T> &cz_out) {
+                                         V3<T> &cz_out, T w = T(0)) {
     using R = Rule<Q_PRISM6>;
     const T h0 = T(0.5 * R::lam(t, 0)), h1 = T(0.5 * R::lam(t, 1)), h2 = T(0.5 * R::lam(t, 2));
     const V3<T> cz = h0 * f.w0 + h1 * f.w1 + h2 * f.w2;
     const V3<T> a1 = cross(cy, cz);
     const V3<T> a2 = cross(cz, cx);
     const T det = dot(cx, a1);
-    const T inv = T(1) / det;
+    T inv = recip_fast(det);
+    if (SQRTVOL) inv *= sqrt((det < T(0) ? -det : det) * w);
     const V3<T> r1 = inv * a1, r2 = inv * a2, r3 = inv * a3;
     const V3<T> P[3] = {T(-1) * (r1 + r2), r1, r2};
     const T zb = T(R::zb(l)), zt = T(R::zt(l));
@@ -521,6 +530,18 @@ __device__ __forceinline__ void prism_poisson_update_rt(const V3<T> g[6], T vol,
 #pragma unroll
         for (int s = r; s < 6; ++s) A[6 * r + s] += dot(gr, g[s]);
         b[r] += (vol * d0) * ph[r];
+    }
+}
+
+// Poisson products at one prism point from gradients already scaled by
+// sqrt(vol): A_rs += g_r . g_s, b_r += vol d0_q phi_r(q) (upper triangle).
+template <class T, int Q>
+__device__ __forceinline__ void prism_poisson_update_scaled(const V3<T> g[6], T vol, T d0, T A[36], T b[6]) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+#pragma unroll
+        for (int s = r; s < 6; ++s) A[6 * r + s] += dot(g[r], g[s]);
+        b[r] += (vol * d0) * T(Rule<Q_PRISM6>::phi(Q, r));
     }
 }
 

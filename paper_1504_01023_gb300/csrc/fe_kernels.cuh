@@ -160,12 +160,18 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 V3<T> g[6], cz;
-                const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
+                // float Laplace form: gradients carry sqrt(vol), see prism_point
+                constexpr bool kSqrtVol = PREC == MIXED && KIND == POISSON;
+                const T w = T(Rule<Q_PRISM6>::w(3 * l + t));
+                const T det = prism_point<T, kSqrtVol>(f, cx, cy, a3, l, t, g, cz, w);
                 if (PREC == MIXED) poor |= prism_poor(static_cast<float>(fxy), to_float(cz), static_cast<float>(det));
                 if (PREC == FP64) degenerate |= !(fabs(static_cast<double>(det)) > 1e-300);
                 neg |= det < T(0);
-                const T vol = abs_t(det) * T(Rule<Q_PRISM6>::w(3 * l + t));
-                update_point(3 * l + t, g, vol, c, A, b);
+                const T vol = abs_t(det) * w;
+                if (kSqrtVol)
+                    update_point_scaled(3 * l + t, g, vol, c, A, b);
+                else
+                    update_point(3 * l + t, g, vol, c, A, b);
             }
         }
         if (KIND == POISSON) mirror(A);
@@ -254,6 +260,19 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             case 3: upd<3>(g, vol, c, A, b); break;
             case 4: upd<4>(g, vol, c, A, b); break;
             default: upd<5>(g, vol, c, A, b); break;
+        }
+    }
+    // Laplace update from sqrt(vol)-scaled gradients (point index constant after unrolling)
+    template <class CS>
+    __device__ __forceinline__ static void update_point_scaled(int q, const V3<T> g[6], T vol, const CS &c, T A[36],
+                                                               T b[6]) {
+        switch (q) {
+            case 0: prism_poisson_update_scaled<T, 0>(g, vol, c(CPQ ? 0 : 0), A, b); break;
+            case 1: prism_poisson_update_scaled<T, 1>(g, vol, c(CPQ ? 1 : 0), A, b); break;
+            case 2: prism_poisson_update_scaled<T, 2>(g, vol, c(CPQ ? 2 : 0), A, b); break;
+            case 3: prism_poisson_update_scaled<T, 3>(g, vol, c(CPQ ? 3 : 0), A, b); break;
+            case 4: prism_poisson_update_scaled<T, 4>(g, vol, c(CPQ ? 4 : 0), A, b); break;
+            default: prism_poisson_update_scaled<T, 5>(g, vol, c(CPQ ? 5 : 0), A, b); break;
         }
     }
     template <int Q, class CS>
