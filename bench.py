@@ -183,25 +183,29 @@ def ncu_traffic(kernel_tag: str):
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(mesh, coefs, target_s=10.0, max_elems=None):
-    """The FP64 oracle as it stands, on all host cores, over the first S elements
-    of the workload (S calibrated for ~target_s of CPU work)."""
+def cpu_baseline(mesh, coefs, target_s=10.0):
+    """The FP64 oracle as it stands, on all host cores, over repeated passes of the
+    workload's elements (a bounded sample of about target_s seconds of CPU work:
+    whole passes while they fit, then a leading part of one more)."""
     import oracle
     cores = os.cpu_count() or 1
     c = coefs.astype(np.float32).astype(np.float64)
-    probe = min(len(mesh), 50_000)
+    n = len(mesh)
+    probe = min(n, 50_000)
     t = time.perf_counter()
     oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:probe], c[:probe], n_threads=cores)
-    dt = time.perf_counter() - t
-    s = int(min(len(mesh), max(probe, probe * target_s / max(dt, 1e-6))))
-    if max_elems:
-        s = min(s, max_elems)
+    rate = probe / max(time.perf_counter() - t, 1e-6)
+    total = int(min(max(probe, rate * target_s), 50 * n))
+    done = 0
     t = time.perf_counter()
-    oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:s], c[:s], n_threads=cores)
+    while done < total:
+        m = min(n, total - done)
+        oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:m], c[:m], n_threads=cores)
+        done += m
     dt = time.perf_counter() - t
-    return {"value": s / dt / 1e6, "unit": "Melem/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {s:,} of {N_ELEM:,} elements of the workload, one pass, FP64, OpenMP over elements",
-            "seconds": dt}
+    return {"value": done / dt / 1e6, "unit": "Melem/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done:,} element integrations ({done / n:.2f} passes over the {n:,}-element workload), FP64, "
+                      f"OpenMP over elements", "seconds": dt}
 
 
 def run_reference(args):
@@ -454,7 +458,10 @@ def e2e(ctx, api, mesh, coefs, args):
     bi = Xh.numel() * 8 + Ch.numel() * 4
     bo = out[0].numel() * 4 + out[1].numel() * 4 + out[2].numel()
     return {"value": n / dt / 1e6, "unit": "Melem/s", "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
-            "ms_per_step": dt * 1e3, "steps": reps}
+            "ms_per_step": dt * 1e3, "steps": reps,
+            "path": "pinned host buffers through fe_integrate_tet (FE_MEM_HOST): the kernels read the inputs and write "
+                    "the outputs in host memory over the host link, no staging copies; the call returns when the "
+                    "outputs are in host memory"}
 
 
 # ---------------------------------------------------------------------------

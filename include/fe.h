@@ -160,9 +160,11 @@ const char *fe_last_error(fe_ctx *ctx);
  * are formed once per element) / n_elem prisms (Algorithm 2, QSS_geo_generic:
  * the Jacobian terms are formed at each integration point).
  * Quadrature: tet FE_QUAD_TET1 or FE_QUAD_TET4; prism FE_QUAD_PRISM6.
- * With memory = FE_MEM_HOST (inputs) and/or FE_MEM_HOST (outputs) the call copies
- * through device staging buffers of the context in chunks, overlapping the copies
- * with the kernels, and returns once the outputs are in host memory.
+ * With memory = FE_MEM_HOST (inputs and/or outputs) the call returns once the
+ * outputs are in host memory. If every host buffer is pinned (page-locked and
+ * mapped), the kernels read and write it in place over the host link (no
+ * copies); otherwise the call copies through device staging buffers of the
+ * context in chunks, overlapping the copies with the kernels.
  * Errors: FE_ERR_INVALID_ARG (null or misaligned pointer, stride < n_elem, quad
  * not valid for the type), FE_ERR_OOM (staging or scratch growth failed),
  * FE_ERR_CUDA. n_elem = 0 is valid and does nothing.

@@ -365,6 +365,41 @@ static fe_status host_pipeline(fe_ctx *ctx, fe_elem_type type, const fe_elem_arg
     return st;
 }
 
+// Device address of pinned (page-locked, mapped) host memory, or null for
+// pageable memory. Through NVLink-C2C (or PCIe) the kernels can then read and
+// write the host buffers directly, with no staging copies.
+static const void *mapped_host(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Host buffers that are all pinned: one launch on the mapped addresses, then wait.
+static bool zero_copy(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, cudaStream_t s,
+                      fe_status &st) {
+    fe_elem_args da = *a;
+    fe_out dout = *o;
+    if (a->memory == FE_MEM_HOST) {
+        da.coords = static_cast<const double *>(mapped_host(a->coords));
+        da.coefs = mapped_host(a->coefs);
+        if (!da.coords || !da.coefs) return false;
+        da.memory = FE_MEM_DEVICE;
+    }
+    if (o->memory == FE_MEM_HOST) {
+        dout.A = const_cast<void *>(mapped_host(o->A));
+        dout.b = const_cast<void *>(mapped_host(o->b));
+        dout.flags = o->flags ? static_cast<uint8_t *>(const_cast<void *>(mapped_host(o->flags))) : nullptr;
+        if (!dout.A || !dout.b || (o->flags && !dout.flags)) return false;
+        dout.memory = FE_MEM_DEVICE;
+    }
+    st = launch_set(ctx, type, &da, &dout, ctx->scratch, s);
+    if (st == FE_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "zero-copy integration");
+    return true;
+}
+
 static fe_status integrate(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, void *stream) {
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
     fe_status st = fe_check_args(type, a, o);
@@ -376,7 +411,11 @@ static fe_status integrate(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a
     if (a->n_elem == 0) return FE_OK;
     cudaSetDevice(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (a->memory == FE_MEM_HOST || o->memory == FE_MEM_HOST) return host_pipeline(ctx, type, a, o, s);
+    if (a->memory == FE_MEM_HOST || o->memory == FE_MEM_HOST) {
+        fe_status zst = FE_OK;
+        if (zero_copy(ctx, type, a, o, s, zst)) return zst;
+        return host_pipeline(ctx, type, a, o, s);   // pageable memory: chunked, staged copies
+    }
     if (ctx->autotune && !ctx->shapes.count(shape_key(type, a, o))) {
         st = fe_tune(ctx, type, a, o, stream);
         if (st != FE_OK) return st;

@@ -140,12 +140,25 @@ def test_sliver_stress_mixed(ctx, fraction):
     assert flagged.sum() >= 0.5 * len(sl)
 
 
-def test_host_buffers_match_device_path(ctx):
-    mesh, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, n=5000, seed=8)
-    Ad, bd, fd, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, api.FP32_MIXED, api.SOA, api.SOA, mesh, c)
-    Ah, bh, fh, _ = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, api.FP32_MIXED, api.SOA, api.SOA, mesh, c,
-                            device=None)
-    assert np.array_equal(Ad, Ah) and np.array_equal(bd, bh) and np.array_equal(fd, fh)
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("lay", [api.SOA, api.AOS])
+def test_host_buffers_match_device_path(ctx, pinned, lay):
+    """Host buffers: pinned ones are read and written in place (zero copy),
+    pageable ones go through the chunked staging pipeline (n > one chunk)."""
+    n = 2_200_000 if not pinned else 5000
+    mesh = meshgen.tet_cube_mesh(72, seed=8)[:n]
+    _, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh=mesh, seed=8)
+    from helpers import to_device_inputs
+    Xd, Cd, _ = to_device_inputs(api.TET, mesh, c, api.FP32_MIXED, lay)
+    Xh, Ch = Xd.cpu(), Cd.cpu()
+    if pinned:
+        Xh, Ch = Xh.pin_memory(), Ch.pin_memory()
+    rd = ctx.integrate(api.TET, Xd, Cd, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP32_MIXED, lay, lay)
+    ctx.sync()
+    outh = api.alloc_out(api.TET, n, api.FP32_MIXED, lay, "cpu", True, pin=pinned)
+    rh = ctx.integrate(api.TET, Xh, Ch, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP32_MIXED, lay, lay, out=outh)
+    for td, th in zip(rd, rh):
+        assert torch.equal(td.cpu(), th)
 
 
 def test_autotune_keeps_results(ctx):
