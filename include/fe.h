@@ -257,6 +257,13 @@ fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket);
    count the kernels in the graph). */
 uint64_t fe_launch_count(void);
 
+/* Failure-detection self-test (no counterpart in the paper): launches one block
+   whose bounded wait on a bulk-copy barrier cannot complete (no copy is issued),
+   with `polls` poll iterations (1..2^22, about 0.3 us each), then reports the
+   device status like fe_ctx_sync. Expected: FE_ERR_TIMEOUT, after which the
+   context remains usable; any other result means the detection is broken. */
+fe_status fe_selftest_bounded_wait(fe_ctx *ctx, unsigned polls, void *stream);
+
 /* Profiling: when on, the integration calls record CUDA events around their main
    kernel on the launching stream; fe_ctx_kernel_time returns the summed device
    time in ms and the launch count since the last reset (it synchronises). */

@@ -94,6 +94,7 @@ _SIGS = [
     ("fe_get_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("fe_integrate_tet_noalloc", ctypes.c_int, [ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
+    ("fe_selftest_bounded_wait", ctypes.c_int, [_P, ctypes.c_uint, _P]),
     ("fe_set_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), ctypes.c_int,
                                     ctypes.c_int]),
 ]
@@ -323,6 +324,10 @@ class Context:
         _check(load().fe_get_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), ctypes.byref(blk),
                                    ctypes.byref(pers)), self.h)
         return blk.value, pers.value
+
+    def selftest_bounded_wait(self, polls: int = 1 << 16) -> int:
+        """Run the failure-detection self-test; returns the status (FE_ERR_TIMEOUT expected)."""
+        return int(load().fe_selftest_bounded_wait(self.h, polls, self._stream(None, True)))
 
     def set_profiling(self, on: bool):
         _check(load().fe_ctx_set_profiling(self.h, int(on)), self.h)

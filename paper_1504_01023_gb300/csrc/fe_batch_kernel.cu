@@ -146,4 +146,22 @@ const void *kernel_batch(int combo) {
 }
 const void *kernel_batch_fixup() { return reinterpret_cast<const void *>(&batch_fixup_kernel); }
 
+// Failure-detection self-test: one block arms its mbarrier for 16 bytes that no
+// copy will ever deliver and waits with the same bounded loop as the tiles. The
+// wait must give up after `polls` polls and record the timeout in the status
+// word; nothing is in flight when the block exits.
+__global__ void selftest_wait_kernel(unsigned polls, int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0, status, polls);
+}
+
+const void *kernel_selftest_wait() { return reinterpret_cast<const void *>(&selftest_wait_kernel); }
+
 }  // namespace fe

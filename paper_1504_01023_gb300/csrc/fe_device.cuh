@@ -132,8 +132,9 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // Bounded wait on an mbarrier phase. Returns false (and sets the status bit) if
 // the copy has not landed after ~2^22 polls with back-off (seconds); callers
 // then skip their work for this block instead of spinning forever.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, int *status) {
-    for (unsigned it = 0; it < (1u << 22); ++it) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, int *status,
+                                                  unsigned polls = 1u << 22) {
+    for (unsigned it = 0; it < polls; ++it) {
         if (mbar_try_wait(bar, phase)) return true;
         if (it > 64) __nanosleep(256);
     }

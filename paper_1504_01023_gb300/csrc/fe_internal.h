@@ -74,6 +74,7 @@ inline int batch_combo(int type, int kind, int quad, int cpq) {
 }
 const void *kernel_batch(int combo);   // persistent kernel of one combination
 const void *kernel_batch_fixup();
+const void *kernel_selftest_wait();
 constexpr int kCombos = 12;
 // Dynamic shared memory of one block of the batched kernel for a combination.
 long long batch_smem_bytes(int combo, int block);

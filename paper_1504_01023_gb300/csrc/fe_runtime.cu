@@ -597,6 +597,19 @@ fe_status fe_integrate_prism(fe_ctx *ctx, const fe_elem_args *args, const fe_out
 
 uint64_t fe_launch_count(void) { return g_launches.load(); }
 
+fe_status fe_selftest_bounded_wait(fe_ctx *ctx, unsigned polls, void *stream) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    if (polls == 0 || polls > (1u << 22)) return set_error(ctx, FE_ERR_INVALID_ARG, "polls must be in [1, 2^22]");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *status = ctx->scratch.status;
+    void *args[] = {&polls, &status};
+    cudaError_t e = cudaLaunchKernel(kernel_selftest_wait(), dim3(1), dim3(32), args, 0, s);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(selftest)");
+    g_launches.fetch_add(1);
+    return fe_ctx_sync(ctx);
+}
+
 fe_status fe_ctx_set_profiling(fe_ctx *ctx, int on) {
     if (!ctx) return FE_ERR_INVALID_ARG;
     ctx->profiling = on != 0;

@@ -185,3 +185,15 @@ def test_profiling_records_kernel_time(ctx):
     ctx.set_profiling(False)
     assert k == 3 and ms > 0
     assert api.launch_count() - n0 == 6          # main + fix-up per call
+
+
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    """A bulk-copy wait that can never complete gives up after its poll limit and
+    reports FE_ERR_TIMEOUT; the context then integrates normally."""
+    st = ctx.selftest_bounded_wait(1 << 14)
+    assert st == -5
+    mesh, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, n=500, seed=21)
+    An, bn, fn, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, api.FP32_MIXED, api.AOS, api.AOS, mesh, c)
+    Ar, br, _ = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh, cu)
+    ea, eb = max_errors(An, bn, Ar, br)
+    assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED]
