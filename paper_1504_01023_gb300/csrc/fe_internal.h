@@ -34,6 +34,13 @@ struct ElemParams {
     unsigned int fix_cap;
     unsigned int item;             // batch item id (0 for a plain call)
     int *status;                   // device status word
+    int tma_in, tma_out;           // SOA tiles moved by 2-D tensor copies (maps in TmaMaps)
+};
+
+// Tensor-copy descriptors (CUtensorMap, 128 bytes each) of the plane-major
+// inputs and outputs of one launch: coordinates, coefficients, A, b.
+struct alignas(64) TmaMaps {
+    unsigned char x[128], c[128], a[128], b[128];
 };
 
 // Compile-time configuration of one element kernel.

@@ -440,7 +440,7 @@ __device__ __forceinline__ void stage_rows_out(T *g, int64_t gpitch, const T *s,
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
 __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, int nb, unsigned char *smem, uint64_t *bar,
-                                             unsigned &phase) {
+                                             unsigned &phase, const TmaMaps *tm = nullptr) {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
     using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ>;
@@ -459,7 +459,21 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     const bool active = tid < nb;
 
     // ---- stage inputs ----
-    {
+    if (INL == SOA && tm && p.tma_in) {
+        // two tensor copies: coordinate planes and coefficient planes of the tile
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, unsigned(B) * NX * 8u + unsigned(B) * NC * unsigned(sizeof(CT)));
+            tma_load_2d(sX, tm->x, int(e0), 0, bar);
+            tma_load_2d(sC, tm->c, int(e0), 0, bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, phase, p.status);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            mbar_wait_bounded(bar, phase ^ 1u, nullptr);
+            return false;
+        }
+    } else {
         // alignment of bases and SOA plane pitches, then of this tile's byte counts
         const bool x_ok = aligned16(X, INL == SOA ? uint64_t(p.xs) * 8 : 0);
         const bool c_ok = aligned16(C, INL == SOA ? uint64_t(p.cs) * sizeof(CT) : 0);
@@ -519,7 +533,14 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     // ---- store outputs ----
     fence_proxy_async_smem();
     __syncthreads();
-    {
+    if (OUTL == SOA && tm && p.tma_out) {
+        if (tid == 0) {
+            tma_store_2d(tm->a, int(e0), 0, sA);
+            tma_store_2d(tm->b, int(e0), 0, sB);
+            bulk_commit();
+            bulk_wait_read0();
+        }
+    } else {
         const bool a_ok = aligned16(Aout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
         const bool b_ok = aligned16(Bout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
         const bool tA = a_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NA) * sizeof(CT)) % 16 == 0);
@@ -545,7 +566,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
 __global__ void __launch_bounds__(ET == TET ? 512 : 256)
-    elem_kernel(const ElemParams p) {
+    elem_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) {
@@ -559,7 +580,7 @@ __global__ void __launch_bounds__(ET == TET ? 512 : 256)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
-        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase)) return;
+        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase, &tm)) return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }

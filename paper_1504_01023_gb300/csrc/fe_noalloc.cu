@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -124,13 +125,16 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
     p.fix_cap = static_cast<unsigned>(kListCap);
     p.item = 0;
     p.status = status;
-    void *kargs[] = {&p};
+    TmaMaps no_maps;                                  // plane copies stay per-plane bulk copies here
+    memset(&no_maps, 0, sizeof no_maps);
+    void *kargs[] = {&p, &no_maps};
     const int64_t grid = (args->n_elem + B - 1) / B;
     ce = cudaLaunchKernel(k, dim3(unsigned(grid)), dim3(B), kargs, size_t(smem), strm);
     if (ce != cudaSuccess) return cuda_check(nullptr, ce, "cudaLaunchKernel(elem, no-alloc)");
     g_launches.fetch_add(1, std::memory_order_relaxed);
     int64_t fgrid = std::min<int64_t>((args->n_elem + 255) / 256, int64_t(s->sms) * 4);
-    ce = cudaLaunchKernel(fk, dim3(unsigned(fgrid < 1 ? 1 : fgrid)), dim3(256), kargs, 0, strm);
+    void *fargs[] = {&p};
+    ce = cudaLaunchKernel(fk, dim3(unsigned(fgrid < 1 ? 1 : fgrid)), dim3(256), fargs, 0, strm);
     if (ce != cudaSuccess) return cuda_check(nullptr, ce, "cudaLaunchKernel(fixup, no-alloc)");
     g_launches.fetch_add(1, std::memory_order_relaxed);
 

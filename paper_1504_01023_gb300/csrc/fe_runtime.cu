@@ -7,7 +7,10 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <mutex>
 #include <sstream>
+
+#include <cudaTypedefs.h>
 
 #include "fe_runtime.h"
 
@@ -132,6 +135,47 @@ static cudaEvent_t pool_event(fe_ctx *ctx) {
     return e;
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-copy descriptors for plane-major (SOA) tiles.
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Planes of `n` elements (`planes` of them, `pitch` bytes apart) as a 2-D tensor
+// with box (box_n elements, all planes). False if the layout does not meet the
+// tensor-copy rules (16-byte aligned base and pitch, box rows of 16-byte multiples,
+// at most 256 elements and 256 planes per box, coordinates within 31 bits).
+static bool encode_planes(void *out, bool dbl, const void *base, uint64_t n, uint64_t planes, uint64_t pitch,
+                          uint32_t box_n) {
+    auto enc = tensor_map_encoder();
+    const uint32_t elt = dbl ? 8 : 4;
+    if (!enc || !base || n == 0 || n >= (1ull << 31) || planes == 0 || planes > 256 || box_n > 256 ||
+        (uint64_t(box_n) * elt) % 16 || reinterpret_cast<uintptr_t>(base) % 16)
+        return false;
+    if (planes == 1) pitch = (n * elt + 15) / 16 * 16;
+    if (pitch % 16 || pitch < n * elt) return false;
+    const cuuint64_t dims[2] = {n, planes};
+    const cuuint64_t strides[1] = {pitch};
+    const cuuint32_t box[2] = {box_n, uint32_t(planes)};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap *>(out), dbl ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, Scratch &s, cudaStream_t st,
                      const Shape *force) {
     if (a->n_elem == 0) return FE_OK;
@@ -187,7 +231,22 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     }
     p.status = s.status;
 
-    void *args[] = {&p};
+    // plane-major tiles of up to 256 elements move as 2-D tensor copies
+    TmaMaps tm;
+    memset(&tm, 0, sizeof tm);
+    if (sh.block <= 256) {
+        const int ns = ns_of(type), nc = nc_of(a);
+        const bool dbl = a->prec == FE_FP64;
+        const uint64_t cs = dbl ? 8 : 4;
+        if (a->coords_layout == FE_LAYOUT_SOA)
+            p.tma_in = encode_planes(tm.x, true, a->coords, uint64_t(a->n_elem), 3 * ns, uint64_t(p.xs) * 8, sh.block) &&
+                       encode_planes(tm.c, dbl, a->coefs, uint64_t(a->n_elem), nc, uint64_t(p.cs) * cs, sh.block);
+        if (o->layout == FE_LAYOUT_SOA)
+            p.tma_out = encode_planes(tm.a, dbl, o->A, uint64_t(a->n_elem), ns * ns, uint64_t(p.os) * cs, sh.block) &&
+                        encode_planes(tm.b, dbl, o->b, uint64_t(a->n_elem), ns, uint64_t(p.os) * cs, sh.block);
+    }
+
+    void *args[] = {&p, &tm};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool profile = ctx->profiling && !force;
     if (profile) {
@@ -213,7 +272,8 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     if (mixed) {
         const void *fk = fix_kernel(type, a, outl);
         const int64_t fgrid = std::min<int64_t>((a->n_elem + 255) / 256, int64_t(ctx->sms) * 4);
-        ce = cudaLaunchKernel(fk, dim3(unsigned(std::max<int64_t>(fgrid, 1))), dim3(256), args, 0, st);
+        void *fargs[] = {&p};
+        ce = cudaLaunchKernel(fk, dim3(unsigned(std::max<int64_t>(fgrid, 1))), dim3(256), fargs, 0, st);
         if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaLaunchKernel(fixup)");
         g_launches.fetch_add(1, std::memory_order_relaxed);
     }

@@ -197,3 +197,28 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
     Ar, br, _ = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh, cu)
     ea, eb = max_errors(An, bn, Ar, br)
     assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED]
+
+
+SOA_TMA_CASES = list(itertools.product([api.TET, api.PRISM], [api.POISSON, api.GENERIC], [0, 1],
+                                       [api.FP64, api.FP32_MIXED]))
+
+
+@pytest.mark.parametrize("et,kind,cpq,prec", SOA_TMA_CASES, ids=["t%d-k%d-c%d-p%d" % c for c in SOA_TMA_CASES])
+def test_plane_major_tensor_copy_path(ctx, et, kind, cpq, prec):
+    """n = 3000: every plane pitch is a 16-byte multiple, so plane-major tiles move
+    as 2-D tensor copies (the n = 2999 cases above take the per-plane fallback);
+    3000 = 46 x 64 + 56 leaves a ragged last tile (zero-filled loads, clipped stores)."""
+    quad = api.QUAD_TET4 if et == api.TET else api.QUAD_PRISM6
+    mesh, c = make_inputs(et, kind, quad, cpq, n=3000, seed=31)
+    for shape in [(64, 0), (256, 1)]:
+        from helpers import to_device_inputs, gpu_outputs_to_numpy
+        X, C, cu = to_device_inputs(et, mesh, c, prec, api.SOA)
+        cm = api.PER_QPOINT if cpq else api.PER_ELEMENT
+        ctx.set_shape(shape[0], shape[1], et, X, C, kind, quad, cm, prec, api.SOA, api.SOA)
+        A, b, f = ctx.integrate(et, X, C, kind, quad, cm, prec, api.SOA, api.SOA)
+        ctx.sync()
+        An, bn, fn = gpu_outputs_to_numpy(et, A, b, f, api.SOA)
+        Ar, br, fr = run_oracle(et, kind, quad, cpq, mesh, cu)
+        ea, eb = max_errors(An, bn, Ar, br)
+        assert ea <= TOL[prec] and eb <= TOL[prec], (shape, ea, eb)
+        assert (fn == fr).all()
