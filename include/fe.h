@@ -65,8 +65,16 @@ typedef enum fe_problem { FE_POISSON = 0, FE_GENERIC = 1 } fe_problem;
    exactly enough in single precision, the coefficient and shape-derivative
    arithmetic and accumulation run in float, coefficients and outputs are float.
    Elements that fail a mean-ratio shape test (quality < 0.1) get their Jacobian,
-   determinant and inverse in double (flag bit 0). */
-typedef enum fe_precision { FE_FP64 = 0, FE_FP32_MIXED = 1 } fe_precision;
+   determinant and inverse in double (flag bit 0).
+   FE_FP64_DW: double inputs and outputs and double accuracy (the FE_FP64
+   tolerance), computed in double-word arithmetic (pairs of floats, about 48
+   significant bits) on the float pipes, with the edge vectors x_k - x_0 formed in
+   double. Elements that fail the shape test above, or whose |det J|, inputs or
+   results leave the double-word window (|det J| in [2^-60, 2^60], nonzero
+   coefficients in [2^-50, 2^51), the sum of |A^e| and of |b^e| zero or in
+   [2^-90, 2^100]), are computed entirely in double (flag bit 0). The paper has
+   no counterpart: its double-precision form is FE_FP64. */
+typedef enum fe_precision { FE_FP64 = 0, FE_FP32_MIXED = 1, FE_FP64_DW = 2 } fe_precision;
 
 /* Gaussian rules (Sec. 2.3; the paper names no points, these are the readings):
    TET1   centroid, weight 1/6 (degree 1);
@@ -105,7 +113,7 @@ typedef struct fe_ctx_config {
  * coords (double, always): NS = 4 (tet) or 6 (prism) vertices x 3 coordinates.
  *   SOA: scalar j = 3*v + d lives at coords[j*coords_stride + e].
  *   AOS: coords[(e*NS + v)*3 + d].
- * coefs (double for FE_FP64, float for FE_FP32_MIXED), NC scalars per element:
+ * coefs (double for FE_FP64 and FE_FP64_DW, float for FE_FP32_MIXED), NC scalars per element:
  *   FE_GENERIC: 20 per point (C[4][4] row-major, then D[4]); FE_POISSON: 1 per
  *   point (d^0). NC = that count times NQ for FE_COEF_PER_QPOINT (point-major:
  *   scalar j = q*per_point + k), times 1 for FE_COEF_PER_ELEMENT.
@@ -129,7 +137,7 @@ typedef struct fe_elem_args {
 
 /*
  * Outputs (Sec. 4.2, Fig. 2): A^e full NS x NS (not symmetric-packed), row-major
- * entry k = r*NS + s; b^e NS entries. Element type: double (FE_FP64) or float.
+ * entry k = r*NS + s; b^e NS entries. Element type: double (FE_FP64, FE_FP64_DW) or float.
  *   SOA ("coalesced"): A[k*stride + e], b[r*stride + e].
  *   AOS (element-contiguous): A[e*NS*NS + k], b[e*NS + r].
  * flags (optional, may be NULL): one byte per element, bit 0 = the double
@@ -217,10 +225,10 @@ fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
  * scheduler thread admits them in arrival order while the resident meshes plus
  * the outputs of admitted, unreleased requests fit the HBM budget, merges every
  * admitted mixed-precision request into one batched launch (continuous
- * batching), runs FE_FP64 requests as their own launches, and keeps up to
+ * batching), runs FE_FP64 and FE_FP64_DW requests as their own launches, and keeps up to
  * serve_slots launches in flight on separate streams, so requests that arrive
  * while others run overlap with them on the device. coefs is a device pointer,
- * element-contiguous (AOS), float for FE_FP32_MIXED and double for FE_FP64. The
+ * element-contiguous (AOS), float for FE_FP32_MIXED and double otherwise. The
  * outputs are context-owned element-contiguous device buffers, valid until
  * fe_serve_release.
  */

@@ -19,7 +19,7 @@ from . import build as _build
 FE_OK, FE_NOT_READY = 0, 1
 TET, PRISM = 0, 1
 POISSON, GENERIC = 0, 1
-FP64, FP32_MIXED = 0, 1
+FP64, FP32_MIXED, FP64_DW = 0, 1, 2
 QUAD_TET1, QUAD_TET4, QUAD_PRISM6 = 0, 1, 2
 PER_ELEMENT, PER_QPOINT = 0, 1
 SOA, AOS = 0, 1
@@ -169,7 +169,7 @@ def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout):
         a.coords_stride = 0
         a.coefs_stride = 0
     assert coords.dtype == torch.float64
-    want = torch.float64 if prec == FP64 else torch.float32
+    want = torch.float32 if prec == FP32_MIXED else torch.float64
     assert coefs.dtype == want, f"coefficients must be {want}"
     a.n_elem = n
     a.coords = coords.data_ptr()
@@ -183,7 +183,7 @@ def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout):
 
 def alloc_out(elem_type, n, prec, out_layout, device, with_flags=True, pin=False):
     ns = NS[elem_type]
-    dt = torch.float64 if prec == FP64 else torch.float32
+    dt = torch.float32 if prec == FP32_MIXED else torch.float64
     kw = dict(dtype=dt, device=device)
     if out_layout == SOA:
         # A and b share one plane stride: one (NS*NS + NS, n) buffer
@@ -365,7 +365,7 @@ class Context:
     def serve_result_tensors(self, ticket, res):
         """(A [n,NS,NS], b [n,NS], flags [n]) views of a finished request's outputs."""
         prec = self._keep[ticket][1]
-        dt = torch.float64 if prec == FP64 else torch.float32
+        dt = torch.float32 if prec == FP32_MIXED else torch.float64
         ns, n = NS[res.type], res.n_elem
         return (device_view(res.A, (n, ns, ns), dt, self.device), device_view(res.b, (n, ns), dt, self.device),
                 device_view(res.flags, (n,), torch.uint8, self.device))

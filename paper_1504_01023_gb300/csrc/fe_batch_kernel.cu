@@ -36,7 +36,7 @@ __device__ __forceinline__ bool tile_combo(const BatchItemDev *item, const Batch
 
 template <int ID> __device__ __forceinline__ void fix_combo(const ElemParams &p, int64_t e) {
     using K = ComboCfg<ID>;
-    fixup_element<K::et, K::kind, K::quad, K::cpq, AOS, AOS>(p, e);
+    fixup_element<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, e);
 }
 
 // Persistent kernel of one combination: blocks take the next tile of this

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "fe_dword.cuh"
 #include "fe_internal.h"
 
 namespace fe {
@@ -81,6 +82,7 @@ template <class T> struct V3 {
 template <class T> __device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 template <class T> __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 template <class T> __device__ __forceinline__ V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class T> __device__ __forceinline__ V3<T> operator-(V3<T> a) { return {-a.x, -a.y, -a.z}; }
 template <class T> __device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 template <class T> __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
@@ -446,6 +448,7 @@ template <class T> __device__ __forceinline__ PrismFrame<T> prism_frame(const V3
 // division.
 __device__ __forceinline__ double recip_fast(double v) { return 1.0 / v; }
 __device__ __forceinline__ float recip_fast(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ DW recip_fast(DW v) { return dw_recip(v); }
 
 // Global gradients at point (l, t) of PRISM6. Returns det J. With SQRTVOL the
 // gradients come out multiplied by sqrt(vol), vol = |det J| w (then the Laplace
@@ -454,19 +457,21 @@ template <class T, bool SQRTVOL = false>
 __device__ __forceinline__ T prism_point(const PrismFrame<T> &f, V3<T> cx, V3<T> cy, V3<T> a3, int l, int t, V3<T> g[6],
                                          V3<T> &cz_out, T w = T(0)) {
     using R = Rule<Q_PRISM6>;
-    const T h0 = T(0.5 * R::lam(t, 0)), h1 = T(0.5 * R::lam(t, 1)), h2 = T(0.5 * R::lam(t, 2));
+    // lambda_k / 2 at triangle point t (t may be a run-time index): 1/3 or 1/12
+    const T h0 = t == 0 ? T(1.0 / 3.0) : T(1.0 / 12.0), h1 = t == 1 ? T(1.0 / 3.0) : T(1.0 / 12.0),
+            h2 = t == 2 ? T(1.0 / 3.0) : T(1.0 / 12.0);
     const V3<T> cz = h0 * f.w0 + h1 * f.w1 + h2 * f.w2;
     const V3<T> a1 = cross(cy, cz);
     const V3<T> a2 = cross(cz, cx);
     const T det = dot(cx, a1);
     T inv = recip_fast(det);
-    if (SQRTVOL) inv *= sqrt((det < T(0) ? -det : det) * w);
+    if constexpr (SQRTVOL) inv *= sqrt((det < T(0) ? -det : det) * w);
     const V3<T> r1 = inv * a1, r2 = inv * a2, r3 = inv * a3;
-    const V3<T> P[3] = {T(-1) * (r1 + r2), r1, r2};
+    const V3<T> P[3] = {-(r1 + r2), r1, r2};
     const T zb = T(R::zb(l)), zt = T(R::zt(l));
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const T hl = T(0.5 * R::lam(t, k));
+        const T hl = k == 0 ? h0 : (k == 1 ? h1 : h2);
         g[k] = zb * P[k] - hl * r3;
         g[k + 3] = zt * P[k] + hl * r3;
     }

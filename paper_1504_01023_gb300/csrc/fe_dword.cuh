@@ -1,0 +1,155 @@
+// Double-word arithmetic on the float pipes: a value is the unevaluated sum
+// h + l of two floats with |l| < ulp(h) (Dekker, Numer. Math. 18, 1971). Sums
+// use Knuth's TwoSum and Dekker's Fast2Sum; the product takes the exact error of
+// h*h' from the fused multiply-add and the cross terms h*l' + l*h' (the
+// double-word times double-word scheme analysed by Joldes, Muller and Popescu,
+// ACM TOMS 44(2), 2017, without the negligible l*l' term). Each operation has a
+// relative error of a few 2^-48 in the absence of cancellation; under
+// cancellation its absolute error stays a few 2^-48 (|x| + |y|), the same order
+// as the error its inputs already carry.
+//
+// This is what lets the double-precision form run on a GPU whose double pipe
+// issues at 1/64 of the float rate: the element arithmetic is done in double-word,
+// the edge vectors x_k - x_0 in double (a handful of DADDs), and the conversions
+// to and from double with integer operations only.
+//
+// Every step uses the round-to-nearest intrinsics so that the compiler neither
+// contracts a product and a sum into one rounding nor reorders them.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace fe {
+
+struct DW {
+    float h, l;
+    DW() = default;
+    __host__ __device__ constexpr DW(float hh, float ll) : h(hh), l(ll) {}
+    // Constants: the nearest float and the nearest float to the remainder.
+    // Only for values known at compile time (a run-time double would cost
+    // double-pipe conversions).
+    __host__ __device__ explicit constexpr DW(double c)
+        : h(static_cast<float>(c)), l(static_cast<float>(c - static_cast<double>(static_cast<float>(c)))) {}
+    __host__ __device__ explicit constexpr DW(int c) : DW(static_cast<double>(c)) {}
+    __device__ explicit operator float() const { return h; }
+};
+
+// s + e = a + b exactly (Knuth).
+__device__ __forceinline__ DW dw_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float ap = __fadd_rn(s, -b);
+    const float bp = __fadd_rn(s, -ap);
+    return {s, __fadd_rn(__fadd_rn(a, -ap), __fadd_rn(b, -bp))};
+}
+// s + e = a + b exactly when exponent(a) >= exponent(b) (Dekker).
+__device__ __forceinline__ DW dw_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+
+__device__ __forceinline__ DW operator+(DW x, DW y) {
+    const DW s = dw_two_sum(x.h, y.h);
+    return dw_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ DW operator-(DW x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ DW operator-(DW x, DW y) { return x + (-y); }
+__device__ __forceinline__ DW operator*(DW x, DW y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return dw_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DW &operator+=(DW &x, DW y) { return x = x + y; }
+__device__ __forceinline__ DW &operator*=(DW &x, DW y) { return x = x * y; }
+__device__ __forceinline__ bool operator<(DW x, DW y) { return x.h < y.h || (x.h == y.h && x.l < y.l); }
+
+__device__ __forceinline__ DW dw_abs(DW x) { return x.h < 0.0f ? -x : x; }
+
+// 1/x: float reciprocal r, then one Newton step r (1 + e) with e = 1 - x r
+// evaluated by fused multiply-adds (1 - x_h r is exact to float precision of
+// e, as x_h r is within an ulp of 1). Relative error a few 2^-48.
+__device__ __forceinline__ DW dw_recip(DW x) {
+    const float r = __frcp_rn(x.h);
+    float e = __fmaf_rn(-x.h, r, 1.0f);
+    e = __fmaf_rn(-x.l, r, e);
+    return dw_fast_two_sum(r, __fmul_rn(r, e));
+}
+
+// ---------------------------------------------------------------------------
+// double -> double-word with integer operations: h = x truncated to 24
+// significant bits, l = the next 23 bits (relative error below 2^-47). The
+// accepted magnitudes are 2^(ELO-1023) <= |x| < 2^(EHI-1022) (ELO, EHI biased
+// double exponents). Zero stays zero; below the window the value becomes zero
+// (FLUSH) or NaN; above it NaN, so that a value outside the window poisons the
+// element's results and sends it to the double path.
+// ---------------------------------------------------------------------------
+template <unsigned ELO, unsigned EHI, bool FLUSH> __device__ __forceinline__ DW split_dw(double x) {
+    static_assert(ELO >= 920 && EHI <= 1150 && ELO <= EHI, "window outside the float range of h and l");
+    const uint32_t hw = static_cast<uint32_t>(__double2hiint(x));
+    const uint32_t lw = static_cast<uint32_t>(__double2loint(x));
+    const uint32_t sign = hw & 0x80000000u;
+    const uint32_t e = (hw >> 20) & 0x7FFu;
+    const uint32_t frac23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const uint32_t elo = (e - 919u) << 23;  // float 2^(E-23)
+    // 2^(E-23) (1 + next23 / 2^23) - 2^(E-23): exact (Sterbenz)
+    const float lo_mag = __fadd_rn(__uint_as_float(elo | ((lw >> 6) & 0x7FFFFFu)), -__uint_as_float(elo));
+    const bool in = (e - ELO) <= (EHI - ELO);
+    const bool zero = FLUSH ? e < ELO : ((hw & 0x7FFFFFFFu) | lw) == 0u;
+    DW r;
+    r.h = in ? __uint_as_float(sign | ((e - 896u) << 23) | frac23) : (zero ? 0.0f : __uint_as_float(0x7FC00000u));
+    r.l = in ? __uint_as_float(__float_as_uint(lo_mag) | sign) : 0.0f;
+    return r;
+}
+
+// Windows of the double-word form. Edge components: |e| < 2^64, tiny ones
+// (< 2^-100) flushed to zero. Coefficients: 2^-50 <= |c| < 2^51 or exactly 0.
+constexpr unsigned kDwEdgeLo = 923, kDwEdgeHi = 1086;
+constexpr unsigned kDwCoefLo = 973, kDwCoefHi = 1073;
+__device__ __forceinline__ DW dw_edge(double d) { return split_dw<kDwEdgeLo, kDwEdgeHi, true>(d); }
+__device__ __forceinline__ DW dw_coef(double c) { return split_dw<kDwCoefLo, kDwCoefHi, false>(c); }
+
+// |det J| of a double-word element must lie in [2^-60, 2^60]: with the shape test
+// passed this keeps every intermediate (edge products up to h^4, 1/det, the
+// coefficient products) well inside the normal float range of both words.
+__device__ __forceinline__ bool dw_det_ok(float det_h) {
+    const float a = fabsf(det_h);
+    return a >= 0x1p-60f && a <= 0x1p60f;
+}
+
+// A group of results (A^e or b^e) is accepted when all are finite and the sum of
+// their magnitudes is zero or in [2^-90, 2^100], so that the low words of the
+// entries that carry the group's norm are normal floats.
+template <int N> __device__ __forceinline__ bool dw_group_ok(const DW *v) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) s = __fadd_rn(s, fabsf(v[k].h));
+    return s == 0.0f || (s >= 0x1p-90f && s <= 0x1p100f);
+}
+
+// ---------------------------------------------------------------------------
+// double-word -> double with integer operations: the double of h is exact (bit
+// re-biasing), and l is added as an integer count k of ulps of that double,
+// k = trunc(l / ulp), |k| < 2^30 (error below one ulp of the result). When h
+// is a power of two and l has the opposite sign the result lies in the binade
+// below, whose ulp is half as large. Zero stays zero; a non-finite h gives NaN.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dw_to_double(DW v) {
+    const DW n = dw_two_sum(v.h, v.l);  // |l| <= ulp(h) / 2
+    const uint32_t bh = __float_as_uint(n.h), bl = __float_as_uint(n.l);
+    const uint32_t eh = (bh >> 23) & 0xFFu, mh = bh & 0x7FFFFFu, sh = bh & 0x80000000u;
+    const uint32_t el = (bl >> 23) & 0xFFu;
+    const uint32_t whi = eh ? (sh | ((eh + 896u) << 20) | (mh >> 3)) : sh;
+    const uint32_t wlo = eh ? (mh << 29) : 0u;
+    const bool down = mh == 0u && ((bl ^ bh) & 0x80000000u) != 0u;
+    // biased exponent of t = l * 2^(52 - E_h) (one more in the binade below)
+    const int te = int(el) - int(eh) + 179 + (down ? 1 : 0);
+    int k = 0;
+    if (el != 0u && te >= 1) k = __float2int_rz(__uint_as_float((bl & 0x807FFFFFu) | (uint32_t(te) << 23)));
+    // k has l's sign; the bit pattern holds |h|, so negate for negative h
+    const long long d = sh ? -static_cast<long long>(k) : static_cast<long long>(k);
+    const unsigned long long bits = ((static_cast<unsigned long long>(whi) << 32) | wlo) + static_cast<unsigned long long>(d);
+    return eh == 0xFFu ? __longlong_as_double(0x7FF8000000000000ll) : __longlong_as_double(static_cast<long long>(bits));
+}
+
+}  // namespace fe

@@ -6,9 +6,9 @@
 #define FE_ELEM_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                  \
     if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
         return reinterpret_cast<const void *>(&fe::elem_kernel<ET, KD, PREC, QUAD, CP, IL, OL>);
-#define FE_FIX_CASE(ET, QUAD, KD, CP, IL, OL)                                         \
+#define FE_FIX_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                   \
     if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
-        return reinterpret_cast<const void *>(&fe::fixup_kernel<ET, KD, QUAD, CP, IL, OL>);
+        return reinterpret_cast<const void *>(&fe::fixup_kernel<ET, KD, PREC, QUAD, CP, IL, OL>);
 
 #define FE_ALL16(M, ...)                                                              \
     M(__VA_ARGS__, 0, 0, 0, 0) M(__VA_ARGS__, 0, 0, 0, 1) M(__VA_ARGS__, 0, 0, 1, 0)  \
@@ -17,3 +17,9 @@
     M(__VA_ARGS__, 1, 0, 0, 1) M(__VA_ARGS__, 1, 0, 1, 0) M(__VA_ARGS__, 1, 0, 1, 1)  \
     M(__VA_ARGS__, 1, 1, 0, 0) M(__VA_ARGS__, 1, 1, 0, 1) M(__VA_ARGS__, 1, 1, 1, 0)  \
     M(__VA_ARGS__, 1, 1, 1, 1)
+
+// The eight (coefficient mode, input layout, output layout) combinations of one kind.
+#define FE_ALL8(M, KD, ...)                                                           \
+    M(__VA_ARGS__, KD, 0, 0, 0) M(__VA_ARGS__, KD, 0, 0, 1) M(__VA_ARGS__, KD, 0, 1, 0) \
+    M(__VA_ARGS__, KD, 0, 1, 1) M(__VA_ARGS__, KD, 1, 0, 0) M(__VA_ARGS__, KD, 1, 0, 1) \
+    M(__VA_ARGS__, KD, 1, 1, 0) M(__VA_ARGS__, KD, 1, 1, 1)

@@ -7,7 +7,7 @@ namespace fe {
 
 enum ElemType { TET = 0, PRISM = 1 };
 enum Kind { POISSON = 0, GENERIC = 1 };
-enum Prec { FP64 = 0, MIXED = 1 };
+enum Prec { FP64 = 0, MIXED = 1, DWORD = 2 };
 enum Quad { Q_TET1 = 0, Q_TET4 = 1, Q_PRISM6 = 2 };
 enum Layout { SOA = 0, AOS = 1 };
 
@@ -54,11 +54,15 @@ const void *kernel_tet_fp64(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_tet_mixed(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_prism_fp64(int kind, int cpq, int inl, int outl);
 const void *kernel_prism_mixed(int kind, int cpq, int inl, int outl);
+const void *kernel_tet_dw(int kind, int quad, int cpq, int inl, int outl);
+const void *kernel_prism_dw(int kind, int cpq, int inl, int outl);
 
-// Fix-up kernels (mixed precision, flagged elements in double); they read the
-// list written by the main kernel.
+// Fix-up kernels (flagged elements of the mixed and double-word forms, redone
+// with the Jacobian terms in double); they read the list written by the main kernel.
 const void *kernel_fixup_tet(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_fixup_prism(int kind, int cpq, int inl, int outl);
+const void *kernel_fixup_tet_dw(int kind, int quad, int cpq, int inl, int outl);
+const void *kernel_fixup_prism_dw(int kind, int cpq, int inl, int outl);
 
 // Batched persistent kernel (fe_batch.cu): one descriptor per element set and
 // one per tile of consecutive elements of a set.

@@ -15,11 +15,29 @@ template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct ElemCfg {
     static constexpr int NA = NS * NS;
     static constexpr int NQ = Rule<QUAD>::NQ;
     static constexpr int NC = (KIND == POISSON ? 1 : 20) * (CPQ ? NQ : 1);
-    using CT = typename std::conditional<PREC == FP64, double, float>::type;
+    using CT = typename std::conditional<PREC == MIXED, float, double>::type;
 };
 
 __device__ __forceinline__ V3<float> to_f(V3<double> v) {
     return {static_cast<float>(v.x), static_cast<float>(v.y), static_cast<float>(v.z)};
+}
+
+// Float view of a value for the shape test (the high word of a double-word).
+__device__ __forceinline__ float hi_f(float v) { return v; }
+__device__ __forceinline__ float hi_f(double v) { return static_cast<float>(v); }
+__device__ __forceinline__ float hi_f(DW v) { return v.h; }
+template <class T> __device__ __forceinline__ V3<float> hi_f(V3<T> v) { return {hi_f(v.x), hi_f(v.y), hi_f(v.z)}; }
+
+// Coefficients of the double-word form: double in memory, split on read.
+template <class CS> struct DwCoef {
+    const CS &c;
+    __device__ __forceinline__ DW operator()(int j) const { return dw_coef(c(j)); }
+};
+
+// Edge vector x_k - x_0 of the double-word form: difference in double (one DADD
+// per component, exact to 2^-53), then split.
+template <class XS> __device__ __forceinline__ V3<DW> dw_edge_vec(const XS &x, int k) {
+    return {dw_edge(x(3 * k) - x(0)), dw_edge(x(3 * k + 1) - x(1)), dw_edge(x(3 * k + 2) - x(2))};
 }
 
 // ---------------------------------------------------------------------------
@@ -122,9 +140,50 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, MIXED, QUAD, C
     }
 };
 
-// Prism (Algorithm 2): T = double or float arithmetic after the edge vectors.
+// Tetrahedron, double-word: Algorithm 3 in double-word arithmetic from double
+// edge vectors. An element that fails the shape test, whose |det J| or results
+// leave the double-word window, or whose inputs do, is flagged and redone in
+// double by the fix-up kernel.
+template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, CPQ> {
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[16], double b[4], bool &poor) {
+        const V3<DW> e1 = dw_edge_vec(x, 1), e2 = dw_edge_vec(x, 2), e3 = dw_edge_vec(x, 3);
+        const TetGeo<DW> geo = tet_geometry(e1, e2, e3);
+        poor = tet_poor(hi_f(e1), hi_f(e2), hi_f(e3), geo.det.h) || !dw_det_ok(geo.det.h);
+        const DwCoef<CS> cd{c};
+        const DW V = dw_abs(geo.det);
+        const DW inv = dw_recip(geo.det);
+        DW Ad[16], bd[4];
+        if (KIND == POISSON) {
+            tet_poisson_products<DW, QUAD, CPQ>(geo, dw_abs(inv), V, cd, Ad, bd);
+        } else {
+            V3<DW> g[4];
+            g[1] = inv * geo.a[0];
+            g[2] = inv * geo.a[1];
+            g[3] = inv * geo.a[2];
+            g[0] = -(g[1] + g[2] + g[3]);
+            tet_generic_products<DW, QUAD, CPQ>(g, V, cd, Ad, bd);
+        }
+        poor = poor || !dw_group_ok<16>(Ad) || !dw_group_ok<4>(bd);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) A[k] = dw_to_double(Ad[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b[k] = dw_to_double(bd[k]);
+        return geo.det.h < 0.0f ? 2 : 0;
+    }
+    // Flagged element: the whole element in double.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t fixup(const XS &x, const CS &c, double A[16], double b[4]) {
+        bool unused;
+        return 1 | ElemMath<TET, KIND, FP64, QUAD, CPQ>::run(x, c, A, b, unused);
+    }
+};
+
+// Prism (Algorithm 2): T = double, float or double-word arithmetic after the
+// edge vectors.
 template <int KIND, int PREC, int CPQ> struct PrismMath {
-    using T = typename std::conditional<PREC == FP64, double, float>::type;
+    using T = typename std::conditional<PREC == FP64, double,
+                                        typename std::conditional<PREC == MIXED, float, DW>::type>::type;
 
     // Q loop on relative coordinates r[0..5] (r[0] = 0). Returns bit1/bit2 flags.
     // Generic coefficients: the three points of a zeta level run in a rolled loop
@@ -152,10 +211,10 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const V3<T> cx = zb * f.ub + zt * f.ut;
             const V3<T> cy = zb * f.vb + zt * f.vt;
             const V3<T> a3 = cross(cx, cy);
-            T fxy = T(0);
-            if (PREC == MIXED) {
-                const V3<T> t1 = T(2) * cy - cx;
-                fxy = dot(cx, cx) + dot(t1, t1) * T(1.0 / 3.0);
+            float fxy = 0.0f;
+            if constexpr (PREC != FP64) {
+                const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
+                fxy = dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f);
             }
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
@@ -164,8 +223,9 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
                 constexpr bool kSqrtVol = PREC == MIXED && KIND == POISSON;
                 const T w = T(Rule<Q_PRISM6>::w(3 * l + t));
                 const T det = prism_point<T, kSqrtVol>(f, cx, cy, a3, l, t, g, cz, w);
-                if (PREC == MIXED) poor |= prism_poor(static_cast<float>(fxy), to_float(cz), static_cast<float>(det));
-                if (PREC == FP64) degenerate |= !(fabs(static_cast<double>(det)) > 1e-300);
+                if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
+                if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
+                if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
                 neg |= det < T(0);
                 const T vol = abs_t(det) * w;
                 if (kSqrtVol)
@@ -201,10 +261,10 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const V3<T> cx = zb * f.ub + zt * f.ut;
             const V3<T> cy = zb * f.vb + zt * f.vt;
             const V3<T> a3 = cross(cx, cy);
-            T fxy = T(0);
-            if (PREC == MIXED) {
-                const V3<T> t1 = T(2) * cy - cx;
-                fxy = dot(cx, cx) + dot(t1, t1) * T(1.0 / 3.0);
+            float fxy = 0.0f;
+            if constexpr (PREC != FP64) {
+                const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
+                fxy = dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f);
             }
 #pragma unroll 1
             for (int t = 0; t < 3; ++t) {
@@ -218,8 +278,9 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
                 }
                 V3<T> g[6], cz;
                 const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
-                if (PREC == MIXED) poor |= prism_poor(static_cast<float>(fxy), to_float(cz), static_cast<float>(det));
-                if (PREC == FP64) degenerate |= !(fabs(static_cast<double>(det)) > 1e-300);
+                if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
+                if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
+                if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
                 neg |= det < T(0);
                 const T vol = abs_t(det) * T(R::w(0));
                 if (KIND == POISSON)
@@ -239,9 +300,6 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
         return neg ? 2 : 0;
     }
 
-    __device__ __forceinline__ static V3<float> to_float(V3<T> v) {
-        return {static_cast<float>(v.x), static_cast<float>(v.y), static_cast<float>(v.z)};
-    }
     __device__ __forceinline__ static T abs_t(T v) { return v < T(0) ? -v : v; }
     __device__ __forceinline__ static void mirror(T A[36]) {
 #pragma unroll
@@ -351,6 +409,31 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> 
             return 1 | 4;
         }
         return 1 | (neg ? 2 : 0);
+    }
+};
+
+template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> {
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[36], double b[6], bool &poor) {
+        V3<DW> r[6];
+        r[0] = {DW(0), DW(0), DW(0)};
+#pragma unroll
+        for (int k = 1; k < 6; ++k) r[k] = dw_edge_vec(x, k);
+        const DwCoef<CS> cd{c};
+        DW Ad[36], bd[6];
+        const uint8_t fl = PrismMath<KIND, DWORD, CPQ>::qloop(r, cd, Ad, bd, poor);
+        poor = poor || !dw_group_ok<36>(Ad) || !dw_group_ok<6>(bd);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) A[k] = dw_to_double(Ad[k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) b[k] = dw_to_double(bd[k]);
+        return fl;
+    }
+    // Flagged element: the whole element in double.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t fixup(const XS &x, const CS &c, double A[36], double b[6]) {
+        bool unused;
+        return 1 | ElemMath<PRISM, KIND, FP64, Q_PRISM6, CPQ>::run(x, c, A, b, unused);
     }
 };
 
@@ -511,7 +594,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
         const SmemSrc<CT> cs{INL == SOA ? sC + tid : sC + tid * NC, INL == SOA ? B : 1};
         uint8_t fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
-        if (PREC == MIXED && poor) fl |= 1;
+        if (PREC != FP64 && poor) fl |= 1;
         if (p.flags) p.flags[e] = fl;
     }
     __syncthreads();   // every input read: the output records reuse the same shared memory
@@ -528,7 +611,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
             for (int k = 0; k < NS; ++k) sB[tid * NS + k] = b[k];
         }
     }
-    if (PREC == MIXED) append_fixup(p, active && poor, e);
+    if (PREC != FP64) append_fixup(p, active && poor, e);
 
     // ---- store outputs ----
     fence_proxy_async_smem();
@@ -565,7 +648,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
 // Main kernel: tiles of blockDim.x elements, grid-stride over tiles.
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
-__global__ void __launch_bounds__(ET == TET ? 512 : 256)
+__global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
     elem_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
@@ -586,26 +669,28 @@ __global__ void __launch_bounds__(ET == TET ? 512 : 256)
 }
 
 // ---------------------------------------------------------------------------
-// Fix-up of one flagged element (mixed precision): read straight from global
-// memory, Jacobian terms in double, results overwrite the float ones.
+// Fix-up of one flagged element (mixed and double-word forms): read straight
+// from global memory, Jacobian terms in double, results overwrite the main
+// kernel's.
 // ---------------------------------------------------------------------------
-template <int ET, int KIND, int QUAD, int CPQ, int INL, int OUTL>
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
 __device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
-    using CF = ElemCfg<ET, KIND, MIXED, QUAD, CPQ>;
+    using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
+    using CT = typename CF::CT;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
-    const float *C = static_cast<const float *>(p.C);
-    float *Aout = static_cast<float *>(p.A);
-    float *Bout = static_cast<float *>(p.B);
-    float A[NA], b[NS];
+    const CT *C = static_cast<const CT *>(p.C);
+    CT *Aout = static_cast<CT *>(p.A);
+    CT *Bout = static_cast<CT *>(p.B);
+    CT A[NA], b[NS];
     uint8_t fl;
     if (INL == SOA) {
         const Src<SOA, double> xs{p.X + e, p.xs};
-        const Src<SOA, float> cs{C + e, p.cs};
-        fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
+        const Src<SOA, CT> cs{C + e, p.cs};
+        fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(xs, cs, A, b);
     } else {
         const Src<AOS, double> xs{p.X + e * NX, 0};
-        const Src<AOS, float> cs{C + e * NC, 0};
-        fl = ElemMath<ET, KIND, MIXED, QUAD, CPQ>::fixup(xs, cs, A, b);
+        const Src<AOS, CT> cs{C + e * NC, 0};
+        fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(xs, cs, A, b);
     }
     if (OUTL == SOA) {
 #pragma unroll
@@ -622,7 +707,7 @@ __device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
 }
 
 // Fix-up kernel of one call: grid-stride over the list written by the main kernel.
-template <int ET, int KIND, int QUAD, int CPQ, int INL, int OUTL>
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
 __global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p) {
     const unsigned cnt = *p.fix_count;
     const unsigned n = cnt < p.fix_cap ? cnt : p.fix_cap;
@@ -632,7 +717,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p) {
             atomicOr(p.status, ST_BAD_TILE);
             continue;
         }
-        fixup_element<ET, KIND, QUAD, CPQ, INL, OUTL>(p, e);
+        fixup_element<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e);
     }
 }
 

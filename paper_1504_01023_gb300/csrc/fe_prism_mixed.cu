@@ -6,7 +6,7 @@ const void *kernel_prism_mixed(int kind, int cpq, int inl, int outl) {
     return nullptr;
 }
 const void *kernel_fixup_prism(int kind, int cpq, int inl, int outl) {
-    FE_ALL16(FE_FIX_CASE, PRISM, Q_PRISM6)
+    FE_ALL16(FE_FIX_CASE, PRISM, MIXED, Q_PRISM6)
     return nullptr;
 }
 }  // namespace fe

@@ -39,7 +39,7 @@ int nq_of(fe_quad q) { return q == FE_QUAD_TET1 ? 1 : (q == FE_QUAD_TET4 ? 4 : 6
 int nc_of(const fe_elem_args *a) {
     return (a->kind == FE_POISSON ? 1 : 20) * (a->coef_mode == FE_COEF_PER_QPOINT ? nq_of(a->quad) : 1);
 }
-static int csize(fe_precision p) { return p == FE_FP64 ? 8 : 4; }
+static int csize(fe_precision p) { return p == FE_FP32_MIXED ? 4 : 8; }
 
 fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n) {
     if (!s.fix_count) {
@@ -72,18 +72,30 @@ void free_scratch(Scratch &s) {
 
 static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
     const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
+    const int il = a->coords_layout;
     if (type == FE_TET) {
-        return a->prec == FE_FP64 ? kernel_tet_fp64(a->kind, a->quad, cpq, a->coords_layout, outl)
-                                  : kernel_tet_mixed(a->kind, a->quad, cpq, a->coords_layout, outl);
+        switch (a->prec) {
+            case FE_FP64: return kernel_tet_fp64(a->kind, a->quad, cpq, il, outl);
+            case FE_FP32_MIXED: return kernel_tet_mixed(a->kind, a->quad, cpq, il, outl);
+            case FE_FP64_DW: return kernel_tet_dw(a->kind, a->quad, cpq, il, outl);
+        }
+        return nullptr;
     }
-    return a->prec == FE_FP64 ? kernel_prism_fp64(a->kind, cpq, a->coords_layout, outl)
-                              : kernel_prism_mixed(a->kind, cpq, a->coords_layout, outl);
+    switch (a->prec) {
+        case FE_FP64: return kernel_prism_fp64(a->kind, cpq, il, outl);
+        case FE_FP32_MIXED: return kernel_prism_mixed(a->kind, cpq, il, outl);
+        case FE_FP64_DW: return kernel_prism_dw(a->kind, cpq, il, outl);
+    }
+    return nullptr;
 }
 
 static const void *fix_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
     const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
-    return type == FE_TET ? kernel_fixup_tet(a->kind, a->quad, cpq, a->coords_layout, outl)
-                          : kernel_fixup_prism(a->kind, cpq, a->coords_layout, outl);
+    const int il = a->coords_layout;
+    if (a->prec == FE_FP64_DW)
+        return type == FE_TET ? kernel_fixup_tet_dw(a->kind, a->quad, cpq, il, outl)
+                              : kernel_fixup_prism_dw(a->kind, cpq, il, outl);
+    return type == FE_TET ? kernel_fixup_tet(a->kind, a->quad, cpq, il, outl) : kernel_fixup_prism(a->kind, cpq, il, outl);
 }
 
 // Dynamic shared memory of one block: the tile's inputs and outputs, each region
@@ -122,7 +134,11 @@ static std::string shape_key(fe_elem_type type, const fe_elem_args *a, const fe_
 
 Shape default_shape(fe_elem_type type) { return Shape{type == FE_TET ? 256 : 128, 0}; }
 
-static int max_block(fe_elem_type type) { return type == FE_TET ? 512 : 256; }
+// Largest block of a kernel (its launch bounds): 512 for float and double
+// tetrahedra, 256 for prisms and double-word tetrahedra.
+static int max_block(fe_elem_type type, fe_precision prec) {
+    return type == FE_TET && prec != FE_FP64_DW ? 512 : 256;
+}
 
 static cudaEvent_t pool_event(fe_ctx *ctx) {
     if (!ctx->event_pool.empty()) {
@@ -216,8 +232,8 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     p.os = o->stride ? o->stride : a->n_elem;
     p.flags = o->flags;
     p.item = 0;
-    const bool mixed = a->prec == FE_FP32_MIXED;
-    if (mixed) {
+    const bool fixup = a->prec != FE_FP64;   // mixed and double-word forms flag elements
+    if (fixup) {
         fe_status e = ensure_scratch(ctx, s, uint64_t(a->n_elem));
         if (e != FE_OK) return e;
         p.fix_list = s.fix_list;
@@ -236,7 +252,7 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     memset(&tm, 0, sizeof tm);
     if (sh.block <= 256) {
         const int ns = ns_of(type), nc = nc_of(a);
-        const bool dbl = a->prec == FE_FP64;
+        const bool dbl = a->prec != FE_FP32_MIXED;
         const uint64_t cs = dbl ? 8 : 4;
         if (a->coords_layout == FE_LAYOUT_SOA)
             p.tma_in = encode_planes(tm.x, true, a->coords, uint64_t(a->n_elem), 3 * ns, uint64_t(p.xs) * 8, sh.block) &&
@@ -269,7 +285,7 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
         cudaEventRecord(ev1, st);
         ctx->prof_events.emplace_back(ev0, ev1);
     }
-    if (mixed) {
+    if (fixup) {
         const void *fk = fix_kernel(type, a, outl);
         const int64_t fgrid = std::min<int64_t>((a->n_elem + 255) / 256, int64_t(ctx->sms) * 4);
         void *fargs[] = {&p};
@@ -510,7 +526,8 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
     if (!a || !o) return set_error(nullptr, FE_ERR_INVALID_ARG, "null args or out");
     if (a->n_elem < 0) return set_error(nullptr, FE_ERR_INVALID_ARG, "n_elem < 0");
     if (a->kind != FE_POISSON && a->kind != FE_GENERIC) return set_error(nullptr, FE_ERR_INVALID_ARG, "bad problem kind");
-    if (a->prec != FE_FP64 && a->prec != FE_FP32_MIXED) return set_error(nullptr, FE_ERR_INVALID_ARG, "bad precision");
+    if (a->prec != FE_FP64 && a->prec != FE_FP32_MIXED && a->prec != FE_FP64_DW)
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "bad precision");
     if (a->coef_mode != FE_COEF_PER_ELEMENT && a->coef_mode != FE_COEF_PER_QPOINT)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "bad coefficient mode");
     if (type == FE_TET && a->quad != FE_QUAD_TET1 && a->quad != FE_QUAD_TET4)
@@ -533,7 +550,7 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
     }
     if (o->layout == FE_LAYOUT_SOA && o->stride != 0 && o->stride < n)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "SOA output stride smaller than n_elem");
-    const unsigned cs = a->prec == FE_FP64 ? 8 : 4;
+    const unsigned cs = unsigned(csize(a->prec));
     if ((reinterpret_cast<uintptr_t>(a->coords) & 7) || (reinterpret_cast<uintptr_t>(a->coefs) & (cs - 1)) ||
         (reinterpret_cast<uintptr_t>(o->A) & (cs - 1)) || (reinterpret_cast<uintptr_t>(o->b) & (cs - 1)))
         return set_error(nullptr, FE_ERR_INVALID_ARG, "misaligned data pointer");
@@ -544,7 +561,7 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
 int64_t fe_bytes_per_element(fe_elem_type type, fe_problem kind, fe_quad quad, fe_coef_mode mode, fe_precision prec) {
     if (type != FE_TET && type != FE_PRISM) return -1;
     if (kind != FE_POISSON && kind != FE_GENERIC) return -1;
-    if (prec != FE_FP64 && prec != FE_FP32_MIXED) return -1;
+    if (prec != FE_FP64 && prec != FE_FP32_MIXED && prec != FE_FP64_DW) return -1;
     if (type == FE_TET && quad != FE_QUAD_TET1 && quad != FE_QUAD_TET4) return -1;
     if (type == FE_PRISM && quad != FE_QUAD_PRISM6) return -1;
     if (mode != FE_COEF_PER_ELEMENT && mode != FE_COEF_PER_QPOINT) return -1;
@@ -552,7 +569,7 @@ int64_t fe_bytes_per_element(fe_elem_type type, fe_problem kind, fe_quad quad, f
     a.kind = kind;
     a.quad = quad;
     a.coef_mode = mode;
-    const int ns = ns_of(type), cs = prec == FE_FP64 ? 8 : 4;
+    const int ns = ns_of(type), cs = csize(prec);
     return int64_t(3 * ns) * 8 + int64_t(nc_of(&a)) * cs + int64_t(ns * ns + ns) * cs;
 }
 
@@ -717,7 +734,7 @@ fe_status fe_set_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
     fe_status st = fe_check_args(type, args, out);
     if (st != FE_OK) return st;
-    if (block_threads < 32 || block_threads > max_block(type) || block_threads % 32 || (persistent != 0 && persistent != 1))
+    if (block_threads < 32 || block_threads > max_block(type, args->prec) || block_threads % 32 || (persistent != 0 && persistent != 1))
         return set_error(ctx, FE_ERR_INVALID_ARG, "bad launch shape");
     if (smem_bytes(type, args, out->layout, block_threads) + kStaticSmem > ctx->max_smem_optin)
         return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
@@ -742,7 +759,7 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const f
     cudaEventCreate(&e1);
     float best = 1e30f;
     Shape best_shape = default_shape(type);
-    for (int B = 64; B <= max_block(type); B *= 2) {
+    for (int B = 64; B <= max_block(type, a->prec); B *= 2) {
         for (int pers = 0; pers < 2; ++pers) {
             Shape sh{B, pers};
             if (smem_bytes(type, a, o->layout, B) + kStaticSmem > ctx->max_smem_optin) continue;

@@ -86,7 +86,7 @@ static void reap(ServeState *s) {
 }
 
 static uint64_t out_bytes_of(const MeshRec &m, fe_precision prec) {
-    const uint64_t ns = uint64_t(ns_of(m.type)), cs = prec == FE_FP64 ? 8 : 4;
+    const uint64_t ns = uint64_t(ns_of(m.type)), cs = prec == FE_FP32_MIXED ? 4 : 8;
     auto r256 = [](uint64_t v) { return (v + 255) / 256 * 256; };
     return r256(uint64_t(m.n_elem) * ns * ns * cs) + r256(uint64_t(m.n_elem) * ns * cs) + r256(uint64_t(m.n_elem));
 }
@@ -107,7 +107,7 @@ static void launch_slot(ServeState *s, int si, std::vector<uint64_t> &batch) {
         q.slot = si;
         const MeshRec &m = q.mesh;
         // outputs from the context's stream-ordered pool
-        const uint64_t ns = ns_of(m.type), cs = q.r.prec == FE_FP64 ? 8 : 4;
+        const uint64_t ns = ns_of(m.type), cs = q.r.prec == FE_FP32_MIXED ? 4 : 8;
         const uint64_t bA = uint64_t(m.n_elem) * ns * ns * cs, bB = uint64_t(m.n_elem) * ns * cs;
         cudaError_t e = cudaMallocFromPoolAsync(&q.A, bA, s->pool, sl.stream);
         if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q.b, bB, s->pool, sl.stream);

@@ -7,8 +7,8 @@ const void *kernel_tet_mixed(int kind, int quad, int cpq, int inl, int outl) {
     return nullptr;
 }
 const void *kernel_fixup_tet(int kind, int quad, int cpq, int inl, int outl) {
-    if (quad == Q_TET1) { FE_ALL16(FE_FIX_CASE, TET, Q_TET1) }
-    if (quad == Q_TET4) { FE_ALL16(FE_FIX_CASE, TET, Q_TET4) }
+    if (quad == Q_TET1) { FE_ALL16(FE_FIX_CASE, TET, MIXED, Q_TET1) }
+    if (quad == Q_TET4) { FE_ALL16(FE_FIX_CASE, TET, MIXED, Q_TET4) }
     return nullptr;
 }
 }  // namespace fe

@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_1504_01023_gb300 import api, meshgen
 
-TOL = {api.FP64: 1e-12, api.FP32_MIXED: 2e-5}
+TOL = {api.FP64: 1e-12, api.FP64_DW: 1e-12, api.FP32_MIXED: 2e-5}
 ORACLE_RULE = {api.QUAD_TET1: oracle.Q_TET1, api.QUAD_TET4: oracle.Q_TET4, api.QUAD_PRISM6: oracle.Q_PRISM6}
 
 
@@ -31,7 +31,7 @@ def to_device_inputs(et, mesh, c, prec, layout, device="cuda"):
     """Torch tensors in the layout the ABI expects; coefficients narrowed to the
     precision of the form (the oracle then reads the same narrowed values)."""
     n = len(mesh)
-    cdt = np.float64 if prec == api.FP64 else np.float32
+    cdt = np.float32 if prec == api.FP32_MIXED else np.float64
     c_used = c.astype(cdt)
     if layout == api.SOA:
         X = torch.from_numpy(meshgen.soa(mesh))

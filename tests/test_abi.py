@@ -45,6 +45,12 @@ def test_bytes_per_element_matches_table3(lib):
     assert b(api.TET, api.POISSON, api.QUAD_TET1, api.PER_ELEMENT, api.FP64) == 264
     assert b(api.TET, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP32_MIXED) == 256
     assert b(api.PRISM, api.GENERIC, api.QUAD_PRISM6, api.PER_QPOINT, api.FP32_MIXED) == 792
+    # the double-word form moves the bytes of the FP64 form
+    for et, q in [(api.TET, api.QUAD_TET1), (api.TET, api.QUAD_TET4), (api.PRISM, api.QUAD_PRISM6)]:
+        for kind in (api.POISSON, api.GENERIC):
+            for cm in (api.PER_ELEMENT, api.PER_QPOINT):
+                assert b(et, kind, q, cm, api.FP64_DW) == b(et, kind, q, cm, api.FP64)
+    assert b(api.TET, api.POISSON, api.QUAD_TET1, api.PER_ELEMENT, 3) == -1
     assert b(api.TET, 7, api.QUAD_TET4, 0, 0) == -1
 
 

@@ -25,7 +25,7 @@ def ctx():
 
 def _run_aos(ctx, et, mesh, coefs, kind, quad, cm, prec, tune=True):
     n = len(mesh)
-    cdt = np.float64 if prec == api.FP64 else np.float32
+    cdt = np.float32 if prec == api.FP32_MIXED else np.float64
     X = torch.from_numpy(np.ascontiguousarray(mesh)).cuda()
     C = torch.from_numpy(np.ascontiguousarray(coefs.reshape(n, -1).astype(cdt))).cuda()
     out = api.alloc_out(et, n, prec, api.AOS, "cuda")
@@ -139,3 +139,31 @@ def test_batched_256_meshes_sampled():
         ea, eb = max_errors(A[it].double().cpu().numpy(), b[it].double().cpu().numpy(), Ar, br)
         assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED], (et, kind, quad, cpq, ea, eb)
     ctx.close()
+
+
+def test_poisson_tets_48k_double_word_every_element(ctx):
+    """The 48,000-element Poisson workload in the double-word form: every element
+    against the oracle at the double-precision tolerance."""
+    mesh = meshgen.tet_cube_mesh(20, 0.2, seed=meshgen.SEED_BASE + 1)
+    d0 = meshgen.poisson_coefs(len(mesh), 1, 1.0)
+    A, b, f, cu = _run_aos(ctx, api.TET, mesh, d0, api.POISSON, api.QUAD_TET1, api.PER_ELEMENT, api.FP64_DW)
+    Ar, br, fr = oracle.integrate(api.TET, api.POISSON, oracle.Q_TET1, mesh, cu.reshape(-1), n_threads=8)
+    ea, eb = max_errors(A.cpu().numpy(), b.cpu().numpy(), Ar, br)
+    assert ea <= TOL[api.FP64_DW] and eb <= TOL[api.FP64_DW], (ea, eb)
+    assert ((f.cpu().numpy() & 6) == fr).all()
+
+
+def test_poisson_tets_6M_double_word_sampled(ctx):
+    """100^3 x 6 Poisson tetrahedra (the double-precision benchmark workload), tuned
+    shape, double-word form."""
+    mesh = meshgen.tet_cube_mesh(100, 0.2, seed=meshgen.SEED_BASE + 2)
+    d0 = meshgen.poisson_coefs(len(mesh), 1, 1.0)
+    A, b, f, cu = _run_aos(ctx, api.TET, mesh, d0, api.POISSON, api.QUAD_TET1, api.PER_ELEMENT, api.FP64_DW)
+    _check_sample(api.TET, A, b, f, mesh, cu.reshape(-1), api.POISSON, oracle.Q_TET1, 0, TOL[api.FP64_DW], 3)
+
+
+def test_generic_tets_6M_double_word_sampled(ctx):
+    mesh = meshgen.tet_cube_mesh(100, 0.2, seed=meshgen.SEED_BASE + 2)
+    c = meshgen.generic_coefs(len(mesh), 1, seed=meshgen.SEED_BASE + 2)
+    A, b, f, cu = _run_aos(ctx, api.TET, mesh, c, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP64_DW)
+    _check_sample(api.TET, A, b, f, mesh, cu, api.GENERIC, oracle.Q_TET4, 0, TOL[api.FP64_DW], 4)

@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances (relative Frobenius per element, A and b separately): 1e-12 for the
-FP64 form, 2e-5 for the mixed form. Inputs span several tiles with a ragged tail.
+FP64 and double-word forms, 2e-5 for the mixed form. Inputs span several tiles
+with a ragged tail.
 """
 import itertools
 
@@ -25,10 +26,11 @@ def ctx():
     c.close()
 
 
+PRECS = [api.FP64, api.FP32_MIXED, api.FP64_DW]
 TET_CASES = list(itertools.product([api.POISSON, api.GENERIC], [api.QUAD_TET1, api.QUAD_TET4], [0, 1],
-                                   [api.FP64, api.FP32_MIXED], [api.SOA, api.AOS], [api.SOA, api.AOS]))
+                                   PRECS, [api.SOA, api.AOS], [api.SOA, api.AOS]))
 PRISM_CASES = list(itertools.product([api.POISSON, api.GENERIC], [api.QUAD_PRISM6], [0, 1],
-                                     [api.FP64, api.FP32_MIXED], [api.SOA, api.AOS], [api.SOA, api.AOS]))
+                                     PRECS, [api.SOA, api.AOS], [api.SOA, api.AOS]))
 
 
 def _ids(cases):
@@ -55,7 +57,7 @@ def test_prism_parity(ctx, kind, quad, cpq, prec, lay, olay):
     assert (fn == fr).all()
 
 
-@pytest.mark.parametrize("prec", [api.FP64, api.FP32_MIXED])
+@pytest.mark.parametrize("prec", PRECS)
 def test_thin_prisms_far_from_origin(ctx, prec):
     """h = 1e-3 elements at coordinates up to 1: the mixed form must form its edge
     vectors without the cancellation of rounding absolute coordinates."""
@@ -73,7 +75,7 @@ def test_small_and_ragged_sizes(ctx, et):
     quad = api.QUAD_TET4 if et == api.TET else api.QUAD_PRISM6
     for n in [1, 2, 31, 33, 255, 257, 513]:
         mesh, c = make_inputs(et, api.GENERIC, quad, 0, n=n, seed=n)
-        for prec in (api.FP64, api.FP32_MIXED):
+        for prec in PRECS:
             for lay, olay in [(api.SOA, api.SOA), (api.AOS, api.AOS)]:
                 An, bn, fn, cu = run_gpu(ctx, et, api.GENERIC, quad, 0, prec, lay, olay, mesh, c)
                 Ar, br, _ = run_oracle(et, api.GENERIC, quad, 0, mesh, cu)
@@ -96,14 +98,14 @@ def test_inverted_and_degenerate_elements(ctx):
     mesh[inv] = mesh[inv][:, [0, 2, 1, 3]]                 # inverted
     deg = np.arange(3, 300, 11)
     mesh[deg, 3] = mesh[deg, 0]                            # vertex 3 on vertex 0: zero volume
-    for prec in (api.FP64, api.FP32_MIXED):
+    for prec in PRECS:
         An, bn, fn, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, prec, api.SOA, api.SOA, mesh, c)
         Ar, br, fr = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh, cu)
         ea, eb = max_errors(An, bn, Ar, br)
         assert ea <= TOL[prec] and eb <= TOL[prec]
         assert ((fn & 6) == fr).all()                      # bits 1, 2 agree with the oracle
         assert (fn[deg] & 4).all() and not An[deg].any()
-        if prec == api.FP32_MIXED:
+        if prec != api.FP64:
             assert (fn[deg] & 1).all()                     # degenerate -> double path
 
 
@@ -112,7 +114,7 @@ def test_nan_coordinates_do_not_fault(ctx):
     mesh = mesh.copy()
     mesh[5, 2, 1] = np.nan
     mesh[9, 0, 0] = np.inf
-    for prec in (api.FP64, api.FP32_MIXED):
+    for prec in PRECS:
         An, bn, fn, cu = run_gpu(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, prec, api.SOA, api.SOA, mesh, c)
         ok = np.ones(200, bool)
         ok[[5, 9]] = False
@@ -199,8 +201,52 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
     assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED]
 
 
-SOA_TMA_CASES = list(itertools.product([api.TET, api.PRISM], [api.POISSON, api.GENERIC], [0, 1],
-                                       [api.FP64, api.FP32_MIXED]))
+def test_sliver_stress_double_word(ctx):
+    """Double-word form: elements with mean ratio < 0.1 (flag bit 0) are computed in
+    double; every element meets the double-precision tolerance."""
+    mesh = meshgen.tet_cube_mesh(12, seed=meshgen.SEED_BASE + 2)
+    sl = meshgen.make_slivers(mesh, 0.1, seed=meshgen.SEED_BASE + 21)
+    for kind, quad in [(api.POISSON, api.QUAD_TET1), (api.GENERIC, api.QUAD_TET4)]:
+        _, c = make_inputs(api.TET, kind, quad, 0, mesh=mesh, seed=6)
+        An, bn, fn, cu = run_gpu(ctx, api.TET, kind, quad, 0, api.FP64_DW, api.AOS, api.AOS, mesh, c)
+        Ar, br, fr = run_oracle(api.TET, kind, quad, 0, mesh, cu)
+        ea, eb = max_errors(An, bn, Ar, br)
+        assert ea <= 1e-12 and eb <= 1e-12, (kind, ea, eb)
+        q = oracle.quality(oracle.TET, mesh, n_threads=8)
+        flagged = (fn & 1).astype(bool)
+        clear = np.abs(q - 0.1) > 1e-3 * 0.1
+        assert (flagged[clear] == (q[clear] < 0.1)).all()
+        assert flagged.sum() >= 0.5 * len(sl)
+        assert ((fn & 6) == fr).all()
+
+
+@pytest.mark.parametrize("et", [api.TET, api.PRISM])
+def test_double_word_windows(ctx, et):
+    """Elements outside the double-word window go to the double path (flag bit 0)
+    and still meet the double-precision tolerance: coordinates scaled by 2^-30 and
+    2^30 (|det J| outside [2^-60, 2^60]), all coefficients scaled by 1e-20 and
+    1e20, one coefficient set to 1e-17 (below 2^-50); untouched elements stay in
+    double-word (bit 0 clear). The scaling is about the origin: the oracle forms
+    J from absolute coordinates, and for prisms (inexact reference derivatives)
+    its rounding grows like |x| / h."""
+    quad = api.QUAD_TET4 if et == api.TET else api.QUAD_PRISM6
+    mesh, c = make_inputs(et, api.GENERIC, quad, 0, n=600, seed=41)
+    mesh, c = mesh.copy(), c.copy()
+    mesh[100:200] *= 2.0 ** -30
+    mesh[200:300] *= 2.0 ** 30
+    c[300:400] *= 1e-20
+    c[400:500] *= 1e20
+    c.reshape(600, -1)[500:600, 5] = 1e-17
+    An, bn, fn, cu = run_gpu(ctx, et, api.GENERIC, quad, 0, api.FP64_DW, api.AOS, api.AOS, mesh, c)
+    Ar, br, fr = run_oracle(et, api.GENERIC, quad, 0, mesh, cu)
+    ea, eb = max_errors(An, bn, Ar, br)
+    assert ea <= 1e-12 and eb <= 1e-12, (ea, eb)
+    assert not (fn[:100] & 1).any()
+    assert (fn[100:] & 1).all()
+    assert ((fn & 6) == fr).all()
+
+
+SOA_TMA_CASES = list(itertools.product([api.TET, api.PRISM], [api.POISSON, api.GENERIC], [0, 1], PRECS))
 
 
 @pytest.mark.parametrize("et,kind,cpq,prec", SOA_TMA_CASES, ids=["t%d-k%d-c%d-p%d" % c for c in SOA_TMA_CASES])
