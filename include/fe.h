@@ -72,7 +72,7 @@ typedef enum fe_problem { FE_POISSON = 0, FE_GENERIC = 1 } fe_problem;
    double. Elements that fail the shape test above, or whose |det J|, inputs or
    results leave the double-word window (|det J| in [2^-60, 2^60], nonzero
    coefficients in [2^-50, 2^51), the sum of |A^e| and of |b^e| zero or in
-   [2^-90, 2^100]), are computed entirely in double (flag bit 0). The paper has
+   [2^-80, 2^100]), are computed entirely in double (flag bit 0). The paper has
    no counterpart: its double-precision form is FE_FP64. */
 typedef enum fe_precision { FE_FP64 = 0, FE_FP32_MIXED = 1, FE_FP64_DW = 2 } fe_precision;
 

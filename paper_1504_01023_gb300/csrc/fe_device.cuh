@@ -87,6 +87,14 @@ template <class T> __device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return a
 template <class T> __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
+// Double-word dot and cross products: one fused accumulation per result.
+__device__ __forceinline__ DW dot(V3<DW> a, V3<DW> b) {
+    const DW x[3] = {a.x, a.y, a.z}, y[3] = {b.x, b.y, b.z};
+    return dw_dot<3>(x, y);
+}
+__device__ __forceinline__ V3<DW> cross(V3<DW> a, V3<DW> b) {
+    return {dw_diff_prod(a.y, b.z, a.z, b.y), dw_diff_prod(a.z, b.x, a.x, b.z), dw_diff_prod(a.x, b.y, a.y, b.x)};
+}
 
 // ---------------------------------------------------------------------------
 // Memory helpers
@@ -340,6 +348,27 @@ __device__ __forceinline__ void tet_generic_products(const V3<T> g[4], T V, cons
     }
 }
 
+// Laplace load vector: b_r = V sum_q w_q d0_q phi_r(q) (d0 per element: V d0 m_r).
+template <class T, int QUAD, int CPQ, class CS> __device__ __forceinline__ void tet_poisson_b(T V, const CS &c, T b[4]) {
+    constexpr TetSums S = tet_sums<QUAD>();
+    if (!CPQ) {
+        const T vd = V * c(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] = vd * T(S.m[r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] = T(0);
+#pragma unroll
+        for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
+            const T wd = T(Rule<QUAD>::w(q)) * c(q);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] += wd * T(Rule<QUAD>::phi(q, r));
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] *= V;
+    }
+}
+
 // Poisson tetrahedron: A_rs = W / |det| (a_r . a_s) for r,s = 1..3; row and column 0
 // from the vanishing row sums (sum_k grad phi_k = 0); b_r = |det| sum_q w d0_q phi_r(q).
 template <class T, int QUAD, int CPQ, class CS>
@@ -368,22 +397,7 @@ __device__ __forceinline__ void tet_poisson_products(const TetGeo<T> &geo, T inv
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int s = 0; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = G[r][s];
-    if (!CPQ) {
-        const T vd = V * c(0);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) b[r] = vd * T(S.m[r]);
-    } else {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) b[r] = T(0);
-#pragma unroll
-        for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
-            const T wd = T(Rule<QUAD>::w(q)) * c(q);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) b[r] += wd * T(Rule<QUAD>::phi(q, r));
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) b[r] *= V;
-    }
+    tet_poisson_b<T, QUAD, CPQ>(V, c, b);
 }
 
 // Poisson tetrahedron from gradients (used by the double-Jacobian fix-up).

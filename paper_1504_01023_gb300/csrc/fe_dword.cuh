@@ -118,38 +118,67 @@ __device__ __forceinline__ bool dw_det_ok(float det_h) {
 }
 
 // A group of results (A^e or b^e) is accepted when all are finite and the sum of
-// their magnitudes is zero or in [2^-90, 2^100], so that the low words of the
-// entries that carry the group's norm are normal floats.
+// their magnitudes is zero or in [2^-80, 2^100], so that the low words of the
+// entries that carry the group's norm are normal floats and what falls below the
+// float range is negligible against the group.
 template <int N> __device__ __forceinline__ bool dw_group_ok(const DW *v) {
     float s = 0.0f;
 #pragma unroll
     for (int k = 0; k < N; ++k) s = __fadd_rn(s, fabsf(v[k].h));
-    return s == 0.0f || (s >= 0x1p-90f && s <= 0x1p100f);
+    return s == 0.0f || (s >= 0x1p-80f && s <= 0x1p100f);
 }
 
 // ---------------------------------------------------------------------------
-// double-word -> double with integer operations: the double of h is exact (bit
-// re-biasing), and l is added as an integer count k of ulps of that double,
-// k = trunc(l / ulp), |k| < 2^30 (error below one ulp of the result). When h
-// is a power of two and l has the opposite sign the result lies in the binade
-// below, whose ulp is half as large. Zero stays zero; a non-finite h gives NaN.
+// double-word -> double: each float becomes its exact double by re-biasing its
+// bits (integer operations), and one double addition rounds h + l correctly; no
+// normalisation of (h, l) is needed. Zero and subnormal floats become zero (an
+// absolute error below 2^-126, negligible against a result group of at least
+// 2^-80); non-finite floats are not preserved, which only matters for flagged
+// elements, whose results the fix-up overwrites.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double dw_to_double(DW v) {
-    const DW n = dw_two_sum(v.h, v.l);  // |l| <= ulp(h) / 2
-    const uint32_t bh = __float_as_uint(n.h), bl = __float_as_uint(n.l);
-    const uint32_t eh = (bh >> 23) & 0xFFu, mh = bh & 0x7FFFFFu, sh = bh & 0x80000000u;
-    const uint32_t el = (bl >> 23) & 0xFFu;
-    const uint32_t whi = eh ? (sh | ((eh + 896u) << 20) | (mh >> 3)) : sh;
-    const uint32_t wlo = eh ? (mh << 29) : 0u;
-    const bool down = mh == 0u && ((bl ^ bh) & 0x80000000u) != 0u;
-    // biased exponent of t = l * 2^(52 - E_h) (one more in the binade below)
-    const int te = int(el) - int(eh) + 179 + (down ? 1 : 0);
-    int k = 0;
-    if (el != 0u && te >= 1) k = __float2int_rz(__uint_as_float((bl & 0x807FFFFFu) | (uint32_t(te) << 23)));
-    // k has l's sign; the bit pattern holds |h|, so negate for negative h
-    const long long d = sh ? -static_cast<long long>(k) : static_cast<long long>(k);
-    const unsigned long long bits = ((static_cast<unsigned long long>(whi) << 32) | wlo) + static_cast<unsigned long long>(d);
-    return eh == 0xFFu ? __longlong_as_double(0x7FF8000000000000ll) : __longlong_as_double(static_cast<long long>(bits));
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const bool normal = (b & 0x7F800000u) != 0u;
+    const uint32_t hi = normal ? ((((b >> 3) & 0x0FFFFFFFu) + 0x38000000u) | (b & 0x80000000u)) : (b & 0x80000000u);
+    const uint32_t lo = normal ? (b << 29) : 0u;
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+__device__ __forceinline__ double dw_to_double(DW v) { return f2d_bits(v.h) + f2d_bits(v.l); }
+
+// Sum of N products of double-words, accumulated as in the Dot2 algorithm of
+// Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26(6), 2005): the float products
+// h_i h'_i are summed with TwoSum, and their rounding errors, the TwoSum errors
+// and the cross terms h_i l'_i + l_i h'_i are gathered in one float. Error a few
+// N^2 2^-48 sum |x_i y_i|. SIGN[i] = -1 subtracts the i-th product.
+template <int N>
+__device__ __forceinline__ DW dw_dot(const DW *x, const DW *y, const int *sign = nullptr) {
+    float p = __fmul_rn(x[0].h, y[0].h);
+    float c = __fmaf_rn(x[0].h, y[0].h, -p);
+    c = __fmaf_rn(x[0].h, y[0].l, c);
+    c = __fmaf_rn(x[0].l, y[0].h, c);
+    if (sign && sign[0] < 0) {
+        p = -p;
+        c = -c;
+    }
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+        const float xh = (sign && sign[i] < 0) ? -x[i].h : x[i].h;
+        const float xl = (sign && sign[i] < 0) ? -x[i].l : x[i].l;
+        const float q = __fmul_rn(xh, y[i].h);
+        const float e = __fmaf_rn(xh, y[i].h, -q);
+        const DW s = dw_two_sum(p, q);
+        p = s.h;
+        c = __fadd_rn(c, __fadd_rn(s.l, e));
+        c = __fmaf_rn(xh, y[i].l, c);
+        c = __fmaf_rn(xl, y[i].h, c);
+    }
+    return dw_fast_two_sum(p, c);
+}
+// a b - c d
+__device__ __forceinline__ DW dw_diff_prod(DW a, DW b, DW c, DW d) {
+    const DW x[2] = {a, c}, y[2] = {b, d};
+    const int sg[2] = {1, -1};
+    return dw_dot<2>(x, y, sg);
 }
 
 }  // namespace fe

@@ -153,23 +153,68 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, C
         const DwCoef<CS> cd{c};
         const DW V = dw_abs(geo.det);
         const DW inv = dw_recip(geo.det);
-        DW Ad[16], bd[4];
-        if (KIND == POISSON) {
-            tet_poisson_products<DW, QUAD, CPQ>(geo, dw_abs(inv), V, cd, Ad, bd);
+        if constexpr (KIND == POISSON) {
+            poisson(geo, dw_abs(inv), V, cd, A, b, poor);
         } else {
+            DW Ad[16], bd[4];
             V3<DW> g[4];
             g[1] = inv * geo.a[0];
             g[2] = inv * geo.a[1];
             g[3] = inv * geo.a[2];
             g[0] = -(g[1] + g[2] + g[3]);
             tet_generic_products<DW, QUAD, CPQ>(g, V, cd, Ad, bd);
+            poor = poor || !dw_group_ok<16>(Ad) || !dw_group_ok<4>(bd);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) A[k] = dw_to_double(Ad[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = dw_to_double(bd[k]);
         }
-        poor = poor || !dw_group_ok<16>(Ad) || !dw_group_ok<4>(bd);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) A[k] = dw_to_double(Ad[k]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) b[k] = dw_to_double(bd[k]);
         return geo.det.h < 0.0f ? 2 : 0;
+    }
+    // Laplace products (as tet_poisson_products): the ten distinct entries of the
+    // symmetric A^e are computed and converted once each; b^e is uniform for
+    // per-element coefficients or a one-point rule (m_r = |T|/4 for both rules).
+    template <class CS>
+    __device__ __forceinline__ static void poisson(const TetGeo<DW> &geo, DW invabs, DW V, const CS &c, double A[16],
+                                                   double b[4], bool &poor) {
+        constexpr TetSums S = tet_sums<QUAD>();
+        const DW k = DW(S.W) * invabs;
+        DW G[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = r; s < 3; ++s) G[r][s] = G[s][r] = k * dot(geo.a[r], geo.a[s]);
+        DW row0[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) row0[s] = -(G[0][s] + G[1][s] + G[2][s]);
+        const DW a00 = -(row0[0] + row0[1] + row0[2]);
+        DW bd[4];
+        tet_poisson_b<DW, QUAD, CPQ>(V, c, bd);
+        constexpr bool uniform_b = !CPQ || Rule<QUAD>::NQ == 1;
+        // window check over all 16 (4) entries, repeated ones counted twice (four times)
+        float sa = fabsf(a00.h) + fabsf(G[0][0].h) + fabsf(G[1][1].h) + fabsf(G[2][2].h);
+        float so = fabsf(G[0][1].h) + fabsf(G[0][2].h) + fabsf(G[1][2].h) + fabsf(row0[0].h) + fabsf(row0[1].h) +
+                   fabsf(row0[2].h);
+        sa = __fmaf_rn(2.0f, so, sa);
+        float sb = uniform_b ? 4.0f * fabsf(bd[0].h)
+                             : fabsf(bd[0].h) + fabsf(bd[1].h) + fabsf(bd[2].h) + fabsf(bd[3].h);
+        poor = poor || !(sa == 0.0f || (sa >= 0x1p-80f && sa <= 0x1p100f)) ||
+               !(sb == 0.0f || (sb >= 0x1p-80f && sb <= 0x1p100f));
+        A[0] = dw_to_double(a00);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) A[1 + s] = A[4 * (1 + s)] = dw_to_double(row0[s]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = r; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = A[4 * (s + 1) + (r + 1)] = dw_to_double(G[r][s]);
+        if (uniform_b) {
+            const double v = dw_to_double(bd[0]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] = v;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] = dw_to_double(bd[r]);
+        }
     }
     // Flagged element: the whole element in double.
     template <class XS, class CS>
