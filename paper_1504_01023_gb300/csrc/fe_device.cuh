@@ -348,6 +348,71 @@ __device__ __forceinline__ void tet_generic_products(const V3<T> g[4], T V, cons
     }
 }
 
+// The same products for per-element coefficients with fewer operations (used
+// where arithmetic, not memory, bounds the kernel). With g_0 = -(g_1 + g_2 + g_3):
+//   K_rs = g_r . (V W C) g_s for r, s = 1..3; row and column 0 of K from the
+//   vanishing sums;
+//   convection m_r (c^{i0} . g_r) pairs with m_s: as m_r = W/4 for both rules,
+//   V (P_s . g_r + R_r . g_s) = V W/4 (cr_r + cs_s);
+//   mass V c^{00} M2_rs with M2 one value off the diagonal and one on it;
+//   b_r = V W (d^i . g_r) + V d^0 W/4.
+template <class T, int QUAD, class CS>
+__device__ __forceinline__ void tet_generic_products_pe(const V3<T> g[3], T V, const CS &c, T A[16], T b[4]) {
+    constexpr TetSums S = tet_sums<QUAD>();
+    const T VW = V * T(S.W);
+    V3<T> Crow[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Crow[i] = {VW * c(4 * i + 5), VW * c(4 * i + 6), VW * c(4 * i + 7)};
+    V3<T> CG[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) CG[s] = {dot(Crow[0], g[s]), dot(Crow[1], g[s]), dot(Crow[2], g[s])};
+    T K[4][4];
+#pragma unroll
+    for (int r = 1; r < 4; ++r)
+#pragma unroll
+        for (int s = 1; s < 4; ++s) K[r][s] = dot(g[r - 1], CG[s - 1]);
+#pragma unroll
+    for (int s = 1; s < 4; ++s) K[0][s] = -(K[1][s] + K[2][s] + K[3][s]);
+#pragma unroll
+    for (int r = 1; r < 4; ++r) K[r][0] = -(K[r][1] + K[r][2] + K[r][3]);
+    K[0][0] = -(K[0][1] + K[0][2] + K[0][3]);
+    const V3<T> ci0 = {c(4), c(8), c(12)}, c0i = {c(1), c(2), c(3)};
+    T cr[4], cs[4];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        cr[k] = dot(ci0, g[k - 1]);
+        cs[k] = dot(c0i, g[k - 1]);
+    }
+    cr[0] = -(cr[1] + cr[2] + cr[3]);
+    cs[0] = -(cs[1] + cs[2] + cs[3]);
+    const T Vm = V * T(S.W / 4);
+    const T Vc00 = V * c(0);
+    const T mo = Vc00 * T(S.M2[0][1]);
+    T rho[4], sig[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        rho[k] = Vm * cr[k] + mo;
+        sig[k] = Vm * cs[k];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) A[4 * r + s] = K[r][s] + rho[r] + sig[s];
+    if constexpr (S.M2[0][0] != S.M2[0][1]) {
+        const T dl = Vc00 * T(S.M2[0][0] - S.M2[0][1]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) A[5 * r] += dl;
+    }
+    const V3<T> dv = {c(17), c(18), c(19)};
+    T t[4];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) t[k] = dot(dv, g[k - 1]);
+    t[0] = -(t[1] + t[2] + t[3]);
+    const T e = Vm * c(16);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) b[r] = VW * t[r] + e;
+}
+
 // Laplace load vector: b_r = V sum_q w_q d0_q phi_r(q) (d0 per element: V d0 m_r).
 template <class T, int QUAD, int CPQ, class CS> __device__ __forceinline__ void tet_poisson_b(T V, const CS &c, T b[4]) {
     constexpr TetSums S = tet_sums<QUAD>();

@@ -145,6 +145,31 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 __device__ __forceinline__ double dw_to_double(DW v) { return f2d_bits(v.h) + f2d_bits(v.l); }
 
+// The same conversion with integer operations only, for kernels whose double pipe
+// is the busier one: after renormalisation (|l| <= ulp(h)/2) the double of h is
+// exact, and l is added as an integer count k of ulps of that double,
+// k = trunc(l / ulp), |k| < 2^30 (error below one ulp of the result). When h is a
+// power of two and l has the opposite sign the result lies in the binade below,
+// whose ulp is half as large. Zero and subnormal h give a signed zero.
+__device__ __forceinline__ double dw_to_double_int(DW v) {
+    const DW n = dw_two_sum(v.h, v.l);
+    const uint32_t bh = __float_as_uint(n.h), bl = __float_as_uint(n.l);
+    const uint32_t eh = (bh >> 23) & 0xFFu, el = (bl >> 23) & 0xFFu;
+    const uint32_t sh = bh & 0x80000000u;
+    const bool nh = eh != 0u;
+    const uint32_t whi = nh ? ((((bh >> 3) & 0x0FFFFFFFu) + 0x38000000u) | sh) : sh;
+    const uint32_t wlo = nh ? (bh << 29) : 0u;
+    const bool down = (bh & 0x7FFFFFu) == 0u && ((bl ^ bh) & 0x80000000u) != 0u;
+    // biased exponent of t = l * 2^(52 - E_h), one more in the binade below
+    const int te = int(el) - int(eh) + (down ? 180 : 179);
+    int k = 0;
+    if (el != 0u && te >= 1 && nh) k = __float2int_rz(__uint_as_float((bl & 0x807FFFFFu) | (uint32_t(te) << 23)));
+    // k has l's sign; the bit pattern holds |h|, so negate for negative h
+    const long long d = sh ? -static_cast<long long>(k) : static_cast<long long>(k);
+    return __longlong_as_double(
+        static_cast<long long>(((static_cast<unsigned long long>(whi) << 32) | wlo) + static_cast<unsigned long long>(d)));
+}
+
 // Sum of N products of double-words, accumulated as in the Dot2 algorithm of
 // Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26(6), 2005): the float products
 // h_i h'_i are summed with TwoSum, and their rounding errors, the TwoSum errors

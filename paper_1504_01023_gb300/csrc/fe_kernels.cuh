@@ -66,6 +66,10 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CP
         const double V = fabs(geo.det);
         if (KIND == POISSON) {
             tet_poisson_products<double, QUAD, CPQ>(geo, 1.0 / V, V, c, A, b);
+        } else if constexpr (!CPQ) {
+            const double inv = 1.0 / geo.det;
+            const V3<double> g[3] = {inv * geo.a[0], inv * geo.a[1], inv * geo.a[2]};
+            tet_generic_products_pe<double, QUAD>(g, V, c, A, b);
         } else {
             const double inv = 1.0 / geo.det;
             V3<double> g[4];
@@ -157,12 +161,17 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, C
             poisson(geo, dw_abs(inv), V, cd, A, b, poor);
         } else {
             DW Ad[16], bd[4];
-            V3<DW> g[4];
-            g[1] = inv * geo.a[0];
-            g[2] = inv * geo.a[1];
-            g[3] = inv * geo.a[2];
-            g[0] = -(g[1] + g[2] + g[3]);
-            tet_generic_products<DW, QUAD, CPQ>(g, V, cd, Ad, bd);
+            if constexpr (!CPQ) {
+                const V3<DW> g[3] = {inv * geo.a[0], inv * geo.a[1], inv * geo.a[2]};
+                tet_generic_products_pe<DW, QUAD>(g, V, cd, Ad, bd);
+            } else {
+                V3<DW> g[4];
+                g[1] = inv * geo.a[0];
+                g[2] = inv * geo.a[1];
+                g[3] = inv * geo.a[2];
+                g[0] = -(g[1] + g[2] + g[3]);
+                tet_generic_products<DW, QUAD, CPQ>(g, V, cd, Ad, bd);
+            }
             poor = poor || !dw_group_ok<16>(Ad) || !dw_group_ok<4>(bd);
 #pragma unroll
             for (int k = 0; k < 16; ++k) A[k] = dw_to_double(Ad[k]);
@@ -174,6 +183,9 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, C
     // Laplace products (as tet_poisson_products): the ten distinct entries of the
     // symmetric A^e are computed and converted once each; b^e is uniform for
     // per-element coefficients or a one-point rule (m_r = |T|/4 for both rules).
+    // The six entries of G convert with integer operations, the rest with one DADD
+    // each, which balances the double and integer pipes of this kernel (measured:
+    // 6 + 5 beats 11 + 0 and 0 + 11).
     template <class CS>
     __device__ __forceinline__ static void poisson(const TetGeo<DW> &geo, DW invabs, DW V, const CS &c, double A[16],
                                                    double b[4], bool &poor) {
@@ -206,7 +218,7 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, C
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int s = r; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = A[4 * (s + 1) + (r + 1)] = dw_to_double(G[r][s]);
+            for (int s = r; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = A[4 * (s + 1) + (r + 1)] = dw_to_double_int(G[r][s]);
         if (uniform_b) {
             const double v = dw_to_double(bd[0]);
 #pragma unroll
