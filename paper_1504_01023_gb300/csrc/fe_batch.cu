@@ -27,11 +27,12 @@ __global__ void soa_to_aos_kernel(const double *__restrict__ in, int64_t stride,
     }
 }
 
-// One persistent launch per combination present: its tiles are a contiguous
-// segment of the plan's tile array, with its own counter.
+// One persistent launch per combination present: its items are a contiguous
+// run of the plan's segment table, its tiles numbered 0..n_tiles-1, with its own
+// counter.
 struct ClassLaunch {
     int combo = 0;
-    unsigned tile_off = 0, n_tiles = 0;
+    unsigned seg_off = 0, n_segs = 0, n_tiles = 0;
     int grid = 0;
     int64_t smem = 0;
 };
@@ -40,8 +41,8 @@ struct BatchPlan {
     size_t key = 0;
     std::vector<unsigned char> items_bytes;
     BatchItemDev *d_items = nullptr;
-    BatchTile *d_tiles = nullptr;
-    unsigned n_items = 0, n_tiles = 0;
+    BatchSeg *d_segs = nullptr;
+    unsigned n_items = 0, n_segs = 0;
     unsigned *d_counter = nullptr;   // kCombos counters
     Scratch scratch;
     int block = 128;
@@ -59,7 +60,7 @@ static void free_plan(BatchPlan *pl) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->d_items) cudaFree(pl->d_items);
-    if (pl->d_tiles) cudaFree(pl->d_tiles);
+    if (pl->d_segs) cudaFree(pl->d_segs);
     if (pl->d_counter) cudaFree(pl->d_counter);
     free_scratch(pl->scratch);
     delete pl;
@@ -74,44 +75,46 @@ void batch_destroy(fe_ctx *ctx) {
 }
 
 // Relative cost of one element of a combination (bytes moved plus arithmetic),
-// used only to order tiles longest-first.
+// used only to launch the heaviest combinations first.
 static double combo_cost(int combo) {
     static const double cost[12] = {1.0, 1.0, 1.1, 1.2, 1.4, 1.5, 1.5, 1.8, 2.5, 2.6, 6.0, 8.0};
     return combo >= 0 && combo < 12 ? cost[combo] : 1.0;
 }
 
-// Tiles of B consecutive elements, grouped by combination (heaviest
-// combination first) and, within one, ordered by decreasing size.
-static std::vector<BatchTile> make_tiles(const std::vector<BatchItemDev> &items, int B, std::vector<ClassLaunch> &classes) {
-    std::vector<std::vector<std::pair<double, BatchTile>>> per(kCombos);
+// Segment table of tiles of B consecutive elements: items grouped by combination
+// (heaviest combination first) and, within one, largest first, each with the
+// index of its first tile. Work is proportional to the number of items, not of
+// tiles. Fails if a combination has 2^32 tiles or more.
+static bool make_segs(const std::vector<BatchItemDev> &items, int B, std::vector<BatchSeg> &out,
+                      std::vector<ClassLaunch> &classes) {
+    std::vector<std::vector<unsigned>> per(kCombos);
     for (unsigned i = 0; i < items.size(); ++i) {
-        const int64_t n = items[i].p.n;
         const int c = items[i].combo;
-        if (c < 0 || c >= kCombos) continue;
-        for (int64_t e0 = 0; e0 < n; e0 += B) {
-            BatchTile tl;
-            tl.item = i;
-            tl.first = e0;
-            tl.count = unsigned(std::min<int64_t>(B, n - e0));
-            per[c].push_back({double(tl.count), tl});
-        }
+        if (c >= 0 && c < kCombos && items[i].p.n > 0) per[c].push_back(i);
     }
     std::vector<int> order(kCombos);
     for (int c = 0; c < kCombos; ++c) order[c] = c;
     std::stable_sort(order.begin(), order.end(), [](int a, int b) { return combo_cost(a) > combo_cost(b); });
-    std::vector<BatchTile> out;
+    out.clear();
     classes.clear();
     for (int c : order) {
         if (per[c].empty()) continue;
-        std::stable_sort(per[c].begin(), per[c].end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+        std::stable_sort(per[c].begin(), per[c].end(),
+                         [&](unsigned a, unsigned b) { return items[a].p.n > items[b].p.n; });
         ClassLaunch cl;
         cl.combo = c;
-        cl.tile_off = unsigned(out.size());
-        cl.n_tiles = unsigned(per[c].size());
-        for (auto &x : per[c]) out.push_back(x.second);
+        cl.seg_off = unsigned(out.size());
+        cl.n_segs = unsigned(per[c].size());
+        uint64_t tiles = 0;
+        for (unsigned i : per[c]) {
+            out.push_back(BatchSeg{i, unsigned(tiles), static_cast<long long>(items[i].p.n)});
+            tiles += uint64_t((items[i].p.n + B - 1) / B);
+            if (tiles >= (uint64_t(1) << 32)) return false;
+        }
+        cl.n_tiles = unsigned(tiles);
         classes.push_back(cl);
     }
-    return out;
+    return true;
 }
 
 static std::mutex g_attr_mu;
@@ -140,16 +143,18 @@ static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes, in
     return FE_OK;
 }
 
-static fe_status upload_tiles(fe_ctx *ctx, BatchPlan *pl, const std::vector<BatchItemDev> &items, int B) {
-    std::vector<BatchTile> tiles = make_tiles(items, B, pl->classes);
-    if (pl->d_tiles) cudaFree(pl->d_tiles);
-    pl->d_tiles = nullptr;
-    pl->n_tiles = unsigned(tiles.size());
-    fe_status st = cuda_check(ctx, cudaMalloc(&pl->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(BatchTile)),
-                              "cudaMalloc(tiles)");
+static fe_status upload_segs(fe_ctx *ctx, BatchPlan *pl, const std::vector<BatchItemDev> &items, int B) {
+    std::vector<BatchSeg> segs;
+    if (!make_segs(items, B, segs, pl->classes))
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "2^32 or more tiles of one combination in a batch");
+    if (pl->d_segs) cudaFree(pl->d_segs);
+    pl->d_segs = nullptr;
+    pl->n_segs = unsigned(segs.size());
+    fe_status st = cuda_check(ctx, cudaMalloc(&pl->d_segs, std::max<size_t>(1, segs.size()) * sizeof(BatchSeg)),
+                              "cudaMalloc(segments)");
     if (st != FE_OK) return st;
-    st = cuda_check(ctx, cudaMemcpy(pl->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice),
-                    "cudaMemcpy(tiles)");
+    st = cuda_check(ctx, cudaMemcpy(pl->d_segs, segs.data(), segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice),
+                    "cudaMemcpy(segments)");
     if (st != FE_OK) return st;
     pl->block = B;
     return size_classes(ctx, pl->classes, B);
@@ -162,10 +167,10 @@ static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemsetAsync(batch)");
     int *status = ctx->scratch.status;
     for (const auto &cl : pl->classes) {
-        const BatchTile *tiles = pl->d_tiles + cl.tile_off;
-        unsigned n_tiles = cl.n_tiles;
+        const BatchSeg *segs = pl->d_segs + cl.seg_off;
+        unsigned n_segs = cl.n_segs, n_tiles = cl.n_tiles;
         unsigned *counter = pl->d_counter + cl.combo;
-        void *args[] = {&pl->d_items, &pl->n_items, &tiles, &n_tiles, &counter, &status};
+        void *args[] = {&pl->d_items, &pl->n_items, &segs, &n_segs, &n_tiles, &counter, &status};
         e = cudaLaunchKernel(kernel_batch(cl.combo), dim3(cl.grid), dim3(pl->block), args, size_t(cl.smem), st);
         if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
     }
@@ -228,7 +233,7 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         for (int B : {64, 128, 256}) {
-            st = upload_tiles(ctx, pl, dev, B);
+            st = upload_segs(ctx, pl, dev, B);
             if (st == FE_ERR_UNSUPPORTED) {   // tile too large for shared memory at this size
                 st = FE_OK;
                 continue;
@@ -254,7 +259,7 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    if (st == FE_OK) st = upload_tiles(ctx, pl, dev, bestB);
+    if (st == FE_OK) st = upload_segs(ctx, pl, dev, bestB);
     // capture the launch sequence once; later submissions replay it
     if (st == FE_OK) {
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -280,9 +285,9 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
 // ---------------------------------------------------------------------------
 void dyn_batch_free(DynBatch &db) {
     if (db.d_items) cudaFree(db.d_items);
-    if (db.d_tiles) cudaFree(db.d_tiles);
+    if (db.d_segs) cudaFree(db.d_segs);
     if (db.h_items) cudaFreeHost(db.h_items);
-    if (db.h_tiles) cudaFreeHost(db.h_tiles);
+    if (db.h_segs) cudaFreeHost(db.h_segs);
     if (db.d_counter) cudaFree(db.d_counter);
     free_scratch(db.scratch);
     db = DynBatch{};
@@ -320,26 +325,28 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
         it.p.status = ctx->scratch.status;
     }
     std::vector<ClassLaunch> classes;
-    std::vector<BatchTile> tiles = make_tiles(items, B, classes);
+    std::vector<BatchSeg> segs;
+    if (!make_segs(items, B, segs, classes))
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "2^32 or more tiles of one combination in a batch");
     r = grow(ctx, reinterpret_cast<void **>(&db.d_items), reinterpret_cast<void **>(&db.h_items), db.cap_items,
              items.size(), sizeof(BatchItemDev));
     if (r == FE_OK)
-        r = grow(ctx, reinterpret_cast<void **>(&db.d_tiles), reinterpret_cast<void **>(&db.h_tiles), db.cap_tiles,
-                 std::max<size_t>(tiles.size(), 1), sizeof(BatchTile));
+        r = grow(ctx, reinterpret_cast<void **>(&db.d_segs), reinterpret_cast<void **>(&db.h_segs), db.cap_segs,
+                 std::max<size_t>(segs.size(), 1), sizeof(BatchSeg));
     if (r != FE_OK) return r;
     memcpy(db.h_items, items.data(), items.size() * sizeof(BatchItemDev));
-    memcpy(db.h_tiles, tiles.data(), tiles.size() * sizeof(BatchTile));
+    memcpy(db.h_segs, segs.data(), segs.size() * sizeof(BatchSeg));
     cudaError_t e = cudaMemcpyAsync(db.d_items, db.h_items, items.size() * sizeof(BatchItemDev), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(db.d_tiles, db.h_tiles, tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(db.d_segs, db.h_segs, segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemcpyAsync(batch tables)");
     r = size_classes(ctx, classes, B);
     if (r != FE_OK) return r;
     BatchPlan pl;
     pl.d_items = db.d_items;
-    pl.d_tiles = db.d_tiles;
+    pl.d_segs = db.d_segs;
     pl.n_items = unsigned(items.size());
-    pl.n_tiles = unsigned(tiles.size());
+    pl.n_segs = unsigned(segs.size());
     pl.d_counter = db.d_counter;
     pl.scratch = db.scratch;
     pl.block = B;
@@ -347,7 +354,7 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     r = enqueue_batch(ctx, &pl, st);
     // the plan only borrowed the tables
     pl.d_items = nullptr;
-    pl.d_tiles = nullptr;
+    pl.d_segs = nullptr;
     pl.d_counter = nullptr;
     pl.scratch = Scratch{};
     if (r == FE_OK) g_launches.fetch_add(uint64_t(plan_launches(&pl)));

@@ -1,7 +1,8 @@
 // Batched persistent kernels: many element sets of uneven size and mixed
 // type/kind. Each block repeatedly takes the next tile of its combination from a
-// global counter (tiles are ordered by decreasing cost on the host) and runs the
-// same tile code as the single-set kernels; nothing waits on another block.
+// global counter and runs the same tile code as the single-set kernels; nothing
+// waits on another block. Tiles are implicit (BatchSeg): the tile index gives the
+// item by binary search over the combination's segment table.
 #include "fe_kernels.cuh"
 
 namespace fe {
@@ -26,12 +27,11 @@ FE_COMBO(11, PRISM, GENERIC, Q_PRISM6, 1)
 #undef FE_COMBO
 
 template <int ID>
-__device__ __forceinline__ bool tile_combo(const BatchItemDev *item, const BatchTile *tile, unsigned char *smem,
+__device__ __forceinline__ bool tile_combo(const BatchItemDev *item, long long first, int count, unsigned char *smem,
                                            uint64_t *bar, unsigned *phase) {
     using K = ComboCfg<ID>;
     const ElemParams p = item->p;
-    return process_tile<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, tile->first, int(tile->count), smem, bar,
-                                                                          *phase);
+    return process_tile<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, first, count, smem, bar, *phase);
 }
 
 template <int ID> __device__ __forceinline__ void fix_combo(const ElemParams &p, int64_t e) {
@@ -39,34 +39,69 @@ template <int ID> __device__ __forceinline__ void fix_combo(const ElemParams &p,
     fixup_element<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, e);
 }
 
+// Next tile of a combination for one thread: counter, then the item by binary
+// search over the segment table (segs[0].first_tile == 0).
+struct TileRef {
+    unsigned t, item;
+    long long first;
+    int count;
+};
+template <int ID>
+__device__ __forceinline__ TileRef next_tile(const BatchItemDev *items, unsigned n_items, const BatchSeg *segs,
+                                             unsigned n_segs, unsigned n_tiles, unsigned *tile_counter, int B) {
+    TileRef r{atomicAdd(tile_counter, 1u), 0xFFFFFFFFu, 0, 0};
+    if (r.t < n_tiles && n_segs > 0) {
+        unsigned lo = 0, hi = n_segs;
+        while (hi - lo > 1) {
+            const unsigned mid = (lo + hi) >> 1;
+            if (segs[mid].first_tile <= r.t) lo = mid;
+            else hi = mid;
+        }
+        const BatchSeg sg = segs[lo];
+        r.first = static_cast<long long>(r.t - sg.first_tile) * B;
+        if (sg.item < n_items && r.first < sg.n && items[sg.item].combo == ID) {
+            r.item = sg.item;
+            const long long left = sg.n - r.first;
+            r.count = left < B ? int(left) : B;
+        }
+    }
+    return r;
+}
+
 // Persistent kernel of one combination: blocks take the next tile of this
 // combination from its counter until none is left. A batch launches one such
 // kernel per combination present (one register allocation per combination).
+// One lane of warp 1 looks up the following tile while the block loads and
+// computes the current one (double-buffered in shared memory), so the counter
+// and the search stay off the block's critical path.
 template <int ID>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchItemDev *__restrict__ items, unsigned n_items,
-                                                    const BatchTile *__restrict__ tiles, unsigned n_tiles,
+                                                    const BatchSeg *__restrict__ segs, unsigned n_segs, unsigned n_tiles,
                                                     unsigned *tile_counter, int *status) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
-    __shared__ unsigned s_tile;
+    __shared__ TileRef s_ref[2];
+    const int B = blockDim.x;
+    const int R = B > 32 ? 32 : 0;  // the looking-up thread (not the copy issuer, thread 0)
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
+    if (threadIdx.x == R) s_ref[0] = next_tile<ID>(items, n_items, segs, n_segs, n_tiles, tile_counter, B);
     __syncthreads();
     unsigned phase = 0;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-        __syncthreads();
-        const unsigned t = s_tile;
-        __syncthreads();
-        if (t >= n_tiles) break;
-        const BatchTile *tp = tiles + t;
-        if (tp->item >= n_items || tp->count > blockDim.x || items[tp->item].combo != ID) {
+    for (unsigned i = 0;; ++i) {
+        const TileRef cur = s_ref[i & 1u];
+        if (cur.t >= n_tiles) break;
+        // s_ref[(i + 1) & 1] was last read at the start of iteration i - 1, before
+        // the barriers of that tile
+        if (threadIdx.x == R) s_ref[(i + 1) & 1u] = next_tile<ID>(items, n_items, segs, n_segs, n_tiles, tile_counter, B);
+        if (cur.item == 0xFFFFFFFFu) {
             if (threadIdx.x == 0) atomicOr(status, ST_BAD_TILE);
+            __syncthreads();
             continue;
         }
-        if (!tile_combo<ID>(items + tp->item, tp, smem, &bar, &phase)) return;
+        if (!tile_combo<ID>(items + cur.item, cur.first, cur.count, smem, &bar, &phase)) return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }

@@ -71,10 +71,13 @@ struct BatchItemDev {
     int combo;                // (type, kind, rule, coefficient mode), see batch_combo()
     int pad;
 };
-struct BatchTile {
+// The tiles of one combination are implicit: its items, largest first, each with
+// the index of its first tile within the combination (a prefix sum of
+// ceil(n / B)). A block maps a tile index to its item by binary search.
+struct BatchSeg {
     unsigned int item;        // index into the item table
-    unsigned int count;       // elements in this tile
-    long long first;          // first element of the tile within the item
+    unsigned int first_tile;  // tiles of earlier items of this combination
+    long long n;              // elements of the item
 };
 // Dense index of the 12 (type, kind, rule, coefficient mode) combinations of the
 // batched kernel, or -1.

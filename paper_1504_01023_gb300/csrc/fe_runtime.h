@@ -36,7 +36,7 @@ struct Shape {
 struct ServeState;          // fe_serve.cu
 struct BatchCache;          // fe_batch.cu
 struct BatchItemDev;
-struct BatchTile;
+struct BatchSeg;
 
 struct MeshRec {
     fe_elem_type type;
@@ -101,8 +101,8 @@ Shape default_shape(fe_elem_type type);
 // from pinned staging with stream-ordered copies, launched without a graph.
 struct DynBatch {
     BatchItemDev *d_items = nullptr, *h_items = nullptr;
-    BatchTile *d_tiles = nullptr, *h_tiles = nullptr;
-    size_t cap_items = 0, cap_tiles = 0;
+    BatchSeg *d_segs = nullptr, *h_segs = nullptr;
+    size_t cap_items = 0, cap_segs = 0;
     unsigned *d_counter = nullptr;
     Scratch scratch;
 };

@@ -1,8 +1,14 @@
 // Serving loop: integration requests on resident meshes arrive at any time; a
-// scheduler thread admits them under the HBM budget, merges every waiting
-// mixed-precision request into one batched launch (continuous batching), keeps
+// scheduler thread admits them under the HBM budget, merges waiting
+// mixed-precision requests into batched launches (continuous batching), keeps
 // up to serve_slots launches in flight on their own streams, and stamps each
 // request's completion from a host callback on its stream.
+//
+// Launch policy: while less than kFeedElems elements are in flight, waiting
+// requests launch at once (an idle or lightly loaded GPU adds no queueing delay);
+// beyond that they accumulate until the work in flight drops below it, so that a
+// loaded GPU runs fewer, larger launches. One launch takes at most kLaunchElems
+// elements (the first request always fits).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,6 +38,9 @@ struct Req {
 };
 
 struct ServeState;
+
+constexpr uint64_t kFeedElems = uint64_t(16) << 20;    // ~1 ms of GPU work in flight
+constexpr uint64_t kLaunchElems = uint64_t(64) << 20;
 struct Slot {
     ServeState *owner = nullptr;
     cudaStream_t stream = nullptr;
@@ -39,6 +48,7 @@ struct Slot {
     std::atomic<int> done{0};          // set by the stream's host callback
     double t_done = 0;                 // written by the callback before `done`
     std::vector<uint64_t> tickets;
+    uint64_t elems = 0;                // elements of the launch in flight (mutex)
     DynBatch dyn;
     Scratch plain;
 };
@@ -80,6 +90,7 @@ static void reap(ServeState *s) {
             }
         }
         sl.tickets.clear();
+        sl.elems = 0;
         sl.done.store(0, std::memory_order_relaxed);
         sl.busy = false;
     }
@@ -97,6 +108,8 @@ static void launch_slot(ServeState *s, int si, std::vector<uint64_t> &batch) {
     Slot &sl = *s->slots[si];
     sl.busy = true;
     sl.tickets = batch;
+    sl.elems = 0;
+    for (uint64_t tk : batch) sl.elems += uint64_t(s->reqs[tk].mesh.n_elem);
     std::vector<BatchItemDev> items;
     const double t = now_us();
     fe_status st = FE_OK;
@@ -171,19 +184,24 @@ static void scheduler(ServeState *s) {
         reap(s);
         // admit waiting requests in arrival order while the budget allows
         int free_slot = -1;
-        for (size_t i = 0; i < s->slots.size(); ++i)
+        uint64_t in_flight = 0;
+        for (size_t i = 0; i < s->slots.size(); ++i) {
             if (!s->slots[i]->busy) {
-                free_slot = int(i);
-                break;
+                if (free_slot < 0) free_slot = int(i);
+            } else {
+                in_flight += s->slots[i]->elems;
             }
-        if (free_slot >= 0 && !s->waiting.empty()) {
+        }
+        if (free_slot >= 0 && !s->waiting.empty() && in_flight < kFeedElems) {
             std::vector<uint64_t> batch;
+            uint64_t elems = 0;
             const uint64_t resident = s->ctx->hbm_used.load();
             while (!s->waiting.empty()) {
                 Req &q = s->reqs[s->waiting.front()];
-                if (resident + s->out_used + q.out_bytes > s->ctx->hbm_budget && !batch.empty()) break;
                 if (resident + s->out_used + q.out_bytes > s->ctx->hbm_budget) break;  // wait for releases
+                if (!batch.empty() && elems + uint64_t(q.mesh.n_elem) > kLaunchElems) break;
                 s->out_used += q.out_bytes;
+                elems += uint64_t(q.mesh.n_elem);
                 batch.push_back(s->waiting.front());
                 s->waiting.pop_front();
             }

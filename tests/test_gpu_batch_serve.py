@@ -146,10 +146,11 @@ def test_serve_alone_and_in_the_mix(ctx, mix):
         Ao, bo, _ = oracle.integrate(et, kind, ORACLE_RULE[quad], mesh, c, coef_per_q=cm == api.PER_QPOINT, n_threads=8)
         ea, eb = max_errors(An, bn, Ao, bo)
         assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED]
-    # in the mix: the large request first, then every small one three times from two
-    # threads while it runs
+    # in the mix: the large request six times first (about a millisecond of GPU
+    # work), then every small one once from this thread and twice more from two
+    # threads while they run
     big = len(reqs) - 1
-    tickets = [(big, ctx.serve_submit(*(reqs[big][:1] + reqs[big][2:6])))]
+    tickets = [(big, ctx.serve_submit(*(reqs[big][:1] + reqs[big][2:6]))) for _ in range(6)]
     lock = threading.Lock()
 
     def client(order):
@@ -159,7 +160,8 @@ def test_serve_alone_and_in_the_mix(ctx, mix):
             with lock:
                 tickets.append((j, tk))
 
-    idx = list(range(big)) * 3
+    client(list(range(big)))
+    idx = list(range(big)) * 2
     th = [threading.Thread(target=client, args=(idx[k::2],)) for k in range(2)]
     for t in th:
         t.start()
@@ -176,8 +178,9 @@ def test_serve_alone_and_in_the_mix(ctx, mix):
         assert oracle.rel_frobenius(An, alone[j][0]).max() <= 1e-6
         assert oracle.rel_frobenius(bn, alone[j][1]).max() <= 1e-6
         ctx.serve_release(tk)
-    # requests that arrived while the large one ran were launched before it finished
-    _, bl, bd = spans[tickets[0][1]]
+    # requests that arrived while the large ones ran were launched before the last
+    # of them finished
+    bd = max(d for tk, (j, l, d) in spans.items() if j == big)
     overlapped = sum(1 for tk, (j, l, d) in spans.items() if j != big and l < bd)
     assert overlapped > 0
     for mid, *_ in reqs:
