@@ -692,8 +692,8 @@ def bench_serve(api, dev, args):
 
 def serve_saturated(api, ctx, meshes, args, depth=48):
     """Capacity of the serving loop: a closed loop keeps `depth` requests of the same
-    mix outstanding (a new one is submitted as each completes) for about
-    args.serve_seconds; throughput = elements completed / (last completion - first
+    mix outstanding (a new one is submitted as each completes, completions taken
+    from the completion queue) for about args.serve_seconds; throughput = elements completed / (last completion - first
     submission), with the library's own timestamps. HBM fraction from the
     algorithmic bytes of each request."""
     from paper_1504_01023_gb300 import meshgen
@@ -714,10 +714,7 @@ def serve_saturated(api, ctx, meshes, args, depth=48):
     for _ in range(depth):
         submit()
     while out:
-        for tk in list(out):
-            r = ctx.serve_poll(tk)
-            if r is None:
-                continue
+        for tk, r in ctx.serve_wait_any(timeout_us=100000, max_results=64):
             m = out.pop(tk)
             errors += r.status != 0
             first = r.t_submit_us if first is None else min(first, r.t_submit_us)
@@ -728,7 +725,6 @@ def serve_saturated(api, ctx, meshes, args, depth=48):
             ctx.serve_release(tk)
             if time.perf_counter() < t_end:
                 submit()
-        time.sleep(0.0001)
     span = (last - first) / 1e6
     peak, src = measured_peaks()
     gbs = nbytes / span / 1e9

@@ -30,7 +30,8 @@
  *    vertices 0..2 the bottom triangle (zeta = -1) and 3..5 the top one, vertex
  *    k+3 above vertex k.
  *  - A context is used by one host thread at a time, except fe_serve_submit,
- *    fe_serve_poll and fe_serve_release, which may be called from any thread.
+ *    fe_serve_poll, fe_serve_wait_any and fe_serve_release, which may be called
+ *    from any thread.
  */
 #ifndef FE_H_
 #define FE_H_
@@ -100,7 +101,7 @@ typedef struct fe_ctx fe_ctx;
 typedef struct fe_ctx_config {
     int device;                    /* CUDA device ordinal */
     uint64_t hbm_budget_bytes;     /* serving admission budget; 0 = 120e9 bytes */
-    int serve_slots;               /* serving launches in flight at once; 0 = 4 */
+    int serve_slots;               /* serving launches in flight at once; 0 = 4, at most 64 */
     int autotune;                  /* 1: time the candidate launch shapes of a key on
                                       its first use and keep the fastest */
     const char *tuning_cache_path; /* text file holding tuned shapes; NULL = none */
@@ -260,6 +261,15 @@ fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket);
 fe_status fe_serve_poll(fe_ctx *ctx, uint64_t ticket, fe_result *res);
 /* Free a finished request's outputs and return their bytes to the budget. */
 fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket);
+/* Completion queue. Waits up to timeout_us microseconds (0: do not wait) until at
+   least one request has finished that this call has not yet returned, then writes
+   up to `max` finished requests, in completion order, to tickets[] and results[]
+   (host arrays of `max` entries) and their number to *n_out (0 on timeout). Each
+   finished request is returned once; requests released before they are returned
+   are skipped. Results are as fe_serve_poll's; the outputs stay valid until
+   fe_serve_release. Thread-safe; a request is returned to exactly one caller. */
+fe_status fe_serve_wait_any(fe_ctx *ctx, int64_t timeout_us, uint64_t *tickets, fe_result *results, int max,
+                            int *n_out);
 
 /* Number of kernels this library has launched in this process (graph replays
    count the kernels in the graph). */

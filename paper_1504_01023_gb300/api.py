@@ -87,6 +87,8 @@ _SIGS = [
     ("fe_serve_submit", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
     ("fe_serve_release", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("fe_serve_wait_any", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result),
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("fe_launch_count", ctypes.c_uint64, []),
     ("fe_ctx_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("fe_ctx_kernel_time", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
@@ -378,6 +380,21 @@ class Context:
             return None
         _check(st, self.h)
         return res
+
+    def serve_wait_any(self, timeout_us=1000, max_results=64):
+        """Finished requests not yet returned by this call, in completion order:
+        a list of (ticket, Result), empty on timeout."""
+        if getattr(self, "_wait_bufs", None) is None or len(self._wait_bufs[0]) < max_results:
+            self._wait_bufs = ((ctypes.c_uint64 * max_results)(), (Result * max_results)())
+        tks, res = self._wait_bufs
+        n = ctypes.c_int()
+        _check(load().fe_serve_wait_any(self.h, int(timeout_us), tks, res, max_results, ctypes.byref(n)), self.h)
+        out = []
+        for i in range(n.value):
+            r = Result()
+            ctypes.pointer(r)[0] = res[i]
+            out.append((tks[i], r))
+        return out
 
     def serve_release(self, ticket):
         self._keep.pop(ticket, None)

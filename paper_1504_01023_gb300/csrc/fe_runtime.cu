@@ -595,7 +595,7 @@ fe_status fe_ctx_create(const fe_ctx_config *cfg, fe_ctx **out) {
         if (ch == ' ') ch = '_';
     ctx->autotune = c.autotune;
     ctx->hbm_budget = c.hbm_budget_bytes ? c.hbm_budget_bytes : 120000000000ull;
-    ctx->serve_slots = c.serve_slots > 0 ? c.serve_slots : 4;
+    ctx->serve_slots = c.serve_slots > 0 ? std::min(c.serve_slots, 64) : 4;
     if (c.tuning_cache_path) ctx->tuning_cache_path = c.tuning_cache_path;
     load_tuning_cache(ctx);
     fe_status st = ensure_scratch(ctx, ctx->scratch, 0);

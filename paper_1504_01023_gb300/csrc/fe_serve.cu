@@ -8,7 +8,8 @@
 // requests launch at once (an idle or lightly loaded GPU adds no queueing delay);
 // beyond that they accumulate until the work in flight drops below it, so that a
 // loaded GPU runs fewer, larger launches. One launch takes at most kLaunchElems
-// elements (the first request always fits).
+// elements (the first request always fits), so completions keep arriving while
+// later launches run.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,12 +36,13 @@ struct Req {
     fe_status status = FE_OK;
     int state = 0;  // 0 waiting, 1 running, 2 done
     int slot = -1;
+    bool returned = false;  // handed out by fe_serve_wait_any
 };
 
 struct ServeState;
 
 constexpr uint64_t kFeedElems = uint64_t(16) << 20;    // ~1 ms of GPU work in flight
-constexpr uint64_t kLaunchElems = uint64_t(64) << 20;
+constexpr uint64_t kLaunchElems = uint64_t(16) << 20;   // measured: 16M > 32M, 64M for large requests
 struct Slot {
     ServeState *owner = nullptr;
     cudaStream_t stream = nullptr;
@@ -49,6 +51,7 @@ struct Slot {
     double t_done = 0;                 // written by the callback before `done`
     std::vector<uint64_t> tickets;
     uint64_t elems = 0;                // elements of the launch in flight (mutex)
+    bool launching = false;            // between admission and publication (mutex)
     DynBatch dyn;
     Scratch plain;
 };
@@ -61,6 +64,11 @@ struct ServeState {
     bool stop = false;
     std::deque<uint64_t> waiting;
     std::unordered_map<uint64_t, Req> reqs;
+    // completion queue: finished tickets in completion order, each returned once
+    // by fe_serve_wait_any; entries of released requests are skipped and, when
+    // they pile up, compacted away (the queue stays O(live requests))
+    std::deque<uint64_t> done_q;
+    std::condition_variable done_cv;
     uint64_t next_ticket = 1;
     std::vector<std::unique_ptr<Slot>> slots;
     cudaMemPool_t pool = nullptr;
@@ -77,16 +85,27 @@ static void CUDART_CB on_slot_done(void *p) {
     sl->owner->cv.notify_all();
 }
 
-// Mark the requests of finished slots done and free the slots (lock held).
+// Mark the requests of finished slots done, in completion order, queue them for
+// fe_serve_wait_any, and free the slots (lock held).
 static void reap(ServeState *s) {
+    Slot *fin[64];
+    int nf = 0;
     for (auto &up : s->slots) {
         Slot &sl = *up;
-        if (!sl.busy || !sl.done.load(std::memory_order_acquire)) continue;
+        if (!sl.busy || sl.launching || !sl.done.load(std::memory_order_acquire)) continue;
+        if (nf < 64) fin[nf++] = &sl;
+    }
+    std::sort(fin, fin + nf, [](const Slot *a, const Slot *b) { return a->t_done < b->t_done; });
+    bool any = false;
+    for (int f = 0; f < nf; ++f) {
+        Slot &sl = *fin[f];
         for (uint64_t tk : sl.tickets) {
             auto it = s->reqs.find(tk);
             if (it != s->reqs.end()) {
                 it->second.t_done = sl.t_done;
                 it->second.state = 2;
+                s->done_q.push_back(tk);
+                any = true;
             }
         }
         sl.tickets.clear();
@@ -94,6 +113,27 @@ static void reap(ServeState *s) {
         sl.done.store(0, std::memory_order_relaxed);
         sl.busy = false;
     }
+    if (any) s->done_cv.notify_all();
+    if (s->done_q.size() > 2 * s->reqs.size() + 4096) {
+        std::deque<uint64_t> keep;
+        for (uint64_t tk : s->done_q) {
+            auto it = s->reqs.find(tk);
+            if (it != s->reqs.end() && !it->second.returned) keep.push_back(tk);
+        }
+        s->done_q.swap(keep);
+    }
+}
+
+static void fill_result(const Req &q, fe_result *res) {
+    res->status = q.status;
+    res->type = q.mesh.type;
+    res->n_elem = q.mesh.n_elem;
+    res->A = q.A;
+    res->b = q.b;
+    res->flags = q.flags;
+    res->t_submit_us = q.t_submit;
+    res->t_launch_us = q.t_launch;
+    res->t_done_us = q.t_done;
 }
 
 static uint64_t out_bytes_of(const MeshRec &m, fe_precision prec) {
@@ -102,79 +142,121 @@ static uint64_t out_bytes_of(const MeshRec &m, fe_precision prec) {
     return r256(uint64_t(m.n_elem) * ns * ns * cs) + r256(uint64_t(m.n_elem) * ns * cs) + r256(uint64_t(m.n_elem));
 }
 
-// Launch everything admitted into a free slot (called with the lock held).
-static void launch_slot(ServeState *s, int si, std::vector<uint64_t> &batch) {
+// One admitted request as the launching code sees it, outside the lock.
+struct Job {
+    uint64_t ticket;
+    fe_request r;
+    MeshRec mesh;
+    void *A = nullptr, *b = nullptr;
+    uint8_t *flags = nullptr;
+    fe_status status = FE_OK;
+};
+
+// Allocate the outputs of the jobs and launch them on the slot's stream: mixed
+// requests as one batched launch, the others as their own launches; then the
+// slot's completion callback. Runs without the lock (it makes CUDA calls, which
+// may wait); touches only the jobs and the slot's own stream and tables.
+static void launch_jobs(ServeState *s, Slot &sl, std::vector<Job> &jobs) {
     fe_ctx *ctx = s->ctx;
-    Slot &sl = *s->slots[si];
-    sl.busy = true;
-    sl.tickets = batch;
-    sl.elems = 0;
-    for (uint64_t tk : batch) sl.elems += uint64_t(s->reqs[tk].mesh.n_elem);
     std::vector<BatchItemDev> items;
-    const double t = now_us();
-    fe_status st = FE_OK;
-    for (uint64_t tk : batch) {
-        Req &q = s->reqs[tk];
-        q.t_launch = t;
-        q.state = 1;
-        q.slot = si;
-        const MeshRec &m = q.mesh;
-        // outputs from the context's stream-ordered pool
-        const uint64_t ns = ns_of(m.type), cs = q.r.prec == FE_FP32_MIXED ? 4 : 8;
-        const uint64_t bA = uint64_t(m.n_elem) * ns * ns * cs, bB = uint64_t(m.n_elem) * ns * cs;
-        cudaError_t e = cudaMallocFromPoolAsync(&q.A, bA, s->pool, sl.stream);
-        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&q.b, bB, s->pool, sl.stream);
-        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&q.flags), size_t(m.n_elem), s->pool, sl.stream);
+    for (Job &j : jobs) {
+        const MeshRec &m = j.mesh;
+        // outputs from the context's stream-ordered pool: one allocation holding
+        // A, b and the flags, each part on a 256-byte boundary
+        const uint64_t ns = ns_of(m.type), cs = j.r.prec == FE_FP32_MIXED ? 4 : 8;
+        auto r256 = [](uint64_t v) { return (v + 255) / 256 * 256; };
+        const uint64_t bA = r256(uint64_t(m.n_elem) * ns * ns * cs), bB = r256(uint64_t(m.n_elem) * ns * cs);
+        void *base = nullptr;
+        cudaError_t e = cudaMallocFromPoolAsync(&base, bA + bB + r256(uint64_t(m.n_elem)), s->pool, sl.stream);
         if (e != cudaSuccess) {
-            q.status = cuda_check(ctx, e, "cudaMallocFromPoolAsync(serve outputs)");
+            j.status = cuda_check(ctx, e, "cudaMallocFromPoolAsync(serve outputs)");
             continue;
         }
-        fe_elem_args a{};
-        a.n_elem = m.n_elem;
-        a.coords = m.coords;
-        a.coords_layout = FE_LAYOUT_AOS;
-        a.kind = q.r.kind;
-        a.quad = q.r.quad;
-        a.coef_mode = q.r.coef_mode;
-        a.coefs = q.r.coefs;
-        a.coefs_layout = FE_LAYOUT_AOS;
-        a.prec = q.r.prec;
-        a.memory = FE_MEM_DEVICE;
-        fe_out o{};
-        o.A = q.A;
-        o.b = q.b;
-        o.layout = FE_LAYOUT_AOS;
-        o.flags = q.flags;
-        o.memory = FE_MEM_DEVICE;
-        if (q.r.prec == FE_FP32_MIXED) {
+        j.A = base;
+        j.b = static_cast<unsigned char *>(base) + bA;
+        j.flags = static_cast<uint8_t *>(base) + bA + bB;
+        if (j.r.prec == FE_FP32_MIXED) {
             BatchItemDev d;
             memset(&d, 0, sizeof d);
             d.p.n = m.n_elem;
             d.p.X = m.coords;
             d.p.xs = m.n_elem;
-            d.p.C = q.r.coefs;
+            d.p.C = j.r.coefs;
             d.p.cs = m.n_elem;
-            d.p.A = q.A;
-            d.p.B = q.b;
+            d.p.A = j.A;
+            d.p.B = j.b;
             d.p.os = m.n_elem;
-            d.p.flags = q.flags;
+            d.p.flags = j.flags;
             d.p.item = unsigned(items.size());
-            d.combo = batch_combo(m.type, q.r.kind, q.r.quad, q.r.coef_mode == FE_COEF_PER_QPOINT);
+            d.combo = batch_combo(m.type, j.r.kind, j.r.quad, j.r.coef_mode == FE_COEF_PER_QPOINT);
             items.push_back(d);
         } else {
+            fe_elem_args a{};
+            a.n_elem = m.n_elem;
+            a.coords = m.coords;
+            a.coords_layout = FE_LAYOUT_AOS;
+            a.kind = j.r.kind;
+            a.quad = j.r.quad;
+            a.coef_mode = j.r.coef_mode;
+            a.coefs = j.r.coefs;
+            a.coefs_layout = FE_LAYOUT_AOS;
+            a.prec = j.r.prec;
+            a.memory = FE_MEM_DEVICE;
+            fe_out o{};
+            o.A = j.A;
+            o.b = j.b;
+            o.layout = FE_LAYOUT_AOS;
+            o.flags = j.flags;
+            o.memory = FE_MEM_DEVICE;
             const Shape sh = default_shape(m.type);
-            q.status = launch_set(ctx, m.type, &a, &o, sl.plain, sl.stream, &sh);
+            j.status = launch_set(ctx, m.type, &a, &o, sl.plain, sl.stream, &sh);
         }
     }
     if (!items.empty()) {
-        st = dyn_batch_launch(ctx, sl.dyn, items, sl.stream);
+        const fe_status st = dyn_batch_launch(ctx, sl.dyn, items, sl.stream);
         if (st != FE_OK)
-            for (uint64_t tk : batch) {
-                Req &q = s->reqs[tk];
-                if (q.r.prec == FE_FP32_MIXED) q.status = st;
-            }
+            for (Job &j : jobs)
+                if (j.r.prec == FE_FP32_MIXED && j.status == FE_OK) j.status = st;
     }
     cudaLaunchHostFunc(sl.stream, on_slot_done, &sl);
+}
+
+// Launch an admitted batch into a free slot. Called with the lock held; releases
+// it around the CUDA calls. While the slot is `launching`, reap leaves it alone
+// (its callback may fire before the results are published); a running request
+// cannot be released, so its record stays in place meanwhile.
+static void launch_slot(ServeState *s, int si, std::vector<uint64_t> &batch, std::unique_lock<std::mutex> &lk) {
+    Slot &sl = *s->slots[si];
+    sl.busy = true;
+    sl.launching = true;
+    sl.elems = 0;
+    std::vector<Job> jobs;
+    jobs.reserve(batch.size());
+    const double t = now_us();
+    for (uint64_t tk : batch) {
+        Req &q = s->reqs[tk];
+        q.t_launch = t;
+        q.state = 1;
+        q.slot = si;
+        sl.elems += uint64_t(q.mesh.n_elem);
+        Job j;
+        j.ticket = tk;
+        j.r = q.r;
+        j.mesh = q.mesh;
+        jobs.push_back(j);
+    }
+    lk.unlock();
+    launch_jobs(s, sl, jobs);
+    lk.lock();
+    for (const Job &j : jobs) {
+        Req &q = s->reqs[j.ticket];
+        q.A = j.A;
+        q.b = j.b;
+        q.flags = j.flags;
+        q.status = j.status;
+    }
+    sl.tickets = batch;
+    sl.launching = false;
 }
 
 static void scheduler(ServeState *s) {
@@ -206,7 +288,7 @@ static void scheduler(ServeState *s) {
                 s->waiting.pop_front();
             }
             if (!batch.empty()) {
-                launch_slot(s, free_slot, batch);
+                launch_slot(s, free_slot, batch, lk);
                 continue;
             }
         }
@@ -225,11 +307,8 @@ void serve_destroy(fe_ctx *ctx) {
     if (s->th.joinable()) s->th.join();
     cudaSetDevice(ctx->device);
     for (auto &sl : s->slots) cudaStreamSynchronize(sl->stream);
-    for (auto &kv : s->reqs) {
+    for (auto &kv : s->reqs)
         if (kv.second.A) cudaFreeAsync(kv.second.A, s->slots[0]->stream);
-        if (kv.second.b) cudaFreeAsync(kv.second.b, s->slots[0]->stream);
-        if (kv.second.flags) cudaFreeAsync(kv.second.flags, s->slots[0]->stream);
-    }
     for (auto &sl : s->slots) {
         cudaStreamSynchronize(sl->stream);
         dyn_batch_free(sl->dyn);
@@ -328,37 +407,70 @@ fe_status fe_serve_poll(fe_ctx *ctx, uint64_t ticket, fe_result *res) {
     Req &q = it->second;
     if (q.state == 1 && q.slot >= 0 && s->slots[q.slot]->done.load(std::memory_order_acquire)) reap(s);
     if (q.state != 2) return FE_NOT_READY;
-    res->status = q.status;
-    res->type = q.mesh.type;
-    res->n_elem = q.mesh.n_elem;
-    res->A = q.A;
-    res->b = q.b;
-    res->flags = q.flags;
-    res->t_submit_us = q.t_submit;
-    res->t_launch_us = q.t_launch;
-    res->t_done_us = q.t_done;
+    fill_result(q, res);
     return q.status == FE_OK ? FE_OK : q.status;
+}
+
+fe_status fe_serve_wait_any(fe_ctx *ctx, int64_t timeout_us, uint64_t *tickets, fe_result *results, int max,
+                            int *n_out) {
+    if (!ctx || !tickets || !results || !n_out || max <= 0 || timeout_us < 0)
+        return set_error(ctx, FE_ERR_INVALID_ARG, "bad argument");
+    *n_out = 0;
+    fe_status st = ensure_serve(ctx);
+    if (st != FE_OK) return st;
+    ServeState *s = ctx->serve;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+    for (;;) {
+        reap(s);
+        int n = 0;
+        while (n < max && !s->done_q.empty()) {
+            const uint64_t tk = s->done_q.front();
+            s->done_q.pop_front();
+            auto it = s->reqs.find(tk);
+            if (it == s->reqs.end() || it->second.returned) continue;  // released meanwhile
+            it->second.returned = true;
+            tickets[n] = tk;
+            fill_result(it->second, &results[n]);
+            ++n;
+        }
+        if (n > 0 || timeout_us == 0) {
+            *n_out = n;
+            return FE_OK;
+        }
+        // the slot callbacks wake the scheduler, whose reap wakes this wait; the
+        // short period bounds the delay if a wake-up is missed
+        if (s->done_cv.wait_until(lk, std::min(deadline, std::chrono::steady_clock::now() +
+                                                             std::chrono::microseconds(500))) ==
+                std::cv_status::timeout &&
+            std::chrono::steady_clock::now() >= deadline) {
+            reap(s);
+            if (s->done_q.empty()) return FE_OK;
+        }
+    }
 }
 
 fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket) {
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
     ServeState *s = ctx->serve;
     if (!s) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown ticket");
+    void *A = nullptr;
+    cudaStream_t st = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(ticket);
         if (it == s->reqs.end()) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown ticket");
         Req &q = it->second;
         if (q.state != 2) return set_error(ctx, FE_ERR_INVALID_ARG, "request still running");
-        cudaSetDevice(ctx->device);
-        cudaStream_t st = s->slots[std::max(q.slot, 0)]->stream;
-        if (q.A) cudaFreeAsync(q.A, st);
-        if (q.b) cudaFreeAsync(q.b, st);
-        if (q.flags) cudaFreeAsync(q.flags, st);
+        st = s->slots[std::max(q.slot, 0)]->stream;
+        A = q.A;  // the one allocation that also holds b and the flags
         s->out_used -= q.out_bytes;
         s->reqs.erase(it);
     }
     s->cv.notify_all();
+    // stream-ordered frees outside the lock
+    cudaSetDevice(ctx->device);
+    if (A) cudaFreeAsync(A, st);
     return FE_OK;
 }
 

@@ -221,3 +221,35 @@ def test_serve_budget(mix):
             small.mesh_register(et, torch.from_numpy(np.ascontiguousarray(meshgen.tet_cube_mesh(30))), api.AOS)
         assert e.value.status == -3
         small.mesh_release(mid)
+
+
+def test_serve_completion_queue(ctx, mix):
+    """fe_serve_wait_any returns every finished request once, in completion order,
+    with the results fe_serve_poll reports; a request released before it is
+    returned is skipped."""
+    ids = []
+    for i, ((et, kind, quad, cpq, n, _), (mesh, c, X, C)) in enumerate(zip(MIX, mix)):
+        ids.append((_register(ctx, et, mesh, "aos-dev"), kind, quad, api.PER_QPOINT if cpq else api.PER_ELEMENT, C))
+    assert ctx.serve_wait_any(timeout_us=0) == []
+    submitted = [ctx.serve_submit(*args) for args in ids * 3]
+    # one request finished and released through poll before the queue returns it
+    skip = submitted[0]
+    _wait(ctx, skip)
+    ctx.serve_release(skip)
+    got = {}
+    t0 = time.time()
+    while len(got) < len(submitted) - 1:
+        for tk, r in ctx.serve_wait_any(timeout_us=20000, max_results=5):
+            assert tk not in got and tk != skip
+            got[tk] = r
+        assert time.time() - t0 < 30, "completion queue stalled"
+    assert set(got) == set(submitted[1:])
+    done_times = [got[tk].t_done_us for tk in got]
+    assert done_times == sorted(done_times)                   # completion order
+    for tk, r in got.items():
+        p = ctx.serve_poll(tk)
+        assert p.status == r.status == 0 and p.A == r.A and p.t_done_us == r.t_done_us
+        ctx.serve_release(tk)
+    assert ctx.serve_wait_any(timeout_us=1000) == []
+    for mid, *_ in ids:
+        ctx.mesh_release(mid)
