@@ -136,8 +136,20 @@ static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes, in
                 g_attr_set[cl.combo] = cl.smem;
             }
         }
+        // resident blocks per SM for (combination, B), queried once per process
+        static std::mutex occ_mu;
+        static std::map<std::pair<int, int>, int> occ;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, B, size_t(cl.smem));
+        {
+            std::lock_guard<std::mutex> lk(occ_mu);
+            auto it = occ.find({cl.combo, B});
+            if (it != occ.end()) {
+                per_sm = it->second;
+            } else {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, B, size_t(cl.smem));
+                occ[{cl.combo, B}] = per_sm;
+            }
+        }
         cl.grid = int(std::min<int64_t>(int64_t(std::max(1, per_sm)) * ctx->sms, cl.n_tiles));
     }
     return FE_OK;
@@ -161,10 +173,13 @@ static fe_status upload_segs(fe_ctx *ctx, BatchPlan *pl, const std::vector<Batch
 }
 
 // Enqueue {counter reset, one persistent kernel per combination, fix-up kernel}.
-static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, kCombos * sizeof(unsigned), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch.fix_count, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemsetAsync(batch)");
+static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st, bool counters_zeroed = false) {
+    cudaError_t e = cudaSuccess;
+    if (!counters_zeroed) {
+        e = cudaMemsetAsync(pl->d_counter, 0, kCombos * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch.fix_count, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemsetAsync(batch)");
+    }
     int *status = ctx->scratch.status;
     for (const auto &cl : pl->classes) {
         const BatchSeg *segs = pl->d_segs + cl.seg_off;
@@ -284,74 +299,64 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
 // Dynamically built batch (serving).
 // ---------------------------------------------------------------------------
 void dyn_batch_free(DynBatch &db) {
-    if (db.d_items) cudaFree(db.d_items);
-    if (db.d_segs) cudaFree(db.d_segs);
-    if (db.h_items) cudaFreeHost(db.h_items);
-    if (db.h_segs) cudaFreeHost(db.h_segs);
-    if (db.d_counter) cudaFree(db.d_counter);
+    if (db.d_tab) cudaFree(db.d_tab);
+    if (db.h_tab) cudaFreeHost(db.h_tab);
     free_scratch(db.scratch);
     db = DynBatch{};
 }
 
-static fe_status grow(fe_ctx *ctx, void **d, void **h, size_t &cap, size_t need, size_t elem) {
-    if (need <= cap) return FE_OK;
-    size_t c = std::max<size_t>(need, cap * 2);
-    if (*d) cudaFree(*d);
-    if (*h) cudaFreeHost(*h);
-    *d = *h = nullptr;
-    cap = 0;
-    fe_status st = cuda_check(ctx, cudaMalloc(d, c * elem), "cudaMalloc(batch table)");
-    if (st == FE_OK) st = cuda_check(ctx, cudaMallocHost(h, c * elem), "cudaMallocHost(batch table)");
-    if (st == FE_OK) cap = c;
-    return st;
-}
-
 // The caller guarantees that the previous launch on this DynBatch has finished
-// (its pinned staging and device tables are reused).
+// (its pinned staging and device table are reused).
 fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> &items, cudaStream_t st) {
     const int B = 128;
+    constexpr size_t kCountersOff = 0, kFixCountOff = 64, kItemsOff = 128;
     uint64_t total = 0;
     for (auto &it : items) total += uint64_t(it.p.n);
     fe_status r = ensure_scratch(ctx, db.scratch, total);
     if (r != FE_OK) return r;
-    if (!db.d_counter) {
-        r = cuda_check(ctx, cudaMalloc(&db.d_counter, 256), "cudaMalloc(counter)");
-        if (r != FE_OK) return r;
-    }
-    for (auto &it : items) {
-        it.p.fix_list = db.scratch.fix_list;
-        it.p.fix_count = db.scratch.fix_count;
-        it.p.fix_cap = db.scratch.fix_cap;
-        it.p.status = ctx->scratch.status;
-    }
     std::vector<ClassLaunch> classes;
     std::vector<BatchSeg> segs;
     if (!make_segs(items, B, segs, classes))
         return set_error(ctx, FE_ERR_UNSUPPORTED, "2^32 or more tiles of one combination in a batch");
-    r = grow(ctx, reinterpret_cast<void **>(&db.d_items), reinterpret_cast<void **>(&db.h_items), db.cap_items,
-             items.size(), sizeof(BatchItemDev));
-    if (r == FE_OK)
-        r = grow(ctx, reinterpret_cast<void **>(&db.d_segs), reinterpret_cast<void **>(&db.h_segs), db.cap_segs,
-                 std::max<size_t>(segs.size(), 1), sizeof(BatchSeg));
-    if (r != FE_OK) return r;
-    memcpy(db.h_items, items.data(), items.size() * sizeof(BatchItemDev));
-    memcpy(db.h_segs, segs.data(), segs.size() * sizeof(BatchSeg));
-    cudaError_t e = cudaMemcpyAsync(db.d_items, db.h_items, items.size() * sizeof(BatchItemDev), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(db.d_segs, db.h_segs, segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemcpyAsync(batch tables)");
+    const size_t items_bytes = (items.size() * sizeof(BatchItemDev) + 15) / 16 * 16;
+    const size_t segs_off = kItemsOff + items_bytes;
+    const size_t need = segs_off + std::max<size_t>(segs.size(), 1) * sizeof(BatchSeg);
+    if (need > db.cap_tab) {
+        if (db.d_tab) cudaFree(db.d_tab);
+        if (db.h_tab) cudaFreeHost(db.h_tab);
+        db.d_tab = db.h_tab = nullptr;
+        db.cap_tab = 0;
+        const size_t cap = std::max(need, size_t(64) << 10);
+        r = cuda_check(ctx, cudaMalloc(&db.d_tab, cap), "cudaMalloc(batch table)");
+        if (r == FE_OK) r = cuda_check(ctx, cudaMallocHost(&db.h_tab, cap), "cudaMallocHost(batch table)");
+        if (r != FE_OK) return r;
+        db.cap_tab = cap;
+    }
+    unsigned *d_fix_count = reinterpret_cast<unsigned *>(db.d_tab + kFixCountOff);
+    for (auto &it : items) {
+        it.p.fix_list = db.scratch.fix_list;
+        it.p.fix_count = d_fix_count;
+        it.p.fix_cap = db.scratch.fix_cap;
+        it.p.status = ctx->scratch.status;
+    }
+    memset(db.h_tab, 0, kItemsOff);
+    memcpy(db.h_tab + kItemsOff, items.data(), items.size() * sizeof(BatchItemDev));
+    memcpy(db.h_tab + segs_off, segs.data(), segs.size() * sizeof(BatchSeg));
+    cudaError_t e = cudaMemcpyAsync(db.d_tab, db.h_tab, segs_off + segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemcpyAsync(batch table)");
     r = size_classes(ctx, classes, B);
     if (r != FE_OK) return r;
     BatchPlan pl;
-    pl.d_items = db.d_items;
-    pl.d_segs = db.d_segs;
+    pl.d_items = reinterpret_cast<BatchItemDev *>(db.d_tab + kItemsOff);
+    pl.d_segs = reinterpret_cast<BatchSeg *>(db.d_tab + segs_off);
     pl.n_items = unsigned(items.size());
     pl.n_segs = unsigned(segs.size());
-    pl.d_counter = db.d_counter;
+    pl.d_counter = reinterpret_cast<unsigned *>(db.d_tab + kCountersOff);
     pl.scratch = db.scratch;
+    pl.scratch.fix_count = d_fix_count;
     pl.block = B;
     pl.classes = classes;
-    r = enqueue_batch(ctx, &pl, st);
+    r = enqueue_batch(ctx, &pl, st, true);
     // the plan only borrowed the tables
     pl.d_items = nullptr;
     pl.d_segs = nullptr;

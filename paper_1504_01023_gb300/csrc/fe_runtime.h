@@ -99,12 +99,12 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
 Shape default_shape(fe_elem_type type);
 // Dynamically built batch (serving): device tables grown on demand, uploaded
 // from pinned staging with stream-ordered copies, launched without a graph.
+// One upload per launch: tile counters and the fix-up counter (zeroed), the item
+// table and the segment table, staged in one pinned buffer.
 struct DynBatch {
-    BatchItemDev *d_items = nullptr, *h_items = nullptr;
-    BatchSeg *d_segs = nullptr, *h_segs = nullptr;
-    size_t cap_items = 0, cap_segs = 0;
-    unsigned *d_counter = nullptr;
-    Scratch scratch;
+    unsigned char *d_tab = nullptr, *h_tab = nullptr;
+    size_t cap_tab = 0;
+    Scratch scratch;        // its fix-up list (the counter lives in the table)
 };
 fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> &items, cudaStream_t st);
 void dyn_batch_free(DynBatch &db);
