@@ -203,9 +203,36 @@ def cpu_baseline(mesh, coefs, target_s=10.0):
         oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:m], c[:m], n_threads=cores)
         done += m
     dt = time.perf_counter() - t
+    # one thread, on a sample of about a second
+    m1 = int(min(n, max(1000, rate / cores * 1.0)))
+    t1 = time.perf_counter()
+    oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:m1], c[:m1], n_threads=1)
+    one = m1 / (time.perf_counter() - t1) / 1e6
     return {"value": done / dt / 1e6, "unit": "Melem/s", "cores": cores, "kind": "oracle",
             "sample": f"{done:,} element integrations ({done / n:.2f} passes over the {n:,}-element workload), FP64, "
-                      f"OpenMP over elements", "seconds": dt}
+                      f"OpenMP over elements", "seconds": dt,
+            "single_thread": {"value": one, "unit": "Melem/s", "sample": f"first {m1:,} elements, one thread"},
+            "cpu": cpu_model()}
+
+
+def cpu_model():
+    """CPU name from /proc/cpuinfo ("model name" on x86; Arm cores give an
+    implementer/part pair, named here for the parts of current servers)."""
+    arm = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+           "0xd49": "Arm Neoverse N2", "0xd8e": "Arm Neoverse N3"}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key == "model name":
+                    return line.split(":", 1)[1].strip()
+                if key == "cpu part":
+                    part = line.split(":", 1)[1].strip()
+                    return arm.get(part, "Arm part " + part)
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -342,7 +369,7 @@ def run_native(args):
         if not args.no_prism:
             result["prism_form"] = prism_form(ctx, dev, api, args)
         if not args.no_fp64:
-            result["fp64_form"] = fp64_form(ctx, dev, api, mesh, coefs, args)
+            result["fp64_form"], result["double_word_form"] = fp64_form(ctx, dev, api, mesh, coefs, args)
         if not args.no_batch:
             result["batched"] = bench_batch(api, dev, args)
         if not args.no_serve:
@@ -456,12 +483,20 @@ def fp64_form(ctx, dev, api, mesh, coefs, args):
     dw.update(dtype="f32 double-word (edges and flagged elements f64)", bound="alu (float pipes)")
     nat.update(dtype="f64", bound="alu (FP64 pipe)")
     out["generic_tet4"] = {"double_word": dw, "native_fp64": nat}
-    # headline of the form: the Poisson tetrahedron in its fastest double-precision form
-    out.update(value=out["poisson_tet1"]["double_word"]["value"], unit="Melem/s",
-               hbm_frac=out["poisson_tet1"]["double_word"]["hbm_frac"], dtype="f32 double-word")
     del X, C
     torch.cuda.empty_cache()
-    return out
+    # the FP64 form (FP64 arithmetic) and, separately, the double-word form (float
+    # pairs; results within the same 1e-12 tolerance)
+    native = {"workload": out["workload"], "value": out["poisson_tet1"]["native_fp64"]["value"], "unit": "Melem/s",
+              "hbm_frac": out["poisson_tet1"]["native_fp64"]["hbm_frac"], "dtype": "f64",
+              "bound": "alu (FP64 pipe: 0.5 T DFMA/DADD per second on this GPU)",
+              "poisson_tet1": out["poisson_tet1"]["native_fp64"], "generic_tet4": out["generic_tet4"]["native_fp64"]}
+    dword = {"workload": out["workload"], "value": out["poisson_tet1"]["double_word"]["value"], "unit": "Melem/s",
+             "hbm_frac": out["poisson_tet1"]["double_word"]["hbm_frac"],
+             "dtype": "f32 double-word (float pairs), f64 edge vectors and f64 for flagged elements",
+             "precision_enum": "FE_FP64_DW", "tolerance": "1e-12 relative Frobenius per element (the FP64 tolerance)",
+             "poisson_tet1": out["poisson_tet1"]["double_word"], "generic_tet4": out["generic_tet4"]["double_word"]}
+    return native, dword
 
 
 def e2e(ctx, api, mesh, coefs, args):
@@ -572,9 +607,9 @@ def bench_batch(api, dev, args):
 def bench_serve(api, dev, args):
     """Poisson arrivals (2000 requests/s, seeded) of requests on a pool of 64
     resident meshes (sizes log-uniform [1e4, 4e6], the batched mix), served under a
-    120 GB HBM budget by the continuous-batching loop; then the same arrival stream
-    replayed against the plain one-request-at-a-time FP64 path (first 0.25 s)."""
-    import threading
+    120 GB HBM budget by the continuous-batching loop; an arrival-rate sweep; the
+    loop's capacity (closed loop); then the same arrival stream replayed against the
+    plain one-request-at-a-time FP64 path (first 0.25 s)."""
     import torch
     from paper_1504_01023_gb300 import meshgen
     specs = meshgen.batch_mix(64, 1e4, 4e6, seed=meshgen.SEED_BASE + 5)
@@ -588,62 +623,20 @@ def bench_serve(api, dev, args):
                            X=X, n=n))
     del pool
     torch.cuda.synchronize(dev)
-    rng = np.random.default_rng(meshgen.SEED_BASE + 55)
-    lam, T = 2000.0, args.serve_seconds
-    gaps = rng.exponential(1.0 / lam, size=int(lam * T * 1.5) + 100)
-    arrivals = np.cumsum(gaps)
-    arrivals = arrivals[arrivals < T]
-    choice = rng.integers(0, len(meshes), size=len(arrivals))
     # warm the serving path (first batched launch, pool growth)
     for m in meshes[:4]:
         tk = ctx.serve_submit(m["id"], m["kind"], m["quad"], m["cm"], m["C"])
         while ctx.serve_poll(tk) is None:
             time.sleep(0.0005)
         ctx.serve_release(tk)
-
-    outstanding, lock, lat, done_elems, errors = [], threading.Lock(), [], [0], []
-    finished = threading.Event()
-
-    def poller():
-        while True:
-            with lock:
-                cur = list(outstanding)
-            if not cur and finished.is_set():
-                return
-            for tk, n in cur:
-                r = ctx.serve_poll(tk)
-                if r is None:
-                    continue
-                if r.status != 0:
-                    errors.append(r.status)
-                lat.append((r.t_done_us - r.t_submit_us, r.t_done_us, r.t_submit_us))
-                done_elems[0] += n
-                ctx.serve_release(tk)
-                with lock:
-                    outstanding.remove((tk, n))
-            time.sleep(0.0002)
-
-    th = threading.Thread(target=poller, daemon=True)
-    th.start()
-    t0 = time.perf_counter()
-    for t_arr, j in zip(arrivals, choice):
-        dt = t_arr - (time.perf_counter() - t0)
-        if dt > 0:
-            time.sleep(dt)
-        m = meshes[j]
-        tk = ctx.serve_submit(m["id"], m["kind"], m["quad"], m["cm"], m["C"])
-        with lock:
-            outstanding.append((tk, m["n"]))
-    finished.set()
-    th.join(timeout=300)
-    wall = time.perf_counter() - t0
-    lat_ms = np.array([x[0] for x in lat]) / 1e3
-    span_s = (max(x[1] for x in lat) - min(x[2] for x in lat)) / 1e6
-    offered = float(sum(meshes[j]["n"] for j in choice)) / T / 1e6
-    served = {"arrival_rate_per_s": lam, "seconds": T, "requests": int(len(lat)), "errors": len(errors),
-              "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-              "mean_ms": float(lat_ms.mean()), "sustained_melem_s": done_elems[0] / span_s / 1e6,
-              "offered_melem_s": offered, "wall_s": wall}
+    lam, T = 2000.0, args.serve_seconds
+    served, arrivals, choice = serve_open_loop(ctx, meshes, lam, T, meshgen.SEED_BASE + 55)
+    # arrival-rate sweep: 2000/s x {2, 4, 8, 16}, a shorter window each
+    sweep = []
+    for k in (2, 4, 8, 16):
+        r, _, _ = serve_open_loop(ctx, meshes, lam * k, min(T, 1.5), meshgen.SEED_BASE + 55 + k)
+        sweep.append({key: r[key] for key in ("arrival_rate_per_s", "seconds", "requests", "errors", "p50_ms",
+                                               "p99_ms", "sustained_melem_s", "offered_melem_s")})
     saturated = serve_saturated(api, ctx, meshes, args)
     ctx.close()
 
@@ -687,7 +680,60 @@ def bench_serve(api, dev, args):
     torch.cuda.empty_cache()
     return {"workload": "Poisson arrivals 2000/s (seeded) on 64 resident meshes, sizes log-uniform [1e4, 4e6], "
                         "50/50 tetrahedra/prisms and Poisson/generic, mixed precision, 120 GB budget, 4 stream slots",
-            "served": served, "saturated": saturated, "plain_fp64": plain}
+            "served": served, "arrival_sweep": sweep, "saturated": saturated, "plain_fp64": plain}
+
+
+def serve_open_loop(ctx, meshes, lam, T, seed):
+    """Open loop: seeded Poisson arrivals at `lam` requests/s for T seconds, each on a
+    mesh drawn from the pool; completions taken from the completion queue by a
+    second thread. Latency = library completion stamp - submission stamp."""
+    import threading
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / lam, size=int(lam * T * 1.5) + 100)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < T]
+    choice = rng.integers(0, len(meshes), size=len(arrivals))
+    sizes, lock, lat, done_elems, errors = {}, threading.Lock(), [], [0], []
+    finished = threading.Event()
+    submitted = [0]
+
+    def collector():
+        while True:
+            with lock:
+                pending = submitted[0] - len(lat)
+            if pending == 0 and finished.is_set():
+                return
+            for tk, r in ctx.serve_wait_any(timeout_us=2000, max_results=64):
+                if r.status != 0:
+                    errors.append(r.status)
+                with lock:
+                    n = sizes.pop(tk)
+                    lat.append((r.t_done_us - r.t_submit_us, r.t_done_us, r.t_submit_us))
+                done_elems[0] += n
+                ctx.serve_release(tk)
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for t_arr, j in zip(arrivals, choice):
+        dt = t_arr - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        m = meshes[j]
+        with lock:
+            tk = ctx.serve_submit(m["id"], m["kind"], m["quad"], m["cm"], m["C"])
+            sizes[tk] = m["n"]
+            submitted[0] += 1
+    finished.set()
+    th.join(timeout=300)
+    wall = time.perf_counter() - t0
+    lat_ms = np.array([x[0] for x in lat]) / 1e3
+    span_s = (max(x[1] for x in lat) - min(x[2] for x in lat)) / 1e6
+    offered = float(sum(meshes[j]["n"] for j in choice)) / T / 1e6
+    return ({"arrival_rate_per_s": lam, "seconds": T, "requests": int(len(lat)), "errors": len(errors),
+             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+             "mean_ms": float(lat_ms.mean()), "sustained_melem_s": done_elems[0] / span_s / 1e6,
+             "offered_melem_s": offered, "wall_s": wall}, arrivals, choice)
 
 
 def serve_saturated(api, ctx, meshes, args, depth=48):
