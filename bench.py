@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--no-indexed", action="store_true")
     ap.add_argument("--no-prism", action="store_true")
     ap.add_argument("--workload", default="tet", choices=["tet", "prism"],
                     help="tet: the 6M generic tetrahedra (default); prism: the 2M generic prisms")
@@ -370,6 +371,8 @@ def run_native(args):
             result["prism_form"] = prism_form(ctx, dev, api, args)
         if not args.no_fp64:
             result["fp64_form"], result["double_word_form"] = fp64_form(ctx, dev, api, mesh, coefs, args)
+        if not args.no_indexed:
+            result["indexed_form"] = indexed_form(ctx, dev, api, coefs, args)
         if not args.no_batch:
             result["batched"] = bench_batch(api, dev, args)
         if not args.no_serve:
@@ -429,6 +432,61 @@ def prism_form(ctx, dev, api, args):
     return {"workload": PRISM_WORKLOAD, "value": n / step_ms / 1e3, "unit": "Melem/s", "ms_per_step": step_ms,
             "kernel_ms": k_ms, "bytes_per_element": bpe, "achieved_gbs": gbs, "hbm_frac": gbs / peak,
             "launch_shape": {"block": shape[0], "persistent": shape[1]}, "dtype": "f32"}
+
+
+def _indexed_run(ctx, dev, api, et, nodes, conn, coefs, kind, quad, cm, args):
+    """Kernel time of one mixed-form set with a node table (tuned shape), and the
+    algorithmic bytes: per element its node indices, coefficients and outputs,
+    plus every node's coordinates once."""
+    import torch
+    n = len(conn)
+    X = torch.from_numpy(nodes).to(dev)
+    K = torch.from_numpy(conn).to(dev)
+    C = torch.from_numpy(np.ascontiguousarray(coefs.reshape(n, -1).astype(np.float32))).to(dev)
+    out = api.alloc_out(et, n, api.FP32_MIXED, api.AOS, dev, with_flags=True)
+    kw = dict(kind=kind, quad=quad, coef_mode=cm, prec=api.FP32_MIXED, layout=api.INDEXED, out_layout=api.AOS,
+              conn=K)
+    shape = ctx.tune(et, X, C, out=out, **kw)
+    for _ in range(3):
+        ctx.integrate(et, X, C, out=out, **kw)
+    torch.cuda.synchronize(dev)
+    reps = max(20, min(200, args.steps // 10))
+    ctx.set_profiling(True)
+    ctx.kernel_time(reset=True)
+    for _ in range(reps):
+        ctx.integrate(et, X, C, out=out, **kw)
+    kms, kn = ctx.kernel_time(reset=True)
+    ctx.set_profiling(False)
+    k_ms = kms / kn
+    ns = api.NS[et]
+    per = api.bytes_per_element(et, kind, quad, cm, api.FP32_MIXED) - 3 * ns * 8 + ns * 4
+    total = n * per + len(nodes) * 24
+    peak, _ = measured_peaks()
+    gbs = total / (k_ms * 1e-3) / 1e9
+    del X, K, C, out
+    torch.cuda.empty_cache()
+    return {"value": n / k_ms / 1e3, "unit": "Melem/s", "kernel_ms": k_ms, "nodes": len(nodes),
+            "bytes_per_element": total / n, "bytes_per_element_element_contiguous":
+                api.bytes_per_element(et, kind, quad, cm, api.FP32_MIXED),
+            "achieved_gbs": gbs, "hbm_frac": gbs / peak, "launch_shape": {"block": shape[0], "persistent": shape[1]}}
+
+
+def indexed_form(ctx, dev, api, coefs, args):
+    """The headline tetrahedra and the 2M generic prisms with connectivity-indexed
+    geometry (a node array plus an int32 element -> node table) instead of
+    per-element coordinates: the same elements, coefficients and results."""
+    from paper_1504_01023_gb300 import meshgen
+    nodes, conn = meshgen.tet_cube_indexed(args.n_cubes, 0.2, seed=SEED)
+    tet = _indexed_run(ctx, dev, api, api.TET, nodes, conn, coefs, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, args)
+    del nodes, conn
+    nodes, conn = meshgen.prism_slab_indexed(args.n_slab, None, 0.1, seed=meshgen.SEED_BASE + 3)
+    pc = meshgen.generic_coefs(len(conn), 6, seed=meshgen.SEED_BASE + 3)
+    prism = _indexed_run(ctx, dev, api, api.PRISM, nodes, conn, pc, api.GENERIC, api.QUAD_PRISM6, api.PER_QPOINT,
+                         args)
+    return {"workload": "the headline generic tetrahedra (100^3 x 6, TET4, per-element coefficients) and the 2M "
+                        "generic prisms (PRISM6, per-point coefficients), mixed form, node array + int32 "
+                        "element -> node table, element-contiguous coefficients and outputs",
+            "value": tet["value"], "unit": "Melem/s", "hbm_frac": tet["hbm_frac"], "tet": tet, "prism": prism}
 
 
 def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args):

@@ -92,7 +92,10 @@ typedef enum fe_coef_mode { FE_COEF_PER_ELEMENT = 0, FE_COEF_PER_QPOINT = 1 } fe
 /* Sec. 4.2 (Figs. 1, 2): SOA = one plane per scalar, elements contiguous inside a
    plane ("coalesced" order); AOS = the "natural" order, all scalars of one
    element contiguous. */
-typedef enum fe_layout { FE_LAYOUT_SOA = 0, FE_LAYOUT_AOS = 1 } fe_layout;
+/* FE_LAYOUT_INDEXED (coordinates only): a shared node array plus an element ->
+   node table, the global structures the integration loop reads its geometry
+   from (Sec. 3.1); see fe_elem_args. */
+typedef enum fe_layout { FE_LAYOUT_SOA = 0, FE_LAYOUT_AOS = 1, FE_LAYOUT_INDEXED = 2 } fe_layout;
 
 typedef enum fe_memory { FE_MEM_DEVICE = 0, FE_MEM_HOST = 1 } fe_memory;
 
@@ -114,6 +117,12 @@ typedef struct fe_ctx_config {
  * coords (double, always): NS = 4 (tet) or 6 (prism) vertices x 3 coordinates.
  *   SOA: scalar j = 3*v + d lives at coords[j*coords_stride + e].
  *   AOS: coords[(e*NS + v)*3 + d].
+ *   INDEXED: coords is the node array, node i at coords[3*i + d], i < n_nodes,
+ *     and vertex v of element e is node conn[e*NS + v] (int32, 0-based). Device
+ *     memory only; coefficients element-contiguous (coefs_layout AOS); the
+ *     batched and serving entry points do not take it. An index outside
+ *     [0, n_nodes) is not read: that element's A^e and b^e are zero and its
+ *     flag has bit 3 set.
  * coefs (double for FE_FP64 and FE_FP64_DW, float for FE_FP32_MIXED), NC scalars per element:
  *   FE_GENERIC: 20 per point (C[4][4] row-major, then D[4]); FE_POISSON: 1 per
  *   point (d^0). NC = that count times NQ for FE_COEF_PER_QPOINT (point-major:
@@ -134,6 +143,8 @@ typedef struct fe_elem_args {
     int64_t coefs_stride;
     fe_precision prec;
     fe_memory memory;              /* where coords and coefs live */
+    const int32_t *conn;           /* FE_LAYOUT_INDEXED: [n_elem][NS] node indices, device */
+    int64_t n_nodes;               /* FE_LAYOUT_INDEXED: nodes in coords, < 2^31 */
 } fe_elem_args;
 
 /*
@@ -143,7 +154,8 @@ typedef struct fe_elem_args {
  *   AOS (element-contiguous): A[e*NS*NS + k], b[e*NS + r].
  * flags (optional, may be NULL): one byte per element, bit 0 = the double
  * Jacobian path was used, bit 1 = det J < 0 somewhere (|det J| is integrated),
- * bit 2 = degenerate (|det J| <= 1e-300 in double): A^e = 0 and b^e = 0.
+ * bit 2 = degenerate (|det J| <= 1e-300 in double): A^e = 0 and b^e = 0,
+ * bit 3 = a node index outside the node array (FE_LAYOUT_INDEXED): A^e = 0, b^e = 0.
  */
 typedef struct fe_out {
     void *A;
@@ -310,7 +322,8 @@ fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
  * real-time loops that forbid allocator calls, or plugins that may not create a
  * context of this library).
  * Same inputs, outputs, layouts and results as fe_integrate_tet with
- * prec = FE_FP32_MIXED and device buffers; no context. Its scratch (the list of
+ * prec = FE_FP32_MIXED and device buffers (SOA or AOS coordinates; a node table
+ * is rejected with FE_ERR_UNSUPPORTED); no context. Its scratch (the list of
  * elements sent to the double-precision Jacobian pass, a counter and a status
  * word) is a fixed 4 MiB array in the library's device image, which every GPU
  * that loads the library holds until the process exits. Hence at most 524,256

@@ -22,7 +22,7 @@ POISSON, GENERIC = 0, 1
 FP64, FP32_MIXED, FP64_DW = 0, 1, 2
 QUAD_TET1, QUAD_TET4, QUAD_PRISM6 = 0, 1, 2
 PER_ELEMENT, PER_QPOINT = 0, 1
-SOA, AOS = 0, 1
+SOA, AOS, INDEXED = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 NS = {TET: 4, PRISM: 6}
 NQ = {QUAD_TET1: 1, QUAD_TET4: 4, QUAD_PRISM6: 6}
@@ -46,7 +46,8 @@ class ElemArgs(ctypes.Structure):
     _fields_ = [("n_elem", ctypes.c_int64), ("coords", ctypes.c_void_p), ("coords_layout", ctypes.c_int),
                 ("coords_stride", ctypes.c_int64), ("kind", ctypes.c_int), ("quad", ctypes.c_int),
                 ("coef_mode", ctypes.c_int), ("coefs", ctypes.c_void_p), ("coefs_layout", ctypes.c_int),
-                ("coefs_stride", ctypes.c_int64), ("prec", ctypes.c_int), ("memory", ctypes.c_int)]
+                ("coefs_stride", ctypes.c_int64), ("prec", ctypes.c_int), ("memory", ctypes.c_int),
+                ("conn", ctypes.c_void_p), ("n_nodes", ctypes.c_int64)]
 
 
 class Out(ctypes.Structure):
@@ -152,10 +153,28 @@ def n_coefs(kind, quad, coef_mode):
     return (1 if kind == POISSON else 20) * (NQ[quad] if coef_mode == PER_QPOINT else 1)
 
 
-def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout):
+def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn=None):
     """ElemArgs for torch tensors. SOA: coords (3*NS, E) and coefs (NC, E), unit
-    stride along elements, any plane stride. AOS: coords (E, NS, 3), coefs (E, ...)."""
+    stride along elements, any plane stride. AOS: coords (E, NS, 3), coefs (E, ...).
+    INDEXED: coords = nodes (N, 3), conn (E, NS) int32, coefs (E, ...)."""
     a = ElemArgs()
+    if layout == INDEXED:
+        assert conn is not None and conn.dtype == torch.int32 and conn.is_contiguous()
+        assert conn.dim() == 2 and conn.shape[1] == NS[elem_type]
+        assert coords.dim() == 2 and coords.shape[1] == 3 and coords.is_contiguous() and coefs.is_contiguous()
+        assert coords.dtype == torch.float64
+        want = torch.float32 if prec == FP32_MIXED else torch.float64
+        assert coefs.dtype == want, f"coefficients must be {want}"
+        a.n_elem = conn.shape[0]
+        a.coords = coords.data_ptr()
+        a.coords_layout = INDEXED
+        a.kind, a.quad, a.coef_mode, a.prec = kind, quad, coef_mode, prec
+        a.coefs = coefs.data_ptr()
+        a.coefs_layout = AOS
+        a.memory = _mem(coords)
+        a.conn = conn.data_ptr()
+        a.n_nodes = coords.shape[0]
+        return a
     if layout == SOA:
         assert coords.dim() == 2 and coords.shape[0] == 3 * NS[elem_type]
         n = coords.shape[1]
@@ -286,10 +305,11 @@ class Context:
         return ctypes.c_void_p(0)
 
     def integrate(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-                  out_layout=SOA, out=None, with_flags=True, stream=None):
+                  out_layout=SOA, out=None, with_flags=True, stream=None, conn=None):
         """Integrate one element set; returns (A, b, flags) tensors (allocated if
-        ``out`` is None, on the device of ``coords``; pinned host memory for host inputs)."""
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+        ``out`` is None, on the device of ``coords``; pinned host memory for host inputs).
+        With layout=INDEXED, coords is the node array and conn the element -> node table."""
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
             on_host = not coords.is_cuda
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, with_flags, pin=on_host)
@@ -300,25 +320,25 @@ class Context:
         return A, b, flags
 
     def tune(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-             out_layout=SOA, out=None, stream=None):
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+             out_layout=SOA, out=None, stream=None, conn=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
         o = make_out(*out, out_layout)
         _check(load().fe_tune(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), self._stream(stream, True)), self.h)
-        return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out)
+        return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out, conn)
 
     def set_shape(self, block, persistent, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT,
-                  prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None):
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+                  prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None, conn=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
         o = make_out(*out, out_layout)
         _check(load().fe_set_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), block, persistent), self.h)
 
     def shape(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-              out_layout=SOA, out=None):
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout)
+              out_layout=SOA, out=None, conn=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
         o = make_out(*out, out_layout)

@@ -1,0 +1,16 @@
+// Tetrahedron kernels with INDEXED geometry (node table), double-word form.
+#include "fe_inst.cuh"
+namespace fe {
+const void *kernel_tet_dw_idx(int kind, int quad, int cpq, int outl) {
+    const int inl = INDEXED;
+    if (quad == Q_TET1) { FE_IDX8(FE_ELEM_CASE, TET, DWORD, Q_TET1) }
+    if (quad == Q_TET4) { FE_IDX8(FE_ELEM_CASE, TET, DWORD, Q_TET4) }
+    return nullptr;
+}
+const void *kernel_fixup_tet_dw_idx(int kind, int quad, int cpq, int outl) {
+    const int inl = INDEXED;
+    if (quad == Q_TET1) { FE_IDX8(FE_FIX_CASE, TET, DWORD, Q_TET1) }
+    if (quad == Q_TET4) { FE_IDX8(FE_FIX_CASE, TET, DWORD, Q_TET4) }
+    return nullptr;
+}
+}  // namespace fe

@@ -23,3 +23,10 @@
     M(__VA_ARGS__, KD, 0, 0, 0) M(__VA_ARGS__, KD, 0, 0, 1) M(__VA_ARGS__, KD, 0, 1, 0) \
     M(__VA_ARGS__, KD, 0, 1, 1) M(__VA_ARGS__, KD, 1, 0, 0) M(__VA_ARGS__, KD, 1, 0, 1) \
     M(__VA_ARGS__, KD, 1, 1, 0) M(__VA_ARGS__, KD, 1, 1, 1)
+
+// The eight (kind, coefficient mode, output layout) combinations with INDEXED
+// geometry (inputs fixed: node table, element-contiguous coefficients).
+#define FE_IDX8(M, ...)                                                               \
+    M(__VA_ARGS__, 0, 0, 2, 0) M(__VA_ARGS__, 0, 0, 2, 1) M(__VA_ARGS__, 0, 1, 2, 0)  \
+    M(__VA_ARGS__, 0, 1, 2, 1) M(__VA_ARGS__, 1, 0, 2, 0) M(__VA_ARGS__, 1, 0, 2, 1)  \
+    M(__VA_ARGS__, 1, 1, 2, 0) M(__VA_ARGS__, 1, 1, 2, 1)

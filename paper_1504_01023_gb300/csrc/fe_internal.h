@@ -9,7 +9,7 @@ enum ElemType { TET = 0, PRISM = 1 };
 enum Kind { POISSON = 0, GENERIC = 1 };
 enum Prec { FP64 = 0, MIXED = 1, DWORD = 2 };
 enum Quad { Q_TET1 = 0, Q_TET4 = 1, Q_PRISM6 = 2 };
-enum Layout { SOA = 0, AOS = 1 };
+enum Layout { SOA = 0, AOS = 1, INDEXED = 2 };
 
 // Bits of the device status word (one per context, read at sync).
 enum StatusBits : int {
@@ -35,6 +35,8 @@ struct ElemParams {
     unsigned int item;             // batch item id (0 for a plain call)
     int *status;                   // device status word
     int tma_in, tma_out;           // SOA tiles moved by 2-D tensor copies (maps in TmaMaps)
+    const int *conn;               // INDEXED: [n][NS] node indices into X (nodes [n_nodes][3])
+    long long n_nodes;
 };
 
 // Tensor-copy descriptors (CUtensorMap, 128 bytes each) of the plane-major
@@ -63,6 +65,18 @@ const void *kernel_fixup_tet(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_fixup_prism(int kind, int cpq, int inl, int outl);
 const void *kernel_fixup_tet_dw(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_fixup_prism_dw(int kind, int cpq, int inl, int outl);
+
+// INDEXED geometry (node table): the same tables, in their own translation units.
+const void *kernel_tet_fp64_idx(int kind, int quad, int cpq, int outl);
+const void *kernel_tet_mixed_idx(int kind, int quad, int cpq, int outl);
+const void *kernel_tet_dw_idx(int kind, int quad, int cpq, int outl);
+const void *kernel_prism_fp64_idx(int kind, int cpq, int outl);
+const void *kernel_prism_mixed_idx(int kind, int cpq, int outl);
+const void *kernel_prism_dw_idx(int kind, int cpq, int outl);
+const void *kernel_fixup_tet_idx(int kind, int quad, int cpq, int outl);
+const void *kernel_fixup_tet_dw_idx(int kind, int quad, int cpq, int outl);
+const void *kernel_fixup_prism_idx(int kind, int cpq, int outl);
+const void *kernel_fixup_prism_dw_idx(int kind, int cpq, int outl);
 
 // Batched persistent kernel (fe_batch.cu): one descriptor per element set and
 // one per tile of consecutive elements of a set.

@@ -499,11 +499,14 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
 // AOS regions hold element records back to back; SOA regions hold one row of B
 // scalars per plane. Every region starts on a 16-byte boundary.
 // ---------------------------------------------------------------------------
-template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct BlockSmem {
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL = AOS> struct BlockSmem {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
     __host__ __device__ static constexpr int64_t r16(int64_t v) { return (v + 15) / 16 * 16; }
-    __host__ __device__ static constexpr int64_t x_bytes(int B) { return int64_t(B) * CF::NX * 8; }
+    // geometry of the tile: coordinates, or node indices for INDEXED
+    __host__ __device__ static constexpr int64_t x_bytes(int B) {
+        return INL == INDEXED ? r16(int64_t(B) * CF::NS * 4) : int64_t(B) * CF::NX * 8;
+    }
     __host__ __device__ static constexpr int64_t c_bytes(int B) { return r16(int64_t(B) * CF::NC * int64_t(sizeof(CT))); }
     __host__ __device__ static constexpr int64_t a_bytes(int B) { return r16(int64_t(B) * CF::NA * int64_t(sizeof(CT))); }
     __host__ __device__ static constexpr int64_t b_bytes(int B) { return r16(int64_t(B) * CF::NS * int64_t(sizeof(CT))); }
@@ -522,6 +525,31 @@ template <class T> struct SmemSrc {
     int stride;
     __device__ __forceinline__ T operator()(int j) const { return base[j * stride]; }
 };
+
+// Register accessor (coordinates gathered through the node table).
+template <class T> struct RegSrc {
+    const T *v;
+    __device__ __forceinline__ T operator()(int j) const { return v[j]; }
+};
+
+// Coordinates of an element of an INDEXED set: vertex v is node idx[v] of the
+// node array X ([n_nodes][3]). An index outside [0, n_nodes) is not followed
+// (node 0 is read instead) and the result is false.
+template <int NS>
+__device__ __forceinline__ bool gather_nodes(const double *__restrict__ X, long long n_nodes, const int *idx,
+                                             double x[3 * NS]) {
+    bool ok = true;
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+        const long long i = idx[v];
+        const bool in = static_cast<unsigned long long>(i) < static_cast<unsigned long long>(n_nodes);
+        ok &= in;
+        const double *q = X + 3 * (in ? i : 0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x[3 * v + d] = __ldg(q + d);
+    }
+    return ok;
+}
 
 // Append flagged elements of this warp to the fix-up list (one atomic per warp).
 __device__ __forceinline__ void append_fixup(const ElemParams &p, bool poor, int64_t e) {
@@ -583,11 +611,12 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
                                              unsigned &phase, const TmaMaps *tm = nullptr) {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
-    using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ>;
+    using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ, INL>;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
     const int B = blockDim.x;
     const int tid = threadIdx.x;
     double *sX = reinterpret_cast<double *>(smem);
+    int *sN = reinterpret_cast<int *>(smem);  // INDEXED: the tile's node indices
     CT *sC = reinterpret_cast<CT *>(smem + SM::x_bytes(B));
     CT *sA = reinterpret_cast<CT *>(smem);
     CT *sB = reinterpret_cast<CT *>(smem + SM::a_bytes(B));
@@ -615,11 +644,13 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         }
     } else {
         // alignment of bases and SOA plane pitches, then of this tile's byte counts
-        const bool x_ok = aligned16(X, INL == SOA ? uint64_t(p.xs) * 8 : 0);
+        // (INDEXED: the node-index records of the tile, element-contiguous)
+        const bool x_ok = INL == INDEXED ? aligned16(p.conn + e0 * NS, 0) : aligned16(X, INL == SOA ? uint64_t(p.xs) * 8 : 0);
         const bool c_ok = aligned16(C, INL == SOA ? uint64_t(p.cs) * sizeof(CT) : 0);
-        const bool tX = x_ok && ((uint64_t(nb) * (INL == SOA ? 8 : NX * 8)) % 16 == 0);
+        constexpr unsigned kXe = INL == INDEXED ? NS * 4u : NX * 8u;  // geometry bytes per element
+        const bool tX = x_ok && ((uint64_t(nb) * (INL == SOA ? 8 : kXe)) % 16 == 0);
         const bool tC = c_ok && ((uint64_t(nb) * (INL == SOA ? 1 : NC) * sizeof(CT)) % 16 == 0);
-        const unsigned tx = (tX ? unsigned(nb) * NX * 8u : 0u) + (tC ? unsigned(nb) * NC * unsigned(sizeof(CT)) : 0u);
+        const unsigned tx = (tX ? unsigned(nb) * kXe : 0u) + (tC ? unsigned(nb) * NC * unsigned(sizeof(CT)) : 0u);
         if (tid == 0 && tx) {
             fence_proxy_async_smem();
             mbar_expect_tx(bar, tx);
@@ -628,6 +659,9 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         if (INL == SOA) {
             stage_rows_in(sX, B, X + e0, p.xs, NX, nb, tX, bar);
             stage_rows_in(sC, B, C + e0, p.cs, NC, nb, tC, bar);
+        } else if (INL == INDEXED) {
+            stage_rows_in(sN, 0, p.conn + e0 * NS, 0, 1, nb * NS, tX, bar);
+            stage_rows_in(sC, 0, C + e0 * NC, 0, 1, nb * NC, tC, bar);
         } else {
             stage_rows_in(sX, 0, X + e0 * NX, 0, 1, nb * NX, tX, bar);
             stage_rows_in(sC, 0, C + e0 * NC, 0, 1, nb * NC, tC, bar);
@@ -648,9 +682,24 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     CT A[NA], b[NS];
     bool poor = false;
     if (active) {
-        const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
         const SmemSrc<CT> cs{INL == SOA ? sC + tid : sC + tid * NC, INL == SOA ? B : 1};
-        uint8_t fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
+        uint8_t fl;
+        if constexpr (INL == INDEXED) {
+            double xr[NX];
+            const bool ok = gather_nodes<NS>(X, p.n_nodes, sN + tid * NS, xr);
+            fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(RegSrc<double>{xr}, cs, A, b, poor);
+            if (!ok) {
+#pragma unroll
+                for (int k = 0; k < NA; ++k) A[k] = CT(0);
+#pragma unroll
+                for (int k = 0; k < NS; ++k) b[k] = CT(0);
+                fl = 8;
+                poor = false;
+            }
+        } else {
+            const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
+            fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
+        }
         if (PREC != FP64 && poor) fl |= 1;
         if (p.flags) p.flags[e] = fl;
     }
@@ -744,6 +793,11 @@ __device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
         const Src<SOA, double> xs{p.X + e, p.xs};
         const Src<SOA, CT> cs{C + e, p.cs};
         fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(xs, cs, A, b);
+    } else if (INL == INDEXED) {
+        double xr[NX];
+        gather_nodes<NS>(p.X, p.n_nodes, p.conn + e * NS, xr);  // flagged elements have valid indices
+        const Src<AOS, CT> cs{C + e * NC, 0};
+        fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(RegSrc<double>{xr}, cs, A, b);
     } else {
         const Src<AOS, double> xs{p.X + e * NX, 0};
         const Src<AOS, CT> cs{C + e * NC, 0};

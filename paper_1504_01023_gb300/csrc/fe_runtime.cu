@@ -104,7 +104,8 @@ static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, in
     (void)outl;
     const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
-    const int64_t in = int64_t(B) * 3 * ns * 8 + r16(int64_t(B) * nc * cs), out = r16(int64_t(B) * ns * ns * cs) + r16(int64_t(B) * ns * cs);
+    const int64_t geo = a->coords_layout == FE_LAYOUT_INDEXED ? r16(int64_t(B) * ns * 4) : int64_t(B) * 3 * ns * 8;
+    const int64_t in = geo + r16(int64_t(B) * nc * cs), out = r16(int64_t(B) * ns * ns * cs) + r16(int64_t(B) * ns * cs);
     return in > out ? in : out;
 }
 
@@ -232,6 +233,8 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     p.os = o->stride ? o->stride : a->n_elem;
     p.flags = o->flags;
     p.item = 0;
+    p.conn = a->coords_layout == FE_LAYOUT_INDEXED ? a->conn : nullptr;
+    p.n_nodes = a->coords_layout == FE_LAYOUT_INDEXED ? a->n_nodes : 0;
     const bool fixup = a->prec != FE_FP64;   // mixed and double-word forms flag elements
     if (fixup) {
         fe_status e = ensure_scratch(ctx, s, uint64_t(a->n_elem));
@@ -534,15 +537,24 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
         return set_error(nullptr, FE_ERR_INVALID_ARG, "tetrahedra take FE_QUAD_TET1 or FE_QUAD_TET4");
     if (type == FE_PRISM && a->quad != FE_QUAD_PRISM6)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "prisms take FE_QUAD_PRISM6");
-    if ((a->coords_layout != FE_LAYOUT_SOA && a->coords_layout != FE_LAYOUT_AOS) ||
+    if ((a->coords_layout != FE_LAYOUT_SOA && a->coords_layout != FE_LAYOUT_AOS && a->coords_layout != FE_LAYOUT_INDEXED) ||
         (o->layout != FE_LAYOUT_SOA && o->layout != FE_LAYOUT_AOS))
         return set_error(nullptr, FE_ERR_INVALID_ARG, "bad layout");
-    if (a->coefs_layout != a->coords_layout)
-        return set_error(nullptr, FE_ERR_UNSUPPORTED, "coefficients must use the layout of the coordinates");
+    const bool indexed = a->coords_layout == FE_LAYOUT_INDEXED;
+    if (indexed ? a->coefs_layout != FE_LAYOUT_AOS : a->coefs_layout != a->coords_layout)
+        return set_error(nullptr, FE_ERR_UNSUPPORTED,
+                         "coefficients must use the layout of the coordinates (element-contiguous with a node table)");
     if ((a->memory != FE_MEM_DEVICE && a->memory != FE_MEM_HOST) || (o->memory != FE_MEM_DEVICE && o->memory != FE_MEM_HOST))
         return set_error(nullptr, FE_ERR_INVALID_ARG, "bad memory kind");
+    if (indexed && (a->memory != FE_MEM_DEVICE || o->memory != FE_MEM_DEVICE))
+        return set_error(nullptr, FE_ERR_UNSUPPORTED, "a node table needs device memory");
     if (a->n_elem == 0) return FE_OK;
     if (!a->coords || !a->coefs || !o->A || !o->b) return set_error(nullptr, FE_ERR_INVALID_ARG, "null data pointer");
+    if (indexed) {
+        if (!a->conn || a->n_nodes <= 0 || a->n_nodes >= (int64_t(1) << 31))
+            return set_error(nullptr, FE_ERR_INVALID_ARG, "node table: null conn or n_nodes outside [1, 2^31)");
+        if (reinterpret_cast<uintptr_t>(a->conn) & 3) return set_error(nullptr, FE_ERR_INVALID_ARG, "misaligned conn");
+    }
     const int64_t n = a->n_elem;
     if (a->coords_layout == FE_LAYOUT_SOA) {
         if ((a->coords_stride != 0 && a->coords_stride < n) || (a->coefs_stride != 0 && a->coefs_stride < n))

@@ -43,6 +43,14 @@ def tet_cube_mesh(n: int, jitter: float = 0.2, seed: int = SEED_BASE + 1, n_elem
     U[-jitter*h, jitter*h] per coordinate (h = 1/n). Returns coords [E, 4, 3]
     (float64), elements ordered cube by cube (x fastest). ``n_elem`` keeps the
     first n_elem elements."""
+    nodes, conn = tet_cube_indexed(n, jitter, seed, n_elem)
+    return nodes[conn]
+
+
+def tet_cube_indexed(n: int, jitter: float = 0.2, seed: int = SEED_BASE + 1, n_elem: int | None = None):
+    """The mesh of tet_cube_mesh as a node array [(n+1)^3, 3] (node id = i +
+    (n+1)(j + (n+1)k)) and an element -> node table [E, 4] (int32);
+    nodes[conn] is exactly tet_cube_mesh's coordinates."""
     rng = np.random.default_rng(seed)
     h = 1.0 / n
     m = n + 1
@@ -62,7 +70,7 @@ def tet_cube_mesh(n: int, jitter: float = 0.2, seed: int = SEED_BASE + 1, n_elem
     jj = cj[:, None, None] + off[None, :, :, 1]
     kk = ck[:, None, None] + off[None, :, :, 2]
     nid = (ii + m * (jj + m * kk)).reshape(-1, 4)[:n_elem]
-    return nodes[nid]                                                    # [E,4,3]
+    return nodes, np.ascontiguousarray(nid.astype(np.int32))
 
 
 def prism_slab_mesh(n: int, hz: float | None = None, zjitter: float = 0.1, seed: int = SEED_BASE + 3,
@@ -72,6 +80,15 @@ def prism_slab_mesh(n: int, hz: float | None = None, zjitter: float = 0.1, seed:
     node's z moved by U[-zjitter*hz, zjitter*hz]. Returns coords [E, 6, 3]:
     bottom triangle (counter-clockwise seen from +z), then the top vertices above
     them."""
+    nodes, conn = prism_slab_indexed(n, hz, zjitter, seed, n_elem)
+    return nodes[conn]
+
+
+def prism_slab_indexed(n: int, hz: float | None = None, zjitter: float = 0.1, seed: int = SEED_BASE + 3,
+                       n_elem: int | None = None):
+    """The mesh of prism_slab_mesh as a node array [2 (n+1)^2, 3] (bottom nodes
+    i + (n+1) j, then the top ones) and an element -> node table [E, 6] (int32);
+    nodes[conn] is exactly prism_slab_mesh's coordinates."""
     rng = np.random.default_rng(seed)
     h = 1.0 / n
     if hz is None:
@@ -93,12 +110,13 @@ def prism_slab_mesh(n: int, hz: float | None = None, zjitter: float = 0.1, seed:
     p01 = p00 + m
     p11 = p01 + 1
     tri = np.stack([np.stack([p00, p10, p11], -1), np.stack([p00, p11, p01], -1)], 1).reshape(-1, 3)[:n_elem]
-    out = np.empty((n_elem, 6, 3))
-    out[:, :3, :2] = xy[tri]
-    out[:, 3:, :2] = xy[tri]
-    out[:, :3, 2] = zb[tri]
-    out[:, 3:, 2] = zt[tri]
-    return out
+    nodes = np.empty((2 * m * m, 3))
+    nodes[:m * m, :2] = xy
+    nodes[m * m:, :2] = xy
+    nodes[:m * m, 2] = zb
+    nodes[m * m:, 2] = zt
+    conn = np.concatenate([tri, tri + m * m], axis=1).astype(np.int32)
+    return nodes, np.ascontiguousarray(conn)
 
 
 def _haar_orthogonal(rng, n: int):

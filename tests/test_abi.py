@@ -96,6 +96,35 @@ def test_argument_validation(lib):
     assert lib.fe_last_error(None)
 
 
+def test_node_table_validation(lib):
+    """FE_LAYOUT_INDEXED: node array + int32 element -> node table, device memory,
+    element-contiguous coefficients."""
+    def idx(**kw):
+        a, o = _args()
+        a.coords_layout, a.coefs_layout = api.INDEXED, api.AOS
+        a.conn, a.n_nodes = 65536, 100
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a, o
+    a, o = idx()
+    assert _chk(lib, api.TET, a, o) == 0
+    assert _chk(lib, api.TET, *idx(conn=0)) == -1                 # no table
+    assert _chk(lib, api.TET, *idx(conn=65538)) == -1             # misaligned int32
+    assert _chk(lib, api.TET, *idx(n_nodes=0)) == -1
+    assert _chk(lib, api.TET, *idx(n_nodes=1 << 31)) == -1        # indices are int32
+    assert _chk(lib, api.TET, *idx(coefs_layout=api.SOA)) == -6   # coefficients element-contiguous
+    assert _chk(lib, api.TET, *idx(memory=api.MEM_HOST)) == -6    # device memory only
+    a, o = idx()
+    o.memory = api.MEM_HOST
+    assert _chk(lib, api.TET, a, o) == -6
+    # the output side has no indexed layout
+    a, o = idx()
+    o.layout = api.INDEXED
+    assert _chk(lib, api.TET, a, o) == -1
+    # no allocation-free call with a node table (rejected before any GPU work)
+    assert lib.fe_integrate_tet_noalloc(ctypes.byref(idx()[0]), ctypes.byref(o), None) in (-1, -6)
+
+
 def test_null_context_rejected(lib):
     a, o = _args()
     assert lib.fe_integrate_tet(None, ctypes.byref(a), ctypes.byref(o), None) == -1
