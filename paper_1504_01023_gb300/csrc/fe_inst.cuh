@@ -30,3 +30,8 @@
     M(__VA_ARGS__, 0, 0, 2, 0) M(__VA_ARGS__, 0, 0, 2, 1) M(__VA_ARGS__, 0, 1, 2, 0)  \
     M(__VA_ARGS__, 0, 1, 2, 1) M(__VA_ARGS__, 1, 0, 2, 0) M(__VA_ARGS__, 1, 0, 2, 1)  \
     M(__VA_ARGS__, 1, 1, 2, 0) M(__VA_ARGS__, 1, 1, 2, 1)
+
+// INDEXED geometry: the kernel that reads straight from global memory.
+#define FE_GATHER_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                \
+    if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
+        return reinterpret_cast<const void *>(&fe::gather_kernel<ET, KD, PREC, QUAD, CP, OL>);

@@ -775,6 +775,141 @@ __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
 }
 
 // ---------------------------------------------------------------------------
+// INDEXED geometry without staging: each thread reads its node-index record,
+// gathers its nodes (the node array is small enough to stay in L2), reads its
+// coefficient record and writes its results with vector accesses straight from
+// and to global memory. No shared memory and no block barrier per tile, so many
+// independent loads stay in flight per thread.
+// ---------------------------------------------------------------------------
+template <class T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int K = 4;
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int K = 2;
+};
+template <> struct Vec16<int> {
+    using type = int4;
+    static constexpr int K = 4;
+};
+
+// N values from src: 16-byte loads through the read-only path when the record is
+// a whole number of 16-byte vectors and vec16 (the base is 16-byte aligned).
+template <class T, int N> __device__ __forceinline__ void ld_record(const T *src, T v[N], bool vec16) {
+    if constexpr ((N * sizeof(T)) % 16 == 0) {
+        if (vec16) {
+            using V = typename Vec16<T>::type;
+            constexpr int K = Vec16<T>::K;
+            const V *s = reinterpret_cast<const V *>(src);
+#pragma unroll
+            for (int i = 0; i < N / K; ++i) {
+                const V q = __ldg(s + i);
+                if constexpr (K == 4) {
+                    v[4 * i] = q.x;
+                    v[4 * i + 1] = q.y;
+                    v[4 * i + 2] = q.z;
+                    v[4 * i + 3] = q.w;
+                } else {
+                    v[2 * i] = q.x;
+                    v[2 * i + 1] = q.y;
+                }
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = __ldg(src + i);
+}
+// N values to dst with streaming stores, 16-byte vectors when possible.
+template <class T, int N> __device__ __forceinline__ void st_record(T *dst, const T v[N], bool vec16) {
+    if constexpr ((N * sizeof(T)) % 16 == 0) {
+        if (vec16) {
+            using V = typename Vec16<T>::type;
+            constexpr int K = Vec16<T>::K;
+            V *d = reinterpret_cast<V *>(dst);
+#pragma unroll
+            for (int i = 0; i < N / K; ++i) {
+                V q;
+                if constexpr (K == 4) {
+                    q.x = v[4 * i];
+                    q.y = v[4 * i + 1];
+                    q.z = v[4 * i + 2];
+                    q.w = v[4 * i + 3];
+                } else {
+                    q.x = v[2 * i];
+                    q.y = v[2 * i + 1];
+                }
+                __stcs(d + i, q);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) __stcs(dst + i, v[i]);
+}
+
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int OUTL>
+__global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
+    gather_kernel(const ElemParams p, const __grid_constant__ TmaMaps) {
+    using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
+    using CT = typename CF::CT;
+    constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
+    // coefficient records up to 160 bytes are read whole into registers; longer
+    // (per-point generic prisms) are read value by value where they are used
+    constexpr bool kCoefRegs = NC * sizeof(CT) <= 160;
+    const CT *C = static_cast<const CT *>(p.C);
+    CT *Aout = static_cast<CT *>(p.A);
+    CT *Bout = static_cast<CT *>(p.B);
+    const bool n16 = aligned16(p.conn, 0), c16 = aligned16(C, 0);
+    const bool o16 = OUTL == AOS && aligned16(Aout, 0) && aligned16(Bout, 0);
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    // whole blocks iterate together (the fix-up append is warp-collective)
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < p.n; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        const bool active = e < p.n;
+        bool poor = false;
+        if (active) {
+            int idx[NS];
+            ld_record<int, NS>(p.conn + e * NS, idx, n16);
+            double xr[NX];
+            const bool ok = gather_nodes<NS>(p.X, p.n_nodes, idx, xr);
+            CT A[NA], b[NS];
+            uint8_t fl;
+            if constexpr (kCoefRegs) {
+                CT cv[NC];
+                ld_record<CT, NC>(C + e * NC, cv, c16);
+                fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(RegSrc<double>{xr}, RegSrc<CT>{cv}, A, b, poor);
+            } else {
+                const Src<AOS, CT> cs{C + e * NC, 0};
+                fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(RegSrc<double>{xr}, cs, A, b, poor);
+            }
+            if (!ok) {
+#pragma unroll
+                for (int k = 0; k < NA; ++k) A[k] = CT(0);
+#pragma unroll
+                for (int k = 0; k < NS; ++k) b[k] = CT(0);
+                fl = 8;
+                poor = false;
+            }
+            if (PREC != FP64 && poor) fl |= 1;
+            if (p.flags) p.flags[e] = fl;
+            if (OUTL == SOA) {
+#pragma unroll
+                for (int k = 0; k < NA; ++k) st_stream(Aout + k * p.os + e, A[k]);
+#pragma unroll
+                for (int k = 0; k < NS; ++k) st_stream(Bout + k * p.os + e, b[k]);
+            } else {
+                st_record<CT, NA>(Aout + e * NA, A, o16);
+                st_record<CT, NS>(Bout + e * NS, b, o16);
+            }
+        }
+        if (PREC != FP64) append_fixup(p, active && poor, e);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Fix-up of one flagged element (mixed and double-word forms): read straight
 // from global memory, Jacobian terms in double, results overwrite the main
 // kernel's.

@@ -102,6 +102,8 @@ static const void *fix_kernel(fe_elem_type type, const fe_elem_args *a, int outl
 // rounded to 16 bytes exactly as BlockSmem in fe_kernels.cuh lays them out.
 static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, int B) {
     (void)outl;
+    // tetrahedra with a node table read straight from global memory (gather_kernel)
+    if (a->coords_layout == FE_LAYOUT_INDEXED && type == FE_TET) return 0;
     const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
     const int64_t geo = a->coords_layout == FE_LAYOUT_INDEXED ? r16(int64_t(B) * ns * 4) : int64_t(B) * 3 * ns * 8;
