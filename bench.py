@@ -373,6 +373,7 @@ def run_native(args):
             result["fp64_form"], result["double_word_form"] = fp64_form(ctx, dev, api, mesh, coefs, args)
         if not args.no_indexed:
             result["indexed_form"] = indexed_form(ctx, dev, api, coefs, args)
+            result["apply_form"] = apply_form(ctx, dev, api, coefs, args)
         if not args.no_batch:
             result["batched"] = bench_batch(api, dev, args)
         if not args.no_serve:
@@ -487,6 +488,46 @@ def indexed_form(ctx, dev, api, coefs, args):
                         "generic prisms (PRISM6, per-point coefficients), mixed form, node array + int32 "
                         "element -> node table, element-contiguous coefficients and outputs",
             "value": tet["value"], "unit": "Melem/s", "hbm_frac": tet["hbm_frac"], "tet": tet, "prism": prism}
+
+
+def apply_form(ctx, dev, api, coefs, args):
+    """Matrix-free y += sum_e P_e^T A^e P_e x and f += sum_e P_e^T b^e over the
+    headline tetrahedra with a node table: the element matrices are consumed
+    where they are computed and never written. Algorithmic bytes: per element its
+    indices and coefficients, plus per node x read once and y, f read and
+    written once."""
+    import torch
+    from paper_1504_01023_gb300 import meshgen
+    nodes, conn = meshgen.tet_cube_indexed(args.n_cubes, 0.2, seed=SEED)
+    n, m = len(conn), len(nodes)
+    X = torch.from_numpy(nodes).to(dev)
+    K = torch.from_numpy(conn).to(dev)
+    C = torch.from_numpy(np.ascontiguousarray(coefs.reshape(n, -1).astype(np.float32))).to(dev)
+    x = torch.from_numpy(np.random.default_rng(SEED).uniform(-1, 1, m).astype(np.float32)).to(dev)
+    y = torch.zeros(m, dtype=torch.float32, device=dev)
+    f = torch.zeros(m, dtype=torch.float32, device=dev)
+    call = lambda: ctx.apply(api.TET, X, K, C, api.GENERIC, api.QUAD_TET4, x, y, f, api.PER_ELEMENT,
+                             api.FP32_MIXED)
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize(dev)
+    reps = max(20, min(200, args.steps // 10))
+    ctx.set_profiling(True)
+    ctx.kernel_time(reset=True)
+    for _ in range(reps):
+        call()
+    kms, kn = ctx.kernel_time(reset=True)
+    ctx.set_profiling(False)
+    k_ms = kms / kn
+    total = n * (4 * 4 + 20 * 4) + m * 4 * 5
+    peak, _ = measured_peaks()
+    gbs = total / (k_ms * 1e-3) / 1e9
+    del X, K, C, x, y, f
+    torch.cuda.empty_cache()
+    return {"workload": "y += A x and f += b, matrix-free (element matrices never stored), the headline generic "
+                        "tetrahedra (TET4, per-element coefficients) with a node table, mixed form, float atomics",
+            "value": n / k_ms / 1e3, "unit": "Melem/s", "kernel_ms": k_ms, "bytes_per_element": total / n,
+            "achieved_gbs": gbs, "hbm_frac": gbs / peak, "nodes": m}
 
 
 def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args):

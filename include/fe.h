@@ -193,6 +193,25 @@ const char *fe_last_error(fe_ctx *ctx);
 fe_status fe_integrate_tet(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream);
 fe_status fe_integrate_prism(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream);
 
+/*
+ * Matrix-free application (the element matrices consumed where they are
+ * computed, never stored; the paper leaves their use to the solver, Sec. 2.2):
+ *   y[conn[e][r]] += sum_s A^e_rs x[conn[e][s]]   and, if f != NULL,
+ *   f[conn[e][r]] += b^e_r,                        for every element e and r.
+ * args must use FE_LAYOUT_INDEXED geometry (device memory). x, y and f are device
+ * arrays of n_nodes values, double for FE_FP64 and FE_FP64_DW, float for
+ * FE_FP32_MIXED; y and f accumulate (zero them first for a plain product), by
+ * atomic additions, so the order of the sums, and the last bits of the result,
+ * vary between calls. flags (optional, device, n_elem bytes) as for
+ * fe_integrate_*. An element whose node index is out of range adds nothing
+ * (flag bit 3); flagged elements of the mixed and double-word forms add their
+ * double-precision results once. Enqueued on `stream`.
+ */
+fe_status fe_apply_tet(fe_ctx *ctx, const fe_elem_args *args, const void *x, void *y, void *f, uint8_t *flags,
+                       void *stream);
+fe_status fe_apply_prism(fe_ctx *ctx, const fe_elem_args *args, const void *x, void *y, void *f, uint8_t *flags,
+                         void *stream);
+
 /* Host-only argument validation used by the calls above (no CUDA call). */
 fe_status fe_check_args(fe_elem_type type, const fe_elem_args *args, const fe_out *out);
 

@@ -88,6 +88,8 @@ _SIGS = [
     ("fe_serve_submit", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
     ("fe_serve_release", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("fe_apply_tet", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), _P, _P, _P, _P, _P]),
+    ("fe_apply_prism", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), _P, _P, _P, _P, _P]),
     ("fe_serve_wait_any", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result),
                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("fe_launch_count", ctypes.c_uint64, []),
@@ -318,6 +320,18 @@ class Context:
         fn = load().fe_integrate_tet if elem_type == TET else load().fe_integrate_prism
         _check(fn(self.h, ctypes.byref(args), ctypes.byref(o), self._stream(stream, coords.is_cuda)), self.h)
         return A, b, flags
+
+    def apply(self, elem_type, nodes, conn, coefs, kind, quad, x, y, f=None, coef_mode=PER_ELEMENT, prec=FP32_MIXED,
+              flags=None, stream=None):
+        """Matrix-free y += sum_e P_e^T A^e P_e x (and f += sum_e P_e^T b^e if f is
+        given) over the elements of a node table; y and f accumulate."""
+        args = make_args(elem_type, nodes, coefs, kind, quad, coef_mode, prec, INDEXED, conn)
+        want = torch.float32 if prec == FP32_MIXED else torch.float64
+        for v in (x, y) + ((f,) if f is not None else ()):
+            assert v.dtype == want and v.is_contiguous() and v.numel() == nodes.shape[0]
+        fn = load().fe_apply_tet if elem_type == TET else load().fe_apply_prism
+        _check(fn(self.h, ctypes.byref(args), x.data_ptr(), y.data_ptr(), f.data_ptr() if f is not None else None,
+                  flags.data_ptr() if flags is not None else None, self._stream(stream, True)), self.h)
 
     def tune(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
              out_layout=SOA, out=None, stream=None, conn=None):

@@ -5,17 +5,17 @@
 namespace fe {
 const void *kernel_prism_fp64_idx(int kind, int cpq, int outl) {
     const int inl = INDEXED;
-    FE_IDX8(FE_ELEM_CASE, PRISM, FP64, Q_PRISM6)
+    FE_IDX8(FE_ELEM_CASE, PRISM, FP64, Q_PRISM6) FE_IDXA4(FE_ELEM_CASE, PRISM, FP64, Q_PRISM6)
     return nullptr;
 }
 const void *kernel_prism_mixed_idx(int kind, int cpq, int outl) {
     const int inl = INDEXED;
-    FE_IDX8(FE_ELEM_CASE, PRISM, MIXED, Q_PRISM6)
+    FE_IDX8(FE_ELEM_CASE, PRISM, MIXED, Q_PRISM6) FE_IDXA4(FE_ELEM_CASE, PRISM, MIXED, Q_PRISM6)
     return nullptr;
 }
 const void *kernel_fixup_prism_idx(int kind, int cpq, int outl) {
     const int inl = INDEXED;
-    FE_IDX8(FE_FIX_CASE, PRISM, MIXED, Q_PRISM6)
+    FE_IDX8(FE_FIX_CASE, PRISM, MIXED, Q_PRISM6) FE_IDXA4(FE_FIX_CASE, PRISM, MIXED, Q_PRISM6)
     return nullptr;
 }
 }  // namespace fe

@@ -5,20 +5,20 @@
 namespace fe {
 const void *kernel_tet_fp64_idx(int kind, int quad, int cpq, int outl) {
     const int inl = INDEXED;
-    if (quad == Q_TET1) { FE_IDX8(FE_GATHER_CASE, TET, FP64, Q_TET1) }
-    if (quad == Q_TET4) { FE_IDX8(FE_GATHER_CASE, TET, FP64, Q_TET4) }
+    if (quad == Q_TET1) { FE_IDX8(FE_GATHER_CASE, TET, FP64, Q_TET1) FE_IDXA4(FE_GATHER_CASE, TET, FP64, Q_TET1) }
+    if (quad == Q_TET4) { FE_IDX8(FE_GATHER_CASE, TET, FP64, Q_TET4) FE_IDXA4(FE_GATHER_CASE, TET, FP64, Q_TET4) }
     return nullptr;
 }
 const void *kernel_tet_mixed_idx(int kind, int quad, int cpq, int outl) {
     const int inl = INDEXED;
-    if (quad == Q_TET1) { FE_IDX8(FE_GATHER_CASE, TET, MIXED, Q_TET1) }
-    if (quad == Q_TET4) { FE_IDX8(FE_GATHER_CASE, TET, MIXED, Q_TET4) }
+    if (quad == Q_TET1) { FE_IDX8(FE_GATHER_CASE, TET, MIXED, Q_TET1) FE_IDXA4(FE_GATHER_CASE, TET, MIXED, Q_TET1) }
+    if (quad == Q_TET4) { FE_IDX8(FE_GATHER_CASE, TET, MIXED, Q_TET4) FE_IDXA4(FE_GATHER_CASE, TET, MIXED, Q_TET4) }
     return nullptr;
 }
 const void *kernel_fixup_tet_idx(int kind, int quad, int cpq, int outl) {
     const int inl = INDEXED;
-    if (quad == Q_TET1) { FE_IDX8(FE_FIX_CASE, TET, MIXED, Q_TET1) }
-    if (quad == Q_TET4) { FE_IDX8(FE_FIX_CASE, TET, MIXED, Q_TET4) }
+    if (quad == Q_TET1) { FE_IDX8(FE_FIX_CASE, TET, MIXED, Q_TET1) FE_IDXA4(FE_FIX_CASE, TET, MIXED, Q_TET1) }
+    if (quad == Q_TET4) { FE_IDX8(FE_FIX_CASE, TET, MIXED, Q_TET4) FE_IDXA4(FE_FIX_CASE, TET, MIXED, Q_TET4) }
     return nullptr;
 }
 }  // namespace fe

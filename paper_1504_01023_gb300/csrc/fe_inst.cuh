@@ -35,3 +35,9 @@
 #define FE_GATHER_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                \
     if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
         return reinterpret_cast<const void *>(&fe::gather_kernel<ET, KD, PREC, QUAD, CP, OL>);
+
+// The four (kind, coefficient mode) combinations of the matrix-free output
+// (INDEXED geometry, OUTL == APPLY).
+#define FE_IDXA4(M, ...)                                                              \
+    M(__VA_ARGS__, 0, 0, 2, 2) M(__VA_ARGS__, 0, 1, 2, 2) M(__VA_ARGS__, 1, 0, 2, 2)  \
+    M(__VA_ARGS__, 1, 1, 2, 2)

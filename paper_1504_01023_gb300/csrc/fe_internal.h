@@ -9,7 +9,7 @@ enum ElemType { TET = 0, PRISM = 1 };
 enum Kind { POISSON = 0, GENERIC = 1 };
 enum Prec { FP64 = 0, MIXED = 1, DWORD = 2 };
 enum Quad { Q_TET1 = 0, Q_TET4 = 1, Q_PRISM6 = 2 };
-enum Layout { SOA = 0, AOS = 1, INDEXED = 2 };
+enum Layout { SOA = 0, AOS = 1, INDEXED = 2, APPLY = 2 };  // APPLY: output mode of fe_apply_*
 
 // Bits of the device status word (one per context, read at sync).
 enum StatusBits : int {
@@ -37,6 +37,7 @@ struct ElemParams {
     int tma_in, tma_out;           // SOA tiles moved by 2-D tensor copies (maps in TmaMaps)
     const int *conn;               // INDEXED: [n][NS] node indices into X (nodes [n_nodes][3])
     long long n_nodes;
+    const void *xv;                // APPLY: nodal input vector; A is y, B is f (may be null)
 };
 
 // Tensor-copy descriptors (CUtensorMap, 128 bytes each) of the plane-major

@@ -551,6 +551,30 @@ __device__ __forceinline__ bool gather_nodes(const double *__restrict__ X, long 
     return ok;
 }
 
+// Matrix-free output (OUTL == APPLY): y[idx[r]] += sum_s A_rs x[idx[s]] and
+// f[idx[r]] += b_r (f may be null), by atomic additions.
+template <class CT, int NS>
+__device__ __forceinline__ void scatter_apply(const ElemParams &p, const int idx[NS], const CT A[NS * NS],
+                                              const CT b[NS]) {
+    const CT *x = static_cast<const CT *>(p.xv);
+    CT *y = static_cast<CT *>(p.A);
+    CT *f = static_cast<CT *>(p.B);
+    CT xs[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) xs[s] = __ldg(x + idx[s]);
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+        CT yr = A[NS * r] * xs[0];
+#pragma unroll
+        for (int s = 1; s < NS; ++s) yr += A[NS * r + s] * xs[s];
+        atomicAdd(y + idx[r], yr);
+    }
+    if (f) {
+#pragma unroll
+        for (int r = 0; r < NS; ++r) atomicAdd(f + idx[r], b[r]);
+    }
+}
+
 // Append flagged elements of this warp to the fix-up list (one atomic per warp).
 __device__ __forceinline__ void append_fixup(const ElemParams &p, bool poor, int64_t e) {
     const unsigned m = __ballot_sync(0xFFFFFFFFu, poor);
@@ -681,14 +705,15 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     // ---- compute ----
     CT A[NA], b[NS];
     bool poor = false;
+    bool idx_ok = true;  // INDEXED: every node index of this element is in range
     if (active) {
         const SmemSrc<CT> cs{INL == SOA ? sC + tid : sC + tid * NC, INL == SOA ? B : 1};
         uint8_t fl;
         if constexpr (INL == INDEXED) {
             double xr[NX];
-            const bool ok = gather_nodes<NS>(X, p.n_nodes, sN + tid * NS, xr);
+            idx_ok = gather_nodes<NS>(X, p.n_nodes, sN + tid * NS, xr);
             fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(RegSrc<double>{xr}, cs, A, b, poor);
-            if (!ok) {
+            if (!idx_ok) {
 #pragma unroll
                 for (int k = 0; k < NA; ++k) A[k] = CT(0);
 #pragma unroll
@@ -702,6 +727,13 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         }
         if (PREC != FP64 && poor) fl |= 1;
         if (p.flags) p.flags[e] = fl;
+    }
+    if constexpr (OUTL == APPLY) {
+        // matrix-free: scatter from registers (indices still in shared memory)
+        if (active && idx_ok && !(PREC != FP64 && poor)) scatter_apply<CT, NS>(p, sN + tid * NS, A, b);
+        if (PREC != FP64) append_fixup(p, active && poor, e);
+        __syncthreads();   // the next tile's copies overwrite the indices
+        return true;
     }
     __syncthreads();   // every input read: the output records reuse the same shared memory
     if (active) {
@@ -895,7 +927,9 @@ __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
             }
             if (PREC != FP64 && poor) fl |= 1;
             if (p.flags) p.flags[e] = fl;
-            if (OUTL == SOA) {
+            if constexpr (OUTL == APPLY) {
+                if (ok && !(PREC != FP64 && poor)) scatter_apply<CT, NS>(p, idx, A, b);  // flagged: the fix-up adds
+            } else if (OUTL == SOA) {
 #pragma unroll
                 for (int k = 0; k < NA; ++k) st_stream(Aout + k * p.os + e, A[k]);
 #pragma unroll
@@ -938,7 +972,9 @@ __device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
         const Src<AOS, CT> cs{C + e * NC, 0};
         fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(xs, cs, A, b);
     }
-    if (OUTL == SOA) {
+    if constexpr (OUTL == APPLY) {
+        if (INL == INDEXED) scatter_apply<CT, NS>(p, p.conn + e * NS, A, b);
+    } else if (OUTL == SOA) {
 #pragma unroll
         for (int k = 0; k < NA; ++k) Aout[k * p.os + e] = A[k];
 #pragma unroll

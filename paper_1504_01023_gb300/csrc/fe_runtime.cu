@@ -100,14 +100,17 @@ static const void *fix_kernel(fe_elem_type type, const fe_elem_args *a, int outl
 
 // Dynamic shared memory of one block: the tile's inputs and outputs, each region
 // rounded to 16 bytes exactly as BlockSmem in fe_kernels.cuh lays them out.
+// Output mode of fe_apply_* (matrix-free), passed where an fe_layout goes.
+static constexpr int kOutApply = 2;
+
 static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, int B) {
-    (void)outl;
     // tetrahedra with a node table read straight from global memory (gather_kernel)
     if (a->coords_layout == FE_LAYOUT_INDEXED && type == FE_TET) return 0;
     const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
     const int64_t geo = a->coords_layout == FE_LAYOUT_INDEXED ? r16(int64_t(B) * ns * 4) : int64_t(B) * 3 * ns * 8;
     const int64_t in = geo + r16(int64_t(B) * nc * cs), out = r16(int64_t(B) * ns * ns * cs) + r16(int64_t(B) * ns * cs);
+    if (outl == kOutApply) return in;  // matrix-free: results leave from registers
     return in > out ? in : out;
 }
 
@@ -196,7 +199,7 @@ static bool encode_planes(void *out, bool dbl, const void *base, uint64_t n, uin
 }
 
 fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, Scratch &s, cudaStream_t st,
-                     const Shape *force) {
+                     const Shape *force, const void *x) {
     if (a->n_elem == 0) return FE_OK;
     const int outl = o->layout;
     const void *k = main_kernel(type, a, outl);
@@ -237,6 +240,7 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     p.item = 0;
     p.conn = a->coords_layout == FE_LAYOUT_INDEXED ? a->conn : nullptr;
     p.n_nodes = a->coords_layout == FE_LAYOUT_INDEXED ? a->n_nodes : 0;
+    p.xv = x;
     const bool fixup = a->prec != FE_FP64;   // mixed and double-word forms flag elements
     if (fixup) {
         fe_status e = ensure_scratch(ctx, s, uint64_t(a->n_elem));
@@ -684,6 +688,50 @@ fe_status fe_integrate_tet(fe_ctx *ctx, const fe_elem_args *args, const fe_out *
 
 fe_status fe_integrate_prism(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream) {
     return integrate(ctx, FE_PRISM, args, out, stream);
+}
+
+// Matrix-free application: the element kernels with the APPLY output mode.
+static fe_status apply(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const void *x, void *y, void *f,
+                       uint8_t *flags, void *stream) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    fe_out o{};
+    o.A = y;
+    o.b = y;          // validation only: f may be null
+    o.layout = FE_LAYOUT_AOS;
+    o.flags = flags;
+    o.memory = FE_MEM_DEVICE;
+    fe_status st = fe_check_args(type, a, &o);
+    if (st == FE_OK && a && a->coords_layout != FE_LAYOUT_INDEXED)
+        st = set_error(nullptr, FE_ERR_UNSUPPORTED, "matrix-free application needs a node table (FE_LAYOUT_INDEXED)");
+    const unsigned cs = a ? unsigned(csize(a->prec)) : 8;
+    if (st == FE_OK && a->n_elem > 0 &&
+        (!x || !y || (reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(f)) & (cs - 1)))
+        st = set_error(nullptr, FE_ERR_INVALID_ARG, "null or misaligned x or y (or misaligned f)");
+    if (st != FE_OK) {
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
+        ctx->last_error = t_last_error;
+        return st;
+    }
+    if (a->n_elem == 0) return FE_OK;
+    cudaSetDevice(ctx->device);
+    o.b = f;
+    o.layout = static_cast<fe_layout>(kOutApply);
+    // launch shape: the tuner cannot time this call (it accumulates into y), so a
+    // key of its own gets the shape measured best for the unstaged node-table
+    // kernels unless fe_set_shape chose one
+    const std::string key = shape_key(type, a, &o);
+    if (!ctx->shapes.count(key)) ctx->shapes[key] = Shape{64, 1};
+    return launch_set(ctx, type, a, &o, ctx->scratch, static_cast<cudaStream_t>(stream), nullptr, x);
+}
+
+fe_status fe_apply_tet(fe_ctx *ctx, const fe_elem_args *args, const void *x, void *y, void *f, uint8_t *flags,
+                       void *stream) {
+    return apply(ctx, FE_TET, args, x, y, f, flags, stream);
+}
+
+fe_status fe_apply_prism(fe_ctx *ctx, const fe_elem_args *args, const void *x, void *y, void *f, uint8_t *flags,
+                         void *stream) {
+    return apply(ctx, FE_PRISM, args, x, y, f, flags, stream);
 }
 
 uint64_t fe_launch_count(void) { return g_launches.load(); }

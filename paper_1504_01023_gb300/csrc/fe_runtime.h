@@ -94,8 +94,9 @@ void free_scratch(Scratch &s);
 // Launch main + fix-up kernels of one homogeneous set (device pointers).
 // With `force`, that launch shape is used and the context's tuned shapes and
 // profiling events are not touched (safe from the serving thread).
+// x: the nodal input vector of the matrix-free output mode (fe_apply_*).
 fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, Scratch &s,
-                     cudaStream_t st, const Shape *force = nullptr);
+                     cudaStream_t st, const Shape *force = nullptr, const void *x = nullptr);
 Shape default_shape(fe_elem_type type);
 // Dynamically built batch (serving): device tables grown on demand, uploaded
 // from pinned staging with stream-ordered copies, launched without a graph.
