@@ -371,6 +371,7 @@ def run_native(args):
             result["prism_form"] = prism_form(ctx, dev, api, args)
         if not args.no_fp64:
             result["fp64_form"], result["double_word_form"] = fp64_form(ctx, dev, api, mesh, coefs, args)
+            result["packed_form"] = packed_form(ctx, dev, api, mesh, args)
         if not args.no_indexed:
             result["indexed_form"] = indexed_form(ctx, dev, api, coefs, args)
             result["apply_form"] = apply_form(ctx, dev, api, coefs, args)
@@ -528,6 +529,48 @@ def apply_form(ctx, dev, api, coefs, args):
                         "tetrahedra (TET4, per-element coefficients) with a node table, mixed form, float atomics",
             "value": n / k_ms / 1e3, "unit": "Melem/s", "kernel_ms": k_ms, "bytes_per_element": total / n,
             "achieved_gbs": gbs, "hbm_frac": gbs / peak, "nodes": m}
+
+
+def packed_form(ctx, dev, api, mesh, args):
+    """The Laplace tetrahedra (TET1, d^0 = 1 per element) on the headline mesh with
+    full and with packed (upper-triangle, 10 of 16 entries) A^e, in the mixed and
+    the double-word forms; kernel times from the library's profiling events."""
+    import torch
+    n = len(mesh)
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)
+    peak, _ = measured_peaks()
+    res = {"workload": "Laplace tetrahedra, 6,000,000 elements, TET1, d^0 = 1 per element, element-contiguous "
+                       "order; A^e full (16 entries) or packed (upper triangle, 10 entries)"}
+    for prec, name in ((api.FP32_MIXED, "mixed"), (api.FP64_DW, "double_word")):
+        dt = torch.float32 if prec == api.FP32_MIXED else torch.float64
+        C = torch.ones((n, 1), dtype=dt, device=dev)
+        for packed in (False, True):
+            out = api.alloc_out(api.TET, n, prec, api.AOS, dev, with_flags=True, packed=packed)
+            kw = dict(kind=api.POISSON, quad=api.QUAD_TET1, coef_mode=api.PER_ELEMENT, prec=prec, layout=api.AOS,
+                      out_layout=api.AOS, packed=packed)
+            ctx.tune(api.TET, X, C, out=out, **kw)
+            for _ in range(3):
+                ctx.integrate(api.TET, X, C, out=out, **kw)
+            torch.cuda.synchronize(dev)
+            ctx.set_profiling(True)
+            ctx.kernel_time(reset=True)
+            for _ in range(max(20, min(200, args.steps // 10))):
+                ctx.integrate(api.TET, X, C, out=out, **kw)
+            kms, kn = ctx.kernel_time(reset=True)
+            ctx.set_profiling(False)
+            k_ms = kms / kn
+            cs = 4 if prec == api.FP32_MIXED else 8
+            bpe = 96 + cs + (10 if packed else 16) * cs + 4 * cs
+            gbs = n * bpe / (k_ms * 1e-3) / 1e9
+            res[f"{name}_{'packed' if packed else 'full'}"] = {"value": n / k_ms / 1e3, "unit": "Melem/s",
+                                                              "bytes_per_element": bpe, "achieved_gbs": gbs,
+                                                              "hbm_frac": gbs / peak}
+            del out
+        del C
+    del X
+    torch.cuda.empty_cache()
+    res.update(value=res["mixed_packed"]["value"], unit="Melem/s", hbm_frac=res["mixed_packed"]["hbm_frac"])
+    return res
 
 
 def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args):

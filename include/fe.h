@@ -148,10 +148,15 @@ typedef struct fe_elem_args {
 } fe_elem_args;
 
 /*
- * Outputs (Sec. 4.2, Fig. 2): A^e full NS x NS (not symmetric-packed), row-major
- * entry k = r*NS + s; b^e NS entries. Element type: double (FE_FP64, FE_FP64_DW) or float.
+ * Outputs (Sec. 4.2, Fig. 2): A^e full NS x NS, row-major entry k = r*NS + s
+ * (NA = NS*NS entries), or, with packed = 1 (FE_POISSON only, whose A^e is
+ * symmetric), its upper triangle row by row: entry k = r*NS - r*(r-1)/2 + (s - r)
+ * for s >= r (NA = NS*(NS+1)/2: 10 for tetrahedra, 21 for prisms); b^e NS
+ * entries. Element type: double (FE_FP64, FE_FP64_DW) or float.
  *   SOA ("coalesced"): A[k*stride + e], b[r*stride + e].
- *   AOS (element-contiguous): A[e*NS*NS + k], b[e*NS + r].
+ *   AOS (element-contiguous): A[e*NA + k], b[e*NS + r].
+ * packed = 1 is not accepted with FE_LAYOUT_INDEXED coordinates, by the batched
+ * and serving entry points or by fe_integrate_tet_noalloc (FE_ERR_UNSUPPORTED).
  * flags (optional, may be NULL): one byte per element, bit 0 = the double
  * Jacobian path was used, bit 1 = det J < 0 somewhere (|det J| is integrated),
  * bit 2 = degenerate (|det J| <= 1e-300 in double): A^e = 0 and b^e = 0,
@@ -164,6 +169,7 @@ typedef struct fe_out {
     int64_t stride;
     uint8_t *flags;
     fe_memory memory;              /* where A, b and flags live */
+    int packed;                    /* 1: upper triangle of a symmetric A^e (FE_POISSON) */
 } fe_out;
 
 /* Create a context on cfg->device (NULL cfg = device 0, defaults). Allocates the

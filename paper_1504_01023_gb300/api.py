@@ -52,7 +52,7 @@ class ElemArgs(ctypes.Structure):
 
 class Out(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("layout", ctypes.c_int), ("stride", ctypes.c_int64),
-                ("flags", ctypes.c_void_p), ("memory", ctypes.c_int)]
+                ("flags", ctypes.c_void_p), ("memory", ctypes.c_int), ("packed", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):
@@ -204,16 +204,26 @@ def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, con
     return a
 
 
-def alloc_out(elem_type, n, prec, out_layout, device, with_flags=True, pin=False):
+def packed_size(elem_type):
+    """Entries of the packed upper triangle of A^e (10 or 21)."""
     ns = NS[elem_type]
+    return ns * (ns + 1) // 2
+
+
+def alloc_out(elem_type, n, prec, out_layout, device, with_flags=True, pin=False, packed=False):
+    """A, b, flags. A is (n, NS, NS) element-contiguous or (NS*NS, n) plane-major;
+    packed: (n, NP) or (NP, n), NP = NS*(NS+1)/2 upper-triangle entries."""
+    ns = NS[elem_type]
+    na = packed_size(elem_type) if packed else ns * ns
     dt = torch.float32 if prec == FP32_MIXED else torch.float64
     kw = dict(dtype=dt, device=device)
     if out_layout == SOA:
-        # A and b share one plane stride: one (NS*NS + NS, n) buffer
-        buf = torch.empty((ns * ns + ns, n), **kw, pin_memory=pin) if pin else torch.empty((ns * ns + ns, n), **kw)
-        A, b = buf[: ns * ns], buf[ns * ns:]
+        # A and b share one plane stride: one (NA + NS, n) buffer
+        buf = torch.empty((na + ns, n), **kw, pin_memory=pin) if pin else torch.empty((na + ns, n), **kw)
+        A, b = buf[:na], buf[na:]
     else:
-        A = torch.empty((n, ns, ns), **kw, pin_memory=pin) if pin else torch.empty((n, ns, ns), **kw)
+        shape = (n, na) if packed else (n, ns, ns)
+        A = torch.empty(shape, **kw, pin_memory=pin) if pin else torch.empty(shape, **kw)
         b = torch.empty((n, ns), **kw, pin_memory=pin) if pin else torch.empty((n, ns), **kw)
     flags = None
     if with_flags:
@@ -222,8 +232,9 @@ def alloc_out(elem_type, n, prec, out_layout, device, with_flags=True, pin=False
     return A, b, flags
 
 
-def make_out(A, b, flags, out_layout):
+def make_out(A, b, flags, out_layout, packed=False):
     o = Out()
+    o.packed = 1 if packed else 0
     o.A, o.b = A.data_ptr(), b.data_ptr()
     o.layout = out_layout
     if out_layout == SOA:
@@ -307,16 +318,17 @@ class Context:
         return ctypes.c_void_p(0)
 
     def integrate(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-                  out_layout=SOA, out=None, with_flags=True, stream=None, conn=None):
+                  out_layout=SOA, out=None, with_flags=True, stream=None, conn=None, packed=False):
         """Integrate one element set; returns (A, b, flags) tensors (allocated if
         ``out`` is None, on the device of ``coords``; pinned host memory for host inputs).
         With layout=INDEXED, coords is the node array and conn the element -> node table."""
         args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
             on_host = not coords.is_cuda
-            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, with_flags, pin=on_host)
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, with_flags, pin=on_host,
+                            packed=packed)
         A, b, flags = out
-        o = make_out(A, b, flags, out_layout)
+        o = make_out(A, b, flags, out_layout, packed)
         fn = load().fe_integrate_tet if elem_type == TET else load().fe_integrate_prism
         _check(fn(self.h, ctypes.byref(args), ctypes.byref(o), self._stream(stream, coords.is_cuda)), self.h)
         return A, b, flags
@@ -334,28 +346,28 @@ class Context:
                   flags.data_ptr() if flags is not None else None, self._stream(stream, True)), self.h)
 
     def tune(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-             out_layout=SOA, out=None, stream=None, conn=None):
+             out_layout=SOA, out=None, stream=None, conn=None, packed=False):
         args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
-            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
-        o = make_out(*out, out_layout)
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
+        o = make_out(*out, out_layout, packed)
         _check(load().fe_tune(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), self._stream(stream, True)), self.h)
-        return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out, conn)
+        return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out, conn, packed)
 
     def set_shape(self, block, persistent, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT,
-                  prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None, conn=None):
+                  prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None, conn=None, packed=False):
         args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
-            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
-        o = make_out(*out, out_layout)
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
+        o = make_out(*out, out_layout, packed)
         _check(load().fe_set_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), block, persistent), self.h)
 
     def shape(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-              out_layout=SOA, out=None, conn=None):
+              out_layout=SOA, out=None, conn=None, packed=False):
         args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
-            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device)
-        o = make_out(*out, out_layout)
+            out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
+        o = make_out(*out, out_layout, packed)
         blk, pers = ctypes.c_int(), ctypes.c_int()
         _check(load().fe_get_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), ctypes.byref(blk),
                                    ctypes.byref(pers)), self.h)

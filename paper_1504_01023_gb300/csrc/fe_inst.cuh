@@ -41,3 +41,10 @@
 #define FE_IDXA4(M, ...)                                                              \
     M(__VA_ARGS__, 0, 0, 2, 2) M(__VA_ARGS__, 0, 1, 2, 2) M(__VA_ARGS__, 1, 0, 2, 2)  \
     M(__VA_ARGS__, 1, 1, 2, 2)
+
+// Packed (upper-triangle) outputs, Laplace kind only: coefficient mode x input
+// layout (SOA, AOS) x output (SOA_PACKED, AOS_PACKED).
+#define FE_PK8(M, ...)                                                                \
+    M(__VA_ARGS__, 0, 0, 0, 3) M(__VA_ARGS__, 0, 0, 0, 4) M(__VA_ARGS__, 0, 0, 1, 3)  \
+    M(__VA_ARGS__, 0, 0, 1, 4) M(__VA_ARGS__, 0, 1, 0, 3) M(__VA_ARGS__, 0, 1, 0, 4)  \
+    M(__VA_ARGS__, 0, 1, 1, 3) M(__VA_ARGS__, 0, 1, 1, 4)

@@ -10,6 +10,12 @@ enum Kind { POISSON = 0, GENERIC = 1 };
 enum Prec { FP64 = 0, MIXED = 1, DWORD = 2 };
 enum Quad { Q_TET1 = 0, Q_TET4 = 1, Q_PRISM6 = 2 };
 enum Layout { SOA = 0, AOS = 1, INDEXED = 2, APPLY = 2 };  // APPLY: output mode of fe_apply_*
+// Output modes beyond the layouts: the upper triangle of a symmetric A^e.
+constexpr int SOA_PACKED = 3, AOS_PACKED = 4;
+constexpr bool out_soa(int o) { return o == SOA || o == SOA_PACKED; }
+constexpr bool out_packed(int o) { return o == SOA_PACKED || o == AOS_PACKED; }
+// Index of entry (r, s), s >= r, of a packed upper triangle of an NS x NS matrix.
+constexpr int packed_index(int ns, int r, int s) { return r * ns - r * (r - 1) / 2 + (s - r); }
 
 // Bits of the device status word (one per context, read at sync).
 enum StatusBits : int {

@@ -499,16 +499,18 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
 // AOS regions hold element records back to back; SOA regions hold one row of B
 // scalars per plane. Every region starts on a 16-byte boundary.
 // ---------------------------------------------------------------------------
-template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL = AOS> struct BlockSmem {
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL = AOS, int OUTL = AOS> struct BlockSmem {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
+    // A^e entries written per element (upper triangle when packed)
+    static constexpr int NAO = out_packed(OUTL) ? CF::NS * (CF::NS + 1) / 2 : CF::NA;
     __host__ __device__ static constexpr int64_t r16(int64_t v) { return (v + 15) / 16 * 16; }
     // geometry of the tile: coordinates, or node indices for INDEXED
     __host__ __device__ static constexpr int64_t x_bytes(int B) {
         return INL == INDEXED ? r16(int64_t(B) * CF::NS * 4) : int64_t(B) * CF::NX * 8;
     }
     __host__ __device__ static constexpr int64_t c_bytes(int B) { return r16(int64_t(B) * CF::NC * int64_t(sizeof(CT))); }
-    __host__ __device__ static constexpr int64_t a_bytes(int B) { return r16(int64_t(B) * CF::NA * int64_t(sizeof(CT))); }
+    __host__ __device__ static constexpr int64_t a_bytes(int B) { return r16(int64_t(B) * NAO * int64_t(sizeof(CT))); }
     __host__ __device__ static constexpr int64_t b_bytes(int B) { return r16(int64_t(B) * CF::NS * int64_t(sizeof(CT))); }
     __host__ __device__ static constexpr int64_t in_bytes(int B) { return x_bytes(B) + c_bytes(B); }
     __host__ __device__ static constexpr int64_t out_bytes(int B) { return a_bytes(B) + b_bytes(B); }
@@ -635,7 +637,8 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
                                              unsigned &phase, const TmaMaps *tm = nullptr) {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
-    using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ, INL>;
+    using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>;
+    constexpr int NAO = SM::NAO;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
     const int B = blockDim.x;
     const int tid = threadIdx.x;
@@ -737,16 +740,23 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     }
     __syncthreads();   // every input read: the output records reuse the same shared memory
     if (active) {
-        if (OUTL == SOA) {
+        // entry k_out of the written A^e: (r, s) row-major, or its upper triangle
 #pragma unroll
-            for (int k = 0; k < NA; ++k) sA[k * B + tid] = A[k];
+        for (int r = 0; r < NS; ++r)
 #pragma unroll
-            for (int k = 0; k < NS; ++k) sB[k * B + tid] = b[k];
-        } else {
+            for (int s = out_packed(OUTL) ? r : 0; s < NS; ++s) {
+                const int ko = out_packed(OUTL) ? packed_index(NS, r, s) : r * NS + s;
+                if (out_soa(OUTL))
+                    sA[ko * B + tid] = A[r * NS + s];
+                else
+                    sA[tid * NAO + ko] = A[r * NS + s];
+            }
 #pragma unroll
-            for (int k = 0; k < NA; ++k) sA[tid * NA + k] = A[k];
-#pragma unroll
-            for (int k = 0; k < NS; ++k) sB[tid * NS + k] = b[k];
+        for (int k = 0; k < NS; ++k) {
+            if (out_soa(OUTL))
+                sB[k * B + tid] = b[k];
+            else
+                sB[tid * NS + k] = b[k];
         }
     }
     if (PREC != FP64) append_fixup(p, active && poor, e);
@@ -754,7 +764,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     // ---- store outputs ----
     fence_proxy_async_smem();
     __syncthreads();
-    if (OUTL == SOA && tm && p.tma_out) {
+    if (out_soa(OUTL) && tm && p.tma_out) {
         if (tid == 0) {
             tma_store_2d(tm->a, int(e0), 0, sA);
             tma_store_2d(tm->b, int(e0), 0, sB);
@@ -762,15 +772,15 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
             bulk_wait_read0();
         }
     } else {
-        const bool a_ok = aligned16(Aout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
-        const bool b_ok = aligned16(Bout, OUTL == SOA ? uint64_t(p.os) * sizeof(CT) : 0);
-        const bool tA = a_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NA) * sizeof(CT)) % 16 == 0);
-        const bool tB = b_ok && ((uint64_t(nb) * (OUTL == SOA ? 1 : NS) * sizeof(CT)) % 16 == 0);
-        if (OUTL == SOA) {
-            stage_rows_out(Aout + e0, p.os, sA, B, NA, nb, tA);
+        const bool a_ok = aligned16(Aout, out_soa(OUTL) ? uint64_t(p.os) * sizeof(CT) : 0);
+        const bool b_ok = aligned16(Bout, out_soa(OUTL) ? uint64_t(p.os) * sizeof(CT) : 0);
+        const bool tA = a_ok && ((uint64_t(nb) * (out_soa(OUTL) ? 1 : NAO) * sizeof(CT)) % 16 == 0);
+        const bool tB = b_ok && ((uint64_t(nb) * (out_soa(OUTL) ? 1 : NS) * sizeof(CT)) % 16 == 0);
+        if (out_soa(OUTL)) {
+            stage_rows_out(Aout + e0, p.os, sA, B, NAO, nb, tA);
             stage_rows_out(Bout + e0, p.os, sB, B, NS, nb, tB);
         } else {
-            stage_rows_out(Aout + e0 * NA, 0, sA, 0, 1, nb * NA, tA);
+            stage_rows_out(Aout + e0 * NAO, 0, sA, 0, 1, nb * NAO, tA);
             stage_rows_out(Bout + e0 * NS, 0, sB, 0, 1, nb * NS, tB);
         }
         if ((tA || tB) && tid < 32) {
@@ -974,16 +984,25 @@ __device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
     }
     if constexpr (OUTL == APPLY) {
         if (INL == INDEXED) scatter_apply<CT, NS>(p, p.conn + e * NS, A, b);
-    } else if (OUTL == SOA) {
-#pragma unroll
-        for (int k = 0; k < NA; ++k) Aout[k * p.os + e] = A[k];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) Bout[k * p.os + e] = b[k];
     } else {
+        constexpr int NAO = out_packed(OUTL) ? NS * (NS + 1) / 2 : NA;
 #pragma unroll
-        for (int k = 0; k < NA; ++k) Aout[e * NA + k] = A[k];
+        for (int r = 0; r < NS; ++r)
 #pragma unroll
-        for (int k = 0; k < NS; ++k) Bout[e * NS + k] = b[k];
+            for (int s = out_packed(OUTL) ? r : 0; s < NS; ++s) {
+                const int ko = out_packed(OUTL) ? packed_index(NS, r, s) : r * NS + s;
+                if (out_soa(OUTL))
+                    Aout[ko * p.os + e] = A[r * NS + s];
+                else
+                    Aout[e * NAO + ko] = A[r * NS + s];
+            }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (out_soa(OUTL))
+                Bout[k * p.os + e] = b[k];
+            else
+                Bout[e * NS + k] = b[k];
+        }
     }
     if (p.flags) p.flags[e] = fl;
 }

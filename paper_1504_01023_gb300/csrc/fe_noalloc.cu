@@ -70,8 +70,8 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
         return set_error(nullptr, FE_ERR_INVALID_ARG, "fe_integrate_tet_noalloc takes FE_FP32_MIXED only");
     if (args->memory != FE_MEM_DEVICE || out->memory != FE_MEM_DEVICE)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "fe_integrate_tet_noalloc takes device buffers only");
-    if (args->coords_layout == FE_LAYOUT_INDEXED)
-        return set_error(nullptr, FE_ERR_UNSUPPORTED, "fe_integrate_tet_noalloc takes no node table");
+    if (args->coords_layout == FE_LAYOUT_INDEXED || out->packed)
+        return set_error(nullptr, FE_ERR_UNSUPPORTED, "fe_integrate_tet_noalloc takes no node table and no packed output");
     if (uint64_t(args->n_elem) > kListCap)
         return set_error(nullptr, FE_ERR_INVALID_ARG,
                          "n_elem exceeds the " + std::to_string(kListCap) +

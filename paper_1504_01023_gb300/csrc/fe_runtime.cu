@@ -103,13 +103,25 @@ static const void *fix_kernel(fe_elem_type type, const fe_elem_args *a, int outl
 // Output mode of fe_apply_* (matrix-free), passed where an fe_layout goes.
 static constexpr int kOutApply = 2;
 
+// Kernel output mode of an fe_out: its layout, or the packed upper triangle.
+static int out_mode(const fe_out *o) {
+    if (o->layout == kOutApply) return kOutApply;
+    return o->packed ? (o->layout == FE_LAYOUT_SOA ? SOA_PACKED : AOS_PACKED) : int(o->layout);
+}
+// A^e entries written per element.
+static int na_out(fe_elem_type type, int outl) {
+    const int ns = ns_of(type);
+    return out_packed(outl) ? ns * (ns + 1) / 2 : ns * ns;
+}
+
 static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, int B) {
     // tetrahedra with a node table read straight from global memory (gather_kernel)
     if (a->coords_layout == FE_LAYOUT_INDEXED && type == FE_TET) return 0;
     const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
     const int64_t geo = a->coords_layout == FE_LAYOUT_INDEXED ? r16(int64_t(B) * ns * 4) : int64_t(B) * 3 * ns * 8;
-    const int64_t in = geo + r16(int64_t(B) * nc * cs), out = r16(int64_t(B) * ns * ns * cs) + r16(int64_t(B) * ns * cs);
+    const int64_t in = geo + r16(int64_t(B) * nc * cs),
+                  out = r16(int64_t(B) * na_out(type, outl) * cs) + r16(int64_t(B) * ns * cs);
     if (outl == kOutApply) return in;  // matrix-free: results leave from registers
     return in > out ? in : out;
 }
@@ -134,7 +146,7 @@ static std::string shape_key(fe_elem_type type, const fe_elem_args *a, const fe_
     for (int64_t n = a->n_elem; n > 1; n >>= 2) ++bucket;  // size class: floor(log4 n)
     std::ostringstream k;
     k << "t" << type << "k" << a->kind << "p" << a->prec << "q" << a->quad << "c" << a->coef_mode << "i"
-      << a->coords_layout << "o" << o->layout << "n" << bucket;
+      << a->coords_layout << "o" << out_mode(o) << "n" << bucket;
     return k.str();
 }
 
@@ -201,7 +213,7 @@ static bool encode_planes(void *out, bool dbl, const void *base, uint64_t n, uin
 fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, Scratch &s, cudaStream_t st,
                      const Shape *force, const void *x) {
     if (a->n_elem == 0) return FE_OK;
-    const int outl = o->layout;
+    const int outl = out_mode(o);
     const void *k = main_kernel(type, a, outl);
     if (!k) return set_error(ctx, FE_ERR_UNSUPPORTED, "no kernel for this combination");
     Shape sh = default_shape(type);
@@ -267,7 +279,8 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
             p.tma_in = encode_planes(tm.x, true, a->coords, uint64_t(a->n_elem), 3 * ns, uint64_t(p.xs) * 8, sh.block) &&
                        encode_planes(tm.c, dbl, a->coefs, uint64_t(a->n_elem), nc, uint64_t(p.cs) * cs, sh.block);
         if (o->layout == FE_LAYOUT_SOA)
-            p.tma_out = encode_planes(tm.a, dbl, o->A, uint64_t(a->n_elem), ns * ns, uint64_t(p.os) * cs, sh.block) &&
+            p.tma_out = encode_planes(tm.a, dbl, o->A, uint64_t(a->n_elem), na_out(type, outl), uint64_t(p.os) * cs,
+                                      sh.block) &&
                         encode_planes(tm.b, dbl, o->b, uint64_t(a->n_elem), ns, uint64_t(p.os) * cs, sh.block);
     }
 
@@ -321,7 +334,7 @@ static fe_status ensure_stage(fe_ctx *ctx, int slot, int idx, uint64_t bytes) {
 static fe_status host_pipeline(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, cudaStream_t user) {
     const int64_t n = a->n_elem;
     const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
-    const int nx = 3 * ns, na = ns * ns;
+    const int nx = 3 * ns, na = na_out(type, out_mode(o));
     const int64_t K = std::min<int64_t>(n, int64_t(1) << 20);
     const bool in_host = a->memory == FE_MEM_HOST, out_host = o->memory == FE_MEM_HOST;
     const uint64_t need[5] = {uint64_t(K) * nx * 8, uint64_t(K) * nc * cs, uint64_t(K) * na * cs, uint64_t(K) * ns * cs,
@@ -547,6 +560,11 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
         (o->layout != FE_LAYOUT_SOA && o->layout != FE_LAYOUT_AOS))
         return set_error(nullptr, FE_ERR_INVALID_ARG, "bad layout");
     const bool indexed = a->coords_layout == FE_LAYOUT_INDEXED;
+    if (o->packed != 0 && o->packed != 1) return set_error(nullptr, FE_ERR_INVALID_ARG, "packed must be 0 or 1");
+    if (o->packed && a->kind != FE_POISSON)
+        return set_error(nullptr, FE_ERR_UNSUPPORTED, "packed output needs a symmetric A^e (FE_POISSON)");
+    if (o->packed && indexed)
+        return set_error(nullptr, FE_ERR_UNSUPPORTED, "packed output is not available with a node table");
     if (indexed ? a->coefs_layout != FE_LAYOUT_AOS : a->coefs_layout != a->coords_layout)
         return set_error(nullptr, FE_ERR_UNSUPPORTED,
                          "coefficients must use the layout of the coordinates (element-contiguous with a node table)");
@@ -798,7 +816,7 @@ fe_status fe_set_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
     if (st != FE_OK) return st;
     if (block_threads < 32 || block_threads > max_block(type, args->prec) || block_threads % 32 || (persistent != 0 && persistent != 1))
         return set_error(ctx, FE_ERR_INVALID_ARG, "bad launch shape");
-    if (smem_bytes(type, args, out->layout, block_threads) + kStaticSmem > ctx->max_smem_optin)
+    if (smem_bytes(type, args, out_mode(out), block_threads) + kStaticSmem > ctx->max_smem_optin)
         return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
     ctx->shapes[shape_key(type, args, out)] = Shape{block_threads, persistent};
     save_tuning_cache(ctx);
@@ -824,7 +842,7 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const f
     for (int B = 64; B <= max_block(type, a->prec); B *= 2) {
         for (int pers = 0; pers < 2; ++pers) {
             Shape sh{B, pers};
-            if (smem_bytes(type, a, o->layout, B) + kStaticSmem > ctx->max_smem_optin) continue;
+            if (smem_bytes(type, a, out_mode(o), B) + kStaticSmem > ctx->max_smem_optin) continue;
             st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);  // warm-up
             if (st != FE_OK) break;
             cudaEventRecord(e0, s);

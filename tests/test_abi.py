@@ -125,6 +125,21 @@ def test_node_table_validation(lib):
     assert lib.fe_integrate_tet_noalloc(ctypes.byref(idx()[0]), ctypes.byref(o), None) in (-1, -6)
 
 
+def test_packed_output_validation(lib):
+    """packed = 1 (upper triangle) for the symmetric Laplace kind only."""
+    a, o = _args()
+    a.kind = api.POISSON
+    o.packed = 1
+    assert _chk(lib, api.TET, a, o) == 0
+    a.kind = api.GENERIC
+    assert _chk(lib, api.TET, a, o) == -6
+    a.kind, o.packed = api.POISSON, 2
+    assert _chk(lib, api.TET, a, o) == -1
+    o.packed = 1
+    a.coords_layout, a.coefs_layout, a.conn, a.n_nodes = api.INDEXED, api.AOS, 65536, 10
+    assert _chk(lib, api.TET, a, o) == -6
+
+
 def test_null_context_rejected(lib):
     a, o = _args()
     assert lib.fe_integrate_tet(None, ctypes.byref(a), ctypes.byref(o), None) == -1
