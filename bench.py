@@ -372,6 +372,7 @@ def run_native(args):
         if not args.no_fp64:
             result["fp64_form"], result["double_word_form"] = fp64_form(ctx, dev, api, mesh, coefs, args)
             result["packed_form"] = packed_form(ctx, dev, api, mesh, args)
+            result["ordering_study"] = ordering_study(ctx, dev, api, mesh, coefs, args)
         if not args.no_indexed:
             result["indexed_form"] = indexed_form(ctx, dev, api, coefs, args)
             result["apply_form"] = apply_form(ctx, dev, api, coefs, args)
@@ -571,6 +572,52 @@ def packed_form(ctx, dev, api, mesh, args):
     torch.cuda.empty_cache()
     res.update(value=res["mixed_packed"]["value"], unit="Melem/s", hbm_frac=res["mixed_packed"]["hbm_frac"])
     return res
+
+
+def ordering_study(ctx, dev, api, mesh, coefs, args):
+    """A counterpart of the paper's Table 7 (Sec. 5): nanoseconds per element of
+    the QSS, SQS and SSQ loop orderings (Algorithms 2-7) for the four cases
+    Poisson / convection-diffusion x tetrahedra / prisms, mixed form, element-
+    contiguous order, tuned launch shape, 1,000,000 tetrahedra (a prefix of the
+    headline mesh) and 500,000 prisms. Poisson: d^0 per point (TET4, PRISM6);
+    convection-diffusion: 20 coefficients per element."""
+    import torch
+    from paper_1504_01023_gb300 import meshgen
+    nt, npr = 1_000_000, 500_000
+    pmesh = meshgen.prism_slab_mesh(1000, None, 0.1, seed=meshgen.SEED_BASE + 3, n_elem=npr)
+    cases = {
+        ("poisson", "tetra"): (api.TET, mesh[:nt], meshgen.poisson_coefs(nt, 4, None, seed=SEED), api.POISSON,
+                               api.QUAD_TET4, api.PER_QPOINT),
+        ("poisson", "prism"): (api.PRISM, pmesh, meshgen.poisson_coefs(npr, 6, None, seed=SEED), api.POISSON,
+                               api.QUAD_PRISM6, api.PER_QPOINT),
+        ("conv-diff", "tetra"): (api.TET, mesh[:nt], coefs[:nt], api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT),
+        ("conv-diff", "prism"): (api.PRISM, pmesh, meshgen.generic_coefs(npr, 1, seed=SEED), api.GENERIC,
+                                 api.QUAD_PRISM6, api.PER_ELEMENT),
+    }
+    table = {}
+    for (problem, elem), (et, m, c, kind, quad, cm) in cases.items():
+        n = len(m)
+        X = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+        C = torch.from_numpy(np.ascontiguousarray(c.reshape(n, -1).astype(np.float32))).to(dev)
+        out = api.alloc_out(et, n, api.FP32_MIXED, api.AOS, dev, with_flags=True)
+        for name, order in (("QSS", api.QSS), ("SQS", api.SQS), ("SSQ", api.SSQ)):
+            kw = dict(kind=kind, quad=quad, coef_mode=cm, prec=api.FP32_MIXED, layout=api.AOS, out_layout=api.AOS,
+                      ordering=order)
+            ctx.tune(et, X, C, out=out, **kw)
+            ctx.integrate(et, X, C, out=out, **kw)
+            torch.cuda.synchronize(dev)
+            ctx.set_profiling(True)
+            ctx.kernel_time(reset=True)
+            for _ in range(10):
+                ctx.integrate(et, X, C, out=out, **kw)
+            kms, kn = ctx.kernel_time(reset=True)
+            ctx.set_profiling(False)
+            table.setdefault(name, {})[f"{problem} {elem}"] = kms / kn * 1e6 / n   # ns per element
+        del X, C, out
+    torch.cuda.empty_cache()
+    return {"workload": "ns per element (lower is better) of the QSS, SQS and SSQ orderings, mixed form: 1,000,000 "
+                        "tetrahedra and 500,000 prisms; Poisson with d^0 per point, convection-diffusion with "
+                        "per-element coefficients", "unit": "ns/element", "table": table}
 
 
 def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args):

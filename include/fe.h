@@ -145,6 +145,10 @@ typedef struct fe_elem_args {
     fe_memory memory;              /* where coords and coefs live */
     const int32_t *conn;           /* FE_LAYOUT_INDEXED: [n_elem][NS] node indices, device */
     int64_t n_nodes;               /* FE_LAYOUT_INDEXED: nodes in coords, < 2^31 */
+    int ordering;                  /* loop ordering (Sec. 3.3): 0 QSS (Algorithms 2, 3; the default),
+                                      1 SQS (Algorithms 4, 5), 2 SSQ (Algorithms 6, 7). SQS and SSQ are
+                                      for comparison: FE_FP32_MIXED, element-contiguous (AOS)
+                                      coordinates and full AOS outputs only */
 } fe_elem_args;
 
 /*

@@ -47,7 +47,7 @@ class ElemArgs(ctypes.Structure):
                 ("coords_stride", ctypes.c_int64), ("kind", ctypes.c_int), ("quad", ctypes.c_int),
                 ("coef_mode", ctypes.c_int), ("coefs", ctypes.c_void_p), ("coefs_layout", ctypes.c_int),
                 ("coefs_stride", ctypes.c_int64), ("prec", ctypes.c_int), ("memory", ctypes.c_int),
-                ("conn", ctypes.c_void_p), ("n_nodes", ctypes.c_int64)]
+                ("conn", ctypes.c_void_p), ("n_nodes", ctypes.c_int64), ("ordering", ctypes.c_int)]
 
 
 class Out(ctypes.Structure):
@@ -155,11 +155,15 @@ def n_coefs(kind, quad, coef_mode):
     return (1 if kind == POISSON else 20) * (NQ[quad] if coef_mode == PER_QPOINT else 1)
 
 
-def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn=None):
+QSS, SQS, SSQ = 0, 1, 2   # loop orderings (Sec. 3.3)
+
+
+def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn=None, ordering=QSS):
     """ElemArgs for torch tensors. SOA: coords (3*NS, E) and coefs (NC, E), unit
     stride along elements, any plane stride. AOS: coords (E, NS, 3), coefs (E, ...).
     INDEXED: coords = nodes (N, 3), conn (E, NS) int32, coefs (E, ...)."""
     a = ElemArgs()
+    a.ordering = ordering
     if layout == INDEXED:
         assert conn is not None and conn.dtype == torch.int32 and conn.is_contiguous()
         assert conn.dim() == 2 and conn.shape[1] == NS[elem_type]
@@ -318,11 +322,11 @@ class Context:
         return ctypes.c_void_p(0)
 
     def integrate(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-                  out_layout=SOA, out=None, with_flags=True, stream=None, conn=None, packed=False):
+                  out_layout=SOA, out=None, with_flags=True, stream=None, conn=None, packed=False, ordering=QSS):
         """Integrate one element set; returns (A, b, flags) tensors (allocated if
         ``out`` is None, on the device of ``coords``; pinned host memory for host inputs).
         With layout=INDEXED, coords is the node array and conn the element -> node table."""
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering)
         if out is None:
             on_host = not coords.is_cuda
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, with_flags, pin=on_host,
@@ -346,13 +350,14 @@ class Context:
                   flags.data_ptr() if flags is not None else None, self._stream(stream, True)), self.h)
 
     def tune(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-             out_layout=SOA, out=None, stream=None, conn=None, packed=False):
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
+             out_layout=SOA, out=None, stream=None, conn=None, packed=False, ordering=QSS):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
         o = make_out(*out, out_layout, packed)
         _check(load().fe_tune(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), self._stream(stream, True)), self.h)
-        return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out, conn, packed)
+        return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out, conn, packed,
+                          ordering)
 
     def set_shape(self, block, persistent, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT,
                   prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None, conn=None, packed=False):
@@ -363,8 +368,8 @@ class Context:
         _check(load().fe_set_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), block, persistent), self.h)
 
     def shape(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-              out_layout=SOA, out=None, conn=None, packed=False):
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
+              out_layout=SOA, out=None, conn=None, packed=False, ordering=QSS):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
         o = make_out(*out, out_layout, packed)

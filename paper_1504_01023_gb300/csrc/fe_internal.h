@@ -7,7 +7,10 @@ namespace fe {
 
 enum ElemType { TET = 0, PRISM = 1 };
 enum Kind { POISSON = 0, GENERIC = 1 };
-enum Prec { FP64 = 0, MIXED = 1, DWORD = 2 };
+enum Prec { FP64 = 0, MIXED = 1, DWORD = 2, MIXED_SQS = 3, MIXED_SSQ = 4 };
+// The mixed form with the loop orderings of Algorithms 4-7 (SQS, SSQ), for the
+// ordering study: float arithmetic, shape test and double-Jacobian fix-up as MIXED.
+constexpr bool float_form(int prec) { return prec == MIXED || prec == MIXED_SQS || prec == MIXED_SSQ; }
 enum Quad { Q_TET1 = 0, Q_TET4 = 1, Q_PRISM6 = 2 };
 enum Layout { SOA = 0, AOS = 1, INDEXED = 2, APPLY = 2 };  // APPLY: output mode of fe_apply_*
 // Output modes beyond the layouts: the upper triangle of a symmetric A^e.
@@ -72,6 +75,11 @@ const void *kernel_fixup_tet(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_fixup_prism(int kind, int cpq, int inl, int outl);
 const void *kernel_fixup_tet_dw(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_fixup_prism_dw(int kind, int cpq, int inl, int outl);
+
+// Ordering study (fe_study.cu): mixed form, element-contiguous in and out,
+// order 1 = SQS, 2 = SSQ.
+const void *kernel_study(int type, int kind, int quad, int cpq, int order);
+const void *kernel_fixup_study(int type, int kind, int quad, int cpq, int order);
 
 // INDEXED geometry (node table): the same tables, in their own translation units.
 const void *kernel_tet_fp64_idx(int kind, int quad, int cpq, int outl);

@@ -15,7 +15,7 @@ template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct ElemCfg {
     static constexpr int NA = NS * NS;
     static constexpr int NQ = Rule<QUAD>::NQ;
     static constexpr int NC = (KIND == POISSON ? 1 : 20) * (CPQ ? NQ : 1);
-    using CT = typename std::conditional<PREC == MIXED, float, double>::type;
+    using CT = typename std::conditional<float_form(PREC), float, double>::type;
 };
 
 __device__ __forceinline__ V3<float> to_f(V3<double> v) {

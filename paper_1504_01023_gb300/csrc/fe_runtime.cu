@@ -72,6 +72,7 @@ void free_scratch(Scratch &s) {
 
 static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
     const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
+    if (a->ordering) return kernel_study(type, a->kind, a->quad, cpq, a->ordering);
     const int il = a->coords_layout;
     if (type == FE_TET) {
         switch (a->prec) {
@@ -91,6 +92,7 @@ static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int out
 
 static const void *fix_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
     const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
+    if (a->ordering) return kernel_fixup_study(type, a->kind, a->quad, cpq, a->ordering);
     const int il = a->coords_layout;
     if (a->prec == FE_FP64_DW)
         return type == FE_TET ? kernel_fixup_tet_dw(a->kind, a->quad, cpq, il, outl)
@@ -146,7 +148,7 @@ static std::string shape_key(fe_elem_type type, const fe_elem_args *a, const fe_
     for (int64_t n = a->n_elem; n > 1; n >>= 2) ++bucket;  // size class: floor(log4 n)
     std::ostringstream k;
     k << "t" << type << "k" << a->kind << "p" << a->prec << "q" << a->quad << "c" << a->coef_mode << "i"
-      << a->coords_layout << "o" << out_mode(o) << "n" << bucket;
+      << a->coords_layout << "o" << out_mode(o) << "r" << a->ordering << "n" << bucket;
     return k.str();
 }
 
@@ -561,6 +563,11 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
         return set_error(nullptr, FE_ERR_INVALID_ARG, "bad layout");
     const bool indexed = a->coords_layout == FE_LAYOUT_INDEXED;
     if (o->packed != 0 && o->packed != 1) return set_error(nullptr, FE_ERR_INVALID_ARG, "packed must be 0 or 1");
+    if (a->ordering < 0 || a->ordering > 2) return set_error(nullptr, FE_ERR_INVALID_ARG, "ordering must be 0, 1 or 2");
+    if (a->ordering && (a->prec != FE_FP32_MIXED || a->coords_layout != FE_LAYOUT_AOS || o->layout != FE_LAYOUT_AOS ||
+                        o->packed))
+        return set_error(nullptr, FE_ERR_UNSUPPORTED,
+                         "the SQS and SSQ orderings take FE_FP32_MIXED with element-contiguous inputs and outputs");
     if (o->packed && a->kind != FE_POISSON)
         return set_error(nullptr, FE_ERR_UNSUPPORTED, "packed output needs a symmetric A^e (FE_POISSON)");
     if (o->packed && indexed)

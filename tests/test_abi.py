@@ -140,6 +140,23 @@ def test_packed_output_validation(lib):
     assert _chk(lib, api.TET, a, o) == -6
 
 
+def test_ordering_validation(lib):
+    """SQS / SSQ (study orderings): mixed form, element-contiguous in and out."""
+    a, o = _args()
+    a.coords_layout = a.coefs_layout = o.layout = api.AOS
+    for ordering in (api.QSS, api.SQS, api.SSQ):
+        a.ordering = ordering
+        assert _chk(lib, api.TET, a, o) == 0
+    a.ordering = 3
+    assert _chk(lib, api.TET, a, o) == -1
+    a.ordering = api.SQS
+    a.prec = api.FP64
+    assert _chk(lib, api.TET, a, o) == -6
+    a.prec = api.FP32_MIXED
+    o.layout = api.SOA
+    assert _chk(lib, api.TET, a, o) == -6
+
+
 def test_null_context_rejected(lib):
     a, o = _args()
     assert lib.fe_integrate_tet(None, ctypes.byref(a), ctypes.byref(o), None) == -1
