@@ -57,6 +57,8 @@ def load_library(path: str):
     lib.oracle_integrate.argtypes = [i32, i32, i32, i32, i32, i64, p, p, p, p, p, i32]
     lib.oracle_integrate.restype = i32
     lib.oracle_quality.argtypes = [i32, i64, p, p, i32]
+    lib.oracle_coefs_from_u.argtypes = [i32, i32, i32, i64, p, p, p]
+    lib.oracle_coefs_from_u.restype = i32
     lib.oracle_quality.restype = i32
     return lib
 
@@ -110,6 +112,22 @@ def integrate(elem_type: int, kind: int, rule: int, coords, coefs, coef_per_q: b
     if rc != 0:
         raise ValueError("oracle_integrate rejected its arguments")
     return A, b, flags
+
+
+def coefs_from_u(elem_type: int, kind: int, rule: int, u, P, lib=None):
+    """Per-point coefficients of the function c_j(u_Q) = P[0][j] + P[1][j] u_Q +
+    P[2][j] u_Q^2, u_Q interpolated from the nodal values u [E, NS] at the rule's
+    points. Returns generic [E, NQ, 20] or Poisson [E, NQ] (slot 16: d^0)."""
+    lib = lib or _load()
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64).reshape(3, 20)
+    n = u.shape[0]
+    assert u.shape == (n, NS[elem_type])
+    nq = lib.oracle_quad_size(rule, 0)
+    out = np.zeros((n, nq, 20) if kind == GENERIC else (n, nq))
+    if lib.oracle_coefs_from_u(elem_type, kind, rule, n, _ptr(u), _ptr(P), _ptr(out)) != 0:
+        raise ValueError("oracle_coefs_from_u rejected its arguments")
+    return out
 
 
 def quality(elem_type: int, coords, n_threads: int = 1):

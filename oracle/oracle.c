@@ -402,6 +402,46 @@ int oracle_integrate(int elem_type, int kind, int rule, int order, int coef_per_
 }
 
 /* ---------------------------------------------------------------------------
+ * Coefficients computed at the integration points by a problem-dependent
+ * function (Sec. 2.3, input list: "problem dependent parameters that are used
+ * for computing coefficients"; Sec. 3.1: the coefficients may come from a
+ * special, problem dependent function). The function here is the one the
+ * library offers: with u_Q = sum_k phi_k(xi_Q) u_k the value at point Q of a
+ * field given by its nodal values u_k, coefficient j (C[4][4] row-major then
+ * D[4]) is P[0][j] + P[1][j] u_Q + P[2][j] u_Q^2. Writes the per-point
+ * coefficients oracle_integrate takes: generic [n][NQ][20], Poisson [n][NQ]
+ * (its d^0, slot 16 of P).
+ * ------------------------------------------------------------------------- */
+int oracle_coefs_from_u(int elem_type, int kind, int rule, int64_t n_elem, const double *u, const double *P,
+                        double *coefs) {
+    if (elem_type != OR_TET && elem_type != OR_PRISM) return -1;
+    if (kind != OR_POISSON && kind != OR_GENERIC) return -1;
+    if (rule != OR_Q_TET1 && rule != OR_Q_TET4 && rule != OR_Q_PRISM6) return -1;
+    if ((elem_type == OR_TET) != (rule != OR_Q_PRISM6)) return -1;
+    const int nq = oracle_quad_size(rule, 0);
+    double pts[3 * 16], wts[16];
+    oracle_quad_rule(rule, 0, pts, wts);
+    const int NS = (elem_type == OR_TET) ? 4 : 6;
+    for (int64_t e = 0; e < n_elem; e++) {
+        for (int q = 0; q < nq; q++) {
+            double phi[6], dphi[6][3];
+            if (elem_type == OR_TET)
+                tet_shape(&pts[3 * q], phi, dphi);
+            else
+                prism_shape(&pts[3 * q], phi, dphi);
+            double uq = 0.0;
+            for (int k = 0; k < NS; k++) uq = uq + phi[k] * u[e * NS + k];
+            if (kind == OR_POISSON) {
+                coefs[e * nq + q] = P[16] + P[20 + 16] * uq + P[40 + 16] * uq * uq;
+            } else {
+                for (int j = 0; j < 20; j++) coefs[(e * nq + q) * 20 + j] = P[j] + P[20 + j] * uq + P[40 + j] * uq * uq;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
  * Mean-ratio shape quality in single precision (not in the paper).
  * q = 3 |det T|^{2/3} / ||T||_F^2 with T = J S^{-1}, where S maps the reference
  * element onto its ideal: the unit-edge equilateral tetrahedron, or the prism of

@@ -425,3 +425,62 @@ def test_quality_ideal_elements_and_invariance():
     # the unjittered Kuhn tetrahedron
     k = meshgen.tet_cube_mesh(1, jitter=0.0)[:1]
     assert abs(oracle.quality(TET, k)[0] - _liu_joe(k)[0]) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Coefficients from a function of a nodal field (c_j(u_Q) = P0_j + P1_j u_Q + P2_j u_Q^2)
+# ---------------------------------------------------------------------------
+def test_coef_function_constant_field_is_per_element():
+    """u constant over the element: every point sees the same coefficients
+    P(u), so the element matrices equal those with per-element coefficients."""
+    from paper_1504_01023_gb300 import meshgen
+    rng = np.random.default_rng(71)
+    P = rng.uniform(-1, 1, (3, 20))
+    for et, rule, mesh in ((oracle.TET, oracle.Q_TET4, meshgen.tet_cube_mesh(3, seed=5)[:40]),
+                           (oracle.PRISM, oracle.Q_PRISM6, meshgen.prism_slab_mesh(5, seed=6)[:40])):
+        n, ns = len(mesh), mesh.shape[1]
+        uv = rng.uniform(-2, 2, n)
+        u = np.repeat(uv[:, None], ns, axis=1)
+        cq = oracle.coefs_from_u(et, oracle.GENERIC, rule, u, P)
+        ce = P[0][None, :] + P[1][None, :] * uv[:, None] + P[2][None, :] * uv[:, None] ** 2
+        Aq, bq, _ = oracle.integrate(et, oracle.GENERIC, rule, mesh, cq, coef_per_q=True)
+        Ae, be, _ = oracle.integrate(et, oracle.GENERIC, rule, mesh, ce)
+        assert np.abs(Aq - Ae).max() <= 1e-12 * np.abs(Ae).max()
+        assert np.abs(bq - be).max() <= 1e-12 * np.abs(be).max()
+
+
+def test_coef_function_linear_field_load_tet():
+    """d^0 = u_Q (P1_16 = 1, all else 0): b_r = int u phi_r = |T|/20 (sum u + u_r)
+    for a linear field on a tetrahedron (TET4 is exact for this quadratic)."""
+    from paper_1504_01023_gb300 import meshgen
+    mesh = meshgen.tet_cube_mesh(3, seed=7)[:50]
+    rng = np.random.default_rng(72)
+    u = rng.uniform(-1, 1, (50, 4))
+    P = np.zeros((3, 20))
+    P[1, 16] = 1.0
+    cq = oracle.coefs_from_u(oracle.TET, oracle.GENERIC, oracle.Q_TET4, u, P)
+    A, b, _ = oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh, cq, coef_per_q=True)
+    e = mesh[:, 1:] - mesh[:, :1]
+    vol = np.abs(np.einsum("ei,ei->e", e[:, 0], np.cross(e[:, 1], e[:, 2]))) / 6.0
+    ref = vol[:, None] / 20.0 * (u.sum(1, keepdims=True) + u)
+    assert np.abs(A).max() == 0.0
+    assert np.abs(b - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_coef_function_field_through_thickness_prism():
+    """A right prism (triangle of area 1/2, height 0.3) with u = 0 on the bottom
+    nodes and 1 on the top ones, d^0 = u_Q: b = |T_a| h / 18 at the bottom nodes
+    and |T_a| h / 9 at the top ones (PRISM6 is exact here)."""
+    tri = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    h = 0.3
+    mesh = np.zeros((1, 6, 3))
+    mesh[0, :3, :2] = tri
+    mesh[0, 3:, :2] = tri
+    mesh[0, 3:, 2] = h
+    u = np.array([[0.0, 0.0, 0.0, 1.0, 1.0, 1.0]])
+    P = np.zeros((3, 20))
+    P[1, 16] = 1.0
+    cq = oracle.coefs_from_u(oracle.PRISM, oracle.POISSON, oracle.Q_PRISM6, u, P)
+    A, b, _ = oracle.integrate(oracle.PRISM, oracle.POISSON, oracle.Q_PRISM6, mesh, cq, coef_per_q=True)
+    ref = np.array([h * 0.5 / 18] * 3 + [h * 0.5 / 9] * 3)
+    assert np.abs(b[0] - ref).max() <= 1e-15
