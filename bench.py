@@ -369,6 +369,7 @@ def run_native(args):
     if rank == 0 and world == 1 and args.workload == "tet":
         if not args.no_prism:
             result["prism_form"] = prism_form(ctx, dev, api, args)
+            result["coef_function_form"] = coef_function_form(ctx, dev, api, args)
         if not args.no_fp64:
             result["fp64_form"], result["double_word_form"] = fp64_form(ctx, dev, api, mesh, coefs, args)
             result["packed_form"] = packed_form(ctx, dev, api, mesh, args)
@@ -618,6 +619,47 @@ def ordering_study(ctx, dev, api, mesh, coefs, args):
     return {"workload": "ns per element (lower is better) of the QSS, SQS and SSQ orderings, mixed form: 1,000,000 "
                         "tetrahedra and 500,000 prisms; Poisson with d^0 per point, convection-diffusion with "
                         "per-element coefficients", "unit": "ns/element", "table": table}
+
+
+def coef_function_form(ctx, dev, api, args):
+    """The 2M generic prisms with the coefficients at every point computed from a
+    function of a nodal field (c_j(u_Q) = P0_j + P1_j u_Q + P2_j u_Q^2) instead of
+    read as 120 per-point values: 24 instead of 480 coefficient bytes per element.
+    Mixed form, element-contiguous order, tuned shape."""
+    import torch
+    mesh, _ = prism_workload(0, args.n_slab)
+    n = len(mesh)
+    x, y, z = mesh[..., 0], mesh[..., 1], mesh[..., 2]
+    u = (np.sin(3.0 * x) + y * y - 0.5 * z).astype(np.float32)
+    P = np.random.default_rng(SEED).uniform(-1.0, 1.0, (3, 20))
+    for i in (5, 10, 15):
+        P[0, i] += 4.0
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)
+    U = torch.from_numpy(np.ascontiguousarray(u)).to(dev)
+    del mesh
+    out = api.alloc_out(api.PRISM, n, api.FP32_MIXED, api.AOS, dev, with_flags=True)
+    kw = dict(kind=api.GENERIC, quad=api.QUAD_PRISM6, coef_mode=api.COEF_FN_U, prec=api.FP32_MIXED, layout=api.AOS,
+              out_layout=api.AOS, coef_fn=P)
+    shape = ctx.tune(api.PRISM, X, U, out=out, **kw)
+    for _ in range(3):
+        ctx.integrate(api.PRISM, X, U, out=out, **kw)
+    torch.cuda.synchronize(dev)
+    ctx.set_profiling(True)
+    ctx.kernel_time(reset=True)
+    for _ in range(max(20, min(200, args.steps // 10))):
+        ctx.integrate(api.PRISM, X, U, out=out, **kw)
+    kms, kn = ctx.kernel_time(reset=True)
+    ctx.set_profiling(False)
+    k_ms = kms / kn
+    bpe = api.bytes_per_element(api.PRISM, api.GENERIC, api.QUAD_PRISM6, api.COEF_FN_U, api.FP32_MIXED)
+    peak, _ = measured_peaks()
+    gbs = n * bpe / (k_ms * 1e-3) / 1e9
+    del X, U, out
+    torch.cuda.empty_cache()
+    return {"workload": "2,000,000 generic prisms, PRISM6, coefficients at every point from c(u) of a nodal field "
+                        "(quadratic in u), mixed form, element-contiguous order", "value": n / k_ms / 1e3,
+            "unit": "Melem/s", "kernel_ms": k_ms, "bytes_per_element": bpe, "achieved_gbs": gbs,
+            "hbm_frac": gbs / peak, "launch_shape": {"block": shape[0], "persistent": shape[1]}}
 
 
 def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args):

@@ -87,7 +87,19 @@ typedef enum fe_quad { FE_QUAD_TET1 = 0, FE_QUAD_TET4 = 1, FE_QUAD_PRISM6 = 2 } 
 
 /* Sec. 3.3 takes coefficients constant per element; per integration point is the
    input mode of the prism workload with varying coefficients. */
-typedef enum fe_coef_mode { FE_COEF_PER_ELEMENT = 0, FE_COEF_PER_QPOINT = 1 } fe_coef_mode;
+/* FE_COEF_FUNCTION_U: the coefficients at each integration point come from a
+   problem-dependent function (Sec. 2.3 input list; Sec. 3.1) of a field u given by
+   its nodal values: coefs holds u_k, NS per element (element-contiguous, in the
+   coefficient precision), u_Q = sum_k phi_k(xi_Q) u_k, and coefficient j (0..15
+   C[4][4] row-major, 16..19 D[4]) at Q is P[0][j] + P[1][j] u_Q + P[2][j] u_Q^2
+   with P = *coef_fn. The Laplace kind uses slot 16 (d^0) only. For nonlinear
+   problems (c(u)) re-integrated at each iterate without materialising the
+   coefficients. */
+typedef enum fe_coef_mode { FE_COEF_PER_ELEMENT = 0, FE_COEF_PER_QPOINT = 1, FE_COEF_FUNCTION_U = 2 } fe_coef_mode;
+
+typedef struct fe_coef_function {
+    double p[3][20];
+} fe_coef_function;
 
 /* Sec. 4.2 (Figs. 1, 2): SOA = one plane per scalar, elements contiguous inside a
    plane ("coalesced" order); AOS = the "natural" order, all scalars of one
@@ -149,6 +161,9 @@ typedef struct fe_elem_args {
                                       1 SQS (Algorithms 4, 5), 2 SSQ (Algorithms 6, 7). SQS and SSQ are
                                       for comparison: FE_FP32_MIXED, element-contiguous (AOS)
                                       coordinates and full AOS outputs only */
+    const fe_coef_function *coef_fn; /* FE_COEF_FUNCTION_U: host, read during the call;
+                                        element-contiguous (AOS) coordinates, full outputs,
+                                        ordering 0; not for batches, serving, noalloc */
 } fe_elem_args;
 
 /*

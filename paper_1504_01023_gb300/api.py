@@ -11,6 +11,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -21,7 +22,7 @@ TET, PRISM = 0, 1
 POISSON, GENERIC = 0, 1
 FP64, FP32_MIXED, FP64_DW = 0, 1, 2
 QUAD_TET1, QUAD_TET4, QUAD_PRISM6 = 0, 1, 2
-PER_ELEMENT, PER_QPOINT = 0, 1
+PER_ELEMENT, PER_QPOINT, COEF_FN_U = 0, 1, 2
 SOA, AOS, INDEXED = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 NS = {TET: 4, PRISM: 6}
@@ -47,7 +48,13 @@ class ElemArgs(ctypes.Structure):
                 ("coords_stride", ctypes.c_int64), ("kind", ctypes.c_int), ("quad", ctypes.c_int),
                 ("coef_mode", ctypes.c_int), ("coefs", ctypes.c_void_p), ("coefs_layout", ctypes.c_int),
                 ("coefs_stride", ctypes.c_int64), ("prec", ctypes.c_int), ("memory", ctypes.c_int),
-                ("conn", ctypes.c_void_p), ("n_nodes", ctypes.c_int64), ("ordering", ctypes.c_int)]
+                ("conn", ctypes.c_void_p), ("n_nodes", ctypes.c_int64), ("ordering", ctypes.c_int),
+                ("coef_fn", ctypes.c_void_p)]
+
+
+class CoefFunction(ctypes.Structure):
+    """c_j(u_Q) = p[0][j] + p[1][j] u_Q + p[2][j] u_Q^2 (FE_COEF_FUNCTION_U)."""
+    _fields_ = [("p", (ctypes.c_double * 20) * 3)]
 
 
 class Out(ctypes.Structure):
@@ -158,12 +165,21 @@ def n_coefs(kind, quad, coef_mode):
 QSS, SQS, SSQ = 0, 1, 2   # loop orderings (Sec. 3.3)
 
 
-def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn=None, ordering=QSS):
+def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn=None, ordering=QSS, coef_fn=None):
     """ElemArgs for torch tensors. SOA: coords (3*NS, E) and coefs (NC, E), unit
     stride along elements, any plane stride. AOS: coords (E, NS, 3), coefs (E, ...).
     INDEXED: coords = nodes (N, 3), conn (E, NS) int32, coefs (E, ...)."""
     a = ElemArgs()
     a.ordering = ordering
+    if coef_mode == COEF_FN_U:
+        assert coef_fn is not None, "COEF_FN_U needs the parameter array coef_fn [3, 20]"
+        P = np.ascontiguousarray(np.asarray(coef_fn, dtype=np.float64).reshape(3, 20))
+        fn = CoefFunction()
+        for i in range(3):
+            for j in range(20):
+                fn.p[i][j] = float(P[i, j])
+        a._fn = fn                       # kept alive with the arguments
+        a.coef_fn = ctypes.addressof(fn)
     if layout == INDEXED:
         assert conn is not None and conn.dtype == torch.int32 and conn.is_contiguous()
         assert conn.dim() == 2 and conn.shape[1] == NS[elem_type]
@@ -322,11 +338,12 @@ class Context:
         return ctypes.c_void_p(0)
 
     def integrate(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-                  out_layout=SOA, out=None, with_flags=True, stream=None, conn=None, packed=False, ordering=QSS):
+                  out_layout=SOA, out=None, with_flags=True, stream=None, conn=None, packed=False, ordering=QSS,
+                  coef_fn=None):
         """Integrate one element set; returns (A, b, flags) tensors (allocated if
         ``out`` is None, on the device of ``coords``; pinned host memory for host inputs).
         With layout=INDEXED, coords is the node array and conn the element -> node table."""
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering)
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering, coef_fn)
         if out is None:
             on_host = not coords.is_cuda
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, with_flags, pin=on_host,
@@ -350,14 +367,14 @@ class Context:
                   flags.data_ptr() if flags is not None else None, self._stream(stream, True)), self.h)
 
     def tune(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-             out_layout=SOA, out=None, stream=None, conn=None, packed=False, ordering=QSS):
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering)
+             out_layout=SOA, out=None, stream=None, conn=None, packed=False, ordering=QSS, coef_fn=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering, coef_fn)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
         o = make_out(*out, out_layout, packed)
         _check(load().fe_tune(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), self._stream(stream, True)), self.h)
         return self.shape(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, out_layout, out, conn, packed,
-                          ordering)
+                          ordering, coef_fn)
 
     def set_shape(self, block, persistent, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT,
                   prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None, conn=None, packed=False):
@@ -368,8 +385,8 @@ class Context:
         _check(load().fe_set_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), block, persistent), self.h)
 
     def shape(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
-              out_layout=SOA, out=None, conn=None, packed=False, ordering=QSS):
-        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering)
+              out_layout=SOA, out=None, conn=None, packed=False, ordering=QSS, coef_fn=None):
+        args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn, ordering, coef_fn)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
         o = make_out(*out, out_layout, packed)

@@ -441,9 +441,10 @@ fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         fe_status st = fe_check_args(it.type, &it.args, &it.out);
         if (st != FE_OK) return set_error(ctx, st, "batch item " + std::to_string(i) + ": " + fe_last_error(nullptr));
         if (it.args.prec != FE_FP32_MIXED || it.args.memory != FE_MEM_DEVICE || it.out.memory != FE_MEM_DEVICE ||
-            it.args.coords_layout != FE_LAYOUT_AOS || it.out.layout != FE_LAYOUT_AOS || it.out.packed)
+            it.args.coords_layout != FE_LAYOUT_AOS || it.out.layout != FE_LAYOUT_AOS || it.out.packed ||
+            it.args.coef_mode == FE_COEF_FUNCTION_U || it.args.ordering)
             return set_error(ctx, FE_ERR_UNSUPPORTED,
-                             "batch items must be FE_FP32_MIXED, device memory, element-contiguous (AOS) in and out, not packed");
+                             "batch items must be FE_FP32_MIXED, device memory, element-contiguous (AOS) in and out, not packed, coefficient arrays, ordering 0");
         if (it.args.n_elem >= (int64_t(1) << 40)) return set_error(ctx, FE_ERR_INVALID_ARG, "batch item too large");
     }
     cudaSetDevice(ctx->device);

@@ -48,3 +48,7 @@
     M(__VA_ARGS__, 0, 0, 0, 3) M(__VA_ARGS__, 0, 0, 0, 4) M(__VA_ARGS__, 0, 0, 1, 3)  \
     M(__VA_ARGS__, 0, 0, 1, 4) M(__VA_ARGS__, 0, 1, 0, 3) M(__VA_ARGS__, 0, 1, 0, 4)  \
     M(__VA_ARGS__, 0, 1, 1, 3) M(__VA_ARGS__, 0, 1, 1, 4)
+
+// The coefficient function of a nodal field (CPQ == 2): element-contiguous input,
+// full output in either layout, one kind.
+#define FE_FN2(M, KD, ...) M(__VA_ARGS__, KD, 2, 1, 0) M(__VA_ARGS__, KD, 2, 1, 1)

@@ -49,6 +49,14 @@ struct ElemParams {
     const void *xv;                // APPLY: nodal input vector; A is y, B is f (may be null)
 };
 
+// Parameters of the coefficient function (FE_COEF_FUNCTION_U), passed by value
+// as a kernel parameter: c_j(u) = p[0][j] + p[1][j] u + p[2][j] u^2, in double and
+// in float (the mixed form reads the float copy).
+struct CoefFn {
+    double pd[3][20];
+    float pf[3][20];
+};
+
 // Tensor-copy descriptors (CUtensorMap, 128 bytes each) of the plane-major
 // inputs and outputs of one launch: coordinates, coefficients, A, b.
 struct alignas(64) TmaMaps {

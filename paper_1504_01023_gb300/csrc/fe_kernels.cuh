@@ -14,7 +14,9 @@ template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct ElemCfg {
     static constexpr int NX = 3 * NS;
     static constexpr int NA = NS * NS;
     static constexpr int NQ = Rule<QUAD>::NQ;
-    static constexpr int NC = (KIND == POISSON ? 1 : 20) * (CPQ ? NQ : 1);
+    // coefficients per element; CPQ == 2: the nodal values of the field u of the
+    // coefficient function
+    static constexpr int NC = CPQ == 2 ? NS : (KIND == POISSON ? 1 : 20) * (CPQ ? NQ : 1);
     using CT = typename std::conditional<float_form(PREC), float, double>::type;
 };
 
@@ -534,6 +536,35 @@ template <class T> struct RegSrc {
     __device__ __forceinline__ T operator()(int j) const { return v[j]; }
 };
 
+// Coefficients from the function of a nodal field (CPQ == 2): u at every point
+// of the rule (u_Q = sum_k phi_k(Q) u_k), then coefficient j of point q as the
+// per-point layout indexes it (generic j = 20 q + k, Laplace j = q with d^0 in
+// slot 16): p0 + u_Q (p1 + u_Q p2).
+template <class CT, int ET, int KIND, int QUAD> struct FnSrc {
+    static constexpr int NS = ET == TET ? 4 : 6;
+    static constexpr int NQ = Rule<QUAD>::NQ;
+    CT uq[NQ];
+    const CoefFn *fn;
+    template <class US> __device__ __forceinline__ FnSrc(const US &u, const CoefFn *f) : fn(f) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            CT s = CT(0);
+#pragma unroll
+            for (int k = 0; k < NS; ++k) s += CT(Rule<QUAD>::phi(q, k)) * u(k);
+            uq[q] = s;
+        }
+    }
+    __device__ __forceinline__ CT operator()(int j) const {
+        const int q = KIND == POISSON ? j : j / 20;
+        const int k = KIND == POISSON ? 16 : j - 20 * q;
+        const CT u = uq[q];
+        if constexpr (sizeof(CT) == 4)
+            return fn->pf[0][k] + u * (fn->pf[1][k] + u * fn->pf[2][k]);
+        else
+            return fn->pd[0][k] + u * (fn->pd[1][k] + u * fn->pd[2][k]);
+    }
+};
+
 // Coordinates of an element of an INDEXED set: vertex v is node idx[v] of the
 // node array X ([n_nodes][3]). An index outside [0, n_nodes) is not followed
 // (node 0 is read instead) and the result is false.
@@ -632,9 +663,51 @@ __device__ __forceinline__ void stage_rows_out(T *g, int64_t gpitch, const T *s,
 // back by bulk copies from shared memory. Returns false (for the whole block) if
 // a bounded wait on a copy ran out; the caller must then stop.
 // ---------------------------------------------------------------------------
+// One element through ElemMath, the coefficients read as given or, for the
+// coefficient function (CPQ == 2), evaluated from the nodal field.
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, class XS, class CS, class CT>
+__device__ __forceinline__ uint8_t run_elem(const XS &x, const CS &c, const CoefFn *fn, CT *A, CT *b, bool &poor) {
+    if constexpr (CPQ == 2) {
+        const FnSrc<CT, ET, KIND, QUAD> cf(c, fn);
+        return ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(x, cf, A, b, poor);
+    } else {
+        return ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(x, c, A, b, poor);
+    }
+}
+// Float values of a double accessor (the fix-up's coefficient function).
+template <class S> struct NarrowSrc {
+    const S &s;
+    __device__ __forceinline__ float operator()(int j) const { return static_cast<float>(s(j)); }
+};
+// Double values of a float accessor (the nodal field of the mixed form).
+template <class S> struct WidenSrc {
+    const S &s;
+    __device__ __forceinline__ double operator()(int j) const { return static_cast<double>(s(j)); }
+};
+
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, class XS, class CS, class CT>
+__device__ __forceinline__ uint8_t fix_elem(const XS &x, const CS &c, const CoefFn *fn, CT *A, CT *b) {
+    if constexpr (CPQ == 2) {
+        // a flagged element evaluates the coefficient function in double (u_Q and
+        // c(u_Q)), so that coefficients near a root of their polynomial keep their
+        // relative accuracy where poorly shaped elements amplify it
+        const WidenSrc<CS> cw{c};
+        const FnSrc<double, ET, KIND, QUAD> cfd(cw, fn);
+        if constexpr (sizeof(CT) == 4) {
+            const NarrowSrc<FnSrc<double, ET, KIND, QUAD>> cf{cfd};
+            return ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(x, cf, A, b);
+        } else {
+            return ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(x, cfd, A, b);
+        }
+    } else {
+        return ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(x, c, A, b);
+    }
+}
+
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
 __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, int nb, unsigned char *smem, uint64_t *bar,
-                                             unsigned &phase, const TmaMaps *tm = nullptr) {
+                                             unsigned &phase, const TmaMaps *tm = nullptr,
+                                             const CoefFn *fn = nullptr) {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
     using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>;
@@ -715,7 +788,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         if constexpr (INL == INDEXED) {
             double xr[NX];
             idx_ok = gather_nodes<NS>(X, p.n_nodes, sN + tid * NS, xr);
-            fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(RegSrc<double>{xr}, cs, A, b, poor);
+            fl = run_elem<ET, KIND, PREC, QUAD, CPQ>(RegSrc<double>{xr}, cs, fn, A, b, poor);
             if (!idx_ok) {
 #pragma unroll
                 for (int k = 0; k < NA; ++k) A[k] = CT(0);
@@ -726,7 +799,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
             }
         } else {
             const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
-            fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b, poor);
+            fl = run_elem<ET, KIND, PREC, QUAD, CPQ>(xs, cs, fn, A, b, poor);
         }
         if (PREC != FP64 && poor) fl |= 1;
         if (p.flags) p.flags[e] = fl;
@@ -797,7 +870,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
 __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
-    elem_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm) {
+    elem_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) {
@@ -811,7 +884,7 @@ __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
-        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase, &tm)) return;
+        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase, &tm, &fn)) return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
@@ -894,7 +967,7 @@ template <class T, int N> __device__ __forceinline__ void st_record(T *dst, cons
 
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int OUTL>
 __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
-    gather_kernel(const ElemParams p, const __grid_constant__ TmaMaps) {
+    gather_kernel(const ElemParams p, const __grid_constant__ TmaMaps, const __grid_constant__ CoefFn) {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
@@ -959,7 +1032,7 @@ __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
 // kernel's.
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
-__device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
+__device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e, const CoefFn *fn = nullptr) {
     using CF = ElemCfg<ET, KIND, PREC, QUAD, CPQ>;
     using CT = typename CF::CT;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
@@ -971,16 +1044,16 @@ __device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
     if (INL == SOA) {
         const Src<SOA, double> xs{p.X + e, p.xs};
         const Src<SOA, CT> cs{C + e, p.cs};
-        fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(xs, cs, A, b);
+        fl = fix_elem<ET, KIND, PREC, QUAD, CPQ>(xs, cs, fn, A, b);
     } else if (INL == INDEXED) {
         double xr[NX];
         gather_nodes<NS>(p.X, p.n_nodes, p.conn + e * NS, xr);  // flagged elements have valid indices
         const Src<AOS, CT> cs{C + e * NC, 0};
-        fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(RegSrc<double>{xr}, cs, A, b);
+        fl = fix_elem<ET, KIND, PREC, QUAD, CPQ>(RegSrc<double>{xr}, cs, fn, A, b);
     } else {
         const Src<AOS, double> xs{p.X + e * NX, 0};
         const Src<AOS, CT> cs{C + e * NC, 0};
-        fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::fixup(xs, cs, A, b);
+        fl = fix_elem<ET, KIND, PREC, QUAD, CPQ>(xs, cs, fn, A, b);
     }
     if constexpr (OUTL == APPLY) {
         if (INL == INDEXED) scatter_apply<CT, NS>(p, p.conn + e * NS, A, b);
@@ -1009,7 +1082,7 @@ __device__ __forceinline__ void fixup_element(const ElemParams &p, int64_t e) {
 
 // Fix-up kernel of one call: grid-stride over the list written by the main kernel.
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
-__global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p) {
+__global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p, const __grid_constant__ CoefFn fn) {
     const unsigned cnt = *p.fix_count;
     const unsigned n = cnt < p.fix_cap ? cnt : p.fix_cap;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1018,7 +1091,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ElemParams p) {
             atomicOr(p.status, ST_BAD_TILE);
             continue;
         }
-        fixup_element<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e);
+        fixup_element<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e, &fn);
     }
 }
 

@@ -70,8 +70,8 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
         return set_error(nullptr, FE_ERR_INVALID_ARG, "fe_integrate_tet_noalloc takes FE_FP32_MIXED only");
     if (args->memory != FE_MEM_DEVICE || out->memory != FE_MEM_DEVICE)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "fe_integrate_tet_noalloc takes device buffers only");
-    if (args->coords_layout == FE_LAYOUT_INDEXED || out->packed)
-        return set_error(nullptr, FE_ERR_UNSUPPORTED, "fe_integrate_tet_noalloc takes no node table and no packed output");
+    if (args->coords_layout == FE_LAYOUT_INDEXED || out->packed || args->coef_mode == FE_COEF_FUNCTION_U)
+        return set_error(nullptr, FE_ERR_UNSUPPORTED, "fe_integrate_tet_noalloc takes no node table, packed output or coefficient function");
     if (uint64_t(args->n_elem) > kListCap)
         return set_error(nullptr, FE_ERR_INVALID_ARG,
                          "n_elem exceeds the " + std::to_string(kListCap) +
@@ -92,7 +92,7 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
 
     // 128 elements per block; shared memory = the tile's input and output records
     const int B = 128;
-    const int nc = nc_of(args);
+    const int nc = nc_of(FE_TET, args);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
     const int64_t smem_in = int64_t(B) * 12 * 8 + r16(int64_t(B) * nc * 4), smem_out = r16(int64_t(B) * 16 * 4) + r16(int64_t(B) * 4 * 4);
     const int64_t smem = smem_in > smem_out ? smem_in : smem_out;
@@ -129,13 +129,15 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
     p.status = status;
     TmaMaps no_maps;                                  // plane copies stay per-plane bulk copies here
     memset(&no_maps, 0, sizeof no_maps);
-    void *kargs[] = {&p, &no_maps};
+    CoefFn no_fn;                                     // coefficient arrays only here
+    memset(&no_fn, 0, sizeof no_fn);
+    void *kargs[] = {&p, &no_maps, &no_fn};
     const int64_t grid = (args->n_elem + B - 1) / B;
     ce = cudaLaunchKernel(k, dim3(unsigned(grid)), dim3(B), kargs, size_t(smem), strm);
     if (ce != cudaSuccess) return cuda_check(nullptr, ce, "cudaLaunchKernel(elem, no-alloc)");
     g_launches.fetch_add(1, std::memory_order_relaxed);
     int64_t fgrid = std::min<int64_t>((args->n_elem + 255) / 256, int64_t(s->sms) * 4);
-    void *fargs[] = {&p};
+    void *fargs[] = {&p, &no_fn};
     ce = cudaLaunchKernel(fk, dim3(unsigned(fgrid < 1 ? 1 : fgrid)), dim3(256), fargs, 0, strm);
     if (ce != cudaSuccess) return cuda_check(nullptr, ce, "cudaLaunchKernel(fixup, no-alloc)");
     g_launches.fetch_add(1, std::memory_order_relaxed);

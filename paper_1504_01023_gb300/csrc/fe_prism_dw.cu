@@ -8,12 +8,12 @@ const void *kernel_fixup_prism_dw_generic(int kind, int cpq, int inl, int outl);
 
 const void *kernel_prism_dw(int kind, int cpq, int inl, int outl) {
     if (inl == INDEXED) return kernel_prism_dw_idx(kind, cpq, outl);
-    FE_ALL8(FE_ELEM_CASE, 0, PRISM, DWORD, Q_PRISM6) FE_PK8(FE_ELEM_CASE, PRISM, DWORD, Q_PRISM6)
+    FE_ALL8(FE_ELEM_CASE, 0, PRISM, DWORD, Q_PRISM6) FE_PK8(FE_ELEM_CASE, PRISM, DWORD, Q_PRISM6) FE_FN2(FE_ELEM_CASE, 0, PRISM, DWORD, Q_PRISM6)
     return kernel_prism_dw_generic(kind, cpq, inl, outl);
 }
 const void *kernel_fixup_prism_dw(int kind, int cpq, int inl, int outl) {
     if (inl == INDEXED) return kernel_fixup_prism_dw_idx(kind, cpq, outl);
-    FE_ALL8(FE_FIX_CASE, 0, PRISM, DWORD, Q_PRISM6) FE_PK8(FE_FIX_CASE, PRISM, DWORD, Q_PRISM6)
+    FE_ALL8(FE_FIX_CASE, 0, PRISM, DWORD, Q_PRISM6) FE_PK8(FE_FIX_CASE, PRISM, DWORD, Q_PRISM6) FE_FN2(FE_FIX_CASE, 0, PRISM, DWORD, Q_PRISM6)
     return kernel_fixup_prism_dw_generic(kind, cpq, inl, outl);
 }
 }  // namespace fe

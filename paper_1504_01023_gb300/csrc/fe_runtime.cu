@@ -36,7 +36,8 @@ fe_status cuda_check(fe_ctx *ctx, cudaError_t e, const char *what) {
 
 int ns_of(fe_elem_type t) { return t == FE_TET ? 4 : 6; }
 int nq_of(fe_quad q) { return q == FE_QUAD_TET1 ? 1 : (q == FE_QUAD_TET4 ? 4 : 6); }
-int nc_of(const fe_elem_args *a) {
+int nc_of(fe_elem_type type, const fe_elem_args *a) {
+    if (a->coef_mode == FE_COEF_FUNCTION_U) return ns_of(type);  // nodal values of the field
     return (a->kind == FE_POISSON ? 1 : 20) * (a->coef_mode == FE_COEF_PER_QPOINT ? nq_of(a->quad) : 1);
 }
 static int csize(fe_precision p) { return p == FE_FP32_MIXED ? 4 : 8; }
@@ -70,8 +71,12 @@ void free_scratch(Scratch &s) {
     s = Scratch{};
 }
 
+// Kernel template value of the coefficient mode: 0 per element, 1 per point,
+// 2 the function of a nodal field.
+static int cpq_of(const fe_elem_args *a) { return a->coef_mode == FE_COEF_FUNCTION_U ? 2 : a->coef_mode == FE_COEF_PER_QPOINT; }
+
 static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
-    const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
+    const int cpq = cpq_of(a);
     if (a->ordering) return kernel_study(type, a->kind, a->quad, cpq, a->ordering);
     const int il = a->coords_layout;
     if (type == FE_TET) {
@@ -91,7 +96,7 @@ static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int out
 }
 
 static const void *fix_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
-    const int cpq = a->coef_mode == FE_COEF_PER_QPOINT;
+    const int cpq = cpq_of(a);
     if (a->ordering) return kernel_fixup_study(type, a->kind, a->quad, cpq, a->ordering);
     const int il = a->coords_layout;
     if (a->prec == FE_FP64_DW)
@@ -119,7 +124,7 @@ static int na_out(fe_elem_type type, int outl) {
 static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, int B) {
     // tetrahedra with a node table read straight from global memory (gather_kernel)
     if (a->coords_layout == FE_LAYOUT_INDEXED && type == FE_TET) return 0;
-    const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
+    const int ns = ns_of(type), nc = nc_of(type, a), cs = csize(a->prec);
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
     const int64_t geo = a->coords_layout == FE_LAYOUT_INDEXED ? r16(int64_t(B) * ns * 4) : int64_t(B) * 3 * ns * 8;
     const int64_t in = geo + r16(int64_t(B) * nc * cs),
@@ -274,7 +279,7 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     TmaMaps tm;
     memset(&tm, 0, sizeof tm);
     if (sh.block <= 256) {
-        const int ns = ns_of(type), nc = nc_of(a);
+        const int ns = ns_of(type), nc = nc_of(type, a);
         const bool dbl = a->prec != FE_FP32_MIXED;
         const uint64_t cs = dbl ? 8 : 4;
         if (a->coords_layout == FE_LAYOUT_SOA)
@@ -286,7 +291,15 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
                         encode_planes(tm.b, dbl, o->b, uint64_t(a->n_elem), ns, uint64_t(p.os) * cs, sh.block);
     }
 
-    void *args[] = {&p, &tm};
+    CoefFn fn;
+    memset(&fn, 0, sizeof fn);
+    if (a->coef_mode == FE_COEF_FUNCTION_U)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 20; ++j) {
+                fn.pd[i][j] = a->coef_fn->p[i][j];
+                fn.pf[i][j] = float(a->coef_fn->p[i][j]);
+            }
+    void *args[] = {&p, &tm, &fn};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool profile = ctx->profiling && !force;
     if (profile) {
@@ -312,7 +325,7 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     if (fixup) {
         const void *fk = fix_kernel(type, a, outl);
         const int64_t fgrid = std::min<int64_t>((a->n_elem + 255) / 256, int64_t(ctx->sms) * 4);
-        void *fargs[] = {&p};
+        void *fargs[] = {&p, &fn};
         ce = cudaLaunchKernel(fk, dim3(unsigned(std::max<int64_t>(fgrid, 1))), dim3(256), fargs, 0, st);
         if (ce != cudaSuccess) return cuda_check(ctx, ce, "cudaLaunchKernel(fixup)");
         g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -335,7 +348,7 @@ static fe_status ensure_stage(fe_ctx *ctx, int slot, int idx, uint64_t bytes) {
 
 static fe_status host_pipeline(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, cudaStream_t user) {
     const int64_t n = a->n_elem;
-    const int ns = ns_of(type), nc = nc_of(a), cs = csize(a->prec);
+    const int ns = ns_of(type), nc = nc_of(type, a), cs = csize(a->prec);
     const int nx = 3 * ns, na = na_out(type, out_mode(o));
     const int64_t K = std::min<int64_t>(n, int64_t(1) << 20);
     const bool in_host = a->memory == FE_MEM_HOST, out_host = o->memory == FE_MEM_HOST;
@@ -552,8 +565,14 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
     if (a->kind != FE_POISSON && a->kind != FE_GENERIC) return set_error(nullptr, FE_ERR_INVALID_ARG, "bad problem kind");
     if (a->prec != FE_FP64 && a->prec != FE_FP32_MIXED && a->prec != FE_FP64_DW)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "bad precision");
-    if (a->coef_mode != FE_COEF_PER_ELEMENT && a->coef_mode != FE_COEF_PER_QPOINT)
+    if (a->coef_mode != FE_COEF_PER_ELEMENT && a->coef_mode != FE_COEF_PER_QPOINT && a->coef_mode != FE_COEF_FUNCTION_U)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "bad coefficient mode");
+    if (a->coef_mode == FE_COEF_FUNCTION_U) {
+        if (!a->coef_fn) return set_error(nullptr, FE_ERR_INVALID_ARG, "FE_COEF_FUNCTION_U without coef_fn");
+        if (a->coords_layout != FE_LAYOUT_AOS || o->packed || a->ordering)
+            return set_error(nullptr, FE_ERR_UNSUPPORTED,
+                             "the coefficient function takes element-contiguous coordinates, full outputs, ordering 0");
+    }
     if (type == FE_TET && a->quad != FE_QUAD_TET1 && a->quad != FE_QUAD_TET4)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "tetrahedra take FE_QUAD_TET1 or FE_QUAD_TET4");
     if (type == FE_PRISM && a->quad != FE_QUAD_PRISM6)
@@ -607,13 +626,13 @@ int64_t fe_bytes_per_element(fe_elem_type type, fe_problem kind, fe_quad quad, f
     if (prec != FE_FP64 && prec != FE_FP32_MIXED && prec != FE_FP64_DW) return -1;
     if (type == FE_TET && quad != FE_QUAD_TET1 && quad != FE_QUAD_TET4) return -1;
     if (type == FE_PRISM && quad != FE_QUAD_PRISM6) return -1;
-    if (mode != FE_COEF_PER_ELEMENT && mode != FE_COEF_PER_QPOINT) return -1;
+    if (mode != FE_COEF_PER_ELEMENT && mode != FE_COEF_PER_QPOINT && mode != FE_COEF_FUNCTION_U) return -1;
     fe_elem_args a{};
     a.kind = kind;
     a.quad = quad;
     a.coef_mode = mode;
     const int ns = ns_of(type), cs = csize(prec);
-    return int64_t(3 * ns) * 8 + int64_t(nc_of(&a)) * cs + int64_t(ns * ns + ns) * cs;
+    return int64_t(3 * ns) * 8 + int64_t(nc_of(type, &a)) * cs + int64_t(ns * ns + ns) * cs;
 }
 
 fe_status fe_ctx_create(const fe_ctx_config *cfg, fe_ctx **out) {

@@ -111,7 +111,7 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
 void dyn_batch_free(DynBatch &db);
 int ns_of(fe_elem_type t);
 int nq_of(fe_quad q);
-int nc_of(const fe_elem_args *a);
+int nc_of(fe_elem_type type, const fe_elem_args *a);
 void batch_destroy(fe_ctx *ctx);
 void serve_destroy(fe_ctx *ctx);
 }  // namespace fe

@@ -361,6 +361,8 @@ fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket) 
         if (it == ctx->meshes.end()) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown mesh id");
         mesh = it->second;
     }
+    if (req->coef_mode == FE_COEF_FUNCTION_U)
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "served requests take coefficient arrays");
     fe_elem_args a{};
     a.n_elem = mesh.n_elem;
     a.coords = mesh.coords;

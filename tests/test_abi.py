@@ -157,6 +157,26 @@ def test_ordering_validation(lib):
     assert _chk(lib, api.TET, a, o) == -6
 
 
+def test_coef_function_validation(lib):
+    """FE_COEF_FUNCTION_U: a parameter block, element-contiguous coordinates."""
+    fn = api.CoefFunction()
+    a, o = _args()
+    a.coords_layout = a.coefs_layout = o.layout = api.AOS
+    a.coef_mode = api.COEF_FN_U
+    assert _chk(lib, api.TET, a, o) == -1                  # no parameter block
+    a.coef_fn = ctypes.addressof(fn)
+    assert _chk(lib, api.TET, a, o) == 0
+    a.coords_layout = a.coefs_layout = api.SOA
+    assert _chk(lib, api.TET, a, o) == -6
+    a.coords_layout = a.coefs_layout = api.AOS
+    a.ordering = api.SQS
+    assert _chk(lib, api.TET, a, o) == -6
+    # per element: coordinates, the NS nodal values, outputs
+    b = api.bytes_per_element
+    assert b(api.TET, api.GENERIC, api.QUAD_TET4, api.COEF_FN_U, api.FP32_MIXED) == 96 + 16 + 80
+    assert b(api.PRISM, api.GENERIC, api.QUAD_PRISM6, api.COEF_FN_U, api.FP32_MIXED) == 144 + 24 + 168
+
+
 def test_null_context_rejected(lib):
     a, o = _args()
     assert lib.fe_integrate_tet(None, ctypes.byref(a), ctypes.byref(o), None) == -1
