@@ -431,11 +431,22 @@ def prism_form(ctx, dev, api, args):
     k_ms = kms / kn
     peak, _ = measured_peaks()
     gbs = n * bpe / (k_ms * 1e-3) / 1e9
-    del X, C, out
+    del C, out
+    torch.cuda.empty_cache()
+    # the Laplace kind on the same prisms: d^0 per point, in the three precision forms
+    from paper_1504_01023_gb300 import meshgen
+    d0 = meshgen.poisson_coefs(n, 6, None, seed=meshgen.SEED_BASE + 3)
+    lap = {"workload": "the same 2,000,000 prisms, Laplace operator, d^0 ~ U[-1,1] per integration point"}
+    for name, prec in (("mixed", api.FP32_MIXED), ("double_word", api.FP64_DW), ("native_fp64", api.FP64)):
+        Cd = torch.from_numpy(np.ascontiguousarray(d0.astype(np.float32 if prec == api.FP32_MIXED else np.float64))).to(dev)
+        lap[name] = _fp64_run(ctx, dev, api, X, Cd, api.PRISM, api.POISSON, api.QUAD_PRISM6, prec, args,
+                              cm=api.PER_QPOINT)
+        del Cd
+    del X
     torch.cuda.empty_cache()
     return {"workload": PRISM_WORKLOAD, "value": n / step_ms / 1e3, "unit": "Melem/s", "ms_per_step": step_ms,
             "kernel_ms": k_ms, "bytes_per_element": bpe, "achieved_gbs": gbs, "hbm_frac": gbs / peak,
-            "launch_shape": {"block": shape[0], "persistent": shape[1]}, "dtype": "f32"}
+            "launch_shape": {"block": shape[0], "persistent": shape[1]}, "dtype": "f32", "laplace": lap}
 
 
 def _indexed_run(ctx, dev, api, et, nodes, conn, coefs, kind, quad, cm, args):
@@ -662,12 +673,13 @@ def coef_function_form(ctx, dev, api, args):
             "hbm_frac": gbs / peak, "launch_shape": {"block": shape[0], "persistent": shape[1]}}
 
 
-def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args):
+def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args, cm=None):
     """Tuned shape, then the average kernel time (profiling events) of repeated calls."""
     import torch
     n = X.shape[0]
+    cm = api.PER_ELEMENT if cm is None else cm
     out = api.alloc_out(et, n, prec, api.AOS, dev, with_flags=True)
-    kw = dict(kind=kind, quad=quad, coef_mode=api.PER_ELEMENT, prec=prec, layout=api.AOS, out_layout=api.AOS)
+    kw = dict(kind=kind, quad=quad, coef_mode=cm, prec=prec, layout=api.AOS, out_layout=api.AOS)
     ctx.tune(et, X, C, out=out, **kw)
     for _ in range(3):
         ctx.integrate(et, X, C, out=out, **kw)
@@ -681,7 +693,7 @@ def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args):
     ctx.set_profiling(False)
     flagged = int((out[2] & 1).sum().item())
     del out
-    bpe = api.bytes_per_element(et, kind, quad, api.PER_ELEMENT, prec)
+    bpe = api.bytes_per_element(et, kind, quad, cm, prec)
     k_ms = kms / kn
     peak, src = measured_peaks()
     gbs = n * bpe / (k_ms * 1e-3) / 1e9

@@ -529,12 +529,10 @@ __device__ __forceinline__ double recip_fast(double v) { return 1.0 / v; }
 __device__ __forceinline__ float recip_fast(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ DW recip_fast(DW v) { return dw_recip(v); }
 
-// Global gradients at point (l, t) of PRISM6. Returns det J. With SQRTVOL the
-// gradients come out multiplied by sqrt(vol), vol = |det J| w (then the Laplace
-// products g_r . g_s carry the volume factor without further multiplies).
-template <class T, bool SQRTVOL = false>
+// Global gradients at point (l, t) of PRISM6. Returns det J.
+template <class T>
 __device__ __forceinline__ T prism_point(const PrismFrame<T> &f, V3<T> cx, V3<T> cy, V3<T> a3, int l, int t, V3<T> g[6],
-                                         V3<T> &cz_out, T w = T(0)) {
+                                         V3<T> &cz_out) {
     using R = Rule<Q_PRISM6>;
     // lambda_k / 2 at triangle point t (t may be a run-time index): 1/3 or 1/12
     const T h0 = t == 0 ? T(1.0 / 3.0) : T(1.0 / 12.0), h1 = t == 1 ? T(1.0 / 3.0) : T(1.0 / 12.0),
@@ -543,8 +541,7 @@ __device__ __forceinline__ T prism_point(const PrismFrame<T> &f, V3<T> cx, V3<T>
     const V3<T> a1 = cross(cy, cz);
     const V3<T> a2 = cross(cz, cx);
     const T det = dot(cx, a1);
-    T inv = recip_fast(det);
-    if constexpr (SQRTVOL) inv *= sqrt((det < T(0) ? -det : det) * w);
+    const T inv = recip_fast(det);
     const V3<T> r1 = inv * a1, r2 = inv * a2, r3 = inv * a3;
     const V3<T> P[3] = {-(r1 + r2), r1, r2};
     const T zb = T(R::zb(l)), zt = T(R::zt(l));
@@ -633,18 +630,6 @@ __device__ __forceinline__ void prism_poisson_update_rt(const V3<T> g[6], T vol,
     }
 }
 
-// Poisson products at one prism point from gradients already scaled by
-// sqrt(vol): A_rs += g_r . g_s, b_r += vol d0_q phi_r(q) (upper triangle).
-template <class T, int Q>
-__device__ __forceinline__ void prism_poisson_update_scaled(const V3<T> g[6], T vol, T d0, T A[36], T b[6]) {
-#pragma unroll
-    for (int r = 0; r < 6; ++r) {
-#pragma unroll
-        for (int s = r; s < 6; ++s) A[6 * r + s] += dot(g[r], g[s]);
-        b[r] += (vol * d0) * T(Rule<Q_PRISM6>::phi(Q, r));
-    }
-}
-
 // Poisson products at one prism point: A_rs += vol grad phi_r . grad phi_s,
 // b_r += vol d0_q phi_r(q) (upper triangle accumulated; mirrored at the end).
 template <class T, int Q>
@@ -655,6 +640,92 @@ __device__ __forceinline__ void prism_poisson_update(const V3<T> g[6], T vol, T 
 #pragma unroll
         for (int s = r; s < 6; ++s) A[6 * r + s] += dot(gr, g[s]);
         b[r] += (vol * d0) * T(Rule<Q_PRISM6>::phi(Q, r));
+    }
+}
+
+// Laplace matrix of a prism from the Gram terms of J^{-1} (the sum over the six
+// points of vol grad phi_m . grad phi_n, regrouped; the same quadrature as
+// Algorithm 2, different rounding order).
+//
+// At a point (l, t), with rho_i the rows of J^{-1} and h_a = lambda_a(t)/2,
+//   grad phi_m = z_m P_a + sigma_m h_a rho_3     (a = m mod 3),
+// where z_m = zb(l), sigma_m = -1 for the bottom nodes, z_m = zt(l), sigma_m = +1
+// for the top ones, and P_0 = -(rho_1 + rho_2), P_1 = rho_1, P_2 = rho_2. Every
+// product vol grad phi_m . grad phi_n is then a combination, with coefficients
+// fixed by the rule, of the six terms gamma_ij = vol rho_i . rho_j =
+// (w / |det J|) a_i . a_j (a_i = det J rho_i, the cross products of the columns
+// of J):
+//   z_m z_n Pi_ab + sigma_n z_m h_b pi_a + sigma_m z_n h_a pi_b + sigma_m sigma_n h_a h_b gamma_33,
+// Pi_ab = vol P_a . P_b (linear in gamma_11, gamma_12, gamma_22) and
+// pi_a = vol P_a . rho_3 (linear in gamma_13, gamma_23). Summed over the points,
+// each coefficient factors into a level part and a triangle-point part, so the
+// point loop keeps only
+//   L[l]    = sum over the points t of level l of (gamma_11, gamma_12, gamma_22),
+//   v[l][t] = (gamma_13, gamma_23) at every point,
+//   c3[t]   = sum over the two levels of gamma_33 at triangle point t,
+// and this function forms the 21 distinct entries from them (upper triangle of
+// A, row-major 6 x 6; the lower triangle is left alone).
+template <class T>
+__device__ __forceinline__ void prism_laplace_assemble(const T L[2][3], const T v[2][3][2], const T c3[3], T A[36]) {
+    using R = Rule<Q_PRISM6>;
+    constexpr double zb0 = R::zb(0), zb1 = R::zb(1), zt0 = R::zt(0), zt1 = R::zt(1);
+    // z_m z_n summed over the levels: bottom-bottom, top-top, bottom-top
+    T Pi[3][3][3];   // [pair kind][a][b]
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double w0 = k == 0 ? zb0 * zb0 : (k == 1 ? zt0 * zt0 : zb0 * zt0);
+        const double w1 = k == 0 ? zb1 * zb1 : (k == 1 ? zt1 * zt1 : zb1 * zt1);
+        T g[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) g[j] = T(w0) * L[0][j] + T(w1) * L[1][j];
+        Pi[k][1][1] = g[0];
+        Pi[k][2][2] = g[2];
+        Pi[k][1][2] = Pi[k][2][1] = g[1];
+        Pi[k][0][1] = Pi[k][1][0] = -(g[0] + g[1]);
+        Pi[k][0][2] = Pi[k][2][0] = -(g[1] + g[2]);
+        Pi[k][0][0] = (g[0] + g[2]) + T(2.0) * g[1];
+    }
+    // nu[side][b] = sum_l z_side(l) sum_t h_b(t) v[l][t], h_b(t) = 1/12 + delta_bt / 4;
+    // then pi[side][a][b] = pi_a(nu[side][b])
+    T pi[2][3][3];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const double z0 = side ? zt0 : zb0, z1 = side ? zt1 : zb1;
+        T V[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            V[i] = T(z0 / 12.0) * ((v[0][0][i] + v[0][1][i]) + v[0][2][i]) +
+                   T(z1 / 12.0) * ((v[1][0][i] + v[1][1][i]) + v[1][2][i]);
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            const T n0 = V[0] + (T(z0 / 4.0) * v[0][bb][0] + T(z1 / 4.0) * v[1][bb][0]);
+            const T n1 = V[1] + (T(z0 / 4.0) * v[0][bb][1] + T(z1 / 4.0) * v[1][bb][1]);
+            pi[side][1][bb] = n0;
+            pi[side][2][bb] = n1;
+            pi[side][0][bb] = -(n0 + n1);
+        }
+    }
+    // H_ab = sum_t h_a(t) h_b(t) c3[t]
+    const T C = T(1.0 / 144.0) * ((c3[0] + c3[1]) + c3[2]);
+    T H[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        H[a][a] = C + T(15.0 / 144.0) * c3[a];
+#pragma unroll
+        for (int bb = a + 1; bb < 3; ++bb) H[a][bb] = H[bb][a] = C + T(3.0 / 144.0) * (c3[a] + c3[bb]);
+    }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+#pragma unroll
+        for (int n = m; n < 6; ++n) {
+            const int a = m % 3, bb = n % 3;
+            const bool tm = m >= 3, tn = n >= 3;
+            const T p = Pi[tm == tn ? (tm ? 1 : 0) : 2][a][bb];
+            const T x = pi[tm ? 1 : 0][a][bb];   // z_m h_b pi_a, sign sigma_n
+            const T y = pi[tn ? 1 : 0][bb][a];   // z_n h_a pi_b, sign sigma_m
+            const T cross_terms = (tn ? x : -x) + (tm ? y : -y);
+            A[6 * m + n] = p + cross_terms + (tm == tn ? H[a][bb] : -H[a][bb]);
+        }
     }
 }
 

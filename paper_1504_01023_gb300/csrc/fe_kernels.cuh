@@ -247,29 +247,33 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     // Q loop on relative coordinates r[0..5] (r[0] = 0). Returns bit1/bit2 flags.
     // Generic coefficients: the three points of a zeta level run in a rolled loop
     // (shape values computed per point), which keeps the large body in the
-    // instruction cache; the lighter Poisson body is fully unrolled.
+    // instruction cache. Laplace: the points only gather Gram terms of J^{-1}
+    // (prism_laplace_assemble forms A^e from them once).
     template <class CS>
     __device__ __forceinline__ static uint8_t qloop(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor) {
-        if (KIND == POISSON) return qloop_unrolled(r, c, A, b, poor);
-        return qloop_rolled(r, c, A, b, poor);
+        if constexpr (KIND == POISSON)
+            return qloop_laplace(r, c, A, b, poor);
+        else
+            return qloop_rolled(r, c, A, b, poor);
     }
 
     template <class CS>
-    __device__ __forceinline__ static uint8_t qloop_unrolled(const V3<T> r[6], const CS &c, T A[36], T b[6],
-                                                             bool &poor) {
+    __device__ __forceinline__ static uint8_t qloop_laplace(const V3<T> r[6], const CS &c, T A[36], T b[6],
+                                                            bool &poor) {
+        using R = Rule<Q_PRISM6>;
         const PrismFrame<T> f = prism_frame(r);
-#pragma unroll
-        for (int k = 0; k < 36; ++k) A[k] = T(0);
 #pragma unroll
         for (int k = 0; k < 6; ++k) b[k] = T(0);
         bool neg = false, degenerate = false;
         poor = false;
+        T L[2][3], v[2][3][2], c3[3];
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-            const T zb = T(Rule<Q_PRISM6>::zb(l)), zt = T(Rule<Q_PRISM6>::zt(l));
+            const T zb = T(R::zb(l)), zt = T(R::zt(l));
             const V3<T> cx = zb * f.ub + zt * f.ut;
             const V3<T> cy = zb * f.vb + zt * f.vt;
             const V3<T> a3 = cross(cx, cy);
+            const T a33 = dot(a3, a3);
             float fxy = 0.0f;
             if constexpr (PREC != FP64) {
                 const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
@@ -277,23 +281,42 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             }
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
-                V3<T> g[6], cz;
-                // float Laplace form: gradients carry sqrt(vol), see prism_point
-                constexpr bool kSqrtVol = PREC == MIXED && KIND == POISSON;
-                const T w = T(Rule<Q_PRISM6>::w(3 * l + t));
-                const T det = prism_point<T, kSqrtVol>(f, cx, cy, a3, l, t, g, cz, w);
+                const int q = 3 * l + t;
+                // lambda_k / 2 at triangle point t
+                const T h0 = T(t == 0 ? 1.0 / 3.0 : 1.0 / 12.0), h1 = T(t == 1 ? 1.0 / 3.0 : 1.0 / 12.0),
+                        h2 = T(t == 2 ? 1.0 / 3.0 : 1.0 / 12.0);
+                const V3<T> cz = h0 * f.w0 + h1 * f.w1 + h2 * f.w2;
+                const V3<T> a1 = cross(cy, cz), a2 = cross(cz, cx);
+                const T det = dot(cx, a1);
                 if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
                 if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
                 if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
                 neg |= det < T(0);
-                const T vol = abs_t(det) * w;
-                if (kSqrtVol)
-                    update_point_scaled(3 * l + t, g, vol, c, A, b);
+                const T adet = abs_t(det);
+                const T sw = T(R::w(q)) * recip_fast(adet);      // vol / det^2
+                const T g11 = sw * dot(a1, a1), g12 = sw * dot(a1, a2), g22 = sw * dot(a2, a2);
+                if (t == 0) {
+                    L[l][0] = g11;
+                    L[l][1] = g12;
+                    L[l][2] = g22;
+                } else {
+                    L[l][0] += g11;
+                    L[l][1] += g12;
+                    L[l][2] += g22;
+                }
+                v[l][t][0] = sw * dot(a1, a3);
+                v[l][t][1] = sw * dot(a2, a3);
+                if (l == 0)
+                    c3[t] = sw * a33;
                 else
-                    update_point(3 * l + t, g, vol, c, A, b);
+                    c3[t] += sw * a33;
+                const T vd = (adet * T(R::w(q))) * c(CPQ ? q : 0);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) b[k] += vd * T(R::phi(q, k));
             }
         }
-        if (KIND == POISSON) mirror(A);
+        prism_laplace_assemble<T>(L, v, c3, A);
+        mirror(A);
         if (degenerate) {
 #pragma unroll
             for (int k = 0; k < 36; ++k) A[k] = T(0);
@@ -377,19 +400,6 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             case 3: upd<3>(g, vol, c, A, b); break;
             case 4: upd<4>(g, vol, c, A, b); break;
             default: upd<5>(g, vol, c, A, b); break;
-        }
-    }
-    // Laplace update from sqrt(vol)-scaled gradients (point index constant after unrolling)
-    template <class CS>
-    __device__ __forceinline__ static void update_point_scaled(int q, const V3<T> g[6], T vol, const CS &c, T A[36],
-                                                               T b[6]) {
-        switch (q) {
-            case 0: prism_poisson_update_scaled<T, 0>(g, vol, c(CPQ ? 0 : 0), A, b); break;
-            case 1: prism_poisson_update_scaled<T, 1>(g, vol, c(CPQ ? 1 : 0), A, b); break;
-            case 2: prism_poisson_update_scaled<T, 2>(g, vol, c(CPQ ? 2 : 0), A, b); break;
-            case 3: prism_poisson_update_scaled<T, 3>(g, vol, c(CPQ ? 3 : 0), A, b); break;
-            case 4: prism_poisson_update_scaled<T, 4>(g, vol, c(CPQ ? 4 : 0), A, b); break;
-            default: prism_poisson_update_scaled<T, 5>(g, vol, c(CPQ ? 5 : 0), A, b); break;
         }
     }
     template <int Q, class CS>
