@@ -880,7 +880,8 @@ def bench_serve(api, dev, args):
         r, _, _ = serve_open_loop(ctx, meshes, lam * k, min(T, 1.5), meshgen.SEED_BASE + 55 + k)
         sweep.append({key: r[key] for key in ("arrival_rate_per_s", "seconds", "requests", "errors", "p50_ms",
                                                "p99_ms", "sustained_melem_s", "offered_melem_s")})
-    saturated = serve_saturated(api, ctx, meshes, args)
+    # capacity: closed loops with 48 and 96 requests outstanding
+    saturated = [serve_saturated(api, ctx, meshes, max(1.0, args.serve_seconds / 2), d) for d in (48, 96)]
     ctx.close()
 
     # plain one-request-at-a-time FP64 path on the same arrivals (first 0.25 s)
@@ -946,14 +947,15 @@ def serve_open_loop(ctx, meshes, lam, T, seed):
                 pending = submitted[0] - len(lat)
             if pending == 0 and finished.is_set():
                 return
-            for tk, r in ctx.serve_wait_any(timeout_us=2000, max_results=64):
+            got = ctx.serve_wait_any(timeout_us=2000, max_results=64)
+            for tk, r in got:
                 if r.status != 0:
                     errors.append(r.status)
                 with lock:
                     n = sizes.pop(tk)
                     lat.append((r.t_done_us - r.t_submit_us, r.t_done_us, r.t_submit_us))
                 done_elems[0] += n
-                ctx.serve_release(tk)
+            ctx.serve_release_many([tk for tk, _ in got])
 
     th = threading.Thread(target=collector, daemon=True)
     th.start()
@@ -979,10 +981,10 @@ def serve_open_loop(ctx, meshes, lam, T, seed):
              "offered_melem_s": offered, "wall_s": wall}, arrivals, choice)
 
 
-def serve_saturated(api, ctx, meshes, args, depth=48):
+def serve_saturated(api, ctx, meshes, seconds, depth):
     """Capacity of the serving loop: a closed loop keeps `depth` requests of the same
-    mix outstanding (a new one is submitted as each completes, completions taken
-    from the completion queue) for about args.serve_seconds; throughput = elements completed / (last completion - first
+    mix outstanding (completions taken from the completion queue, released in one
+    call and replaced one by one) for about `seconds`; throughput = elements completed / (last completion - first
     submission), with the library's own timestamps. HBM fraction from the
     algorithmic bytes of each request."""
     from paper_1504_01023_gb300 import meshgen
@@ -993,17 +995,17 @@ def serve_saturated(api, ctx, meshes, args, depth=48):
         if key not in bpe:
             bpe[key] = api.bytes_per_element(m["et"], m["kind"], m["quad"], m["cm"], api.FP32_MIXED)
     out, lat, first, last, elems, nbytes, errors = {}, [], None, 0.0, 0, 0, 0
-    t_end = time.perf_counter() + args.serve_seconds
+    t_end = time.perf_counter() + seconds
 
     def submit():
         m = meshes[int(rng.integers(0, len(meshes)))]
-        tk = ctx.serve_submit(m["id"], m["kind"], m["quad"], m["cm"], m["C"])
-        out[tk] = m
+        out[ctx.serve_submit(m["id"], m["kind"], m["quad"], m["cm"], m["C"])] = m
 
     for _ in range(depth):
         submit()
     while out:
-        for tk, r in ctx.serve_wait_any(timeout_us=100000, max_results=64):
+        got = ctx.serve_wait_any(timeout_us=100000, max_results=64)
+        for tk, r in got:
             m = out.pop(tk)
             errors += r.status != 0
             first = r.t_submit_us if first is None else min(first, r.t_submit_us)
@@ -1011,8 +1013,12 @@ def serve_saturated(api, ctx, meshes, args, depth=48):
             lat.append((r.t_done_us - r.t_submit_us) / 1e3)
             elems += m["n"]
             nbytes += m["n"] * bpe[(m["et"], m["kind"], m["quad"], m["cm"])]
-            ctx.serve_release(tk)
-            if time.perf_counter() < t_end:
+        # what finished is released in one call; each is replaced by a new request
+        # submitted on its own (submitting the replacements as one group keeps
+        # them together as a cohort, which measured slower at 48 outstanding)
+        ctx.serve_release_many([tk for tk, _ in got])
+        if time.perf_counter() < t_end:
+            for _ in got:
                 submit()
     span = (last - first) / 1e6
     peak, src = measured_peaks()

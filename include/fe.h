@@ -317,6 +317,15 @@ fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket);
 fe_status fe_serve_poll(fe_ctx *ctx, uint64_t ticket, fe_result *res);
 /* Free a finished request's outputs and return their bytes to the budget. */
 fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket);
+/* Several requests at once (host arrays of n entries), under one lock and one
+   scheduler wake-up, so that requests submitted together can share one launch.
+   All or nothing: if any request is invalid (as fe_serve_submit would reject it),
+   none is queued and the status is that request's; tickets[] is written only on
+   FE_OK. n = 0 does nothing. Thread-safe. */
+fe_status fe_serve_submit_n(fe_ctx *ctx, const fe_request *reqs, int n, uint64_t *tickets);
+/* Release several finished requests at once. All or nothing: an unknown,
+   unfinished or repeated ticket releases none (FE_ERR_INVALID_ARG). Thread-safe. */
+fe_status fe_serve_release_n(fe_ctx *ctx, const uint64_t *tickets, int n);
 /* Completion queue. Waits up to timeout_us microseconds (0: do not wait) until at
    least one request has finished that this call has not yet returned, then writes
    up to `max` finished requests, in completion order, to tickets[] and results[]

@@ -95,6 +95,8 @@ _SIGS = [
     ("fe_serve_submit", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
     ("fe_serve_release", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("fe_serve_submit_n", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+    ("fe_serve_release_n", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     ("fe_apply_tet", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), _P, _P, _P, _P, _P]),
     ("fe_apply_prism", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), _P, _P, _P, _P, _P]),
     ("fe_serve_wait_any", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result),
@@ -431,6 +433,30 @@ class Context:
         _check(load().fe_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t)), self.h)
         self._keep[t.value] = (coefs, prec)
         return t.value
+
+    def serve_submit_many(self, requests) -> list:
+        """Several requests in one call (they can share one launch): a list of
+        (mesh_id, kind, quad, coef_mode, coefs[, prec]) tuples. All or nothing."""
+        n = len(requests)
+        arr = (Request * max(n, 1))()
+        for i, rq in enumerate(requests):
+            mesh_id, kind, quad, cm, coefs = rq[:5]
+            prec = rq[5] if len(rq) > 5 else FP32_MIXED
+            arr[i] = Request(mesh_id, kind, quad, cm, coefs.data_ptr(), prec)
+        tks = (ctypes.c_uint64 * max(n, 1))()
+        _check(load().fe_serve_submit_n(self.h, arr, n, tks), self.h)
+        out = list(tks[:n])
+        for t, rq in zip(out, requests):
+            self._keep[t] = (rq[4], rq[5] if len(rq) > 5 else FP32_MIXED)
+        return out
+
+    def serve_release_many(self, tickets):
+        """Release several finished requests in one call. All or nothing."""
+        n = len(tickets)
+        arr = (ctypes.c_uint64 * max(n, 1))(*tickets)
+        _check(load().fe_serve_release_n(self.h, arr, n), self.h)
+        for t in tickets:
+            self._keep.pop(t, None)
 
     def serve_result_tensors(self, ticket, res):
         """(A [n,NS,NS], b [n,NS], flags [n]) views of a finished request's outputs."""

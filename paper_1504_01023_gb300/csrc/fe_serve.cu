@@ -41,7 +41,7 @@ struct Req {
 
 struct ServeState;
 
-constexpr uint64_t kFeedElems = uint64_t(16) << 20;    // ~1 ms of GPU work in flight
+constexpr uint64_t kFeedElems = uint64_t(32) << 20;    // ~2 ms of GPU work (measured: 32M > 16M, 64M)
 constexpr uint64_t kLaunchElems = uint64_t(16) << 20;   // measured: 16M > 32M, 64M for large requests
 struct Slot {
     ServeState *owner = nullptr;
@@ -352,8 +352,13 @@ using namespace fe;
 
 extern "C" {
 
-fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket) {
-    if (!ctx || !req || !ticket) return set_error(ctx, FE_ERR_INVALID_ARG, "null argument");
+}  // extern "C"
+
+namespace {
+
+// Validate one request and fill its record (everything but the ticket and the
+// submission time). No lock held.
+fe_status prepare_request(fe_ctx *ctx, const fe_request *req, Req &q) {
     MeshRec mesh;
     {
         std::lock_guard<std::mutex> lk(ctx->mesh_mu);
@@ -376,24 +381,48 @@ fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket) 
     fe_out o{};
     o.A = o.b = reinterpret_cast<void *>(uintptr_t(256));  // outputs are the context's
     o.layout = FE_LAYOUT_AOS;
-    fe_status st = fe_check_args(mesh.type, &a, &o);
+    const fe_status st = fe_check_args(mesh.type, &a, &o);
     if (st != FE_OK) return set_error(ctx, st, fe_last_error(nullptr));
     const uint64_t ob = out_bytes_of(mesh, req->prec);
     if (ctx->hbm_used.load() + ob > ctx->hbm_budget)
         return set_error(ctx, FE_ERR_BUDGET, "request outputs can never fit the HBM budget");
-    st = ensure_serve(ctx);
+    q.r = *req;
+    q.mesh = mesh;
+    q.out_bytes = ob;
+    return FE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket) {
+    if (!ctx || !req || !ticket) return set_error(ctx, FE_ERR_INVALID_ARG, "null argument");
+    return fe_serve_submit_n(ctx, req, 1, ticket);
+}
+
+fe_status fe_serve_submit_n(fe_ctx *ctx, const fe_request *reqs, int n, uint64_t *tickets) {
+    if (!ctx || n < 0 || (n > 0 && (!reqs || !tickets))) return set_error(ctx, FE_ERR_INVALID_ARG, "bad argument");
+    if (n == 0) return FE_OK;
+    std::vector<Req> recs(static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) {
+        const fe_status st = prepare_request(ctx, &reqs[i], recs[size_t(i)]);
+        if (st != FE_OK) return st;  // nothing queued
+    }
+    fe_status st = ensure_serve(ctx);
     if (st != FE_OK) return st;
     ServeState *s = ctx->serve;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        const uint64_t tk = s->next_ticket++;
-        Req &q = s->reqs[tk];
-        q.r = *req;
-        q.mesh = mesh;
-        q.out_bytes = ob;
-        q.t_submit = now_us();
-        s->waiting.push_back(tk);
-        *ticket = tk;
+        const double t = now_us();
+        for (int i = 0; i < n; ++i) {
+            const uint64_t tk = s->next_ticket++;
+            Req &q = s->reqs[tk];
+            q = recs[size_t(i)];
+            q.t_submit = t;
+            s->waiting.push_back(tk);
+            tickets[i] = tk;
+        }
     }
     s->cv.notify_all();
     return FE_OK;
@@ -452,27 +481,40 @@ fe_status fe_serve_wait_any(fe_ctx *ctx, int64_t timeout_us, uint64_t *tickets, 
     }
 }
 
-fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket) {
+fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket) { return fe_serve_release_n(ctx, &ticket, 1); }
+
+fe_status fe_serve_release_n(fe_ctx *ctx, const uint64_t *tickets, int n) {
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    if (n < 0 || (n > 0 && !tickets)) return set_error(ctx, FE_ERR_INVALID_ARG, "bad argument");
+    if (n == 0) return FE_OK;
     ServeState *s = ctx->serve;
     if (!s) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown ticket");
-    void *A = nullptr;
-    cudaStream_t st = nullptr;
+    std::vector<std::pair<void *, cudaStream_t>> frees;
+    frees.reserve(size_t(n));
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        auto it = s->reqs.find(ticket);
-        if (it == s->reqs.end()) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown ticket");
-        Req &q = it->second;
-        if (q.state != 2) return set_error(ctx, FE_ERR_INVALID_ARG, "request still running");
-        st = s->slots[std::max(q.slot, 0)]->stream;
-        A = q.A;  // the one allocation that also holds b and the flags
-        s->out_used -= q.out_bytes;
-        s->reqs.erase(it);
+        // all or nothing: every ticket must be known, finished and listed once
+        for (int i = 0; i < n; ++i) {
+            auto it = s->reqs.find(tickets[i]);
+            if (it == s->reqs.end()) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown ticket");
+            if (it->second.state != 2) return set_error(ctx, FE_ERR_INVALID_ARG, "request still running");
+            for (int j = 0; j < i; ++j)
+                if (tickets[j] == tickets[i]) return set_error(ctx, FE_ERR_INVALID_ARG, "ticket listed twice");
+        }
+        for (int i = 0; i < n; ++i) {
+            auto it = s->reqs.find(tickets[i]);
+            Req &q = it->second;
+            // the one allocation that also holds b and the flags
+            frees.emplace_back(q.A, s->slots[std::max(q.slot, 0)]->stream);
+            s->out_used -= q.out_bytes;
+            s->reqs.erase(it);
+        }
     }
     s->cv.notify_all();
     // stream-ordered frees outside the lock
     cudaSetDevice(ctx->device);
-    if (A) cudaFreeAsync(A, st);
+    for (auto &f : frees)
+        if (f.first) cudaFreeAsync(f.first, f.second);
     return FE_OK;
 }
 

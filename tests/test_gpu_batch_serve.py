@@ -253,3 +253,56 @@ def test_serve_completion_queue(ctx, mix):
     assert ctx.serve_wait_any(timeout_us=1000) == []
     for mid, *_ in ids:
         ctx.mesh_release(mid)
+
+
+def test_serve_submit_and_release_many(ctx, mix):
+    """fe_serve_submit_n queues every request or none; the results equal those of
+    single submissions; fe_serve_release_n releases every ticket or none."""
+    ids = []
+    for i, ((et, kind, quad, cpq, n, _), (mesh, c, X, C)) in enumerate(zip(MIX, mix)):
+        ids.append((_register(ctx, et, mesh, "aos-dev"), kind, quad, api.PER_QPOINT if cpq else api.PER_ELEMENT, C))
+    # single submissions, for reference
+    ref = {}
+    for j, args in enumerate(ids):
+        tk = ctx.serve_submit(*args)
+        r = _wait(ctx, tk)
+        A, b, f = ctx.serve_result_tensors(tk, r)
+        ref[j] = (A.cpu().numpy().copy(), b.cpu().numpy().copy(), f.cpu().numpy().copy())
+        ctx.serve_release(tk)
+    # a bad request in the middle: nothing is queued
+    bad = list(ids)
+    bad.insert(3, (10 ** 9,) + ids[0][1:])                     # unknown mesh id
+    with pytest.raises(api.FeError) as e:
+        ctx.serve_submit_many(bad)
+    assert e.value.status == -1
+    assert ctx.serve_wait_any(timeout_us=20000) == []
+    # all of them at once, twice
+    tks = ctx.serve_submit_many(ids + ids)
+    assert len(set(tks)) == 2 * len(ids)
+    rs = [_wait(ctx, tk) for tk in tks]
+    launches = {r.t_launch_us for r in rs}
+    assert len(launches) < len(tks)                          # they shared launches
+    for k, (tk, r) in enumerate(zip(tks, rs)):
+        assert r.status == 0
+        A, b, f = ctx.serve_result_tensors(tk, r)
+        An, bn, fn = ref[k % len(ids)]
+        assert np.array_equal(f.cpu().numpy(), fn)
+        assert oracle.rel_frobenius(A.double().cpu().numpy(), An.astype(np.float64)).max() <= 1e-6
+        assert oracle.rel_frobenius(b.double().cpu().numpy(), bn.astype(np.float64)).max() <= 1e-6
+    # a repeated or unknown ticket releases none
+    with pytest.raises(api.FeError):
+        ctx.serve_release_many([tks[0], tks[0]])
+    with pytest.raises(api.FeError):
+        ctx.serve_release_many([tks[1], 10 ** 12])
+    assert ctx.serve_poll(tks[0]).status == 0 and ctx.serve_poll(tks[1]).status == 0
+    ctx.serve_release_many(tks)
+    for tk in tks:
+        with pytest.raises(api.FeError):
+            ctx.serve_poll(tk)
+    ctx.serve_release_many([])
+    assert ctx.serve_submit_many([]) == []
+    # the completion queue skips what was released before it was returned
+    while ctx.serve_wait_any(timeout_us=0):
+        pass
+    for mid, *_ in ids:
+        ctx.mesh_release(mid)
