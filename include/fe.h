@@ -354,7 +354,12 @@ fe_status fe_ctx_set_profiling(fe_ctx *ctx, int on);
 fe_status fe_ctx_kernel_time(fe_ctx *ctx, double *ms, int64_t *launches, int reset);
 
 /* Autotuner: time every candidate launch shape for the key of (type, args, out)
-   now, on these buffers, and keep the fastest. Writes the tuning cache if set. */
+   now, on these buffers, and keep the fastest. Candidates: elements per block
+   (powers of two, 64 threads up to the kernel's limit), persistent or not, and
+   for prisms with element-contiguous coordinates and outputs, coefficient arrays
+   and the QSS order, one or two threads per element (two: each thread takes the
+   three points of one zeta level of Algorithm 2's point loop and the pair adds
+   its partial results). Writes the tuning cache if set. */
 fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                   void *stream);
 /* Pin the launch shape of a key (threads = elements per block: 32..512 for
@@ -362,11 +367,28 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, cons
    autotuner would; FE_ERR_UNSUPPORTED if its shared memory does not fit. */
 fe_status fe_set_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                        int block_threads, int persistent);
-/* The launch shape that the next call with this key would use: threads (=
-   elements) per block, and whether the grid is persistent (one wave of resident
-   blocks striding over tiles) or one block per tile. */
+/* The launch shape that the next call with this key would use: threads per
+   block (elements per block x threads per element), and whether the grid is
+   persistent (one wave of resident blocks striding over tiles) or one block per
+   tile. */
 fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                        int *block_threads, int *persistent);
+
+/* Launch shape with the threads per element made explicit. */
+typedef struct fe_launch_shape {
+    int elems_per_block;           /* elements per tile (one block per tile) */
+    int threads_per_elem;          /* 1, or 2 (prisms as described at fe_tune) */
+    int persistent;                /* 0 or 1 */
+} fe_launch_shape;
+/* As fe_get_shape / fe_set_shape. Set: threads per block = elems_per_block x
+   threads_per_elem must be a multiple of 32 within the kernel's limit (512 for
+   tetrahedra in the FP64 and mixed forms, 256 otherwise); FE_ERR_UNSUPPORTED for
+   two threads per element where the key does not allow it, or if the shared
+   memory does not fit. */
+fe_status fe_get_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
+                              fe_launch_shape *shape);
+fe_status fe_set_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
+                              const fe_launch_shape *shape);
 
 /*
  * Mixed-precision tetrahedron integration that allocates nothing (the paper has

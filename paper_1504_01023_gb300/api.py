@@ -66,6 +66,10 @@ class BatchItem(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("args", ElemArgs), ("out", Out)]
 
 
+class LaunchShape(ctypes.Structure):
+    _fields_ = [("elems_per_block", ctypes.c_int), ("threads_per_elem", ctypes.c_int), ("persistent", ctypes.c_int)]
+
+
 class Request(ctypes.Structure):
     _fields_ = [("mesh_id", ctypes.c_int64), ("kind", ctypes.c_int), ("quad", ctypes.c_int), ("coef_mode", ctypes.c_int),
                 ("coefs", ctypes.c_void_p), ("prec", ctypes.c_int)]
@@ -95,6 +99,10 @@ _SIGS = [
     ("fe_serve_submit", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
     ("fe_serve_release", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("fe_get_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
+                                           ctypes.POINTER(LaunchShape)]),
+    ("fe_set_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
+                                           ctypes.POINTER(LaunchShape)]),
     ("fe_serve_submit_n", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_release_n", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     ("fe_apply_tet", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), _P, _P, _P, _P, _P]),
@@ -379,12 +387,15 @@ class Context:
                           ordering, coef_fn)
 
     def set_shape(self, block, persistent, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT,
-                  prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None, conn=None, packed=False):
+                  prec=FP32_MIXED, layout=SOA, out_layout=SOA, out=None, conn=None, packed=False, tpe=1):
+        """Pin the launch shape: `block` elements per tile, `tpe` threads per element."""
         args = make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, conn)
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
         o = make_out(*out, out_layout, packed)
-        _check(load().fe_set_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), block, persistent), self.h)
+        sh = LaunchShape(block, tpe, persistent)
+        _check(load().fe_set_launch_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), ctypes.byref(sh)),
+               self.h)
 
     def shape(self, elem_type, coords, coefs, kind, quad, coef_mode=PER_ELEMENT, prec=FP32_MIXED, layout=SOA,
               out_layout=SOA, out=None, conn=None, packed=False, ordering=QSS, coef_fn=None):
@@ -392,10 +403,10 @@ class Context:
         if out is None:
             out = alloc_out(elem_type, args.n_elem, prec, out_layout, coords.device, packed=packed)
         o = make_out(*out, out_layout, packed)
-        blk, pers = ctypes.c_int(), ctypes.c_int()
-        _check(load().fe_get_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), ctypes.byref(blk),
-                                   ctypes.byref(pers)), self.h)
-        return blk.value, pers.value
+        sh = LaunchShape()
+        _check(load().fe_get_launch_shape(self.h, elem_type, ctypes.byref(args), ctypes.byref(o), ctypes.byref(sh)),
+               self.h)
+        return sh.elems_per_block, sh.persistent, sh.threads_per_elem
 
     def selftest_bounded_wait(self, polls: int = 1 << 16) -> int:
         """Run the failure-detection self-test; returns the status (FE_ERR_TIMEOUT expected)."""

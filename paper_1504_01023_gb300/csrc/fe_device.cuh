@@ -544,7 +544,7 @@ __device__ __forceinline__ T prism_point(const PrismFrame<T> &f, V3<T> cx, V3<T>
     const T inv = recip_fast(det);
     const V3<T> r1 = inv * a1, r2 = inv * a2, r3 = inv * a3;
     const V3<T> P[3] = {-(r1 + r2), r1, r2};
-    const T zb = T(R::zb(l)), zt = T(R::zt(l));
+    const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const T hl = k == 0 ? h0 : (k == 1 ? h1 : h2);
@@ -616,17 +616,6 @@ __device__ __forceinline__ void prism_generic_update_rt(const V3<T> g[6], T vol,
             for (int s = 0; s < 6; ++s) A[6 * r + s] += phi * Ta[s];
             b[r] += da * phi;
         }
-    }
-}
-
-template <class T>
-__device__ __forceinline__ void prism_poisson_update_rt(const V3<T> g[6], T vol, T d0, const T ph[6], T A[36], T b[6]) {
-#pragma unroll
-    for (int r = 0; r < 6; ++r) {
-        const V3<T> gr = vol * g[r];
-#pragma unroll
-        for (int s = r; s < 6; ++s) A[6 * r + s] += dot(gr, g[s]);
-        b[r] += (vol * d0) * ph[r];
     }
 }
 
@@ -728,5 +717,18 @@ __device__ __forceinline__ void prism_laplace_assemble(const T L[2][3], const T 
         }
     }
 }
+
+// Partner exchange of two threads per element (lanes 2j and 2j+1 of a warp;
+// `mask` holds every lane that takes part, both lanes of each pair).
+__device__ __forceinline__ float pair_other(float v, unsigned mask) { return __shfl_xor_sync(mask, v, 1); }
+__device__ __forceinline__ double pair_other(double v, unsigned mask) { return __shfl_xor_sync(mask, v, 1); }
+__device__ __forceinline__ DW pair_other(DW v, unsigned mask) {
+    return DW(__shfl_xor_sync(mask, v.h, 1), __shfl_xor_sync(mask, v.l, 1));
+}
+__device__ __forceinline__ bool pair_any(bool v, unsigned mask) {
+    return (__shfl_xor_sync(mask, int(v), 1) | int(v)) != 0;
+}
+// Both lanes get the same sum (addition of the two partials commutes).
+template <class T> __device__ __forceinline__ T pair_sum(T v, unsigned mask) { return v + pair_other(v, mask); }
 
 }  // namespace fe

@@ -240,6 +240,15 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, C
 
 // Prism (Algorithm 2): T = double, float or double-word arithmetic after the
 // edge vectors.
+// Entries 2j + part of a prism's A^e and b^e (the half that one lane of a pair writes).
+template <class T>
+__device__ __forceinline__ void pick_half(const T A[36], const T b[6], T Ah[18], T bh[3], int part) {
+#pragma unroll
+    for (int j = 0; j < 18; ++j) Ah[j] = part ? A[2 * j + 1] : A[2 * j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) bh[j] = part ? b[2 * j + 1] : b[2 * j];
+}
+
 template <int KIND, int PREC, int CPQ> struct PrismMath {
     using T = typename std::conditional<PREC == FP64, double,
                                         typename std::conditional<PREC == MIXED, float, DW>::type>::type;
@@ -249,74 +258,64 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     // (shape values computed per point), which keeps the large body in the
     // instruction cache. Laplace: the points only gather Gram terms of J^{-1}
     // (prism_laplace_assemble forms A^e from them once).
-    template <class CS>
-    __device__ __forceinline__ static uint8_t qloop(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor) {
-        if constexpr (KIND == POISSON)
-            return qloop_laplace(r, c, A, b, poor);
-        else
-            return qloop_rolled(r, c, A, b, poor);
-    }
-
-    template <class CS>
-    __device__ __forceinline__ static uint8_t qloop_laplace(const V3<T> r[6], const CS &c, T A[36], T b[6],
-                                                            bool &poor) {
-        using R = Rule<Q_PRISM6>;
+    //
+    // TPE == 2 (two threads per element): the lane of parity `part` takes the three
+    // points of zeta level `part` and the pair combines its partial results
+    // through shuffles within `mask`; both lanes end with the whole A^e and b^e.
+    template <int TPE = 1, class CS>
+    __device__ __forceinline__ static uint8_t qloop(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor,
+                                                    int part = 0, unsigned mask = 0xFFFFFFFFu) {
         const PrismFrame<T> f = prism_frame(r);
 #pragma unroll
         for (int k = 0; k < 6; ++k) b[k] = T(0);
         bool neg = false, degenerate = false;
         poor = false;
-        T L[2][3], v[2][3][2], c3[3];
+        if constexpr (KIND == POISSON) {
+            T L[2][3], v[2][3][2], c3[3];
+            if constexpr (TPE == 1) {
+                T c3l[2][3];
 #pragma unroll
-        for (int l = 0; l < 2; ++l) {
-            const T zb = T(R::zb(l)), zt = T(R::zt(l));
-            const V3<T> cx = zb * f.ub + zt * f.ut;
-            const V3<T> cy = zb * f.vb + zt * f.vt;
-            const V3<T> a3 = cross(cx, cy);
-            const T a33 = dot(a3, a3);
-            float fxy = 0.0f;
-            if constexpr (PREC != FP64) {
-                const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
-                fxy = dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f);
-            }
+                for (int l = 0; l < 2; ++l) level_laplace(f, l, c, L[l], v[l], c3l[l], b, poor, neg, degenerate);
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int q = 3 * l + t;
-                // lambda_k / 2 at triangle point t
-                const T h0 = T(t == 0 ? 1.0 / 3.0 : 1.0 / 12.0), h1 = T(t == 1 ? 1.0 / 3.0 : 1.0 / 12.0),
-                        h2 = T(t == 2 ? 1.0 / 3.0 : 1.0 / 12.0);
-                const V3<T> cz = h0 * f.w0 + h1 * f.w1 + h2 * f.w2;
-                const V3<T> a1 = cross(cy, cz), a2 = cross(cz, cx);
-                const T det = dot(cx, a1);
-                if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
-                if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
-                if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
-                neg |= det < T(0);
-                const T adet = abs_t(det);
-                const T sw = T(R::w(q)) * recip_fast(adet);      // vol / det^2
-                const T g11 = sw * dot(a1, a1), g12 = sw * dot(a1, a2), g22 = sw * dot(a2, a2);
-                if (t == 0) {
-                    L[l][0] = g11;
-                    L[l][1] = g12;
-                    L[l][2] = g22;
-                } else {
-                    L[l][0] += g11;
-                    L[l][1] += g12;
-                    L[l][2] += g22;
+                for (int t = 0; t < 3; ++t) c3[t] = c3l[0][t] + c3l[1][t];
+            } else {
+                T Lm[3], vm[3][2], c3m[3];
+                level_laplace(f, part, c, Lm, vm, c3m, b, poor, neg, degenerate);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const T o = pair_other(Lm[j], mask);
+                    L[0][j] = part ? o : Lm[j];
+                    L[1][j] = part ? Lm[j] : o;
+                    c3[j] = pair_sum(c3m[j], mask);
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const T w = pair_other(vm[j][i], mask);
+                        v[0][j][i] = part ? w : vm[j][i];
+                        v[1][j][i] = part ? vm[j][i] : w;
+                    }
                 }
-                v[l][t][0] = sw * dot(a1, a3);
-                v[l][t][1] = sw * dot(a2, a3);
-                if (l == 0)
-                    c3[t] = sw * a33;
-                else
-                    c3[t] += sw * a33;
-                const T vd = (adet * T(R::w(q))) * c(CPQ ? q : 0);
+            }
+            prism_laplace_assemble<T>(L, v, c3, A);
+            mirror(A);
+        } else {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) b[k] += vd * T(R::phi(q, k));
+            for (int k = 0; k < 36; ++k) A[k] = T(0);
+            if constexpr (TPE == 1) {
+#pragma unroll
+                for (int l = 0; l < 2; ++l) level_generic(f, l, c, A, b, poor, neg, degenerate);
+            } else {
+                level_generic(f, part, c, A, b, poor, neg, degenerate);
+#pragma unroll
+                for (int k = 0; k < 36; ++k) A[k] = pair_sum(A[k], mask);
             }
         }
-        prism_laplace_assemble<T>(L, v, c3, A);
-        mirror(A);
+        if constexpr (TPE == 2) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) b[k] = pair_sum(b[k], mask);
+            poor = pair_any(poor, mask);
+            neg = pair_any(neg, mask);
+            degenerate = pair_any(degenerate, mask);
+        }
         if (degenerate) {
 #pragma unroll
             for (int k = 0; k < 36; ++k) A[k] = T(0);
@@ -327,59 +326,91 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
         return neg ? 2 : 0;
     }
 
+    // Laplace: the three points of zeta level l (a constant after unrolling, or a
+    // run-time lane parity): per-level sum of (gamma_11, gamma_12, gamma_22), the
+    // points' (gamma_13, gamma_23) and gamma_33, and the load vector terms.
     template <class CS>
-    __device__ __forceinline__ static uint8_t qloop_rolled(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor) {
+    __device__ __forceinline__ static void level_laplace(const PrismFrame<T> &f, int l, const CS &c, T Ll[3],
+                                                         T vl[3][2], T c3l[3], T b[6], bool &poor, bool &neg,
+                                                         bool &degenerate) {
         using R = Rule<Q_PRISM6>;
-        const PrismFrame<T> f = prism_frame(r);
+        const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
+        const V3<T> cx = zb * f.ub + zt * f.ut;
+        const V3<T> cy = zb * f.vb + zt * f.vt;
+        const V3<T> a3 = cross(cx, cy);
+        const T a33 = dot(a3, a3);
+        float fxy = 0.0f;
+        if constexpr (PREC != FP64) {
+            const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
+            fxy = dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f);
+        }
 #pragma unroll
-        for (int k = 0; k < 36; ++k) A[k] = T(0);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) b[k] = T(0);
-        bool neg = false, degenerate = false;
-        poor = false;
-#pragma unroll
-        for (int l = 0; l < 2; ++l) {
-            const T zb = T(R::zb(l)), zt = T(R::zt(l));
-            const V3<T> cx = zb * f.ub + zt * f.ut;
-            const V3<T> cy = zb * f.vb + zt * f.vt;
-            const V3<T> a3 = cross(cx, cy);
-            float fxy = 0.0f;
-            if constexpr (PREC != FP64) {
-                const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
-                fxy = dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f);
+        for (int t = 0; t < 3; ++t) {
+            const int q = 3 * l + t;
+            // lambda_k / 2 at triangle point t
+            const T h0 = T(t == 0 ? 1.0 / 3.0 : 1.0 / 12.0), h1 = T(t == 1 ? 1.0 / 3.0 : 1.0 / 12.0),
+                    h2 = T(t == 2 ? 1.0 / 3.0 : 1.0 / 12.0);
+            const V3<T> cz = h0 * f.w0 + h1 * f.w1 + h2 * f.w2;
+            const V3<T> a1 = cross(cy, cz), a2 = cross(cz, cx);
+            const T det = dot(cx, a1);
+            if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
+            if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
+            if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
+            neg |= det < T(0);
+            const T adet = abs_t(det);
+            const T sw = T(R::w(0)) * recip_fast(adet);      // vol / det^2 (equal weights)
+            const T g11 = sw * dot(a1, a1), g12 = sw * dot(a1, a2), g22 = sw * dot(a2, a2);
+            if (t == 0) {
+                Ll[0] = g11;
+                Ll[1] = g12;
+                Ll[2] = g22;
+            } else {
+                Ll[0] += g11;
+                Ll[1] += g12;
+                Ll[2] += g22;
             }
+            vl[t][0] = sw * dot(a1, a3);
+            vl[t][1] = sw * dot(a2, a3);
+            c3l[t] = sw * a33;
+            const T vd = (adet * T(R::w(0))) * c(CPQ ? q : 0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) b[k] += vd * (l ? T(R::phi(3 + t, k)) : T(R::phi(t, k)));
+        }
+    }
+
+    // Generic coefficients: the three points of zeta level l in a rolled loop.
+    template <class CS>
+    __device__ __forceinline__ static void level_generic(const PrismFrame<T> &f, int l, const CS &c, T A[36], T b[6],
+                                                         bool &poor, bool &neg, bool &degenerate) {
+        using R = Rule<Q_PRISM6>;
+        const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
+        const V3<T> cx = zb * f.ub + zt * f.ut;
+        const V3<T> cy = zb * f.vb + zt * f.vt;
+        const V3<T> a3 = cross(cx, cy);
+        float fxy = 0.0f;
+        if constexpr (PREC != FP64) {
+            const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
+            fxy = dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f);
+        }
 #pragma unroll 1
-            for (int t = 0; t < 3; ++t) {
-                const int q = 3 * l + t;
-                T ph[6];
+        for (int t = 0; t < 3; ++t) {
+            const int q = 3 * l + t;
+            T ph[6];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const T lam = t == k ? T(2.0 / 3.0) : T(1.0 / 6.0);
-                    ph[k] = lam * zb;
-                    ph[k + 3] = lam * zt;
-                }
-                V3<T> g[6], cz;
-                const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
-                if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
-                if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
-                if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
-                neg |= det < T(0);
-                const T vol = abs_t(det) * T(R::w(0));
-                if (KIND == POISSON)
-                    prism_poisson_update_rt<T>(g, vol, c(CPQ ? q : 0), ph, A, b);
-                else
-                    prism_generic_update_rt<T>(g, vol, c, CPQ ? 20 * q : 0, ph, A, b);
+            for (int k = 0; k < 3; ++k) {
+                const T lam = t == k ? T(2.0 / 3.0) : T(1.0 / 6.0);
+                ph[k] = lam * zb;
+                ph[k + 3] = lam * zt;
             }
+            V3<T> g[6], cz;
+            const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
+            if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
+            if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
+            if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
+            neg |= det < T(0);
+            const T vol = abs_t(det) * T(R::w(0));
+            prism_generic_update_rt<T>(g, vol, c, CPQ ? 20 * q : 0, ph, A, b);
         }
-        if (KIND == POISSON) mirror(A);
-        if (degenerate) {
-#pragma unroll
-            for (int k = 0; k < 36; ++k) A[k] = T(0);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) b[k] = T(0);
-            return 4;
-        }
-        return neg ? 2 : 0;
     }
 
     __device__ __forceinline__ static T abs_t(T v) { return v < T(0) ? -v : v; }
@@ -421,6 +452,20 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, FP64, Q_PRISM6, CPQ> {
         for (int k = 1; k < 6; ++k) r[k] = V3<double>{x(3 * k), x(3 * k + 1), x(3 * k + 2)} - x0;
         return PrismMath<KIND, FP64, CPQ>::qloop(r, c, A, b, poor);
     }
+    // Two threads per element: this lane's zeta level; entries 2j + part out.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run_pair(const XS &x, const CS &c, double Ah[18], double bh[3], bool &poor,
+                                                       int part, unsigned mask) {
+        V3<double> r[6];
+        const V3<double> x0 = {x(0), x(1), x(2)};
+        r[0] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 1; k < 6; ++k) r[k] = V3<double>{x(3 * k), x(3 * k + 1), x(3 * k + 2)} - x0;
+        double A[36], b[6];
+        const uint8_t fl = PrismMath<KIND, FP64, CPQ>::template qloop<2>(r, c, A, b, poor, part, mask);
+        pick_half(A, b, Ah, bh, part);
+        return fl;
+    }
 };
 
 template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> {
@@ -435,6 +480,23 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> 
         for (int k = 1; k < 6; ++k)
             r[k] = {diff_hilo(h[3 * k], h[0]), diff_hilo(h[3 * k + 1], h[1]), diff_hilo(h[3 * k + 2], h[2])};
         return PrismMath<KIND, MIXED, CPQ>::qloop(r, c, A, b, poor);
+    }
+    // Two threads per element: this lane's zeta level; entries 2j + part out.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run_pair(const XS &x, const CS &c, float Ah[18], float bh[3], bool &poor,
+                                                       int part, unsigned mask) {
+        HiLo h[18];
+#pragma unroll
+        for (int j = 0; j < 18; ++j) h[j] = split_double(x(j));
+        V3<float> r[6];
+        r[0] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int k = 1; k < 6; ++k)
+            r[k] = {diff_hilo(h[3 * k], h[0]), diff_hilo(h[3 * k + 1], h[1]), diff_hilo(h[3 * k + 2], h[2])};
+        float A[36], b[6];
+        const uint8_t fl = PrismMath<KIND, MIXED, CPQ>::template qloop<2>(r, c, A, b, poor, part, mask);
+        pick_half(A, b, Ah, bh, part);
+        return fl;
     }
     // Flagged element: Jacobian terms in double at every point, narrowed to float.
     template <class XS, class CS>
@@ -496,6 +558,25 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
         for (int k = 0; k < 36; ++k) A[k] = dw_to_double(Ad[k]);
 #pragma unroll
         for (int k = 0; k < 6; ++k) b[k] = dw_to_double(bd[k]);
+        return fl;
+    }
+    // Two threads per element: this lane's zeta level; entries 2j + part out
+    // (each lane converts its own half).
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run_pair(const XS &x, const CS &c, double Ah[18], double bh[3], bool &poor,
+                                                       int part, unsigned mask) {
+        V3<DW> r[6];
+        r[0] = {DW(0), DW(0), DW(0)};
+#pragma unroll
+        for (int k = 1; k < 6; ++k) r[k] = dw_edge_vec(x, k);
+        const DwCoef<CS> cd{c};
+        DW Ad[36], bd[6];
+        const uint8_t fl = PrismMath<KIND, DWORD, CPQ>::template qloop<2>(r, cd, Ad, bd, poor, part, mask);
+        poor = poor || !dw_group_ok<36>(Ad) || !dw_group_ok<6>(bd);
+#pragma unroll
+        for (int j = 0; j < 18; ++j) Ah[j] = dw_to_double(part ? Ad[2 * j + 1] : Ad[2 * j]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) bh[j] = dw_to_double(part ? bd[2 * j + 1] : bd[2 * j]);
         return fl;
     }
     // Flagged element: the whole element in double.
@@ -714,7 +795,11 @@ __device__ __forceinline__ uint8_t fix_elem(const XS &x, const CS &c, const Coef
     }
 }
 
-template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
+//
+// TPE == 2 (prisms, element-contiguous input and output, coefficient arrays):
+// two threads per element, lanes 2j and 2j + 1 of a warp; the block holds
+// blockDim.x / 2 elements and each lane writes every other entry of its element.
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL, int TPE = 1>
 __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, int nb, unsigned char *smem, uint64_t *bar,
                                              unsigned &phase, const TmaMaps *tm = nullptr,
                                              const CoefFn *fn = nullptr) {
@@ -723,8 +808,11 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>;
     constexpr int NAO = SM::NAO;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
-    const int B = blockDim.x;
-    const int tid = threadIdx.x;
+    static_assert(TPE == 1 || (TPE == 2 && ET == PRISM && INL == AOS && OUTL == AOS && CPQ < 2),
+                  "two threads per element: prisms, element-contiguous, coefficient arrays");
+    const int B = blockDim.x / TPE;          // elements per tile
+    const int tid = threadIdx.x / TPE;       // this thread's element in the tile
+    const int sub = threadIdx.x % TPE;       // its lane within the element's group
     double *sX = reinterpret_cast<double *>(smem);
     int *sN = reinterpret_cast<int *>(smem);  // INDEXED: the tile's node indices
     CT *sC = reinterpret_cast<CT *>(smem + SM::x_bytes(B));
@@ -740,7 +828,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     // ---- stage inputs ----
     if (INL == SOA && tm && p.tma_in) {
         // two tensor copies: coordinate planes and coefficient planes of the tile
-        if (tid == 0) {
+        if (threadIdx.x == 0) {
             fence_proxy_async_smem();
             mbar_expect_tx(bar, unsigned(B) * NX * 8u + unsigned(B) * NC * unsigned(sizeof(CT)));
             tma_load_2d(sX, tm->x, int(e0), 0, bar);
@@ -761,7 +849,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         const bool tX = x_ok && ((uint64_t(nb) * (INL == SOA ? 8 : kXe)) % 16 == 0);
         const bool tC = c_ok && ((uint64_t(nb) * (INL == SOA ? 1 : NC) * sizeof(CT)) % 16 == 0);
         const unsigned tx = (tX ? unsigned(nb) * kXe : 0u) + (tC ? unsigned(nb) * NC * unsigned(sizeof(CT)) : 0u);
-        if (tid == 0 && tx) {
+        if (threadIdx.x == 0 && tx) {
             fence_proxy_async_smem();
             mbar_expect_tx(bar, tx);
         }
@@ -789,9 +877,11 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     }
 
     // ---- compute ----
-    CT A[NA], b[NS];
+    CT A[NA], b[NS];   // TPE == 2: this lane's entries 2j + sub in A[j], b[j]
     bool poor = false;
     bool idx_ok = true;  // INDEXED: every node index of this element is in range
+    // lanes that take part in the pairs' exchanges (both lanes of an element)
+    const unsigned pmask = TPE > 1 ? __ballot_sync(0xFFFFFFFFu, active) : 0xFFFFFFFFu;
     if (active) {
         const SmemSrc<CT> cs{INL == SOA ? sC + tid : sC + tid * NC, INL == SOA ? B : 1};
         uint8_t fl;
@@ -809,10 +899,13 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
             }
         } else {
             const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
-            fl = run_elem<ET, KIND, PREC, QUAD, CPQ>(xs, cs, fn, A, b, poor);
+            if constexpr (TPE == 1)
+                fl = run_elem<ET, KIND, PREC, QUAD, CPQ>(xs, cs, fn, A, b, poor);
+            else
+                fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run_pair(xs, cs, A, b, poor, sub, pmask);
         }
         if (PREC != FP64 && poor) fl |= 1;
-        if (p.flags) p.flags[e] = fl;
+        if (p.flags && sub == 0) p.flags[e] = fl;
     }
     if constexpr (OUTL == APPLY) {
         // matrix-free: scatter from registers (indices still in shared memory)
@@ -822,7 +915,13 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         return true;
     }
     __syncthreads();   // every input read: the output records reuse the same shared memory
-    if (active) {
+    if (TPE > 1 && active) {
+#pragma unroll
+        for (int j = 0; j < NA / TPE; ++j) sA[tid * NAO + TPE * j + sub] = A[j];
+#pragma unroll
+        for (int j = 0; j < NS / TPE; ++j) sB[tid * NS + TPE * j + sub] = b[j];
+    }
+    if (TPE == 1 && active) {
         // entry k_out of the written A^e: (r, s) row-major, or its upper triangle
 #pragma unroll
         for (int r = 0; r < NS; ++r)
@@ -842,13 +941,13 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
                 sB[tid * NS + k] = b[k];
         }
     }
-    if (PREC != FP64) append_fixup(p, active && poor, e);
+    if (PREC != FP64) append_fixup(p, active && poor && sub == 0, e);
 
     // ---- store outputs ----
     fence_proxy_async_smem();
     __syncthreads();
     if (out_soa(OUTL) && tm && p.tma_out) {
-        if (tid == 0) {
+        if (threadIdx.x == 0) {
             tma_store_2d(tm->a, int(e0), 0, sA);
             tma_store_2d(tm->b, int(e0), 0, sB);
             bulk_commit();
@@ -866,7 +965,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
             stage_rows_out(Aout + e0 * NAO, 0, sA, 0, 1, nb * NAO, tA);
             stage_rows_out(Bout + e0 * NS, 0, sB, 0, 1, nb * NS, tB);
         }
-        if ((tA || tB) && tid < 32) {
+        if ((tA || tB) && threadIdx.x < 32) {
             bulk_commit();
             bulk_wait_read0();
         }
@@ -895,6 +994,32 @@ __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256)
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
         if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase, &tm, &fn)) return;
+    }
+    if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Prisms with two threads per element (element-contiguous input and output):
+// tiles of blockDim.x / 2 elements, grid-stride over tiles.
+// ---------------------------------------------------------------------------
+template <int KIND, int PREC, int CPQ>
+__global__ void __launch_bounds__(256)
+    pair_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    const int B = blockDim.x / 2;
+    const int64_t ntiles = (p.n + B - 1) / B;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t e0 = tile * B;
+        const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
+        if (!process_tile<PRISM, KIND, PREC, Q_PRISM6, CPQ, AOS, AOS, 2>(p, e0, nb, smem, &bar, phase, &tm, &fn))
+            return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }

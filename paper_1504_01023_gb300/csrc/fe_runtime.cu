@@ -75,8 +75,16 @@ void free_scratch(Scratch &s) {
 // 2 the function of a nodal field.
 static int cpq_of(const fe_elem_args *a) { return a->coef_mode == FE_COEF_FUNCTION_U ? 2 : a->coef_mode == FE_COEF_PER_QPOINT; }
 
-static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int outl) {
+// Two threads per element: prisms with element-contiguous coordinates, full
+// element-contiguous outputs, coefficient arrays and the QSS order.
+static bool pair_ok(fe_elem_type type, const fe_elem_args *a, int outl) {
+    return type == FE_PRISM && a->coords_layout == FE_LAYOUT_AOS && outl == AOS && !a->ordering && cpq_of(a) < 2;
+}
+
+static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int outl, int tpe = 1) {
     const int cpq = cpq_of(a);
+    if (tpe == 2) return pair_ok(type, a, outl) ? kernel_prism_pair(a->kind, a->prec, cpq) : nullptr;
+    if (tpe != 1) return nullptr;
     if (a->ordering) return kernel_study(type, a->kind, a->quad, cpq, a->ordering);
     const int il = a->coords_layout;
     if (type == FE_TET) {
@@ -221,8 +229,6 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
                      const Shape *force, const void *x) {
     if (a->n_elem == 0) return FE_OK;
     const int outl = out_mode(o);
-    const void *k = main_kernel(type, a, outl);
-    if (!k) return set_error(ctx, FE_ERR_UNSUPPORTED, "no kernel for this combination");
     Shape sh = default_shape(type);
     if (force) {
         sh = *force;
@@ -230,6 +236,9 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
         auto it = ctx->shapes.find(shape_key(type, a, o));
         if (it != ctx->shapes.end()) sh = it->second;
     }
+    const void *k = main_kernel(type, a, outl, sh.tpe);
+    if (!k) return set_error(ctx, FE_ERR_UNSUPPORTED, "no kernel for this combination");
+    const int threads = sh.block * sh.tpe;
     const int64_t smem = smem_bytes(type, a, outl, sh.block);
     if (smem + kStaticSmem > ctx->max_smem_optin)
         return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
@@ -241,7 +250,7 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     int64_t grid = ntiles;
     if (sh.persistent) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, sh.block, size_t(smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, size_t(smem));
         grid = std::min<int64_t>(ntiles, int64_t(std::max(per_sm, 1)) * ctx->sms);
     }
     grid = std::min<int64_t>(grid, 0x7FFFFFFF);
@@ -307,12 +316,12 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
         ev1 = pool_event(ctx);
         cudaEventRecord(ev0, st);
     }
-    cudaError_t ce = cudaLaunchKernel(k, dim3(unsigned(grid)), dim3(unsigned(sh.block)), args, size_t(smem), st);
+    cudaError_t ce = cudaLaunchKernel(k, dim3(unsigned(grid)), dim3(unsigned(threads)), args, size_t(smem), st);
     if (ce != cudaSuccess) {
         cudaFuncAttributes fa{};
         cudaFuncGetAttributes(&fa, k);
         std::ostringstream m;
-        m << "cudaLaunchKernel(elem) grid " << grid << " block " << sh.block << " smem " << smem
+        m << "cudaLaunchKernel(elem) grid " << grid << " block " << threads << " smem " << smem
           << " (func: max threads " << fa.maxThreadsPerBlock << ", max dyn smem " << fa.maxDynamicSharedSizeBytes
           << ", static smem " << fa.sharedSizeBytes << ", regs " << fa.numRegs << ")";
         return cuda_check(ctx, ce, m.str().c_str());
@@ -539,17 +548,24 @@ static fe_status integrate(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a
 static void load_tuning_cache(fe_ctx *ctx) {
     if (ctx->tuning_cache_path.empty()) return;
     std::ifstream f(ctx->tuning_cache_path);
-    std::string dev, key;
-    int block, pers;
-    while (f >> dev >> key >> block >> pers) {
-        if (dev == ctx->device_name) ctx->shapes[key] = Shape{block, pers};
+    std::string line;
+    while (std::getline(f, line)) {
+        // device key elements persistent [threads-per-element]
+        std::istringstream ls(line);
+        std::string dev, key;
+        int block = 0, pers = 0, tpe = 1;
+        if (!(ls >> dev >> key >> block >> pers)) continue;
+        if (!(ls >> tpe)) tpe = 1;
+        if (dev == ctx->device_name && block > 0 && (tpe == 1 || tpe == 2)) ctx->shapes[key] = Shape{block, pers, tpe};
     }
 }
 
 static void save_tuning_cache(fe_ctx *ctx) {
     if (ctx->tuning_cache_path.empty()) return;
     std::ofstream f(ctx->tuning_cache_path, std::ios::trunc);
-    for (auto &kv : ctx->shapes) f << ctx->device_name << " " << kv.first << " " << kv.second.block << " " << kv.second.persistent << "\n";
+    for (auto &kv : ctx->shapes)
+        f << ctx->device_name << " " << kv.first << " " << kv.second.block << " " << kv.second.persistent << " "
+          << kv.second.tpe << "\n";
 }
 
 }  // namespace fe
@@ -830,8 +846,42 @@ fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
     Shape sh = default_shape(type);
     auto it = ctx->shapes.find(shape_key(type, args, out));
     if (it != ctx->shapes.end()) sh = it->second;
-    *block_threads = sh.block;
+    *block_threads = sh.block * sh.tpe;
     *persistent = sh.persistent;
+    return FE_OK;
+}
+
+fe_status fe_get_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
+                              fe_launch_shape *shape) {
+    if (!ctx || !shape) return set_error(ctx, FE_ERR_INVALID_ARG, "null argument");
+    fe_status st = fe_check_args(type, args, out);
+    if (st != FE_OK) return st;
+    Shape sh = default_shape(type);
+    auto it = ctx->shapes.find(shape_key(type, args, out));
+    if (it != ctx->shapes.end()) sh = it->second;
+    shape->elems_per_block = sh.block;
+    shape->threads_per_elem = sh.tpe;
+    shape->persistent = sh.persistent;
+    return FE_OK;
+}
+
+fe_status fe_set_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
+                              const fe_launch_shape *shape) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    if (!shape) return set_error(ctx, FE_ERR_INVALID_ARG, "null argument");
+    fe_status st = fe_check_args(type, args, out);
+    if (st != FE_OK) return st;
+    const int B = shape->elems_per_block, t = shape->threads_per_elem;
+    if ((t != 1 && t != 2) || B < 1 || B * t < 32 || B * t > max_block(type, args->prec) || (B * t) % 32 ||
+        (shape->persistent != 0 && shape->persistent != 1))
+        return set_error(ctx, FE_ERR_INVALID_ARG, "bad launch shape");
+    if (t == 2 && !pair_ok(type, args, out_mode(out)))
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "two threads per element: prisms with element-contiguous coordinates "
+                                                  "and outputs, coefficient arrays, QSS order only");
+    if (smem_bytes(type, args, out_mode(out), B) + kStaticSmem > ctx->max_smem_optin)
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
+    ctx->shapes[shape_key(type, args, out)] = Shape{B, shape->persistent, t};
+    save_tuning_cache(ctx);
     return FE_OK;
 }
 
@@ -865,30 +915,32 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const f
     cudaEventCreate(&e1);
     float best = 1e30f;
     Shape best_shape = default_shape(type);
-    for (int B = 64; B <= max_block(type, a->prec); B *= 2) {
-        for (int pers = 0; pers < 2; ++pers) {
-            Shape sh{B, pers};
-            if (smem_bytes(type, a, out_mode(o), B) + kStaticSmem > ctx->max_smem_optin) continue;
-            st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);  // warm-up
-            if (st != FE_OK) break;
-            cudaEventRecord(e0, s);
-            const int reps = 3;
-            for (int r = 0; r < reps && st == FE_OK; ++r) st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);
-            cudaEventRecord(e1, s);
-            if (st != FE_OK) break;
-            cudaError_t ce = cudaEventSynchronize(e1);
-            if (ce != cudaSuccess) {
-                st = cuda_check(ctx, ce, "tuning");
-                break;
-            }
-            float t = 0.0f;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (t < best) {
-                best = t;
-                best_shape = sh;
-            }
-        }
+    // candidates: elements per tile x grid kind, and for prisms with element-
+    // contiguous data also two threads per element
+    std::vector<Shape> cands;
+    for (int tpe = 1; tpe <= (pair_ok(type, a, out_mode(o)) ? 2 : 1); ++tpe)
+        for (int B = 64 / tpe; B * tpe <= max_block(type, a->prec); B *= 2)
+            for (int pers = 0; pers < 2; ++pers) cands.push_back(Shape{B, pers, tpe});
+    for (const Shape &sh : cands) {
+        if (smem_bytes(type, a, out_mode(o), sh.block) + kStaticSmem > ctx->max_smem_optin) continue;
+        st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);  // warm-up
         if (st != FE_OK) break;
+        cudaEventRecord(e0, s);
+        const int reps = 3;
+        for (int r = 0; r < reps && st == FE_OK; ++r) st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);
+        cudaEventRecord(e1, s);
+        if (st != FE_OK) break;
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) {
+            st = cuda_check(ctx, ce, "tuning");
+            break;
+        }
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best) {
+            best = t;
+            best_shape = sh;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -29,8 +29,9 @@ struct Scratch {
 };
 
 struct Shape {
-    int block = 0;          // threads per block = elements per tile
+    int block = 0;          // elements per tile
     int persistent = 0;     // 1: grid = SMs x resident blocks, tiles strided
+    int tpe = 1;            // threads per element (2: prisms, element-contiguous)
 };
 
 struct ServeState;          // fe_serve.cu
