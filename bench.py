@@ -166,6 +166,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def shape_dict(shape):
+    """A launch shape (elements per block, persistent[, threads per element]) as JSON."""
+    return {"elements_per_block": shape[0], "persistent": shape[1],
+            "threads_per_element": shape[2] if len(shape) > 2 else 1}
+
+
 def ncu_traffic(kernel_tag: str):
     """DRAM bytes per launch of a kernel from profiles/traffic.md, if its record was
     taken on the current kernel sources (otherwise None)."""
@@ -356,7 +362,7 @@ def run_native(args):
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
               "config": {"workload": wl_name, "n_elem_per_gpu": n, "bytes_per_element": bpe,
-                         "launch_shape": {"block": shape[0], "persistent": shape[1]},
+                         "launch_shape": shape_dict(shape),
                          "l2": "inputs larger than L2: %.2f GB read+written per step per GPU" % (n * bpe / 1e9),
                          "parallelism": f"weak: {world} independent mesh(es), one per GPU"},
               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -431,7 +437,16 @@ def prism_form(ctx, dev, api, args):
     k_ms = kms / kn
     peak, _ = measured_peaks()
     gbs = n * bpe / (k_ms * 1e-3) / 1e9
-    del C, out
+    del out
+    # the same prisms in the double-precision forms (tuned shapes, which may put
+    # two threads on each element)
+    gen = {"workload": "the same 2,000,000 prisms and coefficients, results within 1e-12 of the FP64 oracle"}
+    C64 = C.double()
+    del C
+    for name, prec in (("double_word", api.FP64_DW), ("native_fp64", api.FP64)):
+        gen[name] = _fp64_run(ctx, dev, api, X, C64, api.PRISM, api.GENERIC, api.QUAD_PRISM6, prec, args,
+                              cm=api.PER_QPOINT)
+    del C64
     torch.cuda.empty_cache()
     # the Laplace kind on the same prisms: d^0 per point, in the three precision forms
     from paper_1504_01023_gb300 import meshgen
@@ -446,7 +461,8 @@ def prism_form(ctx, dev, api, args):
     torch.cuda.empty_cache()
     return {"workload": PRISM_WORKLOAD, "value": n / step_ms / 1e3, "unit": "Melem/s", "ms_per_step": step_ms,
             "kernel_ms": k_ms, "bytes_per_element": bpe, "achieved_gbs": gbs, "hbm_frac": gbs / peak,
-            "launch_shape": {"block": shape[0], "persistent": shape[1]}, "dtype": "f32", "laplace": lap}
+            "launch_shape": {"elements_per_block": shape[0], "persistent": shape[1], "threads_per_element": shape[2]},
+            "dtype": "f32", "double_precision_forms": gen, "laplace": lap}
 
 
 def _indexed_run(ctx, dev, api, et, nodes, conn, coefs, kind, quad, cm, args):
@@ -483,7 +499,7 @@ def _indexed_run(ctx, dev, api, et, nodes, conn, coefs, kind, quad, cm, args):
     return {"value": n / k_ms / 1e3, "unit": "Melem/s", "kernel_ms": k_ms, "nodes": len(nodes),
             "bytes_per_element": total / n, "bytes_per_element_element_contiguous":
                 api.bytes_per_element(et, kind, quad, cm, api.FP32_MIXED),
-            "achieved_gbs": gbs, "hbm_frac": gbs / peak, "launch_shape": {"block": shape[0], "persistent": shape[1]}}
+            "achieved_gbs": gbs, "hbm_frac": gbs / peak, "launch_shape": shape_dict(shape)}
 
 
 def indexed_form(ctx, dev, api, coefs, args):
@@ -670,7 +686,7 @@ def coef_function_form(ctx, dev, api, args):
     return {"workload": "2,000,000 generic prisms, PRISM6, coefficients at every point from c(u) of a nodal field "
                         "(quadratic in u), mixed form, element-contiguous order", "value": n / k_ms / 1e3,
             "unit": "Melem/s", "kernel_ms": k_ms, "bytes_per_element": bpe, "achieved_gbs": gbs,
-            "hbm_frac": gbs / peak, "launch_shape": {"block": shape[0], "persistent": shape[1]}}
+            "hbm_frac": gbs / peak, "launch_shape": shape_dict(shape)}
 
 
 def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args, cm=None):
@@ -680,7 +696,7 @@ def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args, cm=None):
     cm = api.PER_ELEMENT if cm is None else cm
     out = api.alloc_out(et, n, prec, api.AOS, dev, with_flags=True)
     kw = dict(kind=kind, quad=quad, coef_mode=cm, prec=prec, layout=api.AOS, out_layout=api.AOS)
-    ctx.tune(et, X, C, out=out, **kw)
+    shape = ctx.tune(et, X, C, out=out, **kw)
     for _ in range(3):
         ctx.integrate(et, X, C, out=out, **kw)
     torch.cuda.synchronize(dev)
@@ -698,7 +714,8 @@ def _fp64_run(ctx, dev, api, X, C, et, kind, quad, prec, args, cm=None):
     peak, src = measured_peaks()
     gbs = n * bpe / (k_ms * 1e-3) / 1e9
     return {"value": n / k_ms / 1e3, "unit": "Melem/s", "kernel_ms": k_ms, "bytes_per_element": bpe,
-            "achieved_gbs": gbs, "hbm_frac": gbs / peak, "peak_source": src, "flagged_to_fp64": flagged}
+            "achieved_gbs": gbs, "hbm_frac": gbs / peak, "peak_source": src, "flagged_to_fp64": flagged,
+            "launch_shape": {"elements_per_block": shape[0], "persistent": shape[1], "threads_per_element": shape[2]}}
 
 
 def fp64_form(ctx, dev, api, mesh, coefs, args):
