@@ -266,7 +266,9 @@ fe_status fe_mesh_release(fe_ctx *ctx, int64_t mesh_id);
  * captured into a CUDA graph on the first submission of an item list (same items
  * byte for byte, i.e. same pointers and sizes) and replayed on later ones; the
  * last 8 lists are kept. With autotune on, the first submission times tiles of
- * 64, 128 and 256 elements and keeps the fastest.
+ * 64, 128 and 256 elements and, when the list holds prisms, one or two threads
+ * per prism element (as described at fe_tune), and keeps the fastest; without,
+ * 128 elements and one thread. fe_batch_set_shape pins the shape instead.
  * Items must be FE_FP32_MIXED, device memory, element-contiguous (AOS) inputs
  * and outputs (FE_ERR_UNSUPPORTED otherwise). At most 2^23 items.
  */
@@ -389,6 +391,13 @@ fe_status fe_get_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args
                               fe_launch_shape *shape);
 fe_status fe_set_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                               const fe_launch_shape *shape);
+/* Pin the shape of batch plans built from now on (fe_batch_submit of a new item
+   list): elems_per_block (32..256, a multiple of 32) elements per tile for every
+   combination, threads_per_elem (1 or 2) threads per prism element, at most 256
+   threads per block; persistent is ignored (batched kernels are persistent).
+   NULL returns to tuned (autotune on) or default shapes. Lists already submitted
+   keep their plans for the shape they were built with. */
+fe_status fe_batch_set_shape(fe_ctx *ctx, const fe_launch_shape *shape);
 
 /*
  * Mixed-precision tetrahedron integration that allocates nothing (the paper has

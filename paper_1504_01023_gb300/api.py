@@ -103,6 +103,7 @@ _SIGS = [
                                            ctypes.POINTER(LaunchShape)]),
     ("fe_set_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
                                            ctypes.POINTER(LaunchShape)]),
+    ("fe_batch_set_shape", ctypes.c_int, [_P, ctypes.POINTER(LaunchShape)]),
     ("fe_serve_submit_n", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_release_n", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     ("fe_apply_tet", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), _P, _P, _P, _P, _P]),
@@ -430,6 +431,15 @@ class Context:
 
     def mesh_release(self, mesh_id: int):
         _check(load().fe_mesh_release(self.h, mesh_id), self.h)
+
+    def batch_set_shape(self, block=None, tpe=1):
+        """Pin the shape of new batch plans (block elements per tile, tpe threads per
+        prism element), or return to tuned/default shapes with block=None."""
+        if block is None:
+            _check(load().fe_batch_set_shape(self.h, None), self.h)
+        else:
+            sh = LaunchShape(block, tpe, 1)
+            _check(load().fe_batch_set_shape(self.h, ctypes.byref(sh)), self.h)
 
     def batch_submit(self, items, stream=None):
         """items: list of (elem_type, ElemArgs, Out)."""

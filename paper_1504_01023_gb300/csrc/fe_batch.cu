@@ -40,12 +40,14 @@ struct ClassLaunch {
 struct BatchPlan {
     size_t key = 0;
     std::vector<unsigned char> items_bytes;
+    int pinned_block = 0, pinned_tpe = 1;   // the pinned shape it was built with (block 0: none)
     BatchItemDev *d_items = nullptr;
     BatchSeg *d_segs = nullptr;
     unsigned n_items = 0, n_segs = 0;
     unsigned *d_counter = nullptr;   // kCombos counters
     Scratch scratch;
-    int block = 128;
+    int block = 128;                 // elements per tile
+    int prism_tpe = 1;               // threads per prism element
     std::vector<ClassLaunch> classes;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -78,6 +80,7 @@ void batch_destroy(fe_ctx *ctx) {
 // used only to launch the heaviest combinations first.
 static double combo_cost(int combo) {
     static const double cost[12] = {1.0, 1.0, 1.1, 1.2, 1.4, 1.5, 1.5, 1.8, 2.5, 2.6, 6.0, 8.0};
+    if (combo >= 12 && combo < kCombos) combo -= 4;   // the same prisms, two threads each
     return combo >= 0 && combo < 12 ? cost[combo] : 1.0;
 }
 
@@ -124,6 +127,8 @@ static int64_t g_attr_set[kCombos] = {0};
 static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes, int B) {
     for (auto &cl : classes) {
         const void *k = kernel_batch(cl.combo);
+        const int threads = B * batch_tpe(cl.combo);
+        if (threads > 256) return set_error(ctx, FE_ERR_UNSUPPORTED, "batched tile of more than 256 threads");
         cl.smem = batch_smem_bytes(cl.combo, B);
         if (cl.smem + 1024 > ctx->max_smem_optin)
             return set_error(ctx, FE_ERR_UNSUPPORTED, "batched tile does not fit in shared memory");
@@ -146,7 +151,7 @@ static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes, in
             if (it != occ.end()) {
                 per_sm = it->second;
             } else {
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, B, size_t(cl.smem));
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, size_t(cl.smem));
                 occ[{cl.combo, B}] = per_sm;
             }
         }
@@ -186,7 +191,8 @@ static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st, bool
         unsigned n_segs = cl.n_segs, n_tiles = cl.n_tiles;
         unsigned *counter = pl->d_counter + cl.combo;
         void *args[] = {&pl->d_items, &pl->n_items, &segs, &n_segs, &n_tiles, &counter, &status};
-        e = cudaLaunchKernel(kernel_batch(cl.combo), dim3(cl.grid), dim3(pl->block), args, size_t(cl.smem), st);
+        e = cudaLaunchKernel(kernel_batch(cl.combo), dim3(cl.grid), dim3(pl->block * batch_tpe(cl.combo)), args,
+                             size_t(cl.smem), st);
         if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
     }
     unsigned long long *list = pl->scratch.fix_list;
@@ -203,6 +209,8 @@ static int plan_launches(const BatchPlan *pl) { return int(pl->classes.size()) +
 static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size_t key, BatchPlan *&out) {
     auto *pl = new BatchPlan();
     pl->key = key;
+    pl->pinned_block = ctx->batch_shape.block;
+    pl->pinned_tpe = ctx->batch_shape.tpe;
     pl->items_bytes.assign(reinterpret_cast<const unsigned char *>(items),
                            reinterpret_cast<const unsigned char *>(items) + sizeof(fe_batch_item) * n);
     std::vector<BatchItemDev> dev(n);
@@ -240,40 +248,59 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
                         "cudaMemcpy(items)");
     if (!ctx->batch->capture_stream) cudaStreamCreateWithFlags(&ctx->batch->capture_stream, cudaStreamNonBlocking);
     cudaStream_t cs = ctx->batch->capture_stream;
-    // launch shape: the tuned elements per tile for this plan, or 128
-    int bestB = 128;
-    if (st == FE_OK && ctx->autotune) {
+    // launch shape: the tuned elements per tile and threads per prism for this
+    // plan, or 128 and one
+    bool any_prism = false;
+    for (const auto &d : dev) any_prism = any_prism || (d.combo >= 8 && d.combo < 12);
+    auto set_prism_tpe = [&](int tpe) -> fe_status {
+        for (auto &d : dev)
+            if (d.combo >= 8) d.combo = tpe == 2 ? batch_pair_combo(d.combo) : (d.combo >= 12 ? d.combo - 4 : d.combo);
+        return cuda_check(ctx, cudaMemcpy(pl->d_items, dev.data(), sizeof(BatchItemDev) * n, cudaMemcpyHostToDevice),
+                          "cudaMemcpy(items)");
+    };
+    int bestB = 128, bestT = 1;
+    if (ctx->batch_shape.block > 0) {            // pinned by fe_batch_set_shape
+        bestB = ctx->batch_shape.block;
+        bestT = ctx->batch_shape.tpe;
+    } else if (st == FE_OK && ctx->autotune) {
         float best = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int B : {64, 128, 256}) {
-            st = upload_segs(ctx, pl, dev, B);
-            if (st == FE_ERR_UNSUPPORTED) {   // tile too large for shared memory at this size
-                st = FE_OK;
-                continue;
-            }
-            if (st != FE_OK) break;
-            st = enqueue_batch(ctx, pl, cs);  // warm-up
-            cudaEventRecord(e0, cs);
-            for (int r = 0; r < 3 && st == FE_OK; ++r) st = enqueue_batch(ctx, pl, cs);
-            cudaEventRecord(e1, cs);
-            if (st != FE_OK) break;
-            cudaError_t ce = cudaEventSynchronize(e1);
-            if (ce != cudaSuccess) {
-                st = cuda_check(ctx, ce, "batch tuning");
-                break;
-            }
-            float t;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (t < best) {
-                best = t;
-                bestB = B;
+        for (int tpe = 1; tpe <= (any_prism ? 2 : 1) && st == FE_OK; ++tpe) {
+            st = set_prism_tpe(tpe);
+            for (int B : {64, 128, 256}) {
+                if (st != FE_OK) break;
+                st = upload_segs(ctx, pl, dev, B);
+                if (st == FE_ERR_UNSUPPORTED) {   // tile too large for shared memory or threads
+                    st = FE_OK;
+                    continue;
+                }
+                if (st != FE_OK) break;
+                st = enqueue_batch(ctx, pl, cs);  // warm-up
+                cudaEventRecord(e0, cs);
+                for (int r = 0; r < 3 && st == FE_OK; ++r) st = enqueue_batch(ctx, pl, cs);
+                cudaEventRecord(e1, cs);
+                if (st != FE_OK) break;
+                cudaError_t ce = cudaEventSynchronize(e1);
+                if (ce != cudaSuccess) {
+                    st = cuda_check(ctx, ce, "batch tuning");
+                    break;
+                }
+                float t;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (t < best) {
+                    best = t;
+                    bestB = B;
+                    bestT = tpe;
+                }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
+    if (st == FE_OK && any_prism) st = set_prism_tpe(bestT);
+    pl->prism_tpe = bestT;
     if (st == FE_OK) st = upload_segs(ctx, pl, dev, bestB);
     // capture the launch sequence once; later submissions replay it
     if (st == FE_OK) {
@@ -432,6 +459,19 @@ fe_status fe_mesh_release(fe_ctx *ctx, int64_t mesh_id) {
     return FE_OK;
 }
 
+fe_status fe_batch_set_shape(fe_ctx *ctx, const fe_launch_shape *shape) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    if (!shape) {
+        ctx->batch_shape = Shape{0, 1, 1};
+        return FE_OK;
+    }
+    const int B = shape->elems_per_block, t = shape->threads_per_elem;
+    if ((t != 1 && t != 2) || B < 32 || B % 32 || B * t > 256)
+        return set_error(ctx, FE_ERR_INVALID_ARG, "bad batched launch shape");
+    ctx->batch_shape = Shape{B, 1, t};
+    return FE_OK;
+}
+
 fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, void *stream) {
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
     if (!items || n_items <= 0) return set_error(ctx, FE_ERR_INVALID_ARG, "empty batch");
@@ -454,6 +494,7 @@ fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
     BatchPlan *pl = nullptr;
     for (auto it = ctx->batch->plans.begin(); it != ctx->batch->plans.end(); ++it) {
         if ((*it)->key == key && (*it)->items_bytes.size() == sizeof(fe_batch_item) * size_t(n_items) &&
+            (*it)->pinned_block == ctx->batch_shape.block && (*it)->pinned_tpe == ctx->batch_shape.tpe &&
             memcmp((*it)->items_bytes.data(), items, (*it)->items_bytes.size()) == 0) {
             pl = *it;
             ctx->batch->plans.erase(it);

@@ -8,22 +8,26 @@
 namespace fe {
 
 template <int COMBO> struct ComboCfg;
-#define FE_COMBO(ID, ET, KD, Q, CP)                                    \
-    template <> struct ComboCfg<ID> {                                  \
-        static constexpr int et = ET, kind = KD, quad = Q, cpq = CP;   \
+#define FE_COMBO(ID, ET, KD, Q, CP, TP)                                          \
+    template <> struct ComboCfg<ID> {                                            \
+        static constexpr int et = ET, kind = KD, quad = Q, cpq = CP, tpe = TP;   \
     };
-FE_COMBO(0, TET, POISSON, Q_TET1, 0)
-FE_COMBO(1, TET, POISSON, Q_TET1, 1)
-FE_COMBO(2, TET, POISSON, Q_TET4, 0)
-FE_COMBO(3, TET, POISSON, Q_TET4, 1)
-FE_COMBO(4, TET, GENERIC, Q_TET1, 0)
-FE_COMBO(5, TET, GENERIC, Q_TET1, 1)
-FE_COMBO(6, TET, GENERIC, Q_TET4, 0)
-FE_COMBO(7, TET, GENERIC, Q_TET4, 1)
-FE_COMBO(8, PRISM, POISSON, Q_PRISM6, 0)
-FE_COMBO(9, PRISM, POISSON, Q_PRISM6, 1)
-FE_COMBO(10, PRISM, GENERIC, Q_PRISM6, 0)
-FE_COMBO(11, PRISM, GENERIC, Q_PRISM6, 1)
+FE_COMBO(0, TET, POISSON, Q_TET1, 0, 1)
+FE_COMBO(1, TET, POISSON, Q_TET1, 1, 1)
+FE_COMBO(2, TET, POISSON, Q_TET4, 0, 1)
+FE_COMBO(3, TET, POISSON, Q_TET4, 1, 1)
+FE_COMBO(4, TET, GENERIC, Q_TET1, 0, 1)
+FE_COMBO(5, TET, GENERIC, Q_TET1, 1, 1)
+FE_COMBO(6, TET, GENERIC, Q_TET4, 0, 1)
+FE_COMBO(7, TET, GENERIC, Q_TET4, 1, 1)
+FE_COMBO(8, PRISM, POISSON, Q_PRISM6, 0, 1)
+FE_COMBO(9, PRISM, POISSON, Q_PRISM6, 1, 1)
+FE_COMBO(10, PRISM, GENERIC, Q_PRISM6, 0, 1)
+FE_COMBO(11, PRISM, GENERIC, Q_PRISM6, 1, 1)
+FE_COMBO(12, PRISM, POISSON, Q_PRISM6, 0, 2)
+FE_COMBO(13, PRISM, POISSON, Q_PRISM6, 1, 2)
+FE_COMBO(14, PRISM, GENERIC, Q_PRISM6, 0, 2)
+FE_COMBO(15, PRISM, GENERIC, Q_PRISM6, 1, 2)
 #undef FE_COMBO
 
 template <int ID>
@@ -31,7 +35,8 @@ __device__ __forceinline__ bool tile_combo(const BatchItemDev *item, long long f
                                            uint64_t *bar, unsigned *phase) {
     using K = ComboCfg<ID>;
     const ElemParams p = item->p;
-    return process_tile<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS>(p, first, count, smem, bar, *phase);
+    return process_tile<K::et, K::kind, MIXED, K::quad, K::cpq, AOS, AOS, K::tpe>(p, first, count, smem, bar,
+                                                                                   *phase);
 }
 
 template <int ID> __device__ __forceinline__ void fix_combo(const ElemParams &p, int64_t e) {
@@ -81,8 +86,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchItemDev *__restri
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     __shared__ TileRef s_ref[2];
-    const int B = blockDim.x;
-    const int R = B > 32 ? 32 : 0;  // the looking-up thread (not the copy issuer, thread 0)
+    const int B = blockDim.x / ComboCfg<ID>::tpe;                 // elements per tile
+    const int R = blockDim.x > 32 ? 32 : 0;  // the looking-up thread (not the copy issuer, thread 0)
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -134,6 +139,10 @@ __global__ void __launch_bounds__(256) batch_fixup_kernel(const BatchItemDev *__
             case 9: fix_combo<9>(p, e); break;
             case 10: fix_combo<10>(p, e); break;
             case 11: fix_combo<11>(p, e); break;
+            case 12: fix_combo<12>(p, e); break;
+            case 13: fix_combo<13>(p, e); break;
+            case 14: fix_combo<14>(p, e); break;
+            case 15: fix_combo<15>(p, e); break;
             default: atomicOr(status, ST_BAD_TILE); break;
         }
     }
@@ -158,6 +167,10 @@ long long batch_smem_bytes(int combo, int B) {
         case 9: return smem_of<9>(B);
         case 10: return smem_of<10>(B);
         case 11: return smem_of<11>(B);
+        case 12: return smem_of<12>(B);
+        case 13: return smem_of<13>(B);
+        case 14: return smem_of<14>(B);
+        case 15: return smem_of<15>(B);
     }
     return -1;
 }
@@ -176,6 +189,10 @@ const void *kernel_batch(int combo) {
         case 9: return reinterpret_cast<const void *>(&batch_kernel<9>);
         case 10: return reinterpret_cast<const void *>(&batch_kernel<10>);
         case 11: return reinterpret_cast<const void *>(&batch_kernel<11>);
+        case 12: return reinterpret_cast<const void *>(&batch_kernel<12>);
+        case 13: return reinterpret_cast<const void *>(&batch_kernel<13>);
+        case 14: return reinterpret_cast<const void *>(&batch_kernel<14>);
+        case 15: return reinterpret_cast<const void *>(&batch_kernel<15>);
     }
     return nullptr;
 }

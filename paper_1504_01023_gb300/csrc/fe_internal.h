@@ -119,16 +119,19 @@ struct BatchSeg {
     long long n;              // elements of the item
 };
 // Dense index of the 12 (type, kind, rule, coefficient mode) combinations of the
-// batched kernel, or -1.
+// batched kernel with one thread per element, or -1.
 inline int batch_combo(int type, int kind, int quad, int cpq) {
     if (type == TET && (quad == Q_TET1 || quad == Q_TET4)) return ((kind * 2 + (quad == Q_TET4)) * 2 + cpq);
     if (type == PRISM && quad == Q_PRISM6) return 8 + kind * 2 + cpq;
     return -1;
 }
+// Combinations 12..15: the prism combinations 8..11 with two threads per element.
+constexpr int kCombos = 16;
+inline int batch_tpe(int combo) { return combo >= 12 ? 2 : 1; }
+inline int batch_pair_combo(int combo) { return combo >= 8 && combo < 12 ? combo + 4 : combo; }
 const void *kernel_batch(int combo);   // persistent kernel of one combination
 const void *kernel_batch_fixup();
 const void *kernel_selftest_wait();
-constexpr int kCombos = 12;
 // Dynamic shared memory of one block of the batched kernel for a combination.
 long long batch_smem_bytes(int combo, int block);
 

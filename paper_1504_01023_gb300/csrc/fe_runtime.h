@@ -67,6 +67,7 @@ struct fe_ctx {
 
     // autotuner
     int autotune = 0;
+    fe::Shape batch_shape{0, 1, 1};  // pinned shape of new batch plans (block 0: tuned or default)
     std::string tuning_cache_path;
     std::map<std::string, fe::Shape> shapes;
 

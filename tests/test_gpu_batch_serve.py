@@ -90,6 +90,34 @@ def test_batch_matches_single_calls_and_oracle(ctx, mix, autotune):
         bctx.close()
 
 
+@pytest.mark.parametrize("block,tpe", [(64, 2), (128, 2), (32, 1), (256, 1)])
+def test_batch_pinned_shapes(mix, block, tpe):
+    """Pinned batch shapes, including two threads per prism element: every set
+    against the oracle, flags as in a single call."""
+    bctx = api.Context(0)
+    bctx.batch_set_shape(block, tpe)
+    outs = [api.alloc_out(et, n, api.FP32_MIXED, api.AOS, "cuda") for (et, kind, quad, cpq, n, _) in MIX]
+    items = _items(mix, outs)
+    bctx.batch_submit(items)
+    bctx.batch_submit(items)                    # graph replay
+    bctx.sync()
+    for (et, kind, quad, cpq, n, _), (mesh, c, X, C), out in zip(MIX, mix, outs):
+        An, bn, fn = (t.double().cpu().numpy() if t.dtype != torch.uint8 else t.cpu().numpy() for t in out)
+        ref = bctx.integrate(et, X, C, kind, quad, api.PER_QPOINT if cpq else api.PER_ELEMENT, api.FP32_MIXED,
+                             api.AOS, api.AOS)
+        bctx.sync()
+        assert np.array_equal(fn, ref[2].cpu().numpy())
+        Ao, bo, _ = oracle.integrate(et, kind, ORACLE_RULE[quad], mesh, c, coef_per_q=bool(cpq), n_threads=8)
+        ea, eb = max_errors(An, bn, Ao, bo)
+        assert ea <= TOL[api.FP32_MIXED] and eb <= TOL[api.FP32_MIXED], (et, kind, quad, cpq, ea, eb)
+    with pytest.raises(api.FeError):
+        bctx.batch_set_shape(256, 2)                 # 512 threads
+    with pytest.raises(api.FeError):
+        bctx.batch_set_shape(48, 1)                  # not a multiple of 32
+    bctx.batch_set_shape(None)
+    bctx.close()
+
+
 def test_batch_rejects_unsupported_items(ctx, mix):
     (et, kind, quad, cpq, n, _), (mesh, c, X, C) = MIX[2], mix[2]
     out = api.alloc_out(et, n, api.FP32_MIXED, api.SOA, "cuda")
