@@ -166,6 +166,24 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+# The paper's own measurements (Table 7, Sec. 5): best loop ordering, ns per
+# element, double precision, OpenCL, on other hardware. Context only: its workloads
+# are per-point d^0 (Laplace) and per-element coefficients (convection-diffusion),
+# 4-point tetrahedra and 6-point prisms; mesh sizes are not given.
+PAPER_TABLE7_NS = {
+    "Tesla K20m": {"laplace_tet": 2.02, "cd_tet": 4.46, "laplace_prism": 12.80, "cd_prism": 15.58},
+    "Xeon Phi 5110P": {"laplace_tet": 8.77, "cd_tet": 15.97, "laplace_prism": 25.09, "cd_prism": 33.29},
+    "2x Xeon E5-2620": {"laplace_tet": 17.76, "cd_tet": 24.86, "laplace_prism": 49.74, "cd_prism": 64.27},
+}
+
+
+def paper_context():
+    return {"source": "the paper's Table 7: best of its three loop orderings, ns per element, FP64 OpenCL, "
+                      "on the hardware named; other machines, context only (not a target)",
+            "melem_s": {hw: {case: round(1000.0 / ns, 1) for case, ns in cases.items()}
+                        for hw, cases in PAPER_TABLE7_NS.items()}}
+
+
 def shape_dict(shape):
     """A launch shape (elements per block, persistent[, threads per element]) as JSON."""
     return {"elements_per_block": shape[0], "persistent": shape[1],
@@ -391,6 +409,7 @@ def run_native(args):
             result["e2e"] = e2e(ctx, api, mesh, coefs, args)
         if not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(mesh, coefs)
+        result["paper_context"] = paper_context()
     elif rank == 0:
         result["e2e"] = {"value": None, "unit": "Melem/s", "note": "measured at N=1 only"}
     if rank == 0:
