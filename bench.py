@@ -208,18 +208,34 @@ def ncu_traffic(kernel_tag: str):
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(mesh, coefs, target_s=10.0):
+def cpu_baseline(mesh, coefs, target_s=10.0, gpu_out=None):
     """The FP64 oracle as it stands, on all host cores, over repeated passes of the
     workload's elements (a bounded sample of about target_s seconds of CPU work:
-    whole passes while they fit, then a leading part of one more)."""
+    whole passes while they fit, then a leading part of one more). With the GPU's
+    results of the timed steps, the oracle's results of its first sample (the
+    leading 50,000 elements) also give the error statistics of those elements."""
     import oracle
     cores = os.cpu_count() or 1
     c = coefs.astype(np.float32).astype(np.float64)
     n = len(mesh)
     probe = min(n, 50_000)
     t = time.perf_counter()
-    oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:probe], c[:probe], n_threads=cores)
+    Ao, bo, _ = oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:probe], c[:probe], n_threads=cores)
     rate = probe / max(time.perf_counter() - t, 1e-6)
+    errors = None
+    if gpu_out is not None:
+        A, b, f = gpu_out
+        An = A[:probe].double().cpu().numpy().reshape(probe, 4, 4)
+        bn = b[:probe].double().cpu().numpy().reshape(probe, 4)
+        flagged = (f[:probe].cpu().numpy() & 1) != 0
+        errors = {"elements": f"the leading {probe:,} elements of the timed steps' results",
+                  "metric": "relative Frobenius error per element against the FP64 oracle (tolerance 2e-5)",
+                  "flagged": int(flagged.sum())}
+        for name, e in (("A", oracle.rel_frobenius(An, Ao)), ("b", oracle.rel_frobenius(bn, bo))):
+            for grp, sel in (("unflagged", ~flagged), ("flagged", flagged)):
+                v = e[sel]
+                errors[f"{name}_{grp}"] = ({"max": float(v.max()), "p99.9": float(np.quantile(v, 0.999))}
+                                           if len(v) else None)
     total = int(min(max(probe, rate * target_s), 50 * n))
     done = 0
     t = time.perf_counter()
@@ -233,11 +249,14 @@ def cpu_baseline(mesh, coefs, target_s=10.0):
     t1 = time.perf_counter()
     oracle.integrate(oracle.TET, oracle.GENERIC, oracle.Q_TET4, mesh[:m1], c[:m1], n_threads=1)
     one = m1 / (time.perf_counter() - t1) / 1e6
-    return {"value": done / dt / 1e6, "unit": "Melem/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done:,} element integrations ({done / n:.2f} passes over the {n:,}-element workload), FP64, "
-                      f"OpenMP over elements", "seconds": dt,
-            "single_thread": {"value": one, "unit": "Melem/s", "sample": f"first {m1:,} elements, one thread"},
-            "cpu": cpu_model()}
+    res = {"value": done / dt / 1e6, "unit": "Melem/s", "cores": cores, "kind": "oracle",
+           "sample": f"{done:,} element integrations ({done / n:.2f} passes over the {n:,}-element workload), FP64, "
+                     f"OpenMP over elements", "seconds": dt,
+           "single_thread": {"value": one, "unit": "Melem/s", "sample": f"first {m1:,} elements, one thread"},
+           "cpu": cpu_model()}
+    if errors is not None:
+        res["gpu_error_vs_oracle"] = errors
+    return res
 
 
 def cpu_model():
@@ -408,7 +427,7 @@ def run_native(args):
         if not args.no_e2e:
             result["e2e"] = e2e(ctx, api, mesh, coefs, args)
         if not args.no_cpu_baseline:
-            result["cpu_baseline"] = cpu_baseline(mesh, coefs)
+            result["cpu_baseline"] = cpu_baseline(mesh, coefs, gpu_out=out)
         result["paper_context"] = paper_context()
     elif rank == 0:
         result["e2e"] = {"value": None, "unit": "Melem/s", "note": "measured at N=1 only"}

@@ -317,6 +317,10 @@ fe_status fe_serve_submit(fe_ctx *ctx, const fe_request *req, uint64_t *ticket);
 /* FE_NOT_READY while waiting or running; FE_OK with res filled when done.
    Thread-safe. */
 fe_status fe_serve_poll(fe_ctx *ctx, uint64_t ticket, fe_result *res);
+/* Withdraw a request that has not been launched yet: FE_OK and its ticket is
+   forgotten. FE_ERR_INVALID_ARG if the ticket is unknown or the request is
+   already running or done (release it once it is done). Thread-safe. */
+fe_status fe_serve_cancel(fe_ctx *ctx, uint64_t ticket);
 /* Free a finished request's outputs and return their bytes to the budget. */
 fe_status fe_serve_release(fe_ctx *ctx, uint64_t ticket);
 /* Several requests at once (host arrays of n entries), under one lock and one

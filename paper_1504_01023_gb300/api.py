@@ -99,6 +99,7 @@ _SIGS = [
     ("fe_serve_submit", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_poll", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(Result)]),
     ("fe_serve_release", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("fe_serve_cancel", ctypes.c_int, [_P, ctypes.c_uint64]),
     ("fe_get_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
                                            ctypes.POINTER(LaunchShape)]),
     ("fe_set_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
@@ -510,6 +511,11 @@ class Context:
             ctypes.pointer(r)[0] = res[i]
             out.append((tks[i], r))
         return out
+
+    def serve_cancel(self, ticket):
+        """Withdraw a request that has not been launched yet."""
+        _check(load().fe_serve_cancel(self.h, ticket), self.h)
+        self._keep.pop(ticket, None)
 
     def serve_release(self, ticket):
         self._keep.pop(ticket, None)

@@ -473,6 +473,7 @@ fe_status fe_batch_set_shape(fe_ctx *ctx, const fe_launch_shape *shape) {
 }
 
 fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, void *stream) {
+    TraceRange tr("fe_batch_submit");
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
     if (!items || n_items <= 0) return set_error(ctx, FE_ERR_INVALID_ARG, "empty batch");
     if (n_items > (1 << 23)) return set_error(ctx, FE_ERR_INVALID_ARG, "too many batch items");

@@ -743,10 +743,12 @@ const char *fe_last_error(fe_ctx *ctx) {
 }
 
 fe_status fe_integrate_tet(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream) {
+    TraceRange tr("fe_integrate_tet");
     return integrate(ctx, FE_TET, args, out, stream);
 }
 
 fe_status fe_integrate_prism(fe_ctx *ctx, const fe_elem_args *args, const fe_out *out, void *stream) {
+    TraceRange tr("fe_integrate_prism");
     return integrate(ctx, FE_PRISM, args, out, stream);
 }
 
@@ -786,11 +788,13 @@ static fe_status apply(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, co
 
 fe_status fe_apply_tet(fe_ctx *ctx, const fe_elem_args *args, const void *x, void *y, void *f, uint8_t *flags,
                        void *stream) {
+    TraceRange tr("fe_apply_tet");
     return apply(ctx, FE_TET, args, x, y, f, flags, stream);
 }
 
 fe_status fe_apply_prism(fe_ctx *ctx, const fe_elem_args *args, const void *x, void *y, void *f, uint8_t *flags,
                          void *stream) {
+    TraceRange tr("fe_apply_prism");
     return apply(ctx, FE_PRISM, args, x, y, f, flags, stream);
 }
 
@@ -900,6 +904,7 @@ fe_status fe_set_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
 }
 
 fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const fe_out *o, void *stream) {
+    TraceRange tr("fe_tune");
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
     fe_status st = fe_check_args(type, a, o);
     if (st != FE_OK) return st;

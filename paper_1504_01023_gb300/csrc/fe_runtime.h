@@ -13,10 +13,21 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fe.h"
 #include "fe_internal.h"
 
 namespace fe {
+
+// NVTX range over a host call (visible in Nsight Systems and any NVTX tool; a
+// push and a pop into an empty stub when no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 extern std::atomic<uint64_t> g_launches;
 

@@ -157,6 +157,7 @@ struct Job {
 // slot's completion callback. Runs without the lock (it makes CUDA calls, which
 // may wait); touches only the jobs and the slot's own stream and tables.
 static void launch_jobs(ServeState *s, Slot &sl, std::vector<Job> &jobs) {
+    TraceRange tr("serve launch");
     fe_ctx *ctx = s->ctx;
     std::vector<BatchItemDev> items;
     for (Job &j : jobs) {
@@ -425,6 +426,20 @@ fe_status fe_serve_submit_n(fe_ctx *ctx, const fe_request *reqs, int n, uint64_t
         }
     }
     s->cv.notify_all();
+    return FE_OK;
+}
+
+fe_status fe_serve_cancel(fe_ctx *ctx, uint64_t ticket) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    ServeState *s = ctx->serve;
+    if (!s) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown ticket");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return set_error(ctx, FE_ERR_INVALID_ARG, "unknown ticket");
+    if (it->second.state != 0) return set_error(ctx, FE_ERR_INVALID_ARG, "request already launched");
+    auto w = std::find(s->waiting.begin(), s->waiting.end(), ticket);
+    if (w != s->waiting.end()) s->waiting.erase(w);
+    s->reqs.erase(it);   // admitted requests are launched under the same lock: nothing was reserved
     return FE_OK;
 }
 

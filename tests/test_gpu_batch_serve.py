@@ -243,7 +243,18 @@ def test_serve_budget(mix):
         small.serve_release(t1)
         r2 = _wait(small, t2)
         assert r2.status == 0 and r2.t_launch_us >= r1.t_done_us
+        # a request waiting for budget can be withdrawn; one that ran cannot
+        t3 = small.serve_submit(mid, kind, quad, api.PER_ELEMENT, C)
+        time.sleep(0.05)
+        assert small.serve_poll(t3) is None                          # waits for t2's release
+        small.serve_cancel(t3)
+        with pytest.raises(api.FeError):
+            small.serve_poll(t3)
+        with pytest.raises(api.FeError):
+            small.serve_cancel(t2)
         small.serve_release(t2)
+        time.sleep(0.05)
+        assert small.serve_wait_any(timeout_us=20000) == []         # t3 never runs
         # a mesh that can never fit
         with pytest.raises(api.FeError) as e:
             small.mesh_register(et, torch.from_numpy(np.ascontiguousarray(meshgen.tet_cube_mesh(30))), api.AOS)
