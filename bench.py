@@ -184,6 +184,10 @@ def paper_context():
                         for hw, cases in PAPER_TABLE7_NS.items()}}
 
 
+# GB300 HBM3e nominal bandwidth (GB/s), reported beside the measured copy ceiling
+NOMINAL_HBM_GBS = 7900.0
+
+
 def shape_dict(shape):
     """A launch shape (elements per block, persistent[, threads per element]) as JSON."""
     return {"elements_per_block": shape[0], "persistent": shape[1],
@@ -404,6 +408,7 @@ def run_native(args):
                          "parallelism": f"weak: {world} independent mesh(es), one per GPU"},
               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak, "traffic": traffic,
+                           "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                            "kernel": kernel_name,
                            "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                            "kernel_ms": k_ms, "algorithmic_bytes_per_launch": n * bpe},
