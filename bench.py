@@ -654,7 +654,7 @@ def ordering_study(ctx, dev, api, mesh, coefs, args):
     convection-diffusion: 20 coefficients per element."""
     import torch
     from paper_1504_01023_gb300 import meshgen
-    nt, npr = 1_000_000, 500_000
+    nt, npr = min(1_000_000, len(mesh)), 500_000
     pmesh = meshgen.prism_slab_mesh(1000, None, 0.1, seed=meshgen.SEED_BASE + 3, n_elem=npr)
     cases = {
         ("poisson", "tetra"): (api.TET, mesh[:nt], meshgen.poisson_coefs(nt, 4, None, seed=SEED), api.POISSON,
