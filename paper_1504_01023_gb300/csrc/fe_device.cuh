@@ -601,8 +601,7 @@ __device__ __forceinline__ void prism_generic_update_rt(const V3<T> g[6], T vol,
     // one row a of the coefficient matrix at a time: T_as = sum_b vol c_ab Phi_bs,
     // then A_rs += Phi_ar T_as and b_r += vol d_a Phi_ar (same products as the
     // full rank-4 update, fewer values live at once)
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    auto row = [&](int a) {
         const T c0 = vol * c(o + 4 * a), c1 = vol * c(o + 4 * a + 1), c2 = vol * c(o + 4 * a + 2),
                 c3 = vol * c(o + 4 * a + 3);
         const T da = vol * c(o + 16 + a);
@@ -616,6 +615,15 @@ __device__ __forceinline__ void prism_generic_update_rt(const V3<T> g[6], T vol,
             for (int s = 0; s < 6; ++s) A[6 * r + s] += phi * Ta[s];
             b[r] += da * phi;
         }
+    };
+    if constexpr (std::is_same<T, DW>::value) {
+        // double-word: one copy of the row code (the unrolled rows overflow the
+        // instruction cache)
+#pragma unroll 1
+        for (int a = 0; a < 4; ++a) row(a);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) row(a);
     }
 }
 
