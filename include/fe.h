@@ -240,6 +240,13 @@ fe_status fe_apply_prism(fe_ctx *ctx, const fe_elem_args *args, const void *x, v
 /* Host-only argument validation used by the calls above (no CUDA call). */
 fe_status fe_check_args(fe_elem_type type, const fe_elem_args *args, const fe_out *out);
 
+/* The quadrature the kernels use (Sec. 2, Eq. quadrature): for each of the rule's
+   points its weight (weights[q], reference-element measure) and the reference
+   shape-function values there (shape_values[q * NS + r], NS = 4 or 6, vertex r
+   of the element record). Host arrays of max_points (x NS) entries; NULL skips
+   an array. Host-only; needs no device. */
+fe_status fe_rule_table(fe_quad quad, int max_points, int *n_points, double *weights, double *shape_values);
+
 /* Algorithmic bytes moved per element (inputs read once, outputs written once):
    8*3*NS for coordinates + coefficient bytes + (NS*NS + NS) output scalars; the
    double-precision cases of Table 3 give 288, 528, 416, 640. -1 if invalid. */

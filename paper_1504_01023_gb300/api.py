@@ -105,6 +105,8 @@ _SIGS = [
     ("fe_set_launch_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out),
                                            ctypes.POINTER(LaunchShape)]),
     ("fe_batch_set_shape", ctypes.c_int, [_P, ctypes.POINTER(LaunchShape)]),
+    ("fe_rule_table", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("fe_serve_submit_n", ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     ("fe_serve_release_n", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
     ("fe_apply_tet", ctypes.c_int, [_P, ctypes.POINTER(ElemArgs), _P, _P, _P, _P, _P]),
@@ -234,6 +236,17 @@ def make_args(elem_type, coords, coefs, kind, quad, coef_mode, prec, layout, con
     a.coefs_layout = layout
     a.memory = _mem(coords)
     return a
+
+
+def rule_table(quad):
+    """The library's quadrature as its kernels use it: (weights [n], reference
+    shape-function values [n, NS]) at the rule's points."""
+    ns = 4 if quad in (QUAD_TET1, QUAD_TET4) else 6
+    n = ctypes.c_int()
+    w = (ctypes.c_double * 64)()
+    phi = (ctypes.c_double * (64 * ns))()
+    _check(load().fe_rule_table(quad, 64, ctypes.byref(n), w, phi), None)
+    return np.array(w[:n.value]), np.array(phi[:n.value * ns]).reshape(n.value, ns)
 
 
 def packed_size(elem_type):

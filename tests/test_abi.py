@@ -181,3 +181,43 @@ def test_null_context_rejected(lib):
     a, o = _args()
     assert lib.fe_integrate_tet(None, ctypes.byref(a), ctypes.byref(o), None) == -1
     assert lib.fe_ctx_sync(None) == -1
+
+
+def _ref_shape_values(elem, pts):
+    """Reference shape functions at reference points (vertex k <-> phi_k): the tet
+    (1 - xi - eta - zeta, xi, eta, zeta); the prism lambda_k(xi, eta) (1 -/+ zeta) / 2
+    with lambda = (1 - xi - eta, xi, eta) on the bottom and top triangles."""
+    import numpy as np
+    xi, eta, zeta = pts[:, 0], pts[:, 1], pts[:, 2]
+    if elem == "tet":
+        return np.stack([1 - xi - eta - zeta, xi, eta, zeta], axis=1)
+    lam = np.stack([1 - xi - eta, xi, eta], axis=1)
+    return np.concatenate([lam * ((1 - zeta) / 2)[:, None], lam * ((1 + zeta) / 2)[:, None]], axis=1)
+
+
+@pytest.mark.parametrize("quad,elem", [(api.QUAD_TET1, "tet"), (api.QUAD_TET4, "tet"), (api.QUAD_PRISM6, "prism")])
+def test_rule_tables_match_the_oracle(lib, quad, elem):
+    """The kernels' quadrature (weights and shape values at the points, compile-time
+    constants of the library) against the oracle's rule, typed in separately: the
+    same points, up to order, and the same weights."""
+    import numpy as np
+    import oracle
+    w, phi = api.rule_table(quad)
+    rule = {api.QUAD_TET1: oracle.Q_TET1, api.QUAD_TET4: oracle.Q_TET4, api.QUAD_PRISM6: oracle.Q_PRISM6}[quad]
+    pts, wts = oracle.quad_rule(rule)
+    ref = _ref_shape_values(elem, pts)
+    assert len(w) == len(wts)
+    used = set()
+    for q in range(len(w)):
+        d = np.abs(ref - phi[q]).max(axis=1)
+        j = int(np.argmin(d))
+        assert d[j] < 1e-15 and j not in used, (q, d)
+        used.add(j)
+        assert abs(w[q] - wts[j]) < 1e-16
+    # partition of unity and the reference measure
+    assert np.allclose(phi.sum(axis=1), 1.0, rtol=0, atol=1e-15)
+    assert abs(w.sum() - (1 / 6 if elem == "tet" else 1.0)) < 1e-15
+    with pytest.raises(api.FeError):
+        n = ctypes.c_int()
+        arr = (ctypes.c_double * 1)()
+        api._check(lib.fe_rule_table(quad, 0 if quad == api.QUAD_TET1 else 1, ctypes.byref(n), arr, None))
