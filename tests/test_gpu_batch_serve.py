@@ -345,3 +345,96 @@ def test_serve_submit_and_release_many(ctx, mix):
         pass
     for mid, *_ in ids:
         ctx.mesh_release(mid)
+
+
+def test_serve_concurrent_clients_stress(ctx, mix):
+    """Four client threads submit (one by one and in groups), cancel and release
+    while a fifth drains the completion queue: every request that was not
+    cancelled completes exactly once, with the results of its single call."""
+    import random
+    ids, refs = [], []
+    for i, ((et, kind, quad, cpq, n, _), (mesh, c, X, C)) in enumerate(zip(MIX, mix)):
+        cm = api.PER_QPOINT if cpq else api.PER_ELEMENT
+        ids.append((_register(ctx, et, mesh, "aos-dev"), kind, quad, cm, C))
+        A, b, f = ctx.integrate(et, X, C, kind, quad, cm, api.FP32_MIXED, api.AOS, api.AOS)
+        ctx.sync()
+        refs.append((A.double().cpu().numpy(), b.double().cpu().numpy(), f.cpu().numpy()))
+    lock = threading.Lock()
+    owner, cancelled, done = {}, set(), {}
+    errors = []
+    stop = threading.Event()
+
+    def client(seed):
+        rng = random.Random(seed)
+        try:
+            for _ in range(60):
+                k = rng.randint(1, 4)
+                js = [rng.randrange(len(ids)) for _ in range(k)]
+                tks = ctx.serve_submit_many([ids[j] for j in js]) if k > 1 else [ctx.serve_submit(*ids[js[0]])]
+                with lock:
+                    owner.update(zip(tks, js))
+                if rng.random() < 0.3:
+                    tk = rng.choice(tks)
+                    try:
+                        ctx.serve_cancel(tk)
+                        with lock:
+                            cancelled.add(tk)
+                    except api.FeError:
+                        pass                      # already launched: it completes normally
+        except Exception as e:                    # noqa: BLE001
+            errors.append(e)
+
+    def owner_of(tk):
+        # a completion can arrive before its client has recorded the ticket
+        t0 = time.time()
+        while time.time() - t0 < 10:
+            with lock:
+                if tk in owner:
+                    return owner[tk]
+            time.sleep(0.0002)
+        return None
+
+    def collector():
+        deadline = time.time() + 120
+        while time.time() < deadline:
+            got = ctx.serve_wait_any(timeout_us=20000, max_results=32)
+            for tk, r in got:
+                j = owner_of(tk)
+                with lock:
+                    if j is None or tk in done or tk in cancelled:
+                        errors.append(("unexpected completion", tk))
+                        continue
+                    done[tk] = r
+                A, b, f = ctx.serve_result_tensors(tk, r)
+                An, bn, fn = refs[j]
+                if not (r.status == 0 and np.array_equal(f.cpu().numpy(), fn) and
+                        oracle.rel_frobenius(A.double().cpu().numpy(), An).max() <= 1e-6 and
+                        oracle.rel_frobenius(b.double().cpu().numpy(), bn).max() <= 1e-6):
+                    errors.append(("mismatch", tk, j))
+            if got:
+                ctx.serve_release_many([tk for tk, _ in got])
+            with lock:
+                finished = stop.is_set() and len(done) + len(cancelled) == len(owner)
+            if finished:
+                return
+
+    def collector_guarded():
+        try:
+            collector()
+        except Exception as e:                    # noqa: BLE001
+            errors.append(("collector", repr(e)))
+
+    col = threading.Thread(target=collector_guarded, daemon=True)
+    col.start()
+    clients = [threading.Thread(target=client, args=(s,)) for s in range(4)]
+    for t in clients:
+        t.start()
+    for t in clients:
+        t.join()
+    stop.set()
+    col.join(timeout=150)
+    assert not col.is_alive(), "completion queue stalled"
+    assert not errors, errors[:3]
+    assert set(done) | cancelled == set(owner) and not (set(done) & cancelled)
+    for mid, *_ in ids:
+        ctx.mesh_release(mid)
