@@ -188,6 +188,23 @@ def paper_context():
 NOMINAL_HBM_GBS = 7900.0
 
 
+# Roofline of the plain FP64 forms: the FP64 pipe. FP64-pipe instructions per
+# element of each kernel, from ncu (smsp__inst_executed_pipe_fp64.sum x 32 /
+# elements; profiles/fp64_pipe.md), and the pipe's rate: 2 per clock per SM (the
+# nominal 1.25 TFLOP/s of FP64 FMAs) x 152 SMs x 2.07 GHz.
+FP64_PIPE_INST_PER_ELEM = {"tet_poisson_tet1": 77.0, "tet_generic_tet4": 205.0, "prism_poisson_per_point": 571.0,
+                           "prism_generic_per_point": 2239.0}
+FP64_PIPE_PEAK_TINST = 2 * 152 * 2.07e9 / 1e12
+
+
+def fp64_pipe(melem_s, key):
+    n = FP64_PIPE_INST_PER_ELEM[key]
+    achieved = melem_s * 1e6 * n / 1e12
+    return {"bound": "alu (FP64 pipe)", "instructions_per_element": n, "achieved": achieved,
+            "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-pipe instructions/s", "frac": achieved / FP64_PIPE_PEAK_TINST,
+            "peak_kind": "nominal: 2 per clock per SM x 152 SMs x 2.07 GHz"}
+
+
 def shape_dict(shape):
     """A launch shape (elements per block, persistent[, threads per element]) as JSON."""
     return {"elements_per_block": shape[0], "persistent": shape[1],
@@ -489,6 +506,8 @@ def prism_form(ctx, dev, api, args):
     for name, prec in (("double_word", api.FP64_DW), ("native_fp64", api.FP64)):
         gen[name] = _fp64_run(ctx, dev, api, X, C64, api.PRISM, api.GENERIC, api.QUAD_PRISM6, prec, args,
                               cm=api.PER_QPOINT)
+        if prec == api.FP64:
+            gen[name]["fp64_pipe"] = fp64_pipe(gen[name]["value"], "prism_generic_per_point")
     del C64
     torch.cuda.empty_cache()
     # the Laplace kind on the same prisms: d^0 per point, in the three precision forms
@@ -499,6 +518,8 @@ def prism_form(ctx, dev, api, args):
         Cd = torch.from_numpy(np.ascontiguousarray(d0.astype(np.float32 if prec == api.FP32_MIXED else np.float64))).to(dev)
         lap[name] = _fp64_run(ctx, dev, api, X, Cd, api.PRISM, api.POISSON, api.QUAD_PRISM6, prec, args,
                               cm=api.PER_QPOINT)
+        if prec == api.FP64:
+            lap[name]["fp64_pipe"] = fp64_pipe(lap[name]["value"], "prism_poisson_per_point")
         del Cd
     del X
     torch.cuda.empty_cache()
@@ -777,14 +798,14 @@ def fp64_form(ctx, dev, api, mesh, coefs, args):
     dw = _fp64_run(ctx, dev, api, X, C, api.TET, api.POISSON, api.QUAD_TET1, api.FP64_DW, args)
     nat = _fp64_run(ctx, dev, api, X, C, api.TET, api.POISSON, api.QUAD_TET1, api.FP64, args)
     dw.update(dtype="f32 double-word (edges and flagged elements f64)", bound="hbm")
-    nat.update(dtype="f64", bound="alu (FP64 pipe)")
+    nat.update(dtype="f64", bound="alu (FP64 pipe)", fp64_pipe=fp64_pipe(nat["value"], "tet_poisson_tet1"))
     out["poisson_tet1"] = {"double_word": dw, "native_fp64": nat}
     del C
     C = torch.from_numpy(np.ascontiguousarray(coefs)).to(dev)
     dw = _fp64_run(ctx, dev, api, X, C, api.TET, api.GENERIC, api.QUAD_TET4, api.FP64_DW, args)
     nat = _fp64_run(ctx, dev, api, X, C, api.TET, api.GENERIC, api.QUAD_TET4, api.FP64, args)
     dw.update(dtype="f32 double-word (edges and flagged elements f64)", bound="alu (float pipes)")
-    nat.update(dtype="f64", bound="alu (FP64 pipe)")
+    nat.update(dtype="f64", bound="alu (FP64 pipe)", fp64_pipe=fp64_pipe(nat["value"], "tet_generic_tet4"))
     out["generic_tet4"] = {"double_word": dw, "native_fp64": nat}
     del X, C
     torch.cuda.empty_cache()
@@ -792,6 +813,7 @@ def fp64_form(ctx, dev, api, mesh, coefs, args):
     # pairs; results within the same 1e-12 tolerance)
     native = {"workload": out["workload"], "value": out["poisson_tet1"]["native_fp64"]["value"], "unit": "Melem/s",
               "hbm_frac": out["poisson_tet1"]["native_fp64"]["hbm_frac"], "dtype": "f64",
+              "fp64_pipe": out["poisson_tet1"]["native_fp64"]["fp64_pipe"],
               "bound": "alu (FP64 pipe: 0.5 T DFMA/DADD per second on this GPU)",
               "poisson_tet1": out["poisson_tet1"]["native_fp64"], "generic_tet4": out["generic_tet4"]["native_fp64"]}
     dword = {"workload": out["workload"], "value": out["poisson_tet1"]["double_word"]["value"], "unit": "Melem/s",
