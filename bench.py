@@ -205,6 +205,22 @@ def fp64_pipe(melem_s, key):
             "peak_kind": "nominal: 2 per clock per SM x 152 SMs x 2.07 GHz"}
 
 
+# Roofline of the double-word forms: instruction issue. Instructions per element
+# from ncu (smsp__inst_executed.sum x 32 / elements; profiles/tet_dw_1M_full.md);
+# issue rate: one warp instruction per clock per SM sub-partition, 4 x 32 x 152 x
+# 2.07 GHz thread instructions per second.
+DW_INST_PER_ELEM = {"tet_poisson_tet1": 1436.0, "tet_generic_tet4": 3333.0}
+ISSUE_PEAK_TINST = 4 * 32 * 152 * 2.07e9 / 1e12
+
+
+def issue_roofline(melem_s, key):
+    n = DW_INST_PER_ELEM[key]
+    achieved = melem_s * 1e6 * n / 1e12
+    return {"bound": "alu (instruction issue)", "instructions_per_element": n, "achieved": achieved,
+            "peak": ISSUE_PEAK_TINST, "unit": "T thread instructions/s", "frac": achieved / ISSUE_PEAK_TINST,
+            "peak_kind": "nominal: 1 warp instruction per clock per sub-partition"}
+
+
 def shape_dict(shape):
     """A launch shape (elements per block, persistent[, threads per element]) as JSON."""
     return {"elements_per_block": shape[0], "persistent": shape[1],
@@ -797,14 +813,16 @@ def fp64_form(ctx, dev, api, mesh, coefs, args):
     C = torch.ones((n, 1), dtype=torch.float64, device=dev)
     dw = _fp64_run(ctx, dev, api, X, C, api.TET, api.POISSON, api.QUAD_TET1, api.FP64_DW, args)
     nat = _fp64_run(ctx, dev, api, X, C, api.TET, api.POISSON, api.QUAD_TET1, api.FP64, args)
-    dw.update(dtype="f32 double-word (edges and flagged elements f64)", bound="hbm")
+    dw.update(dtype="f32 double-word (edges and flagged elements f64)", bound="hbm",
+              issue=issue_roofline(dw["value"], "tet_poisson_tet1"))
     nat.update(dtype="f64", bound="alu (FP64 pipe)", fp64_pipe=fp64_pipe(nat["value"], "tet_poisson_tet1"))
     out["poisson_tet1"] = {"double_word": dw, "native_fp64": nat}
     del C
     C = torch.from_numpy(np.ascontiguousarray(coefs)).to(dev)
     dw = _fp64_run(ctx, dev, api, X, C, api.TET, api.GENERIC, api.QUAD_TET4, api.FP64_DW, args)
     nat = _fp64_run(ctx, dev, api, X, C, api.TET, api.GENERIC, api.QUAD_TET4, api.FP64, args)
-    dw.update(dtype="f32 double-word (edges and flagged elements f64)", bound="alu (float pipes)")
+    dw.update(dtype="f32 double-word (edges and flagged elements f64)", bound="alu (float pipes)",
+              issue=issue_roofline(dw["value"], "tet_generic_tet4"))
     nat.update(dtype="f64", bound="alu (FP64 pipe)", fp64_pipe=fp64_pipe(nat["value"], "tet_generic_tet4"))
     out["generic_tet4"] = {"double_word": dw, "native_fp64": nat}
     del X, C
