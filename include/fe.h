@@ -287,7 +287,8 @@ typedef struct fe_batch_item {
 fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, void *stream);
 
 /*
- * Serving: integration requests on resident meshes arrive at any time. A
+ * Serving (no counterpart in the paper, whose kernels run one element set per
+ * call, Sec. 3.2): integration requests on resident meshes arrive at any time. A
  * scheduler thread admits them in arrival order while the resident meshes plus
  * the outputs of admitted, unreleased requests fit the HBM budget, merges every
  * admitted mixed-precision request into one batched launch (continuous
