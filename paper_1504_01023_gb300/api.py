@@ -321,12 +321,25 @@ def device_view(ptr, shape, dtype, device=0):
     return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=f"cuda:{device}")
 
 
+def context_settings(autotune=None, tuning_cache=None, environ=None):
+    """Autotuning and the tuning-cache path of a new context: the arguments when
+    given, else the environment (FE_AUTOTUNE=1, FE_TUNING_CACHE=<path>), else off
+    and no cache."""
+    env = os.environ if environ is None else environ
+    if autotune is None:
+        autotune = env.get("FE_AUTOTUNE", "0").strip() not in ("", "0", "false", "False", "no")
+    if tuning_cache is None:
+        tuning_cache = env.get("FE_TUNING_CACHE") or None
+    return bool(autotune), tuning_cache
+
+
 class Context:
     """One library context on one CUDA device."""
 
-    def __init__(self, device: int = 0, autotune: bool = False, tuning_cache: str | None = None,
+    def __init__(self, device: int = 0, autotune: bool | None = None, tuning_cache: str | None = None,
                  hbm_budget: int = 0, serve_slots: int = 0):
         lib = load()
+        autotune, tuning_cache = context_settings(autotune, tuning_cache)
         cfg = CtxConfig(device, hbm_budget, serve_slots, int(autotune),
                         tuning_cache.encode() if tuning_cache else None)
         h = ctypes.c_void_p()

@@ -92,3 +92,11 @@ def test_wrong_dtypes_are_caught_before_the_library(lib):
     with pytest.raises(AssertionError):
         api.make_args(api.TET, X.float(), torch.zeros((len(mesh), 20), dtype=torch.float32), api.GENERIC,
                       api.QUAD_TET4, api.PER_ELEMENT, api.FP32_MIXED, api.AOS)
+
+
+def test_context_settings_from_arguments_and_environment():
+    assert api.context_settings(environ={}) == (False, None)
+    assert api.context_settings(environ={"FE_AUTOTUNE": "1", "FE_TUNING_CACHE": "/tmp/t.txt"}) == (True, "/tmp/t.txt")
+    assert api.context_settings(environ={"FE_AUTOTUNE": "0"}) == (False, None)
+    # explicit arguments win over the environment
+    assert api.context_settings(False, "a.txt", environ={"FE_AUTOTUNE": "1", "FE_TUNING_CACHE": "b"}) == (False, "a.txt")
