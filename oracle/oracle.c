@@ -41,6 +41,11 @@
  * The mean-ratio shape quality (oracle_quality) is not in the paper; it restates,
  * in single precision as the kernel decides it, the test that selects elements
  * for the double-precision Jacobian path.
+ *
+ * Parity unpinned: the diffusion term of non-affine (z-jittered) prisms with
+ * per-point coefficients has no closed form. It is pinned only indirectly: by
+ * exact agreement with the rational closed forms on affine prisms, exact mass
+ * and convection terms, and convergence of the brute-force high-order rules.
  */
 #include <math.h>
 #include <stdint.h>
