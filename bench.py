@@ -156,6 +156,33 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def same_run_copy_gbs(dev, nbytes=2 << 30, reps=10):
+    """A STREAM-style copy in this run (the paper reports STREAM beside its kernels,
+    Sec. 4.5): device-to-device copy of a 2 GiB buffer, bytes read + written per
+    second, CUDA events. Context for the roofline, whose denominator stays the
+    measured peak; None if it cannot run."""
+    import torch
+    try:
+        a = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+        b = torch.empty_like(a)
+        a.fill_(1.0)
+        for _ in range(3):
+            b.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        gbs = 2.0 * nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del a, b
+        torch.cuda.empty_cache()
+        return gbs
+    except Exception:
+        return None
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1504_01023_gb300", "csrc")
@@ -442,6 +469,7 @@ def run_native(args):
               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                            "frac": achieved / peak, "traffic": traffic,
                            "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                           "same_run_copy_gbs": same_run_copy_gbs(dev) if rank == 0 else None,
                            "kernel": kernel_name,
                            "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                            "kernel_ms": k_ms, "algorithmic_bytes_per_launch": n * bpe},
