@@ -130,9 +130,10 @@ def coefs_from_u(elem_type: int, kind: int, rule: int, u, P, lib=None):
     return out
 
 
-def quality(elem_type: int, coords, n_threads: int = 1):
-    """Single-precision mean-ratio quality per element (min over PRISM6 points for prisms)."""
-    lib = _load()
+def quality(elem_type: int, coords, n_threads: int = 1, lib=None):
+    """Single-precision mean-ratio quality per element (min over PRISM6 points for
+    prisms). ``lib`` selects another compiled oracle (planted-mistake tests)."""
+    lib = lib or _load()
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     n = coords.shape[0]
     q = np.zeros(n, dtype=np.float32)

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle import exact
 from paper_1504_01023_gb300 import meshgen
+from prism_quality_ref import affine_prism_quality, prism_quality_per_point
 
 TET, PRISM = oracle.TET, oracle.PRISM
 POI, GEN = oracle.POISSON, oracle.GENERIC
@@ -484,3 +485,86 @@ def test_coef_function_field_through_thickness_prism():
     A, b, _ = oracle.integrate(oracle.PRISM, oracle.POISSON, oracle.Q_PRISM6, mesh, cq, coef_per_q=True)
     ref = np.array([h * 0.5 / 18] * 3 + [h * 0.5 / 9] * 3)
     assert np.abs(b[0] - ref).max() <= 1e-15
+
+
+def test_coef_function_quadratic_term_poisson_kind():
+    """The quadratic term of the coefficient function in the Laplace kind
+    (d^0 = u_Q^2, P2_16 = 1, all else 0), against closed forms:
+    - a right prism (triangle area |T_a|, height h) with u = 0 on the bottom nodes
+      and 1 on the top ones: u = t (t = z/h) and u^2 phi is cubic in t and linear
+      in the triangle, which PRISM6 integrates exactly, so
+      b_bottom = |T_a| h / 3 * int t^2 (1 - t) dt = |T_a| h / 36 and
+      b_top = |T_a| h / 3 * int t^3 dt = |T_a| h / 12;
+    - a tetrahedron with TET1, whose one point is the centroid, where u is the mean
+      of the nodal values: b_r = |T| / 4 * mean(u)^2;
+    - a tetrahedron with TET4 and a constant field c: b_r = |T| / 4 * c^2.
+    The generic kind reads d^0 from the same slot and must give the same b."""
+    tri = np.array([[0.0, 0.0], [0.8, 0.1], [0.2, 0.7]])
+    area = 0.5 * abs((tri[1, 0] - tri[0, 0]) * (tri[2, 1] - tri[0, 1]) - (tri[1, 1] - tri[0, 1]) * (tri[2, 0] - tri[0, 0]))
+    h = 0.4
+    prism = np.zeros((1, 6, 3))
+    prism[0, :3, :2] = tri
+    prism[0, 3:, :2] = tri
+    prism[0, 3:, 2] = h
+    u = np.array([[0.0, 0.0, 0.0, 1.0, 1.0, 1.0]])
+    P = np.zeros((3, 20))
+    P[2, 16] = 1.0
+    ref = np.array([area * h / 36] * 3 + [area * h / 12] * 3)
+    for kind in (oracle.POISSON, oracle.GENERIC):
+        cq = oracle.coefs_from_u(oracle.PRISM, kind, oracle.Q_PRISM6, u, P)
+        A, b, _ = oracle.integrate(oracle.PRISM, kind, oracle.Q_PRISM6, prism, cq, coef_per_q=True)
+        assert np.abs(b[0] - ref).max() <= 1e-15 * 8, (kind, b[0], ref)
+        if kind == oracle.GENERIC:
+            assert np.abs(A).max() == 0.0
+    mesh = meshgen.tet_cube_mesh(2, seed=31)[:24]
+    e = mesh[:, 1:] - mesh[:, :1]
+    vol = np.abs(np.einsum("ei,ei->e", e[:, 0], np.cross(e[:, 1], e[:, 2]))) / 6.0
+    rng = np.random.default_rng(32)
+    uf = rng.uniform(-2, 2, (24, 4))
+    uc = np.repeat(rng.uniform(-2, 2, (24, 1)), 4, axis=1)
+    for rule, field, ubar in ((oracle.Q_TET1, uf, uf.mean(axis=1)), (oracle.Q_TET4, uc, uc[:, 0])):
+        ref = np.repeat((vol * ubar ** 2 / 4)[:, None], 4, axis=1)
+        for kind in (oracle.POISSON, oracle.GENERIC):
+            cq = oracle.coefs_from_u(oracle.TET, kind, rule, field, P)
+            _, b, _ = oracle.integrate(oracle.TET, kind, rule, mesh, cq, coef_per_q=True)
+            assert np.abs(b - ref).max() <= 1e-14 * np.abs(ref).max(), (rule, kind)
+
+
+def test_prism_quality_affine_closed_form():
+    """oracle.quality on prisms whose top is a translate of the bottom (J constant):
+    right and oblique, from flat to tall, rotated and moved; against the edge-length
+    formula of prism_quality_ref (single precision on the oracle's side)."""
+    rng = np.random.default_rng(41)
+    n = 400
+    base = rng.uniform(-1, 1, (n, 3, 3))
+    base[:, :, 2] = 0.0
+    normal = np.cross(base[:, 1] - base[:, 0], base[:, 2] - base[:, 0])
+    normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+    height = 10.0 ** rng.uniform(-2.5, 0.5, n)
+    shear = rng.uniform(-0.7, 0.7, (n, 3)) * height[:, None] * (rng.random((n, 1)) < 0.5)
+    d = height[:, None] * normal + shear
+    x = np.concatenate([base, base + d[:, None, :]], axis=1)
+    R = _rotation(rng)
+    x = x @ R.T + rng.uniform(-3, 3, 3)
+    q = oracle.quality(PRISM, x)
+    e1, e2 = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]
+    ref = affine_prism_quality(e1, e2, x[:, 3] - x[:, 0])
+    assert ref.min() < 0.05 and ref.max() > 0.5
+    assert np.max(np.abs(q - ref) / ref) < 5e-5
+
+
+def test_prism_quality_min_over_points_non_affine():
+    """Prisms with independently jittered top nodes (J varies): the oracle's quality
+    is the minimum over the six PRISM6 points of the mean ratio of J there. The test
+    takes J at each point by central differences of the map and applies the affine
+    closed form to the prism with the same Jacobian (prism_quality_ref)."""
+    rng = np.random.default_rng(43)
+    x = meshgen.prism_slab_mesh(12, seed=44).copy()
+    n = len(x)
+    x[:, 3:] += rng.uniform(-0.06, 0.06, (n, 3, 3))
+    x = x - x[:, :1]
+    per_point = prism_quality_per_point(x)
+    ref = per_point.min(axis=0)
+    assert np.mean(per_point.argmin(axis=0) != per_point.argmax(axis=0)) > 0.9   # the points differ
+    q = oracle.quality(PRISM, x)
+    assert np.max(np.abs(q - ref) / ref) < 5e-5

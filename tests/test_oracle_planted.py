@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from oracle import exact
+from prism_quality_ref import prism_quality_per_point
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -76,3 +77,73 @@ def test_planted_mistake_is_caught(tmp_path, desc, old, new):
     mutated.write_text(src.replace(old, new))
     lib = oracle.load_library(oracle.compile_source(str(mutated), str(tmp_path / "liboracle_mut.so")))
     assert not _pins_pass(lib), f"pins did not catch: {desc}"
+
+
+# Mistakes in the coefficient function and in the shape quality, each against
+# the pins of its own part (the closed forms of tests/test_oracle_pins.py).
+MUTATIONS_AUX = [
+    ("coefficient function: quadratic term of d^0 from the wrong slot (Laplace kind)",
+     "P[40 + 16] * uq * uq", "P[40 + 17] * uq * uq", "coef_fn"),
+    ("coefficient function: linear term squared (Laplace kind)",
+     "P[20 + 16] * uq + P[40 + 16]", "P[20 + 16] * uq * uq + P[40 + 16]", "coef_fn"),
+    ("prism quality: ideal height 1/2 instead of 1", "{0.0, 0.0, 0.5}};", "{0.0, 0.0, 1.0}};", "quality"),
+    ("prism quality: maximum over the points instead of the minimum", "if (!(qq >= qmin)) qmin = qq;",
+     "if (!(qq <= qmin) || qmin > 1e29f) qmin = qq;", "quality"),
+]
+
+
+def _coef_fn_pins_pass(lib):
+    """Laplace-kind coefficient function against the closed forms of the quadratic
+    and linear terms: a right prism with u = 0 below and 1 above (PRISM6 exact)."""
+    tri = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    h = 0.5
+    prism = np.zeros((1, 6, 3))
+    prism[0, :3, :2] = tri
+    prism[0, 3:, :2] = tri
+    prism[0, 3:, 2] = h
+    u = np.array([[0.0, 0.0, 0.0, 1.0, 1.0, 1.0]])
+    for slot, ref in ((2, [0.5 * h / 36] * 3 + [0.5 * h / 12] * 3), (1, [0.5 * h / 18] * 3 + [0.5 * h / 9] * 3)):
+        P = np.zeros((3, 20))
+        P[slot, 16] = 1.0
+        cq = oracle.coefs_from_u(oracle.PRISM, oracle.POISSON, oracle.Q_PRISM6, u, P, lib=lib)
+        _, b, _ = oracle.integrate(oracle.PRISM, oracle.POISSON, oracle.Q_PRISM6, prism, cq, coef_per_q=True)
+        if np.abs(b[0] - np.array(ref)).max() > 1e-14:
+            return False
+    return True
+
+
+def _quality_pins_pass(lib):
+    """Prism quality against the affine closed form on right prisms of the unit-edge
+    equilateral triangle, and against the minimum over the points of the per-point
+    closed form on prisms with a tilted top (prism_quality_ref)."""
+    s3 = np.sqrt(3.0)
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.5, s3 / 2, 0.0]])
+    out = []
+    for hgt in (0.25, 1.0, 3.0):
+        x = np.concatenate([tri, tri + [0.0, 0.0, hgt]])[None]
+        # det T = 4 |T_a| h / sqrt3 = h, ||T||_F^2 = 2 + h^2
+        ref = 3.0 * hgt ** (2.0 / 3.0) / (2.0 + hgt ** 2)
+        out.append(abs(oracle.quality(oracle.PRISM, x, lib=lib)[0] - ref) <= 1e-5 * ref)
+    # top vertex 3 lifted by different amounts: the points differ
+    x = np.repeat(np.concatenate([tri, tri + [0.0, 0.0, 1.0]])[None], 4, axis=0)
+    x[:, 3, 2] += np.array([0.3, 0.8, 1.5, 2.5])
+    ref = prism_quality_per_point(x).min(axis=0)
+    q = oracle.quality(oracle.PRISM, x, lib=lib)
+    out.append(bool(np.all(np.abs(q - ref) <= 5e-5 * ref)))
+    return all(out)
+
+
+def test_unmodified_oracle_passes_aux_pins():
+    assert _coef_fn_pins_pass(oracle._load())
+    assert _quality_pins_pass(oracle._load())
+
+
+@pytest.mark.parametrize("desc,old,new,part", MUTATIONS_AUX, ids=[m[0] for m in MUTATIONS_AUX])
+def test_planted_mistake_in_aux_part_is_caught(tmp_path, desc, old, new, part):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique/not found: {desc}"
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = oracle.load_library(oracle.compile_source(str(mutated), str(tmp_path / "liboracle_mut.so")))
+    check = _coef_fn_pins_pass if part == "coef_fn" else _quality_pins_pass
+    assert not check(lib), f"pins did not catch: {desc}"
