@@ -418,15 +418,17 @@ fe_status fe_batch_set_shape(fe_ctx *ctx, const fe_launch_shape *shape);
  * real-time loops that forbid allocator calls, or plugins that may not create a
  * context of this library).
  * Same inputs, outputs, layouts and results as fe_integrate_tet with
- * prec = FE_FP32_MIXED and device buffers (SOA or AOS coordinates; a node table
- * is rejected with FE_ERR_UNSUPPORTED); no context. Its scratch (the list of
+ * prec = FE_FP32_MIXED and device buffers (SOA or AOS coordinates); no context.
+ * A node table, packed output, the coefficient function and the SQS / SSQ
+ * orderings are rejected with FE_ERR_UNSUPPORTED. Its scratch (the list of
  * elements sent to the double-precision Jacobian pass, a counter and a status
  * word) is a fixed 4 MiB array in the library's device image, which every GPU
  * that loads the library holds until the process exits. Hence at most 524,256
  * elements per call; larger n_elem is rejected with FE_ERR_INVALID_ARG before any
  * GPU work. Runs on the calling thread's current device. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture. Every call clears the counter and the
+ * first call before any stream capture. The address is kept for the life of the
+ * process: calls after a device reset (cudaDeviceReset) are not supported. Every call clears the counter and the
  * status word, launches its two kernels on `stream` and returns after they
  * finish, reporting FE_ERR_TIMEOUT if a bulk-copy wait ran out. All calls share
  * the array: calls that overlap on the GPU (other streams or threads at the same

@@ -42,7 +42,8 @@ DeviceSetup g_setup[256];
 
 // Host code cannot pass the array's name to a kernel: it is a host-side stand-in.
 // The device address comes from cudaGetSymbolAddress, once per device, with that
-// device current.
+// device current. It is kept for the life of the process: a device reset by the
+// host application unloads the module, and calls after one are not supported.
 fe_status setup_device(int dev, DeviceSetup *&out) {
     if (dev < 0 || dev >= 256) return fe::set_error(nullptr, FE_ERR_INVALID_ARG, "device ordinal out of range");
     std::lock_guard<std::mutex> lk(g_setup_mu);
@@ -70,8 +71,11 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
         return set_error(nullptr, FE_ERR_INVALID_ARG, "fe_integrate_tet_noalloc takes FE_FP32_MIXED only");
     if (args->memory != FE_MEM_DEVICE || out->memory != FE_MEM_DEVICE)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "fe_integrate_tet_noalloc takes device buffers only");
-    if (args->coords_layout == FE_LAYOUT_INDEXED || out->packed || args->coef_mode == FE_COEF_FUNCTION_U)
-        return set_error(nullptr, FE_ERR_UNSUPPORTED, "fe_integrate_tet_noalloc takes no node table, packed output or coefficient function");
+    if (args->coords_layout == FE_LAYOUT_INDEXED || out->packed || args->coef_mode == FE_COEF_FUNCTION_U ||
+        args->ordering != 0)
+        return set_error(nullptr, FE_ERR_UNSUPPORTED,
+                         "fe_integrate_tet_noalloc takes no node table, packed output, coefficient function or "
+                         "loop ordering other than QSS");
     if (uint64_t(args->n_elem) > kListCap)
         return set_error(nullptr, FE_ERR_INVALID_ARG,
                          "n_elem exceeds the " + std::to_string(kListCap) +
@@ -96,15 +100,10 @@ extern "C" fe_status fe_integrate_tet_noalloc(const fe_elem_args *args, const fe
     auto r16 = [](int64_t v) { return (v + 15) / 16 * 16; };
     const int64_t smem_in = int64_t(B) * 12 * 8 + r16(int64_t(B) * nc * 4), smem_out = r16(int64_t(B) * 16 * 4) + r16(int64_t(B) * 4 * 4);
     const int64_t smem = smem_in > smem_out ? smem_in : smem_out;
-    // raise the kernel's dynamic shared-memory limit if needed, never lower it
-    // (other entry points of the library launch the same kernel with larger tiles)
-    cudaFuncAttributes fa{};
-    ce = cudaFuncGetAttributes(&fa, k);
-    if (ce != cudaSuccess) return cuda_check(nullptr, ce, "cudaFuncGetAttributes");
-    if (fa.maxDynamicSharedSizeBytes < smem) {
-        ce = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (ce != cudaSuccess) return cuda_check(nullptr, ce, "cudaFuncSetAttribute");
-    }
+    // raise the kernel's dynamic shared-memory limit if needed, never lower it,
+    // through the same record as the other entry points that launch this kernel
+    st = set_smem_attr(nullptr, k, smem);
+    if (st != FE_OK) return st;
 
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     unsigned int *count = reinterpret_cast<unsigned int *>(s->scratch);

@@ -144,7 +144,7 @@ static int64_t smem_bytes(fe_elem_type type, const fe_elem_args *a, int outl, in
 // Static shared memory of the kernels (the mbarrier), kept out of the dynamic budget.
 static constexpr int64_t kStaticSmem = 1024;
 
-static fe_status set_smem_attr(fe_ctx *ctx, const void *k, int64_t smem) {
+fe_status set_smem_attr(fe_ctx *ctx, const void *k, int64_t smem) {
     static std::mutex mu;
     static std::map<const void *, int64_t> done;
     std::lock_guard<std::mutex> lk(mu);

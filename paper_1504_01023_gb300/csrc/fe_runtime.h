@@ -102,6 +102,10 @@ struct fe_ctx {
 namespace fe {
 fe_status set_error(fe_ctx *ctx, fe_status st, const std::string &msg);
 fe_status cuda_check(fe_ctx *ctx, cudaError_t e, const char *what);
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes, never
+// lower it; one process-wide record under a mutex, shared by every entry point
+// that launches the kernel (ctx may be null).
+fe_status set_smem_attr(fe_ctx *ctx, const void *k, int64_t smem);
 fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n);
 void free_scratch(Scratch &s);
 // Launch main + fix-up kernels of one homogeneous set (device pointers).
