@@ -52,7 +52,8 @@ typedef enum fe_status {
     FE_ERR_BUDGET = -3,        /* serving: the request can never fit the HBM budget */
     FE_ERR_CUDA = -4,          /* a CUDA runtime call failed (text in fe_last_error) */
     FE_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
-    FE_ERR_UNSUPPORTED = -6    /* valid but not implemented combination */
+    FE_ERR_UNSUPPORTED = -6,   /* valid but not implemented combination */
+    FE_ERR_PARTIAL = -7        /* tiles were skipped (injected fault only): outputs incomplete */
 } fe_status;
 
 typedef enum fe_elem_type { FE_TET = 0, FE_PRISM = 1 } fe_elem_type;
@@ -360,6 +361,26 @@ uint64_t fe_launch_count(void);
    device status like fe_ctx_sync. Expected: FE_ERR_TIMEOUT, after which the
    context remains usable; any other result means the detection is broken. */
 fe_status fe_selftest_bounded_wait(fe_ctx *ctx, unsigned polls, void *stream);
+
+/* Fault injection on the host, for tests of failure detection (no counterpart in
+   the paper). Nothing is made to fault, trap or hang on the GPU:
+   FE_FAULT_ALLOC       the next `count` device allocations of this context
+                        (scratch growth, staging buffers, resident meshes, batch
+                        plans, served outputs) fail as out of memory without
+                        calling the allocator; the entry point that needed one
+                        returns FE_ERR_OOM (a served request finishes with it) and
+                        the context stays usable. `param` is ignored.
+   FE_FAULT_SKIP_TILES  the next `count` main-kernel launches of fe_integrate_tet
+                        and fe_integrate_prism (tiled kernels, one or two threads
+                        per element) skip every tile whose index is a multiple of
+                        `param` (>= 1): its elements are neither read nor
+                        written, and a status bit makes the next fe_ctx_sync
+                        return FE_ERR_PARTIAL.
+   FE_FAULT_NONE        clears both.
+   FE_ERR_INVALID_ARG for a null context, count < 0, param < 1 with
+   FE_FAULT_SKIP_TILES or an unknown kind. */
+typedef enum fe_fault { FE_FAULT_NONE = 0, FE_FAULT_ALLOC = 1, FE_FAULT_SKIP_TILES = 2 } fe_fault;
+fe_status fe_ctx_inject_fault(fe_ctx *ctx, fe_fault kind, int64_t count, int64_t param);
 
 /* Profiling: when on, the integration calls record CUDA events around their main
    kernel on the launching stream; fe_ctx_kernel_time returns the summed device

@@ -29,7 +29,7 @@ NS = {TET: 4, PRISM: 6}
 NQ = {QUAD_TET1: 1, QUAD_TET4: 4, QUAD_PRISM6: 6}
 
 _STATUS = {0: "FE_OK", 1: "FE_NOT_READY", -1: "FE_ERR_INVALID_ARG", -2: "FE_ERR_OOM", -3: "FE_ERR_BUDGET",
-           -4: "FE_ERR_CUDA", -5: "FE_ERR_TIMEOUT", -6: "FE_ERR_UNSUPPORTED"}
+           -4: "FE_ERR_CUDA", -5: "FE_ERR_TIMEOUT", -6: "FE_ERR_UNSUPPORTED", -7: "FE_ERR_PARTIAL"}
 
 
 class FeError(RuntimeError):
@@ -121,6 +121,7 @@ _SIGS = [
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("fe_integrate_tet_noalloc", ctypes.c_int, [ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
     ("fe_selftest_bounded_wait", ctypes.c_int, [_P, ctypes.c_uint, _P]),
+    ("fe_ctx_inject_fault", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64]),
     ("fe_set_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), ctypes.c_int,
                                     ctypes.c_int]),
 ]
@@ -176,6 +177,7 @@ def n_coefs(kind, quad, coef_mode):
     return (1 if kind == POISSON else 20) * (NQ[quad] if coef_mode == PER_QPOINT else 1)
 
 
+FAULT_NONE, FAULT_ALLOC, FAULT_SKIP_TILES = 0, 1, 2   # fe_ctx_inject_fault kinds
 QSS, SQS, SSQ = 0, 1, 2   # loop orderings (Sec. 3.3)
 
 
@@ -439,6 +441,13 @@ class Context:
     def selftest_bounded_wait(self, polls: int = 1 << 16) -> int:
         """Run the failure-detection self-test; returns the status (FE_ERR_TIMEOUT expected)."""
         return int(load().fe_selftest_bounded_wait(self.h, polls, self._stream(None, True)))
+
+    def inject_fault(self, kind: int, count: int = 1, param: int = 1):
+        """Host-side fault injection for failure-detection tests (FAULT_ALLOC: the next
+        `count` device allocations fail as out of memory; FAULT_SKIP_TILES: the next
+        `count` main-kernel launches skip every tile whose index is a multiple of
+        `param` and the next sync reports FE_ERR_PARTIAL; FAULT_NONE clears both)."""
+        _check(load().fe_ctx_inject_fault(self.h, kind, count, param), self.h)
 
     def set_profiling(self, on: bool):
         _check(load().fe_ctx_set_profiling(self.h, int(on)), self.h)

@@ -167,8 +167,8 @@ static fe_status upload_segs(fe_ctx *ctx, BatchPlan *pl, const std::vector<Batch
     if (pl->d_segs) cudaFree(pl->d_segs);
     pl->d_segs = nullptr;
     pl->n_segs = unsigned(segs.size());
-    fe_status st = cuda_check(ctx, cudaMalloc(&pl->d_segs, std::max<size_t>(1, segs.size()) * sizeof(BatchSeg)),
-                              "cudaMalloc(segments)");
+    fe_status st = ctx_malloc(ctx, reinterpret_cast<void **>(&pl->d_segs),
+                              std::max<size_t>(1, segs.size()) * sizeof(BatchSeg), "cudaMalloc(segments)");
     if (st != FE_OK) return st;
     st = cuda_check(ctx, cudaMemcpy(pl->d_segs, segs.data(), segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice),
                     "cudaMemcpy(segments)");
@@ -217,7 +217,7 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
     uint64_t total = 0;
     for (int i = 0; i < n; ++i) total += uint64_t(items[i].args.n_elem);
     fe_status st = ensure_scratch(ctx, pl->scratch, total);
-    if (st == FE_OK) st = cuda_check(ctx, cudaMalloc(&pl->d_counter, 256), "cudaMalloc(counter)");
+    if (st == FE_OK) st = ctx_malloc(ctx, reinterpret_cast<void **>(&pl->d_counter), 256, "cudaMalloc(counter)");
     for (int i = 0; i < n && st == FE_OK; ++i) {
         const fe_elem_args &a = items[i].args;
         const fe_out &o = items[i].out;
@@ -241,7 +241,7 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
     }
     if (st == FE_OK) {
         pl->n_items = unsigned(n);
-        st = cuda_check(ctx, cudaMalloc(&pl->d_items, sizeof(BatchItemDev) * n), "cudaMalloc(items)");
+        st = ctx_malloc(ctx, reinterpret_cast<void **>(&pl->d_items), sizeof(BatchItemDev) * n, "cudaMalloc(items)");
     }
     if (st == FE_OK)
         st = cuda_check(ctx, cudaMemcpy(pl->d_items, dev.data(), sizeof(BatchItemDev) * n, cudaMemcpyHostToDevice),
@@ -354,7 +354,7 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
         db.d_tab = db.h_tab = nullptr;
         db.cap_tab = 0;
         const size_t cap = std::max(need, size_t(64) << 10);
-        r = cuda_check(ctx, cudaMalloc(&db.d_tab, cap), "cudaMalloc(batch table)");
+        r = ctx_malloc(ctx, reinterpret_cast<void **>(&db.d_tab), cap, "cudaMalloc(batch table)");
         if (r == FE_OK) r = cuda_check(ctx, cudaMallocHost(&db.h_tab, cap), "cudaMallocHost(batch table)");
         if (r != FE_OK) return r;
         db.cap_tab = cap;
@@ -412,7 +412,7 @@ fe_status fe_mesh_register(fe_ctx *ctx, fe_elem_type type, int64_t n_elem, const
     if (ctx->hbm_used.load() + bytes > ctx->hbm_budget)
         return set_error(ctx, FE_ERR_BUDGET, "resident mesh does not fit the HBM budget");
     double *d = nullptr;
-    fe_status st = cuda_check(ctx, cudaMalloc(&d, bytes), "cudaMalloc(mesh)");
+    fe_status st = ctx_malloc(ctx, reinterpret_cast<void **>(&d), bytes, "cudaMalloc(mesh)");
     if (st != FE_OK) return st;
     cudaError_t e = cudaSuccess;
     if (layout == FE_LAYOUT_AOS) {

@@ -24,7 +24,8 @@ constexpr int packed_index(int ns, int r, int s) { return r * ns - r * (r - 1) /
 enum StatusBits : int {
     ST_TMA_TIMEOUT = 1,       // a bounded wait on a bulk copy ran out
     ST_FIXUP_OVERFLOW = 2,    // the fix-up list was too short (never with capacity = n)
-    ST_BAD_TILE = 4           // a batch tile descriptor was out of range
+    ST_BAD_TILE = 4,          // a batch tile descriptor was out of range
+    ST_SKIPPED_TILES = 8      // injected fault: tiles were skipped, outputs incomplete
 };
 
 // One homogeneous element set as the kernels see it (device pointers).
@@ -47,6 +48,8 @@ struct ElemParams {
     const int *conn;               // INDEXED: [n][NS] node indices into X (nodes [n_nodes][3])
     long long n_nodes;
     const void *xv;                // APPLY: nodal input vector; A is y, B is f (may be null)
+    long long skip_mod;            // injected fault (fe_ctx_inject_fault): > 0 skips every
+                                   // tile whose index is a multiple of it; 0 in normal use
 };
 
 // Parameters of the coefficient function (FE_COEF_FUNCTION_U), passed by value

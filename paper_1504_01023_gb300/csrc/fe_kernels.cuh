@@ -995,6 +995,10 @@ __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256,
     const int B = blockDim.x;
     const int64_t ntiles = (p.n + B - 1) / B;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (p.skip_mod > 0 && tile % p.skip_mod == 0) {   // injected fault: no load, no store
+            if (threadIdx.x == 0) atomicOr(p.status, ST_SKIPPED_TILES);
+            continue;
+        }
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
         if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase, &tm, &fn)) return;
@@ -1020,6 +1024,10 @@ __global__ void __launch_bounds__(256)
     const int B = blockDim.x / 2;
     const int64_t ntiles = (p.n + B - 1) / B;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (p.skip_mod > 0 && tile % p.skip_mod == 0) {   // injected fault: no load, no store
+            if (threadIdx.x == 0) atomicOr(p.status, ST_SKIPPED_TILES);
+            continue;
+        }
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
         if (!process_tile<PRISM, KIND, PREC, Q_PRISM6, CPQ, AOS, AOS, 2>(p, e0, nb, smem, &bar, phase, &tm, &fn))

@@ -34,6 +34,22 @@ fe_status cuda_check(fe_ctx *ctx, cudaError_t e, const char *what) {
     return set_error(ctx, e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA, msg);
 }
 
+bool take_alloc_fault(fe_ctx *ctx) {
+    if (!ctx) return false;
+    int64_t left = ctx->fail_allocs.load();
+    while (left > 0)
+        if (ctx->fail_allocs.compare_exchange_weak(left, left - 1)) return true;
+    return false;
+}
+
+fe_status ctx_malloc(fe_ctx *ctx, void **p, size_t bytes, const char *what) {
+    if (take_alloc_fault(ctx)) {
+        *p = nullptr;
+        return set_error(ctx, FE_ERR_OOM, std::string(what) + ": injected allocation failure");
+    }
+    return cuda_check(ctx, cudaMalloc(p, bytes), what);
+}
+
 int ns_of(fe_elem_type t) { return t == FE_TET ? 4 : 6; }
 int nq_of(fe_quad q) { return q == FE_QUAD_TET1 ? 1 : (q == FE_QUAD_TET4 ? 4 : 6); }
 int nc_of(fe_elem_type type, const fe_elem_args *a) {
@@ -44,9 +60,9 @@ static int csize(fe_precision p) { return p == FE_FP32_MIXED ? 4 : 8; }
 
 fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n) {
     if (!s.fix_count) {
-        fe_status st = cuda_check(ctx, cudaMalloc(&s.fix_count, 64), "cudaMalloc(fix_count)");
+        fe_status st = ctx_malloc(ctx, reinterpret_cast<void **>(&s.fix_count), 64, "cudaMalloc(fix_count)");
         if (st != FE_OK) return st;
-        st = cuda_check(ctx, cudaMalloc(&s.status, 64), "cudaMalloc(status)");
+        st = ctx_malloc(ctx, reinterpret_cast<void **>(&s.status), 64, "cudaMalloc(status)");
         if (st != FE_OK) return st;
         cudaMemset(s.fix_count, 0, 64);
         cudaMemset(s.status, 0, 64);
@@ -57,7 +73,8 @@ fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n) {
         s.fix_list = nullptr;
         s.fix_cap = 0;
         uint64_t cap = std::max<uint64_t>(n, 1024);
-        fe_status st = cuda_check(ctx, cudaMalloc(&s.fix_list, cap * sizeof(unsigned long long)), "cudaMalloc(fix_list)");
+        fe_status st = ctx_malloc(ctx, reinterpret_cast<void **>(&s.fix_list), cap * sizeof(unsigned long long),
+                                  "cudaMalloc(fix_list)");
         if (st != FE_OK) return st;
         s.fix_cap = static_cast<unsigned>(cap);
     }
@@ -269,6 +286,9 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     p.conn = a->coords_layout == FE_LAYOUT_INDEXED ? a->conn : nullptr;
     p.n_nodes = a->coords_layout == FE_LAYOUT_INDEXED ? a->n_nodes : 0;
     p.xv = x;
+    if (ctx->skip_launches.load() > 0 && !force) {   // injected fault: this launch skips tiles
+        if (ctx->skip_launches.fetch_sub(1) > 0) p.skip_mod = ctx->skip_mod;
+    }
     const bool fixup = a->prec != FE_FP64;   // mixed and double-word forms flag elements
     if (fixup) {
         fe_status e = ensure_scratch(ctx, s, uint64_t(a->n_elem));
@@ -350,7 +370,7 @@ static fe_status ensure_stage(fe_ctx *ctx, int slot, int idx, uint64_t bytes) {
     ctx->stage[slot][idx] = nullptr;
     ctx->stage_bytes[slot][idx] = 0;
     bytes = std::max<uint64_t>(bytes, 256);
-    fe_status st = cuda_check(ctx, cudaMalloc(&ctx->stage[slot][idx], bytes), "cudaMalloc(stage)");
+    fe_status st = ctx_malloc(ctx, &ctx->stage[slot][idx], bytes, "cudaMalloc(stage)");
     if (st == FE_OK) ctx->stage_bytes[slot][idx] = bytes;
     return st;
 }
@@ -723,6 +743,8 @@ fe_status fe_ctx_sync(fe_ctx *ctx) {
         if (s) {
             cudaMemset(ctx->scratch.status, 0, sizeof(int));
             if (s & ST_TMA_TIMEOUT) return set_error(ctx, FE_ERR_TIMEOUT, "a bulk copy wait ran out");
+            if (s & ST_SKIPPED_TILES)
+                return set_error(ctx, FE_ERR_PARTIAL, "tiles were skipped (injected fault): outputs incomplete");
             return set_error(ctx, FE_ERR_CUDA, "device status word " + std::to_string(s));
         }
     }
@@ -799,6 +821,27 @@ fe_status fe_apply_prism(fe_ctx *ctx, const fe_elem_args *args, const void *x, v
 }
 
 uint64_t fe_launch_count(void) { return g_launches.load(); }
+
+fe_status fe_ctx_inject_fault(fe_ctx *ctx, fe_fault kind, int64_t count, int64_t param) {
+    if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");
+    if (count < 0) return set_error(ctx, FE_ERR_INVALID_ARG, "negative fault count");
+    switch (kind) {
+        case FE_FAULT_NONE:
+            ctx->fail_allocs = 0;
+            ctx->skip_launches = 0;
+            ctx->skip_mod = 0;
+            return FE_OK;
+        case FE_FAULT_ALLOC:
+            ctx->fail_allocs = count;
+            return FE_OK;
+        case FE_FAULT_SKIP_TILES:
+            if (param < 1) return set_error(ctx, FE_ERR_INVALID_ARG, "tile period must be >= 1");
+            ctx->skip_mod = param;
+            ctx->skip_launches = count;
+            return FE_OK;
+    }
+    return set_error(ctx, FE_ERR_INVALID_ARG, "unknown fault kind");
+}
 
 fe_status fe_selftest_bounded_wait(fe_ctx *ctx, unsigned polls, void *stream) {
     if (!ctx) return set_error(nullptr, FE_ERR_INVALID_ARG, "null context");

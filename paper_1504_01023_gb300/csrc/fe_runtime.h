@@ -97,6 +97,11 @@ struct fe_ctx {
     fe::BatchCache *batch = nullptr;
     fe::ServeState *serve = nullptr;
     int serve_slots = 4;
+
+    // injected faults (fe_ctx_inject_fault; test only)
+    std::atomic<int64_t> fail_allocs{0};   // device allocations still to fail
+    std::atomic<int64_t> skip_launches{0}; // main-kernel launches still to skip tiles
+    int64_t skip_mod = 0;                  // their tile period
 };
 
 namespace fe {
@@ -106,6 +111,11 @@ fe_status cuda_check(fe_ctx *ctx, cudaError_t e, const char *what);
 // lower it; one process-wide record under a mutex, shared by every entry point
 // that launches the kernel (ctx may be null).
 fe_status set_smem_attr(fe_ctx *ctx, const void *k, int64_t smem);
+// cudaMalloc for the context's own buffers; an injected allocation fault
+// (fe_ctx_inject_fault) makes it fail with FE_ERR_OOM without allocating.
+fe_status ctx_malloc(fe_ctx *ctx, void **p, size_t bytes, const char *what);
+// True (and one injected fault used up) if the context's next allocation must fail.
+bool take_alloc_fault(fe_ctx *ctx);
 fe_status ensure_scratch(fe_ctx *ctx, Scratch &s, uint64_t n);
 void free_scratch(Scratch &s);
 // Launch main + fix-up kernels of one homogeneous set (device pointers).

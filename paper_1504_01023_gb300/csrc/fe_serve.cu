@@ -168,7 +168,9 @@ static void launch_jobs(ServeState *s, Slot &sl, std::vector<Job> &jobs) {
         auto r256 = [](uint64_t v) { return (v + 255) / 256 * 256; };
         const uint64_t bA = r256(uint64_t(m.n_elem) * ns * ns * cs), bB = r256(uint64_t(m.n_elem) * ns * cs);
         void *base = nullptr;
-        cudaError_t e = cudaMallocFromPoolAsync(&base, bA + bB + r256(uint64_t(m.n_elem)), s->pool, sl.stream);
+        cudaError_t e = take_alloc_fault(ctx)   // an injected fault fails it as out of memory
+                            ? cudaErrorMemoryAllocation
+                            : cudaMallocFromPoolAsync(&base, bA + bB + r256(uint64_t(m.n_elem)), s->pool, sl.stream);
         if (e != cudaSuccess) {
             j.status = cuda_check(ctx, e, "cudaMallocFromPoolAsync(serve outputs)");
             continue;
