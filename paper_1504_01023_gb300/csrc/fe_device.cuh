@@ -413,6 +413,100 @@ __device__ __forceinline__ void tet_generic_products_pe(const V3<T> g[3], T V, c
     for (int r = 0; r < 4; ++r) b[r] = VW * t[r] + e;
 }
 
+// z + x . y and 4 q - (p1 + p2 + p3): double with fused multiply-adds, double-word
+// with one compensated accumulation each.
+__device__ __forceinline__ double dot3_add(const double x[3], const double y[3], double z) {
+    return fma(x[2], y[2], fma(x[1], y[1], fma(x[0], y[0], z)));
+}
+__device__ __forceinline__ DW dot3_add(const DW x[3], const DW y[3], DW z) { return dw_dot_add<3>(x, y, z); }
+__device__ __forceinline__ double lin4(double p1, double p2, double p3, double q) {
+    return fma(4.0, q, -((p1 + p2) + p3));
+}
+__device__ __forceinline__ DW lin4(DW p1, DW p2, DW p3, DW q) { return dw_lin4(p1, p2, p3, q); }
+
+// w / v in double for v in [2^-1022, 2^1021] (v > 0). The float reciprocal of v's
+// leading 24 bits scaled by v's exponent (integer operations) gives y0 with a
+// relative error below 2^-22; one step of the third-order Newton iteration
+// (Householder) y = y0 (1 + e + e^2), e = 1 - v y0, leaves e^3 < 2^-66, so w y is
+// within about an ulp of w / v: four double operations instead of a correctly
+// rounded division (a few times as many on this GPU's double pipe).
+__device__ __forceinline__ double recip_scaled(double v, double w) {
+    const uint32_t hw = static_cast<uint32_t>(__double2hiint(v));
+    const uint32_t lw = static_cast<uint32_t>(__double2loint(v));
+    const uint32_t ev = (hw >> 20) & 0x7FFu;
+    const float m = __uint_as_float(0x3F800000u | ((hw & 0xFFFFFu) << 3) | (lw >> 29));   // in [1, 2)
+    const uint32_t rb = __float_as_uint(__frcp_rn(m));                                      // in (1/2, 1]
+    const uint32_t er = (rb >> 23) & 0xFFu;
+    // r 2^(1023 - ev): double exponent field er - 127 + 1023 - (ev - 1023)
+    const uint32_t yh = ((er + 1919u - ev) << 20) | ((rb & 0x7FFFFFu) >> 3);
+    const double y0 = __hiloint2double(static_cast<int>(yh), static_cast<int>(rb << 29));
+    const double wy0 = w * y0;
+    const double e = fma(-v, y0, 1.0);
+    return fma(wy0, fma(e, e, e), wy0);
+}
+
+// Generic tetrahedron with per-element coefficients as one bilinear form (FP64
+// and double-word forms, whose arithmetic bounds the kernel). With the cofactor
+// rows a_m = det J grad phi_m (m = 1..3), a_0 = -(a_1 + a_2 + a_3), the augmented
+// rows at_r = (a_r, 1) and
+//   M = [ f C      sm c^{i0} ]      f = W / |det J|, sm = sign(det J) W / 4,
+//       [ sm c^{0j}   mu     ]      mu = |det J| c^{00} M2_01,
+// every entry of A^e is at_r M at_s^T, plus (M2_00 - M2_01) |det J| c^{00} on
+// the diagonal: the diffusion V W grad phi_r C grad phi_s, the convection
+// V m (c^{i0} . grad phi_r) + V m (c^{0i} . grad phi_s) (m_r = W/4 for both rules)
+// and the mass V c^{00} M2_rs of tet_generic_products_pe, regrouped (the same
+// quadrature, another rounding order). Row and column 0 follow from
+// at_0 = -(at_1 + at_2 + at_3) + (0, 0, 0, 4). Likewise b_r = at_r . (sW d, e)
+// with sW = sign(det J) W, e = |det J| d^0 W / 4.
+template <class T, int QUAD, class CS>
+__device__ __forceinline__ void tet_generic_aug(const V3<T> a3[3], T f, T sm, T sW, T V, const CS &c, T A[16],
+                                                T b[4]) {
+    constexpr TetSums S = tet_sums<QUAD>();
+    const T a[3][3] = {{a3[0].x, a3[0].y, a3[0].z}, {a3[1].x, a3[1].y, a3[1].z}, {a3[2].x, a3[2].y, a3[2].z}};
+    T M[3][4], M3[4];          // rows i = 0..2 of M (columns 0..3), then row 3
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[i][j] = f * c(4 * (i + 1) + (j + 1));
+        M[i][3] = sm * c(4 * (i + 1));
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M3[j] = sm * c(j + 1);
+    const T mu = (V * c(0)) * T(S.M2[0][1]);
+    M3[3] = mu;
+    // P_r = at_r M, r = 1..3, then P_0
+    T P[4][4];
+#pragma unroll
+    for (int r = 1; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T col[3] = {M[0][k], M[1][k], M[2][k]};
+            P[r][k] = dot3_add(a[r - 1], col, M3[k]);
+        }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) P[0][k] = lin4(P[1][k], P[2][k], P[3][k], M3[k]);
+    // A_rs = P_r . at_s
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const T pr[3] = {P[r][0], P[r][1], P[r][2]};
+#pragma unroll
+        for (int s = 1; s < 4; ++s) A[4 * r + s] = dot3_add(pr, a[s - 1], P[r][3]);
+        A[4 * r] = lin4(A[4 * r + 1], A[4 * r + 2], A[4 * r + 3], P[r][3]);
+    }
+    if constexpr (S.M2[0][0] != S.M2[0][1]) {
+        // the diagonal of the mass term: M2_00 - M2_01 = M2_01 for TET4
+        constexpr double ratio = (S.M2[0][0] - S.M2[0][1]) / S.M2[0][1];
+        const T dl = ratio == 1.0 ? mu : mu * T(ratio);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) A[5 * r] += dl;
+    }
+    const T d[3] = {sW * c(17), sW * c(18), sW * c(19)};
+    const T e = (V * c(16)) * T(S.W / 4);
+#pragma unroll
+    for (int r = 1; r < 4; ++r) b[r] = dot3_add(a[r - 1], d, e);
+    b[0] = lin4(b[1], b[2], b[3], e);
+}
+
 // Laplace load vector: b_r = V sum_q w_q d0_q phi_r(q) (d0 per element: V d0 m_r).
 template <class T, int QUAD, int CPQ, class CS> __device__ __forceinline__ void tet_poisson_b(T V, const CS &c, T b[4]) {
     constexpr TetSums S = tet_sums<QUAD>();

@@ -199,6 +199,37 @@ __device__ __forceinline__ DW dw_dot(const DW *x, const DW *y, const int *sign =
     }
     return dw_fast_two_sum(p, c);
 }
+// z + sum of N products of double-words, the same accumulation started from z.
+template <int N> __device__ __forceinline__ DW dw_dot_add(const DW *x, const DW *y, DW z) {
+    float p = z.h;
+    float c = z.l;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float q = __fmul_rn(x[i].h, y[i].h);
+        const float e = __fmaf_rn(x[i].h, y[i].h, -q);
+        const DW s = dw_two_sum(p, q);
+        p = s.h;
+        c = __fadd_rn(c, __fadd_rn(s.l, e));
+        c = __fmaf_rn(x[i].h, y[i].l, c);
+        c = __fmaf_rn(x[i].l, y[i].h, c);
+    }
+    return dw_fast_two_sum(p, c);
+}
+// 4 q - (p1 + p2 + p3), the high words summed with TwoSum and every error and
+// low word gathered in one float (4 q is exact).
+__device__ __forceinline__ DW dw_lin4(DW p1, DW p2, DW p3, DW q) {
+    float p = __fmul_rn(4.0f, q.h);
+    float c = __fmul_rn(4.0f, q.l);
+    const DW v[3] = {p1, p2, p3};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const DW s = dw_two_sum(p, -v[i].h);
+        p = s.h;
+        c = __fadd_rn(c, __fadd_rn(s.l, -v[i].l));
+    }
+    return dw_fast_two_sum(p, c);
+}
+
 // a b - c d
 __device__ __forceinline__ DW dw_diff_prod(DW a, DW b, DW c, DW d) {
     const DW x[2] = {a, c}, y[2] = {b, d};

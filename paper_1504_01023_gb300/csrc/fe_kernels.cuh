@@ -58,20 +58,25 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CP
         const V3<double> e2 = V3<double>{x(6), x(7), x(8)} - x0;
         const V3<double> e3 = V3<double>{x(9), x(10), x(11)} - x0;
         const TetGeo<double> geo = tet_geometry(e1, e2, e3);
-        if (!(fabs(geo.det) > 1e-300)) {
+        const double V = fabs(geo.det);
+        // !(V > 1e-300), NaN included, on the bit pattern (ordered like the value
+        // for V >= 0) instead of a double comparison
+        const long long vb = __double_as_longlong(V);
+        if (!(vb > __double_as_longlong(1e-300) && vb <= 0x7FF0000000000000ll)) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) A[k] = 0.0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) b[k] = 0.0;
             return 4;
         }
-        const double V = fabs(geo.det);
+        const bool neg = __double2hiint(geo.det) < 0;
         if (KIND == POISSON) {
             tet_poisson_products<double, QUAD, CPQ>(geo, 1.0 / V, V, c, A, b);
         } else if constexpr (!CPQ) {
-            const double inv = 1.0 / geo.det;
-            const V3<double> g[3] = {inv * geo.a[0], inv * geo.a[1], inv * geo.a[2]};
-            tet_generic_products_pe<double, QUAD>(g, V, c, A, b);
+            constexpr TetSums S = tet_sums<QUAD>();
+            const double f = recip_scaled(V, S.W);
+            tet_generic_aug<double, QUAD>(geo.a, f, neg ? -S.W / 4 : S.W / 4, neg ? -S.W : S.W, V, c, A, b);
+            return neg ? 2 : 0;
         } else {
             const double inv = 1.0 / geo.det;
             V3<double> g[4];
@@ -164,8 +169,11 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, C
         } else {
             DW Ad[16], bd[4];
             if constexpr (!CPQ) {
-                const V3<DW> g[3] = {inv * geo.a[0], inv * geo.a[1], inv * geo.a[2]};
-                tet_generic_products_pe<DW, QUAD>(g, V, cd, Ad, bd);
+                constexpr TetSums S = tet_sums<QUAD>();
+                const bool neg = geo.det.h < 0.0f;
+                const DW f = DW(S.W) * dw_recip(V);
+                tet_generic_aug<DW, QUAD>(geo.a, f, neg ? DW(-S.W / 4) : DW(S.W / 4), neg ? DW(-S.W) : DW(S.W), V, cd,
+                                          Ad, bd);
             } else {
                 V3<DW> g[4];
                 g[1] = inv * geo.a[0];

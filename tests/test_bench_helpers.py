@@ -1,38 +1,57 @@
-"""Host-side pieces of bench.py that need no GPU: the traffic record lookup keyed
-by the kernel-source hash, the roofline helpers and the JSON shapes."""
+"""Host-side pieces of bench.py that need no GPU: the ncu record lookup keyed by
+the kernel-source hash, the roofline helpers and the JSON shapes."""
 import json
-import os
 
 import pytest
 
 import bench
 
 
-def test_traffic_record_matches_current_sources():
-    """When profiles/traffic.md holds a record for the current kernel sources, its
-    DRAM bytes per launch are close to the algorithmic bytes."""
-    t = bench.ncu_traffic("tet_generic_mixed_aos_6M")
-    if t is None:
-        pytest.skip("kernel sources changed since profiles/traffic.md was captured (traffic reads null)")
-    # the DRAM bytes of a launch are within a few percent of the algorithmic bytes
-    assert 0.95 * 1.536e9 <= t <= 1.02 * 1.536e9
-    p = bench.ncu_traffic("prism_generic_mixed_aos_2M")
-    assert p is not None and 0.95 * 1.584e9 <= p <= 1.02 * 1.584e9
+def _records():
+    with open(bench.NCU_RECORDS) as f:
+        return json.load(f)["records"]
 
 
-def test_traffic_lookup_needs_the_hash(tmp_path, monkeypatch):
+def test_ncu_records_are_well_formed():
+    recs = _records()
+    assert recs
+    for tag, r in recs.items():
+        assert len(r["source_hash"]) == 16 and r["elements"] > 0 and r["kernel"]
+        assert any(k in r for k in ("dram_bytes", "fp64_pipe_inst_per_elem", "inst_per_elem")), tag
+
+
+def test_ncu_record_needs_the_current_hash(monkeypatch):
+    recs = _records()
+    tag, r = next(iter(recs.items()))
+    field = next(k for k in ("dram_bytes", "fp64_pipe_inst_per_elem", "inst_per_elem") if k in r)
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: r["source_hash"])
+    assert bench.ncu_record(tag, field) == pytest.approx(float(r[field]))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
-    assert bench.ncu_traffic("tet_generic_mixed_aos_6M") is None
+    assert bench.ncu_record(tag, field) is None
+    assert bench.ncu_record("no such kernel", field) is None
+
+
+def test_traffic_records_close_to_the_algorithmic_bytes():
+    """Every DRAM-bytes record of a full-size capture is within a few percent of
+    the algorithmic bytes of its launch (no re-reads)."""
+    alg = {"tet_generic_mixed_aos": 256, "prism_generic_mixed_aos": 792, "tet_generic_fp64_aos": 416}
+    for tag, r in _records().items():
+        if "dram_bytes" in r and tag in alg and r.get("full_size", True):
+            assert 0.9 * alg[tag] * r["elements"] <= r["dram_bytes"] <= 1.02 * alg[tag] * r["elements"], tag
 
 
 def test_rooflines_of_the_alu_bound_forms():
-    f = bench.fp64_pipe(7000.0, "tet_poisson_tet1")
+    f = bench.pipe_roofline(7000.0, 77.0, 152, 2070.0, bench.FP64_PIPE_PER_CLK_SM, "FP64-pipe", "t")
     assert f["peak"] == pytest.approx(2 * 152 * 2.07e9 / 1e12)
     assert f["achieved"] == pytest.approx(7000e6 * 77 / 1e12)
-    assert 0 < f["frac"] < 1
-    i = bench.issue_roofline(19000.0, "tet_poisson_tet1")
+    assert 0 < f["frac"] < 1 and f["bound"] == "alu"
+    i = bench.pipe_roofline(19000.0, 1436.0, 152, 2070.0, bench.ISSUE_PER_CLK_SM, "thread", "t")
     assert i["peak"] == pytest.approx(4 * 32 * 152 * 2.07e9 / 1e12)
     assert i["frac"] == pytest.approx(19000e6 * 1436 / 1e12 / i["peak"])
+    n = bench.pipe_roofline(19000.0, None, 152, 1900.0, bench.ISSUE_PER_CLK_SM, "thread", "t")
+    assert n["frac"] is None and n["achieved"] is None and n["peak"] == pytest.approx(4 * 32 * 152 * 1.9e9 / 1e12)
+    h = bench.hbm_roofline(6_000_000, 416, 1.0, 6781.1, "measured")
+    assert h["achieved"] == pytest.approx(6e6 * 416 / 1e-3 / 1e9) and h["bound"] == "hbm"
 
 
 def test_shape_and_context_records_are_json():
