@@ -531,6 +531,7 @@ def run_native(args):
         if not args.no_fp64:
             result["double_word_form"], result["fp64_forms"] = double_forms(ctx, dev, api, X, coefs, args, rates)
             result["cfg1_stated"] = cfg1_stated(ctx, dev, api, args, rates)
+            result["threads_per_element"] = tpe_study(ctx, dev, api, mesh, coefs, args)
         del X, C
         torch.cuda.empty_cache()
         if not args.no_e2e:
@@ -1000,6 +1001,63 @@ def cfg1_stated(ctx, dev, api, args, rates):
         del out
     del X, C
     torch.cuda.empty_cache()
+    return res
+
+
+def tpe_study(ctx, dev, api, mesh, coefs, args):
+    """Threads per element (the thread-per-element versus group-per-element
+    variants): for the generic tetrahedra (TET4, per-element coefficients; 2,000,000
+    of the headline mesh) and the generic prisms (PRISM6, per-point coefficients;
+    1,000,000 of the prism workload), in each precision form, the best launch shape
+    of every threads-per-element value (elements per block x persistent, timed
+    like the autotuner), its Melem/s, and the shape the autotuner keeps."""
+    import torch
+    from paper_1504_01023_gb300 import meshgen
+    nt, npr = min(2_000_000, len(mesh)), 1_000_000
+    pm, pc = prism_workload(0, args.n_slab)
+    cases = {"generic tetrahedra, TET4, per-element coefficients, 2,000,000 elements":
+                 (api.TET, mesh[:nt], coefs[:nt], api.QUAD_TET4, api.PER_ELEMENT, (1, 4)),
+             "generic prisms, PRISM6, per-point coefficients, 1,000,000 elements":
+                 (api.PRISM, pm[:npr], pc[:npr], api.QUAD_PRISM6, api.PER_QPOINT, (1, 2, 6))}
+    res = {"unit": "Melem/s", "note": "best shape per threads-per-element value; main-kernel time from profiling "
+                                      "events, 10 calls after one warm-up"}
+    for name, (et, m, c, quad, cm, tpes) in cases.items():
+        n = len(m)
+        X = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+        row = {}
+        for fname, prec in (("fp64", api.FP64), ("mixed", api.FP32_MIXED), ("double_word", api.FP64_DW)):
+            cdt = np.float32 if prec == api.FP32_MIXED else np.float64
+            C = torch.from_numpy(np.ascontiguousarray(c.reshape(n, -1).astype(cdt))).to(dev)
+            out = api.alloc_out(et, n, prec, api.AOS, dev, with_flags=True)
+            kw = dict(kind=api.GENERIC, quad=quad, coef_mode=cm, prec=prec, layout=api.AOS, out_layout=api.AOS,
+                      out=out)
+            call = lambda: ctx.integrate(et, X, C, **kw)
+            per = {}
+            for tpe in tpes:
+                epw = 32 // tpe
+                lim = 512 if (tpe == 1 and et == api.TET and prec != api.FP64_DW) else 256
+                best = None
+                warps = 2
+                while warps * 32 <= lim:
+                    for pers in (0, 1):
+                        try:
+                            ctx.set_shape(warps * epw, pers, et, X, C, tpe=tpe, **kw)
+                        except api.FeError:          # the tile's shared memory does not fit
+                            continue
+                        call()
+                        ms = kernel_ms(ctx, call, 10)
+                        if best is None or ms < best[0]:
+                            best = (ms, warps * epw, pers)
+                    warps *= 2
+                if best is not None:
+                    per[f"tpe{tpe}"] = {"value": n / best[0] / 1e3, "elements_per_block": best[1],
+                                        "persistent": best[2]}
+            tuned = ctx.tune(et, X, C, **kw)
+            row[fname] = {"threads_per_element": per, "tuner_keeps": shape_dict(tuned)}
+            del C, out
+        res[name] = row
+        del X
+        torch.cuda.empty_cache()
     return res
 
 

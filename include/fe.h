@@ -267,11 +267,14 @@ fe_status fe_mesh_release(fe_ctx *ctx, int64_t mesh_id);
 
 /*
  * Batched integration: many element sets of uneven size and mixed type, kind,
- * rule and coefficient mode in one persistent kernel (not in the paper, which
- * runs one homogeneous set per kernel, Sec. 3.2). Blocks take tiles of
- * consecutive elements from a global counter; tiles are ordered by decreasing
- * cost. The launch sequence {counter reset, persistent kernel, fix-up kernel} is
- * captured into a CUDA graph on the first submission of an item list (same items
+ * rule and coefficient mode in one step (not in the paper, which runs one
+ * homogeneous set per kernel, Sec. 3.2): one persistent kernel per combination
+ * (type, kind, rule, coefficient mode) present, all on parallel branches of one
+ * CUDA graph, so that each combination's blocks fill the SMs the others leave
+ * idle. Blocks take tiles of consecutive elements from their combination's
+ * counter; tiles are ordered by decreasing size. The launch sequence {counter
+ * reset, the combinations' persistent kernels, fix-up kernel} is captured into
+ * the graph on the first submission of an item list (same items
  * byte for byte, i.e. same pointers and sizes) and replayed on later ones; the
  * last 8 lists are kept. With autotune on, the first submission times tiles of
  * 64, 128 and 256 elements and, when the list holds prisms, one or two threads
@@ -389,12 +392,18 @@ fe_status fe_ctx_set_profiling(fe_ctx *ctx, int on);
 fe_status fe_ctx_kernel_time(fe_ctx *ctx, double *ms, int64_t *launches, int reset);
 
 /* Autotuner: time every candidate launch shape for the key of (type, args, out)
-   now, on these buffers, and keep the fastest. Candidates: elements per block
-   (powers of two, 64 threads up to the kernel's limit), persistent or not, and
-   for prisms with element-contiguous coordinates and outputs, coefficient arrays
-   and the QSS order, one or two threads per element (two: each thread takes the
-   three points of one zeta level of Algorithm 2's point loop and the pair adds
-   its partial results). Writes the tuning cache if set. */
+   now, on these buffers, and keep the fastest. Candidates: blocks of 64 threads
+   up to the kernel's limit (powers of two), persistent or not, and with
+   element-contiguous coordinates and outputs, coefficient arrays and the QSS
+   order, several threads per element (the intra-element parallelism of Sec. 3.3,
+   Algorithms 4 and 5, with the QSS loop order kept):
+     2 per prism: each thread takes the three points of one zeta level of
+       Algorithm 2's point loop and the pair adds its partial results;
+     4 per tetrahedron: one row of A^e and one entry of b^e per thread, the
+       Jacobian terms formed once per element and shared by shuffles;
+     6 per prism: thread q forms the Jacobian terms at point q, passes them to the
+       group by shuffles and owns row q of A^e and entry q of b^e.
+   Writes the tuning cache if set. */
 fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                   void *stream);
 /* Pin the launch shape of a key (threads = elements per block: 32..512 for
@@ -403,23 +412,26 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, cons
 fe_status fe_set_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                        int block_threads, int persistent);
 /* The launch shape that the next call with this key would use: threads per
-   block (elements per block x threads per element), and whether the grid is
-   persistent (one wave of resident blocks striding over tiles) or one block per
-   tile. */
+   block (elements per block x threads per element, in whole warps of groups as
+   fe_set_launch_shape describes), and whether the grid is persistent (one wave
+   of resident blocks striding over tiles) or one block per tile. */
 fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                        int *block_threads, int *persistent);
 
 /* Launch shape with the threads per element made explicit. */
 typedef struct fe_launch_shape {
     int elems_per_block;           /* elements per tile (one block per tile) */
-    int threads_per_elem;          /* 1, or 2 (prisms as described at fe_tune) */
+    int threads_per_elem;          /* 1; 2 or 6 (prisms), 4 (tetrahedra), as described at fe_tune */
     int persistent;                /* 0 or 1 */
 } fe_launch_shape;
-/* As fe_get_shape / fe_set_shape. Set: threads per block = elems_per_block x
-   threads_per_elem must be a multiple of 32 within the kernel's limit (512 for
-   tetrahedra in the FP64 and mixed forms, 256 otherwise); FE_ERR_UNSUPPORTED for
-   two threads per element where the key does not allow it, or if the shared
-   memory does not fit. */
+/* As fe_get_shape / fe_set_shape. Set: a warp holds 32 / threads_per_elem
+   elements (5 with 6 threads per element, two lanes idle), so elems_per_block
+   must be a multiple of that, and the block's threads (elems_per_block /
+   (32 / threads_per_elem) x 32) at most the kernel's limit (512 for tetrahedra
+   with one thread per element in the FP64 and mixed forms, 256 otherwise);
+   FE_ERR_INVALID_ARG otherwise. FE_ERR_UNSUPPORTED for several threads per
+   element where the key does not allow it (fe_tune), or if the shared memory does
+   not fit. */
 fe_status fe_get_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                               fe_launch_shape *shape);
 fe_status fe_set_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,

@@ -1,6 +1,7 @@
 // Resident meshes and batched integration (host side): tile plans, the
 // autotuner of the batched launch, and CUDA-graph capture of
-// {counter reset, persistent kernel, fix-up kernel}.
+// {counter reset, one persistent kernel per combination on parallel branches,
+// fix-up kernel}.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +57,9 @@ struct BatchPlan {
 struct BatchCache {
     std::list<BatchPlan *> plans;  // most recent first
     cudaStream_t capture_stream = nullptr;
+    // parallel branches of one step: a stream per combination, fork and join events
+    cudaStream_t branch[kCombos] = {nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[kCombos] = {nullptr};
 };
 
 static void free_plan(BatchPlan *pl) {
@@ -72,6 +76,11 @@ void batch_destroy(fe_ctx *ctx) {
     if (!ctx->batch) return;
     for (auto *pl : ctx->batch->plans) free_plan(pl);
     if (ctx->batch->capture_stream) cudaStreamDestroy(ctx->batch->capture_stream);
+    for (int i = 0; i < kCombos; ++i) {
+        if (ctx->batch->branch[i]) cudaStreamDestroy(ctx->batch->branch[i]);
+        if (ctx->batch->ev_join[i]) cudaEventDestroy(ctx->batch->ev_join[i]);
+    }
+    if (ctx->batch->ev_fork) cudaEventDestroy(ctx->batch->ev_fork);
     delete ctx->batch;
     ctx->batch = nullptr;
 }
@@ -177,8 +186,25 @@ static fe_status upload_segs(fe_ctx *ctx, BatchPlan *pl, const std::vector<Batch
     return size_classes(ctx, pl->classes, B);
 }
 
+// Streams and events of the parallel branches (created once per context).
+static fe_status ensure_branches(fe_ctx *ctx, size_t n) {
+    BatchCache *bc = ctx->batch;
+    cudaError_t e = cudaSuccess;
+    if (!bc->ev_fork) e = cudaEventCreateWithFlags(&bc->ev_fork, cudaEventDisableTiming);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        if (!bc->branch[i]) e = cudaStreamCreateWithFlags(&bc->branch[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !bc->ev_join[i]) e = cudaEventCreateWithFlags(&bc->ev_join[i], cudaEventDisableTiming);
+    }
+    return cuda_check(ctx, e, "batch branch streams");
+}
+
 // Enqueue {counter reset, one persistent kernel per combination, fix-up kernel}.
-static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st, bool counters_zeroed = false) {
+// With `branches`, the combinations' kernels go on parallel branches (a fork
+// from `st`, one stream each, a join back before the fix-up), so that the blocks
+// of the next combinations fill the SMs that a finishing one leaves idle instead
+// of waiting for its last tiles; captured, they become parallel graph branches.
+static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st, bool counters_zeroed = false,
+                               bool branches = false) {
     cudaError_t e = cudaSuccess;
     if (!counters_zeroed) {
         e = cudaMemsetAsync(pl->d_counter, 0, kCombos * sizeof(unsigned), st);
@@ -186,14 +212,33 @@ static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st, bool
         if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemsetAsync(batch)");
     }
     int *status = ctx->scratch.status;
-    for (const auto &cl : pl->classes) {
+    const bool fork = branches && pl->classes.size() > 1;
+    BatchCache *bc = ctx->batch;
+    if (fork) {
+        fe_status fs = ensure_branches(ctx, pl->classes.size());
+        if (fs != FE_OK) return fs;
+        e = cudaEventRecord(bc->ev_fork, st);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "cudaEventRecord(batch fork)");
+    }
+    for (size_t i = 0; i < pl->classes.size(); ++i) {
+        const auto &cl = pl->classes[i];
+        cudaStream_t ls = fork ? bc->branch[i] : st;
+        if (fork) {
+            e = cudaStreamWaitEvent(ls, bc->ev_fork, 0);
+            if (e != cudaSuccess) return cuda_check(ctx, e, "cudaStreamWaitEvent(batch fork)");
+        }
         const BatchSeg *segs = pl->d_segs + cl.seg_off;
         unsigned n_segs = cl.n_segs, n_tiles = cl.n_tiles;
         unsigned *counter = pl->d_counter + cl.combo;
         void *args[] = {&pl->d_items, &pl->n_items, &segs, &n_segs, &n_tiles, &counter, &status};
         e = cudaLaunchKernel(kernel_batch(cl.combo), dim3(cl.grid), dim3(pl->block * batch_tpe(cl.combo)), args,
-                             size_t(cl.smem), st);
+                             size_t(cl.smem), ls);
         if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
+        if (fork) {
+            e = cudaEventRecord(bc->ev_join[i], ls);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, bc->ev_join[i], 0);
+            if (e != cudaSuccess) return cuda_check(ctx, e, "batch join");
+        }
     }
     unsigned long long *list = pl->scratch.fix_list;
     unsigned *count = pl->scratch.fix_count;
@@ -277,9 +322,9 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
                     continue;
                 }
                 if (st != FE_OK) break;
-                st = enqueue_batch(ctx, pl, cs);  // warm-up
+                st = enqueue_batch(ctx, pl, cs, false, true);  // warm-up
                 cudaEventRecord(e0, cs);
-                for (int r = 0; r < 3 && st == FE_OK; ++r) st = enqueue_batch(ctx, pl, cs);
+                for (int r = 0; r < 3 && st == FE_OK; ++r) st = enqueue_batch(ctx, pl, cs, false, true);
                 cudaEventRecord(e1, cs);
                 if (st != FE_OK) break;
                 cudaError_t ce = cudaEventSynchronize(e1);
@@ -307,7 +352,7 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) st = cuda_check(ctx, e, "cudaStreamBeginCapture");
         if (st == FE_OK) {
-            fe_status est = enqueue_batch(ctx, pl, cs);
+            fe_status est = enqueue_batch(ctx, pl, cs, false, true);
             e = cudaStreamEndCapture(cs, &pl->graph);
             if (est != FE_OK) st = est;
             else if (e != cudaSuccess) st = cuda_check(ctx, e, "cudaStreamEndCapture");

@@ -419,6 +419,10 @@ __device__ __forceinline__ double dot3_add(const double x[3], const double y[3],
     return fma(x[2], y[2], fma(x[1], y[1], fma(x[0], y[0], z)));
 }
 __device__ __forceinline__ DW dot3_add(const DW x[3], const DW y[3], DW z) { return dw_dot_add<3>(x, y, z); }
+__device__ __forceinline__ float dot3_add(const float x[3], const float y[3], float z) {
+    return fmaf(x[2], y[2], fmaf(x[1], y[1], fmaf(x[0], y[0], z)));
+}
+__device__ __forceinline__ float lin4(float p1, float p2, float p3, float q) { return fmaf(4.0f, q, -((p1 + p2) + p3)); }
 __device__ __forceinline__ double lin4(double p1, double p2, double p3, double q) {
     return fma(4.0, q, -((p1 + p2) + p3));
 }
@@ -443,6 +447,17 @@ __device__ __forceinline__ double recip_scaled(double v, double w) {
     const double wy0 = w * y0;
     const double e = fma(-v, y0, 1.0);
     return fma(wy0, fma(e, e, e), wy0);
+}
+
+// Sign and degeneracy tests on the bit pattern (integer operations; the double
+// comparisons issue on the double pipe): det < 0, and !(|det| > 1e-300) with NaN
+// counted as degenerate (non-negative doubles order like their bit patterns).
+__device__ __forceinline__ bool is_neg(double v) { return __double2hiint(v) < 0; }
+__device__ __forceinline__ bool is_neg(float v) { return v < 0.0f; }
+__device__ __forceinline__ bool is_neg(DW v) { return v.h < 0.0f; }
+__device__ __forceinline__ bool degenerate_det(double det) {
+    const long long vb = __double_as_longlong(det) & 0x7FFFFFFFFFFFFFFFll;
+    return !(vb > __double_as_longlong(1e-300) && vb <= 0x7FF0000000000000ll);
 }
 
 // Generic tetrahedron with per-element coefficients as one bilinear form (FP64
@@ -616,10 +631,14 @@ template <class T> __device__ __forceinline__ PrismFrame<T> prism_frame(const V3
     return f;
 }
 
-// 1/v: IEEE division in double; in float the hardware reciprocal (within 2 ulp),
-// ample for the float form's tolerance and far cheaper than a correctly rounded
-// division.
-__device__ __forceinline__ double recip_fast(double v) { return 1.0 / v; }
+// 1/v: in double the scaled float reciprocal and one third-order Newton step
+// (recip_scaled, within about an ulp; v's sign copied with integer operations);
+// in float the hardware reciprocal (within 2 ulp), ample for the float form's
+// tolerance; both far cheaper than a correctly rounded division.
+__device__ __forceinline__ double recip_fast(double v) {
+    const double r = recip_scaled(fabs(v), 1.0);
+    return __hiloint2double(__double2hiint(r) | (__double2hiint(v) & int(0x80000000u)), __double2loint(r));
+}
 __device__ __forceinline__ float recip_fast(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ DW recip_fast(DW v) { return dw_recip(v); }
 
@@ -832,5 +851,25 @@ __device__ __forceinline__ bool pair_any(bool v, unsigned mask) {
 }
 // Both lanes get the same sum (addition of the two partials commutes).
 template <class T> __device__ __forceinline__ T pair_sum(T v, unsigned mask) { return v + pair_other(v, mask); }
+
+// Groups of n lanes per element (lanes base .. base + n - 1 of a warp; `mask`
+// holds every lane that takes part): the value of lane `src` to every lane.
+__device__ __forceinline__ float grp_get(float v, unsigned mask, int src) { return __shfl_sync(mask, v, src); }
+__device__ __forceinline__ double grp_get(double v, unsigned mask, int src) { return __shfl_sync(mask, v, src); }
+__device__ __forceinline__ DW grp_get(DW v, unsigned mask, int src) {
+    return DW(__shfl_sync(mask, v.h, src), __shfl_sync(mask, v.l, src));
+}
+template <class T> __device__ __forceinline__ V3<T> grp_get(V3<T> v, unsigned mask, int src) {
+    return {grp_get(v.x, mask, src), grp_get(v.y, mask, src), grp_get(v.z, mask, src)};
+}
+// OR of a flag, and sum of a float, over the group (every lane gets the result).
+__device__ __forceinline__ bool grp_any(bool v, unsigned mask, int base, int n) {
+    return ((__ballot_sync(mask, v) >> base) & ((1u << n) - 1u)) != 0u;
+}
+__device__ __forceinline__ float grp_sum(float v, unsigned mask, int base, int n) {
+    float s = 0.0f;
+    for (int k = 0; k < n; ++k) s = __fadd_rn(s, __shfl_sync(mask, v, base + k));
+    return s;
+}
 
 }  // namespace fe

@@ -81,6 +81,9 @@ const void *kernel_tet_dw(int kind, int quad, int cpq, int inl, int outl);
 const void *kernel_prism_dw(int kind, int cpq, int inl, int outl);
 // prisms, two threads per element (element-contiguous input and output)
 const void *kernel_prism_pair(int kind, int prec, int cpq);
+// One group of NS lanes per element (4 for tetrahedra, 6 for prisms), one row each.
+const void *kernel_group_tet(int kind, int prec, int quad, int cpq);
+const void *kernel_group_prism(int kind, int prec, int cpq);
 
 // Fix-up kernels (flagged elements of the mixed and double-word forms, redone
 // with the Jacobian terms in double); they read the list written by the main kernel.

@@ -59,26 +59,23 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CP
         const V3<double> e3 = V3<double>{x(9), x(10), x(11)} - x0;
         const TetGeo<double> geo = tet_geometry(e1, e2, e3);
         const double V = fabs(geo.det);
-        // !(V > 1e-300), NaN included, on the bit pattern (ordered like the value
-        // for V >= 0) instead of a double comparison
-        const long long vb = __double_as_longlong(V);
-        if (!(vb > __double_as_longlong(1e-300) && vb <= 0x7FF0000000000000ll)) {
+        if (degenerate_det(geo.det)) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) A[k] = 0.0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) b[k] = 0.0;
             return 4;
         }
-        const bool neg = __double2hiint(geo.det) < 0;
+        const bool neg = is_neg(geo.det);
         if (KIND == POISSON) {
-            tet_poisson_products<double, QUAD, CPQ>(geo, 1.0 / V, V, c, A, b);
+            tet_poisson_products<double, QUAD, CPQ>(geo, recip_scaled(V, 1.0), V, c, A, b);
         } else if constexpr (!CPQ) {
             constexpr TetSums S = tet_sums<QUAD>();
             const double f = recip_scaled(V, S.W);
             tet_generic_aug<double, QUAD>(geo.a, f, neg ? -S.W / 4 : S.W / 4, neg ? -S.W : S.W, V, c, A, b);
             return neg ? 2 : 0;
         } else {
-            const double inv = 1.0 / geo.det;
+            const double inv = recip_fast(geo.det);
             V3<double> g[4];
             g[1] = inv * geo.a[0];
             g[2] = inv * geo.a[1];
@@ -86,7 +83,7 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CP
             g[0] = -1.0 * (g[1] + g[2] + g[3]);
             tet_generic_products<double, QUAD, CPQ>(g, V, c, A, b);
         }
-        return geo.det < 0.0 ? 2 : 0;
+        return neg ? 2 : 0;
     }
 };
 
@@ -363,10 +360,10 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const T det = dot(cx, a1);
             if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
             if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
-            if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
-            neg |= det < T(0);
+            if constexpr (PREC == FP64) degenerate |= degenerate_det(det);
+            neg |= is_neg(det);
             const T adet = abs_t(det);
-            const T sw = T(R::w(0)) * recip_fast(adet);      // vol / det^2 (equal weights)
+            const T sw = recip_w(adet, T(R::w(0)));          // vol / det^2 (equal weights)
             const T g11 = sw * dot(a1, a1), g12 = sw * dot(a1, a2), g22 = sw * dot(a2, a2);
             if (t == 0) {
                 Ll[0] = g11;
@@ -414,14 +411,21 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
             if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
             if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
-            if constexpr (PREC == FP64) degenerate |= !(fabs(det) > 1e-300);
-            neg |= det < T(0);
+            if constexpr (PREC == FP64) degenerate |= degenerate_det(det);
+            neg |= is_neg(det);
             const T vol = abs_t(det) * T(R::w(0));
             prism_generic_update_rt<T>(g, vol, c, CPQ ? 20 * q : 0, ph, A, b);
         }
     }
 
     __device__ __forceinline__ static T abs_t(T v) { return v < T(0) ? -v : v; }
+    // w / v for v > 0
+    __device__ __forceinline__ static T recip_w(T v, T w) {
+        if constexpr (PREC == FP64)
+            return recip_scaled(v, w);
+        else
+            return w * recip_fast(v);
+    }
     __device__ __forceinline__ static void mirror(T A[36]) {
 #pragma unroll
         for (int r = 0; r < 6; ++r)
@@ -592,6 +596,329 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
     __device__ __forceinline__ static uint8_t fixup(const XS &x, const CS &c, double A[36], double b[6]) {
         bool unused;
         return 1 | ElemMath<PRISM, KIND, FP64, Q_PRISM6, CPQ>::run(x, c, A, b, unused);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Several threads per element, one row each (the intra-element parallelism of
+// the paper's SQS ordering, Algorithms 4 and 5, with the QSS loop order kept):
+// a group of NS lanes per element, lane r owns row r of A^e and entry r of b^e.
+// The Jacobian terms are formed once per element (tetrahedra) or once per point
+// (prisms, lane q at point q) and passed to the group by shuffles, not recomputed
+// per row as Algorithm 4 does.
+// ---------------------------------------------------------------------------
+template <int PREC> struct Form;
+template <> struct Form<FP64> { using T = double; };
+template <> struct Form<MIXED> { using T = float; };
+template <> struct Form<DWORD> { using T = DW; };
+
+// Edge vector x_k - x_0 in the arithmetic of a form (as ElemMath forms it).
+template <int PREC, class XS> __device__ __forceinline__ V3<typename Form<PREC>::T> form_edge(const XS &x, int k) {
+    if constexpr (PREC == FP64) {
+        return V3<double>{x(3 * k), x(3 * k + 1), x(3 * k + 2)} - V3<double>{x(0), x(1), x(2)};
+    } else if constexpr (PREC == DWORD) {
+        return dw_edge_vec(x, k);
+    } else {
+        return {diff_hilo(split_double(x(3 * k)), split_double(x(0))),
+                diff_hilo(split_double(x(3 * k + 1)), split_double(x(1))),
+                diff_hilo(split_double(x(3 * k + 2)), split_double(x(2)))};
+    }
+}
+__device__ __forceinline__ double form_abs(double v) { return fabs(v); }
+__device__ __forceinline__ float form_abs(float v) { return fabsf(v); }
+__device__ __forceinline__ DW form_abs(DW v) { return dw_abs(v); }
+// w / v for v > 0
+__device__ __forceinline__ double form_recip_w(double v, double w) { return recip_scaled(v, w); }
+__device__ __forceinline__ float form_recip_w(float v, float w) { return w * recip_fast(v); }
+__device__ __forceinline__ DW form_recip_w(DW v, DW w) { return w * dw_recip(v); }
+template <class T> __device__ __forceinline__ T sel4(int r, T v0, T v1, T v2, T v3) {
+    return r == 0 ? v0 : (r == 1 ? v1 : (r == 2 ? v2 : v3));
+}
+template <class T> __device__ __forceinline__ T sel3(int r, T v0, T v1, T v2) { return r == 0 ? v0 : (r == 1 ? v1 : v2); }
+// Double-word results of a row: the group's windows (as dw_group_ok over the whole
+// A^e and b^e, from the sums of the rows' magnitudes), then conversion.
+template <int N>
+__device__ __forceinline__ bool dw_rows_out(const DW *A, DW b, double *Ar, double &br, unsigned mask, int base) {
+    float sa = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) sa = __fadd_rn(sa, fabsf(A[k].h));
+    sa = grp_sum(sa, mask, base, N);
+    const float sb = grp_sum(fabsf(b.h), mask, base, N);
+#pragma unroll
+    for (int k = 0; k < N; ++k) Ar[k] = dw_to_double(A[k]);
+    br = dw_to_double(b);
+    return (sa == 0.0f || (sa >= 0x1p-80f && sa <= 0x1p100f)) && (sb == 0.0f || (sb >= 0x1p-80f && sb <= 0x1p100f));
+}
+
+template <int KIND, int PREC, int QUAD, int CPQ> struct TetRows {
+    using T = typename Form<PREC>::T;
+    using CT = typename std::conditional<PREC == MIXED, float, double>::type;
+
+    // Lane r of the group (lanes base .. base + 3): row r of A^e in Ar, b^e_r in br.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, CT Ar[4], CT &br, bool &poor, int r,
+                                                  unsigned mask, int base) {
+        // edge e_r on lanes 1..3, then every edge on every lane
+        const V3<T> er = form_edge<PREC>(x, r > 0 ? r : 1);
+        V3<T> e[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) e[k] = grp_get(er, mask, base + 1 + k);
+        // cofactor row a_r on lane r (a_1 = e2 x e3, a_2 = e3 x e1, a_3 = e1 x e2), det = e1 . a_1 on lane 1
+        const V3<T> u = sel3(r % 3, e[0], e[1], e[2]), v = sel3((r + 1) % 3, e[0], e[1], e[2]);
+        const V3<T> ar = cross(u, v);
+        const T det_r = dot(e[0], ar);
+        V3<T> a[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] = grp_get(ar, mask, base + 1 + k);
+        const T det = grp_get(det_r, mask, base + 1);
+        const bool neg = is_neg(det);
+        poor = false;
+        if constexpr (PREC != FP64) poor = tet_poor(hi_f(e[0]), hi_f(e[1]), hi_f(e[2]), hi_f(det));
+        if constexpr (PREC == DWORD) poor = poor || !dw_det_ok(det.h);
+        if constexpr (PREC == FP64) {
+            if (degenerate_det(det)) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) Ar[s] = 0.0;
+                br = 0.0;
+                return 4;
+            }
+        }
+        if constexpr (PREC == DWORD) {
+            const DwCoef<CS> cd{c};
+            DW A[4], b;
+            products(a, det, neg, cd, r, A, b);
+            poor = !dw_rows_out<4>(A, b, Ar, br, mask, base) || poor;
+        } else {
+            products(a, det, neg, c, r, Ar, br);
+        }
+        return neg ? 2 : 0;
+    }
+
+    // Row r of A^e and b^e_r from the cofactor rows a_1..a_3 and det J.
+    template <class CS>
+    __device__ __forceinline__ static void products(const V3<T> a[3], T det, bool neg, const CS &c, int r, T A[4],
+                                                    T &b) {
+        constexpr TetSums S = tet_sums<QUAD>();
+        const T V = form_abs(det);
+        const V3<T> a0 = -(a[0] + a[1] + a[2]);
+        const V3<T> arow = sel4(r, a0, a[0], a[1], a[2]);
+        if constexpr (KIND == POISSON) {
+            // A_rs = W / |det| a_r . a_s
+            const T k = form_recip_w(V, T(S.W));
+            const V3<T> kr = k * arow;
+            A[0] = dot(kr, a0);
+#pragma unroll
+            for (int s = 1; s < 4; ++s) A[s] = dot(kr, a[s - 1]);
+            T bb[4];
+            tet_poisson_b<T, QUAD, CPQ>(V, c, bb);
+            b = sel4(r, bb[0], bb[1], bb[2], bb[3]);
+        } else if constexpr (!CPQ) {
+            // row r of the augmented bilinear form of tet_generic_aug
+            const T f = form_recip_w(V, T(S.W));
+            const T sm = neg ? T(-S.W / 4) : T(S.W / 4), sW = neg ? T(-S.W) : T(S.W);
+            T M[3][4], M3[4];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) M[i][j] = f * c(4 * (i + 1) + (j + 1));
+                M[i][3] = sm * c(4 * (i + 1));
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M3[j] = sm * c(j + 1);
+            const T mu = (V * c(0)) * T(S.M2[0][1]);
+            M3[3] = mu;
+            const T at[3] = {arow.x, arow.y, arow.z};
+            T P[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const T col[3] = {M[0][k], M[1][k], M[2][k]};
+                P[k] = dot3_add(at, col, M3[k]);
+            }
+            const T pr[3] = {P[0], P[1], P[2]};
+#pragma unroll
+            for (int s = 1; s < 4; ++s) {
+                const T as[3] = {a[s - 1].x, a[s - 1].y, a[s - 1].z};
+                A[s] = dot3_add(pr, as, P[3]);
+            }
+            A[0] = lin4(A[1], A[2], A[3], P[3]);
+            if constexpr (S.M2[0][0] != S.M2[0][1]) {
+                constexpr double ratio = (S.M2[0][0] - S.M2[0][1]) / S.M2[0][1];
+                const T dl = ratio == 1.0 ? mu : mu * T(ratio);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    if (s == r) A[s] += dl;
+            }
+            const T d[3] = {sW * c(17), sW * c(18), sW * c(19)};
+            b = dot3_add(at, d, (V * c(16)) * T(S.W / 4));
+        } else {
+            // per-point coefficients: the weighted sums of tet_generic_products, row r
+            const T inv = recip_fast(det);
+            V3<T> g[4];
+#pragma unroll
+            for (int k = 1; k < 4; ++k) g[k] = inv * a[k - 1];
+            g[0] = -(g[1] + g[2] + g[3]);
+            const V3<T> gr = inv * arow;
+            T Cb[3][3];
+            V3<T> db = {T(0), T(0), T(0)}, Rr = {T(0), T(0), T(0)}, Ps[4];
+            T Mr[4], er = T(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) Cb[i][j] = T(0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                Ps[s] = {T(0), T(0), T(0)};
+                Mr[s] = T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
+                const int o = 20 * q;
+                const T w = T(Rule<QUAD>::w(q));
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) Cb[i][j] += w * c(o + 4 * (i + 1) + (j + 1));
+                const V3<T> ci0 = {w * c(o + 4), w * c(o + 8), w * c(o + 12)};
+                const V3<T> c0i = {w * c(o + 1), w * c(o + 2), w * c(o + 3)};
+                db = db + w * V3<T>{c(o + 17), c(o + 18), c(o + 19)};
+                const T phr = sel4(r, T(Rule<QUAD>::phi(q, 0)), T(Rule<QUAD>::phi(q, 1)), T(Rule<QUAD>::phi(q, 2)),
+                                   T(Rule<QUAD>::phi(q, 3)));
+                Rr = Rr + phr * c0i;
+                er += (phr * w) * c(o + 16);
+                const T c00 = (w * c(o)) * phr;
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    Ps[s] = Ps[s] + T(Rule<QUAD>::phi(q, s)) * ci0;
+                    Mr[s] += c00 * T(Rule<QUAD>::phi(q, s));
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const V3<T> Cg = {Cb[0][0] * g[s].x + Cb[0][1] * g[s].y + Cb[0][2] * g[s].z,
+                                  Cb[1][0] * g[s].x + Cb[1][1] * g[s].y + Cb[1][2] * g[s].z,
+                                  Cb[2][0] * g[s].x + Cb[2][1] * g[s].y + Cb[2][2] * g[s].z};
+                A[s] = V * (dot(gr, Cg) + dot(Ps[s], gr) + dot(Rr, g[s]) + Mr[s]);
+            }
+            b = V * (dot(db, gr) + er);
+        }
+    }
+};
+
+template <int KIND, int PREC, int CPQ> struct PrismRows {
+    using T = typename Form<PREC>::T;
+    using CT = typename std::conditional<PREC == MIXED, float, double>::type;
+
+    // Lane k of the group (lanes base .. base + 5): the Jacobian terms at point
+    // q = k, then row k of A^e in Ar and b^e_k in br over all six points.
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, CT Ar[6], CT &br, bool &poor, int k,
+                                                  unsigned mask, int base) {
+        using R = Rule<Q_PRISM6>;
+        const V3<T> ek = form_edge<PREC>(x, k > 0 ? k : 1);
+        V3<T> rv[6];
+        rv[0] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int j = 1; j < 6; ++j) rv[j] = grp_get(ek, mask, base + j);
+        const PrismFrame<T> f = prism_frame(rv);
+        // this lane's point: level l, triangle point t
+        const int l = k >= 3, t = k - 3 * l;
+        const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
+        const T h0 = t == 0 ? T(1.0 / 3.0) : T(1.0 / 12.0), h1 = t == 1 ? T(1.0 / 3.0) : T(1.0 / 12.0),
+                h2 = t == 2 ? T(1.0 / 3.0) : T(1.0 / 12.0);
+        const V3<T> cx = zb * f.ub + zt * f.ut;
+        const V3<T> cy = zb * f.vb + zt * f.vt;
+        const V3<T> cz = h0 * f.w0 + h1 * f.w1 + h2 * f.w2;
+        const V3<T> a1 = cross(cy, cz), a2 = cross(cz, cx), a3 = cross(cx, cy);
+        const T det = dot(cx, a1);
+        bool bad = false, degenerate = false;
+        if constexpr (PREC != FP64) {
+            const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
+            bad = prism_poor(dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f), hi_f(cz), hi_f(det));
+        }
+        if constexpr (PREC == DWORD) bad = bad || !dw_det_ok(det.h);
+        if constexpr (PREC == FP64) degenerate = degenerate_det(det);
+        poor = grp_any(bad, mask, base, 6);
+        const bool neg = grp_any(is_neg(det), mask, base, 6);
+        degenerate = grp_any(degenerate, mask, base, 6);
+        const T inv = recip_fast(det);
+        const V3<T> rho1 = inv * a1, rho2 = inv * a2, rho3 = inv * a3;
+        const T vol = form_abs(det) * T(R::w(0));
+        if constexpr (PREC == DWORD) {
+            const DwCoef<CS> cd{c};
+            DW A[6], b;
+            accumulate(rho1, rho2, rho3, vol, cd, k, mask, base, A, b);
+            poor = !dw_rows_out<6>(A, b, Ar, br, mask, base) || poor;
+        } else {
+            accumulate(rho1, rho2, rho3, vol, c, k, mask, base, Ar, br);
+        }
+        if (degenerate) {
+#pragma unroll
+            for (int s = 0; s < 6; ++s) Ar[s] = CT(0);
+            br = CT(0);
+            return 4;
+        }
+        return neg ? 2 : 0;
+    }
+
+    // Row k over the six points: the point's rows of J^{-1} and vol from lane q.
+    // With Phi_0s = phi_s, Phi_is = (grad phi_s)_i and u_b = vol sum_a Phi_ak c_ab,
+    // A_ks += sum_b u_b Phi_bs = u_0 phi_s + z_s (u . P_{s mod 3}) + sigma_s h_{s mod 3} (u . rho_3),
+    // grad phi_s = z_s P_a + sigma_s h_a rho_3 (P_0 = -(rho_1 + rho_2), P_1 = rho_1,
+    // P_2 = rho_2; z = zb, sigma = -1 for the bottom nodes, z = zt, sigma = +1 for
+    // the top ones; h_a = lambda_a / 2 at the triangle point).
+    template <class CS>
+    __device__ __forceinline__ static void accumulate(V3<T> rho1, V3<T> rho2, V3<T> rho3, T vol, const CS &c, int k,
+                                                      unsigned mask, int base, T A[6], T &b) {
+        using R = Rule<Q_PRISM6>;
+        const int ak = k - 3 * (k >= 3);
+#pragma unroll
+        for (int s = 0; s < 6; ++s) A[s] = T(0);
+        b = T(0);
+#pragma unroll 1
+        for (int q = 0; q < 6; ++q) {
+            const V3<T> p1 = grp_get(rho1, mask, base + q), p2 = grp_get(rho2, mask, base + q),
+                        p3 = grp_get(rho3, mask, base + q);
+            const T vq = grp_get(vol, mask, base + q);
+            const int lq = q >= 3, tq = q - 3 * lq;
+            const T zb = lq ? T(R::zb(1)) : T(R::zb(0)), zt = lq ? T(R::zt(1)) : T(R::zt(0));
+            T hq[3], lam[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                hq[a] = a == tq ? T(1.0 / 3.0) : T(1.0 / 12.0);
+                lam[a] = a == tq ? T(2.0 / 3.0) : T(1.0 / 6.0);
+            }
+            const V3<T> P0 = -(p1 + p2);
+            // this lane's shape function at q: value and gradient
+            const T zk = k < 3 ? zb : zt;
+            const T hk = sel3(ak, hq[0], hq[1], hq[2]);
+            const V3<T> gk = zk * sel3(ak, P0, p1, p2) + (k < 3 ? -hk : hk) * p3;
+            const T phk = sel3(ak, lam[0], lam[1], lam[2]) * zk;
+            T u0 = T(0);
+            V3<T> u;
+            if constexpr (KIND == GENERIC) {
+                const int o = CPQ ? 20 * q : 0;
+                T ub[4];
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb)
+                    ub[bb] = vq * (phk * c(o + bb) + gk.x * c(o + 4 + bb) + gk.y * c(o + 8 + bb) + gk.z * c(o + 12 + bb));
+                u0 = ub[0];
+                u = {ub[1], ub[2], ub[3]};
+                b += vq * (c(o + 16) * phk + c(o + 17) * gk.x + c(o + 18) * gk.y + c(o + 19) * gk.z);
+            } else {
+                u = vq * gk;
+                b += (vq * c(CPQ ? q : 0)) * phk;
+            }
+            const T w1 = dot(u, p1), w2 = dot(u, p2), w3 = dot(u, p3);
+            const T uP[3] = {-(w1 + w2), w1, w2};
+#pragma unroll
+            for (int s = 0; s < 6; ++s) {
+                const int as = s % 3;
+                const T zs = s < 3 ? zb : zt;
+                T v = zs * uP[as] + (s < 3 ? -hq[as] : hq[as]) * w3;
+                if constexpr (KIND == GENERIC) v = v + u0 * (lam[as] * zs);
+                A[s] += v;
+            }
+        }
     }
 };
 
@@ -804,9 +1131,14 @@ __device__ __forceinline__ uint8_t fix_elem(const XS &x, const CS &c, const Coef
 }
 
 //
-// TPE == 2 (prisms, element-contiguous input and output, coefficient arrays):
-// two threads per element, lanes 2j and 2j + 1 of a warp; the block holds
-// blockDim.x / 2 elements and each lane writes every other entry of its element.
+// TPE > 1 (element-contiguous input and output, coefficient arrays, QSS):
+// a group of TPE lanes of one warp per element, 32 / TPE groups per warp (for
+// TPE = 6 five groups, lanes 30 and 31 idle); the block holds
+// (blockDim.x / 32) x (32 / TPE) elements.
+//   TPE == 2 (prisms): lanes 2j and 2j + 1, one zeta level of the point loop
+//     each; each lane writes every other entry of its element.
+//   TPE == NS (4 for tetrahedra, 6 for prisms): one row of A^e and one entry of
+//     b^e per lane (TetRows, PrismRows).
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL, int TPE = 1>
 __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, int nb, unsigned char *smem, uint64_t *bar,
                                              unsigned &phase, const TmaMaps *tm = nullptr,
@@ -816,11 +1148,13 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>;
     constexpr int NAO = SM::NAO;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
-    static_assert(TPE == 1 || (TPE == 2 && ET == PRISM && INL == AOS && OUTL == AOS && CPQ < 2),
-                  "two threads per element: prisms, element-contiguous, coefficient arrays");
-    const int B = blockDim.x / TPE;          // elements per tile
-    const int tid = threadIdx.x / TPE;       // this thread's element in the tile
-    const int sub = threadIdx.x % TPE;       // its lane within the element's group
+    static_assert(TPE == 1 || (INL == AOS && OUTL == AOS && CPQ < 2 && (TPE == NS || (TPE == 2 && ET == PRISM))),
+                  "several threads per element: element-contiguous, coefficient arrays; 2 (prisms) or NS");
+    constexpr int EPW = 32 / TPE;            // elements (groups) per warp
+    const int lane = threadIdx.x & 31;
+    const int B = (blockDim.x >> 5) * EPW;   // elements per tile
+    const int tid = (threadIdx.x >> 5) * EPW + lane / TPE;  // this thread's element in the tile
+    const int sub = lane % TPE;              // its lane within the element's group
     double *sX = reinterpret_cast<double *>(smem);
     int *sN = reinterpret_cast<int *>(smem);  // INDEXED: the tile's node indices
     CT *sC = reinterpret_cast<CT *>(smem + SM::x_bytes(B));
@@ -831,7 +1165,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     CT *Aout = static_cast<CT *>(p.A);
     CT *Bout = static_cast<CT *>(p.B);
     const int64_t e = e0 + tid;
-    const bool active = tid < nb;
+    const bool active = lane < EPW * TPE && tid < nb;
 
     // ---- stage inputs ----
     if (INL == SOA && tm && p.tma_in) {
@@ -885,7 +1219,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     }
 
     // ---- compute ----
-    CT A[NA], b[NS];   // TPE == 2: this lane's entries 2j + sub in A[j], b[j]
+    CT A[NA], b[NS];   // TPE == 2: this lane's entries 2j + sub in A[j], b[j]; TPE == NS: row sub in A[0..NS), b[0]
     bool poor = false;
     bool idx_ok = true;  // INDEXED: every node index of this element is in range
     // lanes that take part in the pairs' exchanges (both lanes of an element)
@@ -909,8 +1243,12 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
             const SmemSrc<double> xs{INL == SOA ? sX + tid : sX + tid * NX, INL == SOA ? B : 1};
             if constexpr (TPE == 1)
                 fl = run_elem<ET, KIND, PREC, QUAD, CPQ>(xs, cs, fn, A, b, poor);
-            else
+            else if constexpr (TPE == 2)
                 fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run_pair(xs, cs, A, b, poor, sub, pmask);
+            else if constexpr (ET == TET)
+                fl = TetRows<KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b[0], poor, sub, pmask, lane - sub);
+            else
+                fl = PrismRows<KIND, PREC, CPQ>::run(xs, cs, A, b[0], poor, sub, pmask, lane - sub);
         }
         if (PREC != FP64 && poor) fl |= 1;
         if (p.flags && sub == 0) p.flags[e] = fl;
@@ -923,11 +1261,16 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
         return true;
     }
     __syncthreads();   // every input read: the output records reuse the same shared memory
-    if (TPE > 1 && active) {
+    if (TPE == 2 && active) {
 #pragma unroll
         for (int j = 0; j < NA / TPE; ++j) sA[tid * NAO + TPE * j + sub] = A[j];
 #pragma unroll
         for (int j = 0; j < NS / TPE; ++j) sB[tid * NS + TPE * j + sub] = b[j];
+    }
+    if (TPE == NS && TPE > 2 && active) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) sA[tid * NAO + NS * sub + j] = A[j];
+        sB[tid * NS + sub] = b[0];
     }
     if (TPE == 1 && active) {
         // entry k_out of the written A^e: (r, s) row-major, or its upper triangle
@@ -1040,6 +1383,37 @@ __global__ void __launch_bounds__(256)
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
         if (!process_tile<PRISM, KIND, PREC, Q_PRISM6, CPQ, AOS, AOS, 2>(p, e0, nb, smem, &bar, phase, &tm, &fn))
             return;
+    }
+    if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// One group of NS lanes per element (TetRows, PrismRows), element-contiguous
+// input and output: tiles of (blockDim.x / 32) x (32 / NS) elements, grid-stride
+// over tiles.
+// ---------------------------------------------------------------------------
+template <int ET, int KIND, int PREC, int QUAD, int CPQ>
+__global__ void __launch_bounds__(256)
+    group_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
+    constexpr int TPE = ET == TET ? 4 : 6;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    const int B = (blockDim.x >> 5) * (32 / TPE);
+    const int64_t ntiles = (p.n + B - 1) / B;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (p.skip_mod > 0 && tile % p.skip_mod == 0) {   // injected fault: no load, no store
+            if (threadIdx.x == 0) atomicOr(p.status, ST_SKIPPED_TILES);
+            continue;
+        }
+        const int64_t e0 = tile * B;
+        const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
+        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, AOS, AOS, TPE>(p, e0, nb, smem, &bar, phase, &tm, &fn)) return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }

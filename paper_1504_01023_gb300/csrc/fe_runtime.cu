@@ -98,9 +98,27 @@ static bool pair_ok(fe_elem_type type, const fe_elem_args *a, int outl) {
     return type == FE_PRISM && a->coords_layout == FE_LAYOUT_AOS && outl == AOS && !a->ordering && cpq_of(a) < 2;
 }
 
+// Several threads per element of any type (one row each): the same inputs and
+// outputs as two threads per prism.
+static bool group_ok(fe_elem_type type, const fe_elem_args *a, int outl) {
+    return a->coords_layout == FE_LAYOUT_AOS && outl == AOS && !a->ordering && cpq_of(a) < 2 && (type == FE_TET || type == FE_PRISM);
+}
+
+// Threads per element a key may use: 1; 2 (prisms) and NS (4 for tetrahedra, 6 for
+// prisms) with element-contiguous inputs and outputs, coefficient arrays, QSS.
+static bool tpe_ok(fe_elem_type type, const fe_elem_args *a, int outl, int tpe) {
+    if (tpe == 1) return true;
+    if (tpe == 2) return pair_ok(type, a, outl);
+    return tpe == ns_of(type) && group_ok(type, a, outl);
+}
+
 static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int outl, int tpe = 1) {
     const int cpq = cpq_of(a);
     if (tpe == 2) return pair_ok(type, a, outl) ? kernel_prism_pair(a->kind, a->prec, cpq) : nullptr;
+    if (tpe > 2) {
+        if (!tpe_ok(type, a, outl, tpe)) return nullptr;
+        return type == FE_TET ? kernel_group_tet(a->kind, a->prec, a->quad, cpq) : kernel_group_prism(a->kind, a->prec, cpq);
+    }
     if (tpe != 1) return nullptr;
     if (a->ordering) return kernel_study(type, a->kind, a->quad, cpq, a->ordering);
     const int il = a->coords_layout;
@@ -190,6 +208,15 @@ static int max_block(fe_elem_type type, fe_precision prec) {
     return type == FE_TET && prec != FE_FP64_DW ? 512 : 256;
 }
 
+// Threads of a block of `block` elements with `tpe` threads each: groups of tpe
+// lanes fill a warp 32 / tpe at a time (6 lanes per prism: 5 groups per warp, two
+// lanes idle). 0 if `block` is not a whole number of warps' groups.
+static int shape_threads(int block, int tpe) {
+    const int epw = 32 / tpe;
+    if (block < 1 || block % epw) return 0;
+    return block / epw * 32;
+}
+
 static cudaEvent_t pool_event(fe_ctx *ctx) {
     if (!ctx->event_pool.empty()) {
         cudaEvent_t e = ctx->event_pool.back();
@@ -255,7 +282,8 @@ fe_status launch_set(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, cons
     }
     const void *k = main_kernel(type, a, outl, sh.tpe);
     if (!k) return set_error(ctx, FE_ERR_UNSUPPORTED, "no kernel for this combination");
-    const int threads = sh.block * sh.tpe;
+    const int threads = shape_threads(sh.block, sh.tpe);
+    if (!threads) return set_error(ctx, FE_ERR_INVALID_ARG, "bad launch shape");
     const int64_t smem = smem_bytes(type, a, outl, sh.block);
     if (smem + kStaticSmem > ctx->max_smem_optin)
         return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
@@ -576,7 +604,9 @@ static void load_tuning_cache(fe_ctx *ctx) {
         int block = 0, pers = 0, tpe = 1;
         if (!(ls >> dev >> key >> block >> pers)) continue;
         if (!(ls >> tpe)) tpe = 1;
-        if (dev == ctx->device_name && block > 0 && (tpe == 1 || tpe == 2)) ctx->shapes[key] = Shape{block, pers, tpe};
+        if (dev == ctx->device_name && block > 0 && (tpe == 1 || tpe == 2 || tpe == 4 || tpe == 6) &&
+            shape_threads(block, tpe))
+            ctx->shapes[key] = Shape{block, pers, tpe};
     }
 }
 
@@ -893,7 +923,7 @@ fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
     Shape sh = default_shape(type);
     auto it = ctx->shapes.find(shape_key(type, args, out));
     if (it != ctx->shapes.end()) sh = it->second;
-    *block_threads = sh.block * sh.tpe;
+    *block_threads = shape_threads(sh.block, sh.tpe);
     *persistent = sh.persistent;
     return FE_OK;
 }
@@ -919,12 +949,14 @@ fe_status fe_set_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args
     fe_status st = fe_check_args(type, args, out);
     if (st != FE_OK) return st;
     const int B = shape->elems_per_block, t = shape->threads_per_elem;
-    if ((t != 1 && t != 2) || B < 1 || B * t < 32 || B * t > max_block(type, args->prec) || (B * t) % 32 ||
+    const int threads = (t == 1 || t == 2 || t == 4 || t == 6) ? shape_threads(B, t) : 0;
+    if (!threads || threads > (t == 1 ? max_block(type, args->prec) : 256) ||
         (shape->persistent != 0 && shape->persistent != 1))
         return set_error(ctx, FE_ERR_INVALID_ARG, "bad launch shape");
-    if (t == 2 && !pair_ok(type, args, out_mode(out)))
-        return set_error(ctx, FE_ERR_UNSUPPORTED, "two threads per element: prisms with element-contiguous coordinates "
-                                                  "and outputs, coefficient arrays, QSS order only");
+    if (!tpe_ok(type, args, out_mode(out), t))
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "several threads per element: 2 for prisms, 4 for tetrahedra, 6 for "
+                                                  "prisms, with element-contiguous coordinates and outputs, "
+                                                  "coefficient arrays and the QSS order only");
     if (smem_bytes(type, args, out_mode(out), B) + kStaticSmem > ctx->max_smem_optin)
         return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
     ctx->shapes[shape_key(type, args, out)] = Shape{B, shape->persistent, t};
@@ -963,12 +995,16 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const f
     cudaEventCreate(&e1);
     float best = 1e30f;
     Shape best_shape = default_shape(type);
-    // candidates: elements per tile x grid kind, and for prisms with element-
-    // contiguous data also two threads per element
+    // candidates: elements per tile x grid kind, and with element-contiguous data
+    // also several threads per element (2 or 6 per prism, 4 per tetrahedron):
+    // blocks of 64 up to the kernel's limit of threads
     std::vector<Shape> cands;
-    for (int tpe = 1; tpe <= (pair_ok(type, a, out_mode(o)) ? 2 : 1); ++tpe)
-        for (int B = 64 / tpe; B * tpe <= max_block(type, a->prec); B *= 2)
-            for (int pers = 0; pers < 2; ++pers) cands.push_back(Shape{B, pers, tpe});
+    for (int tpe : {1, 2, 4, 6}) {
+        if (!tpe_ok(type, a, out_mode(o), tpe)) continue;
+        const int lim = tpe == 1 ? max_block(type, a->prec) : 256, epw = 32 / tpe;
+        for (int warps = 2; warps * 32 <= lim; warps *= 2)
+            for (int pers = 0; pers < 2; ++pers) cands.push_back(Shape{warps * epw, pers, tpe});
+    }
     for (const Shape &sh : cands) {
         if (smem_bytes(type, a, out_mode(o), sh.block) + kStaticSmem > ctx->max_smem_optin) continue;
         st = launch_set(ctx, type, a, o, ctx->scratch, s, &sh);  // warm-up
