@@ -385,6 +385,21 @@ fe_status fe_selftest_bounded_wait(fe_ctx *ctx, unsigned polls, void *stream);
 typedef enum fe_fault { FE_FAULT_NONE = 0, FE_FAULT_ALLOC = 1, FE_FAULT_SKIP_TILES = 2 } fe_fault;
 fe_status fe_ctx_inject_fault(fe_ctx *ctx, fe_fault kind, int64_t count, int64_t param);
 
+/* Self-test of the double multiplications and additions that the FP64 kernels
+   run in integer instructions (no counterpart in the paper; a test of the
+   implementation): the same inputs through the integer-instruction operations
+   (out_int) and the double-precision instructions (out_hw), which must agree bit
+   for bit. Device arrays on the current device; enqueued on `stream`, returns
+   after it finishes.
+     what = 0: x, y operands [n]; out [2n]: the n products, then the n sums.
+     what = 1: generic tetrahedra, TET4, per-element coefficients: x coordinates
+               [n][4][3], y coefficients [n][20]; out [n][20]: A^e (16) then b^e.
+     what = 2: Laplace tetrahedra, TET1: x as above, y d^0 [n]; out as above.
+   Degenerate elements give zeros. FE_ERR_INVALID_ARG for a bad `what`, n < 0 or
+   null arrays. */
+fe_status fe_selftest_f64_int(int what, const double *x, const double *y, int64_t n, double *out_int,
+                              double *out_hw, void *stream);
+
 /* Profiling: when on, the integration calls record CUDA events around their main
    kernel on the launching stream; fe_ctx_kernel_time returns the summed device
    time in ms and the launch count since the last reset (it synchronises). */

@@ -122,6 +122,7 @@ _SIGS = [
     ("fe_integrate_tet_noalloc", ctypes.c_int, [ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), _P]),
     ("fe_selftest_bounded_wait", ctypes.c_int, [_P, ctypes.c_uint, _P]),
     ("fe_ctx_inject_fault", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64]),
+    ("fe_selftest_f64_int", ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int64, _P, _P, _P]),
     ("fe_set_shape", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ElemArgs), ctypes.POINTER(Out), ctypes.c_int,
                                     ctypes.c_int]),
 ]

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "fe_dword.cuh"
+#include "fe_f64int.cuh"
 #include "fe_internal.h"
 
 namespace fe {
@@ -521,6 +522,150 @@ __device__ __forceinline__ void tet_generic_aug(const V3<T> a3[3], T f, T sm, T 
     for (int r = 1; r < 4; ++r) b[r] = dot3_add(a[r - 1], d, e);
     b[0] = lin4(b[1], b[2], b[3], e);
 }
+
+// ---------------------------------------------------------------------------
+// Plain FP64 tetrahedra with the double multiplications and additions in
+// integer instructions (F64<true>) and the fused multiply-adds on the double
+// pipe: the same IEEE operations in the same order as with F64<false>, so the
+// same bits. The arithmetic is that of tet_geometry, recip_scaled and
+// tet_generic_aug / tet_poisson_products, written out with explicit operations.
+// ---------------------------------------------------------------------------
+template <class O> struct TetF64 {
+    // a = u x v, component i = u_j v_k - u_k v_j as fma(u_j, v_k, -(u_k v_j))
+    __device__ __forceinline__ static void cross(const double u[3], const double v[3], double w[3]) {
+        w[0] = O::fma(u[1], v[2], -O::mul(u[2], v[1]));
+        w[1] = O::fma(u[2], v[0], -O::mul(u[0], v[2]));
+        w[2] = O::fma(u[0], v[1], -O::mul(u[1], v[0]));
+    }
+    __device__ __forceinline__ static double dot3(const double u[3], const double v[3]) {
+        return O::fma(u[2], v[2], O::fma(u[1], v[1], O::mul(u[0], v[0])));
+    }
+    __device__ __forceinline__ static double dot3_add(const double u[3], const double v[3], double z) {
+        return O::fma(u[2], v[2], O::fma(u[1], v[1], O::fma(u[0], v[0], z)));
+    }
+    // 4 q - (p1 + p2 + p3)
+    __device__ __forceinline__ static double lin4(double p1, double p2, double p3, double q) {
+        return O::fma(4.0, q, -O::add(O::add(p1, p2), p3));
+    }
+    // w / v as recip_scaled
+    __device__ __forceinline__ static double recip_w(double v, double w) {
+        const uint32_t hw = static_cast<uint32_t>(__double2hiint(v));
+        const uint32_t lw = static_cast<uint32_t>(__double2loint(v));
+        const uint32_t ev = (hw >> 20) & 0x7FFu;
+        const float m = __uint_as_float(0x3F800000u | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+        const uint32_t rb = __float_as_uint(__frcp_rn(m));
+        const uint32_t er = (rb >> 23) & 0xFFu;
+        const uint32_t yh = ((er + 1919u - ev) << 20) | ((rb & 0x7FFFFFu) >> 3);
+        const double y0 = __hiloint2double(static_cast<int>(yh), static_cast<int>(rb << 29));
+        const double wy0 = O::mul(w, y0);
+        const double e = O::fma(-v, y0, 1.0);
+        return O::fma(wy0, O::fma(e, e, e), wy0);
+    }
+    // Edge vectors, cofactor rows a_1..a_3 and det J of the element; false if
+    // degenerate (!(|det J| > 1e-300), NaN included).
+    template <class XS> __device__ __forceinline__ static bool geometry(const XS &x, double a[3][3], double &det) {
+        double e[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) e[k][i] = O::add(x(3 * (k + 1) + i), -x(i));
+        cross(e[1], e[2], a[0]);
+        cross(e[2], e[0], a[1]);
+        cross(e[0], e[1], a[2]);
+        det = dot3(e[0], a[0]);
+        return !degenerate_det(det);
+    }
+    // tet_generic_aug with explicit operations
+    template <int QUAD, class CS>
+    __device__ __forceinline__ static void generic(const double a[3][3], double det, const CS &c, double A[16],
+                                                   double b[4]) {
+        constexpr TetSums S = tet_sums<QUAD>();
+        const bool neg = is_neg(det);
+        const double V = fabs(det);
+        const double f = recip_w(V, S.W);
+        const double sm = neg ? -S.W / 4 : S.W / 4, sW = neg ? -S.W : S.W;
+        double M[3][4], M3[4];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M[i][j] = O::mul(f, c(4 * (i + 1) + (j + 1)));
+            M[i][3] = O::mul(sm, c(4 * (i + 1)));
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M3[j] = O::mul(sm, c(j + 1));
+        const double mu = O::mul(O::mul(V, c(0)), S.M2[0][1]);
+        M3[3] = mu;
+        double P[4][4];
+#pragma unroll
+        for (int r = 1; r < 4; ++r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double col[3] = {M[0][k], M[1][k], M[2][k]};
+                P[r][k] = dot3_add(a[r - 1], col, M3[k]);
+            }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) P[0][k] = lin4(P[1][k], P[2][k], P[3][k], M3[k]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const double pr[3] = {P[r][0], P[r][1], P[r][2]};
+#pragma unroll
+            for (int s = 1; s < 4; ++s) A[4 * r + s] = dot3_add(pr, a[s - 1], P[r][3]);
+            A[4 * r] = lin4(A[4 * r + 1], A[4 * r + 2], A[4 * r + 3], P[r][3]);
+        }
+        if constexpr (S.M2[0][0] != S.M2[0][1]) {
+            constexpr double ratio = (S.M2[0][0] - S.M2[0][1]) / S.M2[0][1];
+            const double dl = ratio == 1.0 ? mu : O::mul(mu, ratio);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) A[5 * r] = O::add(A[5 * r], dl);
+        }
+        const double d[3] = {O::mul(sW, c(17)), O::mul(sW, c(18)), O::mul(sW, c(19))};
+        const double e = O::mul(O::mul(V, c(16)), S.W / 4);
+#pragma unroll
+        for (int r = 1; r < 4; ++r) b[r] = dot3_add(a[r - 1], d, e);
+        b[0] = lin4(b[1], b[2], b[3], e);
+    }
+    // tet_poisson_products with explicit operations: A_rs = W / |det| a_r . a_s
+    // (r, s = 1..3), row and column 0 from the vanishing sums; b as tet_poisson_b.
+    template <int QUAD, int CPQ, class CS>
+    __device__ __forceinline__ static void poisson(const double a[3][3], double det, const CS &c, double A[16],
+                                                   double b[4]) {
+        constexpr TetSums S = tet_sums<QUAD>();
+        const double V = fabs(det);
+        const double k = recip_w(V, S.W);
+        double G[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = r; s < 3; ++s) G[r][s] = G[s][r] = O::mul(k, dot3(a[r], a[s]));
+        double row0[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) row0[s] = -O::add(O::add(G[0][s], G[1][s]), G[2][s]);
+        A[0] = -O::add(O::add(row0[0], row0[1]), row0[2]);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) A[1 + s] = A[4 * (1 + s)] = row0[s];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = G[r][s];
+        if constexpr (!CPQ || Rule<QUAD>::NQ == 1) {
+            // d^0 per element or a one-point rule: b_r = V d0 m_r, m_r = W / 4
+            const double vd = O::mul(O::mul(V, c(0)), S.m[0]);   // m_r = W / 4 for both rules
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] = vd;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] = 0.0;
+#pragma unroll
+            for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
+                const double wd = O::mul(Rule<QUAD>::w(q), c(q));
+#pragma unroll
+                for (int r = 0; r < 4; ++r) b[r] = O::fma(wd, Rule<QUAD>::phi(q, r), b[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) b[r] = O::mul(b[r], V);
+        }
+    }
+};
 
 // Laplace load vector: b_r = V sum_q w_q d0_q phi_r(q) (d0 per element: V d0 m_r).
 template <class T, int QUAD, int CPQ, class CS> __device__ __forceinline__ void tet_poisson_b(T V, const CS &c, T b[4]) {

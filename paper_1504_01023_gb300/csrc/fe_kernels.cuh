@@ -48,33 +48,22 @@ template <class XS> __device__ __forceinline__ V3<DW> dw_edge_vec(const XS &x, i
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct ElemMath;
 
-// Tetrahedron, FP64 (Algorithm 3 in double).
+// Tetrahedron, FP64 (Algorithm 3 in double). The Laplace kind and the generic
+// kind with per-element coefficients run their double multiplications and
+// additions in integer instructions (TetF64<F64<true>>, the same IEEE results);
+// per-point coefficients take the general products.
 template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CPQ> {
     template <class XS, class CS>
     __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[16], double b[4], bool &poor) {
         poor = false;
-        const V3<double> x0 = {x(0), x(1), x(2)};
-        const V3<double> e1 = V3<double>{x(3), x(4), x(5)} - x0;
-        const V3<double> e2 = V3<double>{x(6), x(7), x(8)} - x0;
-        const V3<double> e3 = V3<double>{x(9), x(10), x(11)} - x0;
-        const TetGeo<double> geo = tet_geometry(e1, e2, e3);
-        const double V = fabs(geo.det);
-        if (degenerate_det(geo.det)) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) A[k] = 0.0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) b[k] = 0.0;
-            return 4;
-        }
-        const bool neg = is_neg(geo.det);
-        if (KIND == POISSON) {
-            tet_poisson_products<double, QUAD, CPQ>(geo, recip_scaled(V, 1.0), V, c, A, b);
-        } else if constexpr (!CPQ) {
-            constexpr TetSums S = tet_sums<QUAD>();
-            const double f = recip_scaled(V, S.W);
-            tet_generic_aug<double, QUAD>(geo.a, f, neg ? -S.W / 4 : S.W / 4, neg ? -S.W : S.W, V, c, A, b);
-            return neg ? 2 : 0;
-        } else {
+        if constexpr (KIND == GENERIC && CPQ) {
+            const V3<double> x0 = {x(0), x(1), x(2)};
+            const V3<double> e1 = V3<double>{x(3), x(4), x(5)} - x0;
+            const V3<double> e2 = V3<double>{x(6), x(7), x(8)} - x0;
+            const V3<double> e3 = V3<double>{x(9), x(10), x(11)} - x0;
+            const TetGeo<double> geo = tet_geometry(e1, e2, e3);
+            if (degenerate_det(geo.det)) return zero(A, b);
+            const double V = fabs(geo.det);
             const double inv = recip_fast(geo.det);
             V3<double> g[4];
             g[1] = inv * geo.a[0];
@@ -82,8 +71,24 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CP
             g[3] = inv * geo.a[2];
             g[0] = -1.0 * (g[1] + g[2] + g[3]);
             tet_generic_products<double, QUAD, CPQ>(g, V, c, A, b);
+            return is_neg(geo.det) ? 2 : 0;
+        } else {
+            using TF = TetF64<F64<true>>;
+            double a[3][3], det;
+            if (!TF::geometry(x, a, det)) return zero(A, b);
+            if constexpr (KIND == POISSON)
+                TF::template poisson<QUAD, CPQ>(a, det, c, A, b);
+            else
+                TF::template generic<QUAD>(a, det, c, A, b);
+            return is_neg(det) ? 2 : 0;
         }
-        return neg ? 2 : 0;
+    }
+    __device__ __forceinline__ static uint8_t zero(double A[16], double b[4]) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) A[k] = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b[k] = 0.0;
+        return 4;
     }
 };
 
