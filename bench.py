@@ -75,8 +75,11 @@ def parse():
                     help="precision form of the timed step: fp64 (default, the line's value), mixed or dw "
                          "(double-word); other forms only for profiling")
     ap.add_argument("--only", action="store_true", help="time the step only (no other keys; profiling)")
-    ap.add_argument("--shape", default=None, help="BLOCK,PERSISTENT: pin the main kernel's launch shape instead of "
-                                                  "autotuning it (profiling)")
+    ap.add_argument("--kind", default="generic", choices=["generic", "poisson"],
+                    help="generic (default) or the Laplace kind (tetrahedra: TET1, d^0 = 1; prisms: d^0 per "
+                         "point); other kinds only for profiling")
+    ap.add_argument("--shape", default=None, help="BLOCK,PERSISTENT[,THREADS_PER_ELEMENT]: pin the main kernel's "
+                                                  "launch shape instead of autotuning it (profiling)")
     ap.add_argument("--n-slab", type=int, default=1000,
                     help="squares per axis of the prism slab (2 n^2 elements); smaller only for profiling")
     return ap.parse_args()
@@ -195,11 +198,17 @@ def same_run_copy_gbs(dev, nbytes=2 << 30, reps=10):
         return None
 
 
+# The sources that determine the element kernels' code: every header, and the
+# translation units that instantiate the single-set kernels (host runtime, batch,
+# serving, study and self-test units are left out).
+KERNEL_UNITS = ("fe_tet_", "fe_prism_", "fe_idx_", "fe_group_")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1504_01023_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith((".cuh", ".h")) or (name.endswith(".cu") and name.startswith(KERNEL_UNITS)):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -433,29 +442,39 @@ def run_native(args):
     ctx = api.Context(dev.index)
     prec = getattr(api, FORMS[args.form][0])
     cdt = np.float32 if prec == api.FP32_MIXED else np.float64
+    lap = args.kind == "poisson"
     if args.workload == "tet":
         et, mesh, coefs = api.TET, *workload(rank, args.n_cubes)
-        kw = dict(kind=api.GENERIC, quad=api.QUAD_TET4, coef_mode=api.PER_ELEMENT, prec=prec,
-                  layout=api.AOS, out_layout=api.AOS)
+        if lap:
+            coefs = np.ones((len(mesh), 1))
+        kw = dict(kind=api.POISSON if lap else api.GENERIC, quad=api.QUAD_TET1 if lap else api.QUAD_TET4,
+                  coef_mode=api.PER_ELEMENT, prec=prec, layout=api.AOS, out_layout=api.AOS)
         wl_name = {"fp64": WORKLOAD, "mixed": MIXED_WORKLOAD}.get(args.form, MESH + ", double-word form")
-        kernel_name = f"elem_kernel<TET,GENERIC,{PREC_TAG[args.form]},TET4,per-element,AOS,AOS>"
-        tag = f"tet_generic_{args.form}_aos"
+        if lap:
+            wl_name = MESH.split(", TET4")[0] + ", Laplace operator, TET1, d^0 = 1, " + args.form + " form"
+        kernel_name = (f"elem_kernel<TET,{'POISSON' if lap else 'GENERIC'},{PREC_TAG[args.form]},"
+                       f"{'TET1' if lap else 'TET4'},per-element,AOS,AOS>")
+        tag = f"tet_{'poisson_tet1' if lap else 'generic'}_{args.form}_aos"
     else:
         et, mesh, coefs = api.PRISM, *prism_workload(rank, args.n_slab)
-        kw = dict(kind=api.GENERIC, quad=api.QUAD_PRISM6, coef_mode=api.PER_QPOINT, prec=prec,
-                  layout=api.AOS, out_layout=api.AOS)
+        if lap:
+            from paper_1504_01023_gb300 import meshgen
+            coefs = meshgen.poisson_coefs(len(mesh), 6, None, seed=meshgen.SEED_BASE + 3)
+        kw = dict(kind=api.POISSON if lap else api.GENERIC, quad=api.QUAD_PRISM6, coef_mode=api.PER_QPOINT,
+                  prec=prec, layout=api.AOS, out_layout=api.AOS)
         wl_name = PRISM_WORKLOAD
-        kernel_name = f"elem_kernel<PRISM,GENERIC,{PREC_TAG[args.form]},PRISM6,per-point,AOS,AOS>"
-        tag = f"prism_generic_{args.form}_aos"
+        kernel_name = f"elem_kernel<PRISM,{'POISSON' if lap else 'GENERIC'},{PREC_TAG[args.form]},PRISM6,per-point,AOS,AOS>"
+        tag = f"prism_{'poisson' if lap else 'generic'}_{args.form}_aos"
     n = len(mesh)
     X = torch.from_numpy(np.ascontiguousarray(mesh)).to(dev)                       # [E,NS,3] f64
     C = torch.from_numpy(np.ascontiguousarray(coefs.reshape(n, -1).astype(cdt))).to(dev)
     out = api.alloc_out(et, n, prec, api.AOS, dev, with_flags=True)
     stream = torch.cuda.current_stream(dev)
     if args.shape:
-        blk, pers = (int(v) for v in args.shape.split(","))
-        ctx.set_shape(blk, pers, et, X, C, out=out, **kw)
-        shape = (blk, pers)
+        vals = [int(v) for v in args.shape.split(",")]
+        blk, pers, tpe = vals[0], vals[1], vals[2] if len(vals) > 2 else 1
+        ctx.set_shape(blk, pers, et, X, C, out=out, tpe=tpe, **kw)
+        shape = (blk, pers, tpe)
     else:
         shape = ctx.tune(et, X, C, out=out, **kw)                                  # autotuner (untimed)
     step = lambda: ctx.integrate(et, X, C, out=out, **kw)
@@ -520,7 +539,7 @@ def run_native(args):
               "roofline": roofline, "gpu_launches": int(launches), "clocks": clk}
     if args.only:
         pass
-    elif rank == 0 and world == 1 and args.workload == "tet":
+    elif rank == 0 and world == 1 and args.workload == "tet" and not lap:
         if args.form == "fp64":
             # the GPU's FP64 results of the timed steps, for the error statistics
             gpu_out = tuple(t.clone() for t in out)

@@ -524,28 +524,32 @@ __device__ __forceinline__ void tet_generic_aug(const V3<T> a3[3], T f, T sm, T 
 }
 
 // ---------------------------------------------------------------------------
-// Plain FP64 tetrahedra with the double multiplications and additions in
-// integer instructions (F64<true>) and the fused multiply-adds on the double
-// pipe: the same IEEE operations in the same order as with F64<false>, so the
-// same bits. The arithmetic is that of tet_geometry, recip_scaled and
-// tet_generic_aug / tet_poisson_products, written out with explicit operations.
+// Plain FP64 tetrahedra with explicit double operations. Each group of
+// multiplications and additions runs on the double pipe (F64<false>) or in
+// integer instructions (F64<true>): OE the edge vectors, OX the products of the
+// cofactors and det J, OM the scalings of the coefficients and of det J, OS the
+// sums of rows and columns; the fused multiply-adds always on the double pipe.
+// Every choice gives the same bits (the same IEEE operations in the same order).
+// The arithmetic is that of tet_geometry, recip_scaled and tet_generic_aug /
+// tet_poisson_products, written out with explicit operations.
 // ---------------------------------------------------------------------------
-template <class O> struct TetF64 {
+template <class OE, class OX, class OM, class OS> struct TetF64 {
+    using O = F64<false>;   // fused multiply-adds
     // a = u x v, component i = u_j v_k - u_k v_j as fma(u_j, v_k, -(u_k v_j))
     __device__ __forceinline__ static void cross(const double u[3], const double v[3], double w[3]) {
-        w[0] = O::fma(u[1], v[2], -O::mul(u[2], v[1]));
-        w[1] = O::fma(u[2], v[0], -O::mul(u[0], v[2]));
-        w[2] = O::fma(u[0], v[1], -O::mul(u[1], v[0]));
+        w[0] = O::fma(u[1], v[2], -OX::mul(u[2], v[1]));
+        w[1] = O::fma(u[2], v[0], -OX::mul(u[0], v[2]));
+        w[2] = O::fma(u[0], v[1], -OX::mul(u[1], v[0]));
     }
-    __device__ __forceinline__ static double dot3(const double u[3], const double v[3]) {
-        return O::fma(u[2], v[2], O::fma(u[1], v[1], O::mul(u[0], v[0])));
+    template <class OP = OX> __device__ __forceinline__ static double dot3(const double u[3], const double v[3]) {
+        return O::fma(u[2], v[2], O::fma(u[1], v[1], OP::mul(u[0], v[0])));
     }
     __device__ __forceinline__ static double dot3_add(const double u[3], const double v[3], double z) {
         return O::fma(u[2], v[2], O::fma(u[1], v[1], O::fma(u[0], v[0], z)));
     }
     // 4 q - (p1 + p2 + p3)
     __device__ __forceinline__ static double lin4(double p1, double p2, double p3, double q) {
-        return O::fma(4.0, q, -O::add(O::add(p1, p2), p3));
+        return O::fma(4.0, q, -OS::add(OS::add(p1, p2), p3));
     }
     // w / v as recip_scaled
     __device__ __forceinline__ static double recip_w(double v, double w) {
@@ -557,7 +561,7 @@ template <class O> struct TetF64 {
         const uint32_t er = (rb >> 23) & 0xFFu;
         const uint32_t yh = ((er + 1919u - ev) << 20) | ((rb & 0x7FFFFFu) >> 3);
         const double y0 = __hiloint2double(static_cast<int>(yh), static_cast<int>(rb << 29));
-        const double wy0 = O::mul(w, y0);
+        const double wy0 = OM::mul(w, y0);
         const double e = O::fma(-v, y0, 1.0);
         return O::fma(wy0, O::fma(e, e, e), wy0);
     }
@@ -568,7 +572,7 @@ template <class O> struct TetF64 {
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) e[k][i] = O::add(x(3 * (k + 1) + i), -x(i));
+            for (int i = 0; i < 3; ++i) e[k][i] = OE::add(x(3 * (k + 1) + i), -x(i));
         cross(e[1], e[2], a[0]);
         cross(e[2], e[0], a[1]);
         cross(e[0], e[1], a[2]);
@@ -588,12 +592,12 @@ template <class O> struct TetF64 {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) M[i][j] = O::mul(f, c(4 * (i + 1) + (j + 1)));
-            M[i][3] = O::mul(sm, c(4 * (i + 1)));
+            for (int j = 0; j < 3; ++j) M[i][j] = OM::mul(f, c(4 * (i + 1) + (j + 1)));
+            M[i][3] = OM::mul(sm, c(4 * (i + 1)));
         }
 #pragma unroll
-        for (int j = 0; j < 3; ++j) M3[j] = O::mul(sm, c(j + 1));
-        const double mu = O::mul(O::mul(V, c(0)), S.M2[0][1]);
+        for (int j = 0; j < 3; ++j) M3[j] = OM::mul(sm, c(j + 1));
+        const double mu = OM::mul(OM::mul(V, c(0)), S.M2[0][1]);
         M3[3] = mu;
         double P[4][4];
 #pragma unroll
@@ -614,12 +618,12 @@ template <class O> struct TetF64 {
         }
         if constexpr (S.M2[0][0] != S.M2[0][1]) {
             constexpr double ratio = (S.M2[0][0] - S.M2[0][1]) / S.M2[0][1];
-            const double dl = ratio == 1.0 ? mu : O::mul(mu, ratio);
+            const double dl = ratio == 1.0 ? mu : OM::mul(mu, ratio);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) A[5 * r] = O::add(A[5 * r], dl);
+            for (int r = 0; r < 4; ++r) A[5 * r] = OS::add(A[5 * r], dl);
         }
-        const double d[3] = {O::mul(sW, c(17)), O::mul(sW, c(18)), O::mul(sW, c(19))};
-        const double e = O::mul(O::mul(V, c(16)), S.W / 4);
+        const double d[3] = {OM::mul(sW, c(17)), OM::mul(sW, c(18)), OM::mul(sW, c(19))};
+        const double e = OM::mul(OM::mul(V, c(16)), S.W / 4);
 #pragma unroll
         for (int r = 1; r < 4; ++r) b[r] = dot3_add(a[r - 1], d, e);
         b[0] = lin4(b[1], b[2], b[3], e);
@@ -636,11 +640,11 @@ template <class O> struct TetF64 {
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int s = r; s < 3; ++s) G[r][s] = G[s][r] = O::mul(k, dot3(a[r], a[s]));
+            for (int s = r; s < 3; ++s) G[r][s] = G[s][r] = OM::mul(k, dot3<OM>(a[r], a[s]));
         double row0[3];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) row0[s] = -O::add(O::add(G[0][s], G[1][s]), G[2][s]);
-        A[0] = -O::add(O::add(row0[0], row0[1]), row0[2]);
+        for (int s = 0; s < 3; ++s) row0[s] = -OS::add(OS::add(G[0][s], G[1][s]), G[2][s]);
+        A[0] = -OS::add(OS::add(row0[0], row0[1]), row0[2]);
 #pragma unroll
         for (int s = 0; s < 3; ++s) A[1 + s] = A[4 * (1 + s)] = row0[s];
 #pragma unroll
@@ -649,7 +653,7 @@ template <class O> struct TetF64 {
             for (int s = 0; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = G[r][s];
         if constexpr (!CPQ || Rule<QUAD>::NQ == 1) {
             // d^0 per element or a one-point rule: b_r = V d0 m_r, m_r = W / 4
-            const double vd = O::mul(O::mul(V, c(0)), S.m[0]);   // m_r = W / 4 for both rules
+            const double vd = OM::mul(OM::mul(V, c(0)), S.m[0]);   // m_r = W / 4 for both rules
 #pragma unroll
             for (int r = 0; r < 4; ++r) b[r] = vd;
         } else {
@@ -657,12 +661,12 @@ template <class O> struct TetF64 {
             for (int r = 0; r < 4; ++r) b[r] = 0.0;
 #pragma unroll
             for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
-                const double wd = O::mul(Rule<QUAD>::w(q), c(q));
+                const double wd = OM::mul(Rule<QUAD>::w(q), c(q));
 #pragma unroll
                 for (int r = 0; r < 4; ++r) b[r] = O::fma(wd, Rule<QUAD>::phi(q, r), b[r]);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) b[r] = O::mul(b[r], V);
+            for (int r = 0; r < 4; ++r) b[r] = OM::mul(b[r], V);
         }
     }
 };

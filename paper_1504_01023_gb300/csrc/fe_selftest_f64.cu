@@ -45,8 +45,8 @@ __global__ void selftest_tet_kernel(const double *__restrict__ x, const double *
             for (int k = 0; k < 16; ++k) o[k] = A[k];
             for (int k = 0; k < 4; ++k) o[16 + k] = b[k];
         };
-        one(TetF64<F64<true>>{}, oi);
-        one(TetF64<F64<false>>{}, oh);
+        one(TetF64<F64<true>, F64<true>, F64<true>, F64<true>>{}, oi);
+        one(TetF64<F64<false>, F64<false>, F64<false>, F64<false>>{}, oh);
     }
 }
 
