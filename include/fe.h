@@ -276,10 +276,13 @@ fe_status fe_mesh_release(fe_ctx *ctx, int64_t mesh_id);
  * reset, the combinations' persistent kernels, fix-up kernel} is captured into
  * the graph on the first submission of an item list (same items
  * byte for byte, i.e. same pointers and sizes) and replayed on later ones; the
- * last 8 lists are kept. With autotune on, the first submission times tiles of
- * 64, 128 and 256 elements and, when the list holds prisms, one or two threads
- * per prism element (as described at fe_tune), and keeps the fastest; without,
- * 128 elements and one thread. fe_batch_set_shape pins the shape instead.
+ * last 8 lists are kept. With autotune on, the first submission times each
+ * combination present on its own with tiles of 64, 128 and 256 elements,
+ * persistent grids (blocks take tiles from the combination's counter) or one
+ * block per tile, and for prisms one or two threads per element (as described at
+ * fe_tune), and keeps the fastest shape of each combination; without, 128
+ * elements, persistent, one thread. fe_batch_set_shape pins one shape for all
+ * combinations instead.
  * Items must be FE_FP32_MIXED, device memory, element-contiguous (AOS) inputs
  * and outputs (FE_ERR_UNSUPPORTED otherwise). At most 2^23 items.
  */
@@ -454,7 +457,8 @@ fe_status fe_set_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args
 /* Pin the shape of batch plans built from now on (fe_batch_submit of a new item
    list): elems_per_block (32..256, a multiple of 32) elements per tile for every
    combination, threads_per_elem (1 or 2) threads per prism element, at most 256
-   threads per block; persistent is ignored (batched kernels are persistent).
+   threads per block; persistent 1 (counter-driven persistent grids) or 0 (one
+   block per tile).
    NULL returns to tuned (autotune on) or default shapes. Lists already submitted
    keep their plans for the shape they were built with. */
 fe_status fe_batch_set_shape(fe_ctx *ctx, const fe_launch_shape *shape);

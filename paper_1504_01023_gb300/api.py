@@ -469,13 +469,14 @@ class Context:
     def mesh_release(self, mesh_id: int):
         _check(load().fe_mesh_release(self.h, mesh_id), self.h)
 
-    def batch_set_shape(self, block=None, tpe=1):
+    def batch_set_shape(self, block=None, tpe=1, persistent=1):
         """Pin the shape of new batch plans (block elements per tile, tpe threads per
-        prism element), or return to tuned/default shapes with block=None."""
+        prism element, persistent grids or one block per tile), or return to
+        tuned/default shapes with block=None."""
         if block is None:
             _check(load().fe_batch_set_shape(self.h, None), self.h)
         else:
-            sh = LaunchShape(block, tpe, 1)
+            sh = LaunchShape(block, tpe, persistent)
             _check(load().fe_batch_set_shape(self.h, ctypes.byref(sh)), self.h)
 
     def batch_submit(self, items, stream=None):

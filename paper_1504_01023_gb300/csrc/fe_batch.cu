@@ -33,6 +33,8 @@ __global__ void soa_to_aos_kernel(const double *__restrict__ in, int64_t stride,
 // counter.
 struct ClassLaunch {
     int combo = 0;
+    int block = 128;                 // elements per tile of this combination
+    int persistent = 1;              // 1: counter-driven persistent grid; 0: one block per tile
     unsigned seg_off = 0, n_segs = 0, n_tiles = 0;
     int grid = 0;
     int64_t smem = 0;
@@ -41,14 +43,12 @@ struct ClassLaunch {
 struct BatchPlan {
     size_t key = 0;
     std::vector<unsigned char> items_bytes;
-    int pinned_block = 0, pinned_tpe = 1;   // the pinned shape it was built with (block 0: none)
+    int pinned_block = 0, pinned_tpe = 1, pinned_pers = 1;   // the pinned shape it was built with (block 0: none)
     BatchItemDev *d_items = nullptr;
     BatchSeg *d_segs = nullptr;
     unsigned n_items = 0, n_segs = 0;
     unsigned *d_counter = nullptr;   // kCombos counters
     Scratch scratch;
-    int block = 128;                 // elements per tile
-    int prism_tpe = 1;               // threads per prism element
     std::vector<ClassLaunch> classes;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -93,11 +93,11 @@ static double combo_cost(int combo) {
     return combo >= 0 && combo < 12 ? cost[combo] : 1.0;
 }
 
-// Segment table of tiles of B consecutive elements: items grouped by combination
-// (heaviest combination first) and, within one, largest first, each with the
-// index of its first tile. Work is proportional to the number of items, not of
-// tiles. Fails if a combination has 2^32 tiles or more.
-static bool make_segs(const std::vector<BatchItemDev> &items, int B, std::vector<BatchSeg> &out,
+// Segment table of tiles of Bc[combination] consecutive elements: items grouped
+// by combination (heaviest combination first) and, within one, largest first,
+// each with the index of its first tile. Work is proportional to the number of
+// items, not of tiles. Fails if a combination has 2^32 tiles or more.
+static bool make_segs(const std::vector<BatchItemDev> &items, const int *Bc, const int *Pc, std::vector<BatchSeg> &out,
                       std::vector<ClassLaunch> &classes) {
     std::vector<std::vector<unsigned>> per(kCombos);
     for (unsigned i = 0; i < items.size(); ++i) {
@@ -115,6 +115,9 @@ static bool make_segs(const std::vector<BatchItemDev> &items, int B, std::vector
                          [&](unsigned a, unsigned b) { return items[a].p.n > items[b].p.n; });
         ClassLaunch cl;
         cl.combo = c;
+        cl.block = Bc[c];
+        cl.persistent = Pc[c];
+        const int B = cl.block;
         cl.seg_off = unsigned(out.size());
         cl.n_segs = unsigned(per[c].size());
         uint64_t tiles = 0;
@@ -132,9 +135,11 @@ static bool make_segs(const std::vector<BatchItemDev> &items, int B, std::vector
 static std::mutex g_attr_mu;
 static int64_t g_attr_set[kCombos] = {0};
 
-// Shared memory attribute and grid (SMs x resident blocks) of each class launch.
-static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes, int B) {
+// Shared memory attribute and grid of each class launch: SMs x resident blocks
+// (persistent) or one block per tile.
+static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes) {
     for (auto &cl : classes) {
+        const int B = cl.block;
         const void *k = kernel_batch(cl.combo);
         const int threads = B * batch_tpe(cl.combo);
         if (threads > 256) return set_error(ctx, FE_ERR_UNSUPPORTED, "batched tile of more than 256 threads");
@@ -164,14 +169,16 @@ static fe_status size_classes(fe_ctx *ctx, std::vector<ClassLaunch> &classes, in
                 occ[{cl.combo, B}] = per_sm;
             }
         }
-        cl.grid = int(std::min<int64_t>(int64_t(std::max(1, per_sm)) * ctx->sms, cl.n_tiles));
+        cl.grid = int(std::min<int64_t>(cl.persistent ? int64_t(std::max(1, per_sm)) * ctx->sms : int64_t(0x7FFFFFFF),
+                                        cl.n_tiles));
     }
     return FE_OK;
 }
 
-static fe_status upload_segs(fe_ctx *ctx, BatchPlan *pl, const std::vector<BatchItemDev> &items, int B) {
+static fe_status upload_segs(fe_ctx *ctx, BatchPlan *pl, const std::vector<BatchItemDev> &items, const int *Bc,
+                             const int *Pc) {
     std::vector<BatchSeg> segs;
-    if (!make_segs(items, B, segs, pl->classes))
+    if (!make_segs(items, Bc, Pc, segs, pl->classes))
         return set_error(ctx, FE_ERR_UNSUPPORTED, "2^32 or more tiles of one combination in a batch");
     if (pl->d_segs) cudaFree(pl->d_segs);
     pl->d_segs = nullptr;
@@ -182,8 +189,7 @@ static fe_status upload_segs(fe_ctx *ctx, BatchPlan *pl, const std::vector<Batch
     st = cuda_check(ctx, cudaMemcpy(pl->d_segs, segs.data(), segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice),
                     "cudaMemcpy(segments)");
     if (st != FE_OK) return st;
-    pl->block = B;
-    return size_classes(ctx, pl->classes, B);
+    return size_classes(ctx, pl->classes);
 }
 
 // Streams and events of the parallel branches (created once per context).
@@ -196,6 +202,25 @@ static fe_status ensure_branches(fe_ctx *ctx, size_t n) {
         if (e == cudaSuccess && !bc->ev_join[i]) e = cudaEventCreateWithFlags(&bc->ev_join[i], cudaEventDisableTiming);
     }
     return cuda_check(ctx, e, "batch branch streams");
+}
+
+// The kernel of one combination on stream `s`; with `reset`, its tile counter and
+// the fix-up count are zeroed first (the combination run alone, when tuning).
+static fe_status launch_class(fe_ctx *ctx, BatchPlan *pl, const ClassLaunch &cl, cudaStream_t s, bool reset) {
+    cudaError_t e = cudaSuccess;
+    if (reset) {
+        e = cudaMemsetAsync(pl->d_counter + cl.combo, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(pl->scratch.fix_count, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemsetAsync(batch class)");
+    }
+    int *status = ctx->scratch.status;
+    const BatchSeg *segs = pl->d_segs + cl.seg_off;
+    unsigned n_segs = cl.n_segs, n_tiles = cl.n_tiles;
+    unsigned *counter = cl.persistent ? pl->d_counter + cl.combo : nullptr;
+    void *args[] = {&pl->d_items, &pl->n_items, &segs, &n_segs, &n_tiles, &counter, &status};
+    e = cudaLaunchKernel(kernel_batch(cl.combo), dim3(cl.grid), dim3(cl.block * batch_tpe(cl.combo)), args,
+                         size_t(cl.smem), s);
+    return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
 }
 
 // Enqueue {counter reset, one persistent kernel per combination, fix-up kernel}.
@@ -227,13 +252,8 @@ static fe_status enqueue_batch(fe_ctx *ctx, BatchPlan *pl, cudaStream_t st, bool
             e = cudaStreamWaitEvent(ls, bc->ev_fork, 0);
             if (e != cudaSuccess) return cuda_check(ctx, e, "cudaStreamWaitEvent(batch fork)");
         }
-        const BatchSeg *segs = pl->d_segs + cl.seg_off;
-        unsigned n_segs = cl.n_segs, n_tiles = cl.n_tiles;
-        unsigned *counter = pl->d_counter + cl.combo;
-        void *args[] = {&pl->d_items, &pl->n_items, &segs, &n_segs, &n_tiles, &counter, &status};
-        e = cudaLaunchKernel(kernel_batch(cl.combo), dim3(cl.grid), dim3(pl->block * batch_tpe(cl.combo)), args,
-                             size_t(cl.smem), ls);
-        if (e != cudaSuccess) return cuda_check(ctx, e, "cudaLaunchKernel(batch)");
+        fe_status ls_st = launch_class(ctx, pl, cl, ls, false);
+        if (ls_st != FE_OK) return ls_st;
         if (fork) {
             e = cudaEventRecord(bc->ev_join[i], ls);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(st, bc->ev_join[i], 0);
@@ -256,6 +276,7 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
     pl->key = key;
     pl->pinned_block = ctx->batch_shape.block;
     pl->pinned_tpe = ctx->batch_shape.tpe;
+    pl->pinned_pers = ctx->batch_shape.persistent;
     pl->items_bytes.assign(reinterpret_cast<const unsigned char *>(items),
                            reinterpret_cast<const unsigned char *>(items) + sizeof(fe_batch_item) * n);
     std::vector<BatchItemDev> dev(n);
@@ -293,60 +314,78 @@ static fe_status build_plan(fe_ctx *ctx, const fe_batch_item *items, int n, size
                         "cudaMemcpy(items)");
     if (!ctx->batch->capture_stream) cudaStreamCreateWithFlags(&ctx->batch->capture_stream, cudaStreamNonBlocking);
     cudaStream_t cs = ctx->batch->capture_stream;
-    // launch shape: the tuned elements per tile and threads per prism for this
-    // plan, or 128 and one
+    // launch shape of each combination: elements per tile, persistent or one block
+    // per tile and, for prisms, one or two threads per element; tuned per
+    // combination (each timed alone), pinned, or 128 / persistent / one
     bool any_prism = false;
     for (const auto &d : dev) any_prism = any_prism || (d.combo >= 8 && d.combo < 12);
-    auto set_prism_tpe = [&](int tpe) -> fe_status {
+    auto base_of = [](int c) { return c >= 12 ? c - 4 : c; };   // the one-thread combination of a pair one
+    int Bb[kCombos], Tb[kCombos], Pb[kCombos];                  // per base combination
+    for (int c = 0; c < kCombos; ++c) Bb[c] = 128, Tb[c] = 1, Pb[c] = 1;
+    auto set_tpe = [&](const int *T) -> fe_status {
         for (auto &d : dev)
-            if (d.combo >= 8) d.combo = tpe == 2 ? batch_pair_combo(d.combo) : (d.combo >= 12 ? d.combo - 4 : d.combo);
+            if (d.combo >= 8) {
+                const int b = base_of(d.combo);
+                d.combo = T[b] == 2 ? batch_pair_combo(b) : b;
+            }
         return cuda_check(ctx, cudaMemcpy(pl->d_items, dev.data(), sizeof(BatchItemDev) * n, cudaMemcpyHostToDevice),
                           "cudaMemcpy(items)");
     };
-    int bestB = 128, bestT = 1;
+    auto upload = [&](const int *B, const int *P) -> fe_status {
+        int Bf[kCombos], Pf[kCombos];
+        for (int c = 0; c < kCombos; ++c) Bf[c] = B[base_of(c)], Pf[c] = P[base_of(c)];
+        return upload_segs(ctx, pl, dev, Bf, Pf);
+    };
     if (ctx->batch_shape.block > 0) {            // pinned by fe_batch_set_shape
-        bestB = ctx->batch_shape.block;
-        bestT = ctx->batch_shape.tpe;
+        for (int c = 0; c < kCombos; ++c)
+            Bb[c] = ctx->batch_shape.block, Tb[c] = ctx->batch_shape.tpe, Pb[c] = ctx->batch_shape.persistent;
     } else if (st == FE_OK && ctx->autotune) {
-        float best = 1e30f;
+        float best[kCombos];
+        for (int c = 0; c < kCombos; ++c) best[c] = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int tpe = 1; tpe <= (any_prism ? 2 : 1) && st == FE_OK; ++tpe) {
-            st = set_prism_tpe(tpe);
-            for (int B : {64, 128, 256}) {
-                if (st != FE_OK) break;
-                st = upload_segs(ctx, pl, dev, B);
-                if (st == FE_ERR_UNSUPPORTED) {   // tile too large for shared memory or threads
-                    st = FE_OK;
-                    continue;
+        for (int tpe = 1; tpe <= (any_prism ? 2 : 1) && st == FE_OK; ++tpe)
+            for (int pers = 1; pers >= 0 && st == FE_OK; --pers)
+                for (int B : {64, 128, 256}) {
+                    int Bt[kCombos], Tt[kCombos], Pt[kCombos];
+                    for (int c = 0; c < kCombos; ++c) Bt[c] = B, Tt[c] = tpe, Pt[c] = pers;
+                    st = set_tpe(Tt);
+                    if (st == FE_OK) st = upload(Bt, Pt);
+                    if (st == FE_ERR_UNSUPPORTED) {   // tile too large for shared memory or threads
+                        st = FE_OK;
+                        continue;
+                    }
+                    if (st != FE_OK) break;
+                    // each combination alone: counter and fix-up count reset, then its kernel
+                    for (const auto &cl : pl->classes) {
+                        float t = 0.0f;
+                        for (int r = 0; r < 4 && st == FE_OK; ++r) {   // one warm-up, three timed
+                            if (r == 1) cudaEventRecord(e0, cs);
+                            st = launch_class(ctx, pl, cl, cs, true);
+                        }
+                        cudaEventRecord(e1, cs);
+                        if (st != FE_OK) break;
+                        cudaError_t ce = cudaEventSynchronize(e1);
+                        if (ce != cudaSuccess) {
+                            st = cuda_check(ctx, ce, "batch tuning");
+                            break;
+                        }
+                        cudaEventElapsedTime(&t, e0, e1);
+                        const int b = base_of(cl.combo);
+                        if (t < best[b]) {
+                            best[b] = t;
+                            Bb[b] = B;
+                            Tb[b] = tpe;
+                            Pb[b] = pers;
+                        }
+                    }
                 }
-                if (st != FE_OK) break;
-                st = enqueue_batch(ctx, pl, cs, false, true);  // warm-up
-                cudaEventRecord(e0, cs);
-                for (int r = 0; r < 3 && st == FE_OK; ++r) st = enqueue_batch(ctx, pl, cs, false, true);
-                cudaEventRecord(e1, cs);
-                if (st != FE_OK) break;
-                cudaError_t ce = cudaEventSynchronize(e1);
-                if (ce != cudaSuccess) {
-                    st = cuda_check(ctx, ce, "batch tuning");
-                    break;
-                }
-                float t;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (t < best) {
-                    best = t;
-                    bestB = B;
-                    bestT = tpe;
-                }
-            }
-        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
-    if (st == FE_OK && any_prism) st = set_prism_tpe(bestT);
-    pl->prism_tpe = bestT;
-    if (st == FE_OK) st = upload_segs(ctx, pl, dev, bestB);
+    if (st == FE_OK) st = set_tpe(Tb);
+    if (st == FE_OK) st = upload(Bb, Pb);
     // capture the launch sequence once; later submissions replay it
     if (st == FE_OK) {
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -380,7 +419,9 @@ void dyn_batch_free(DynBatch &db) {
 // The caller guarantees that the previous launch on this DynBatch has finished
 // (its pinned staging and device table are reused).
 fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> &items, cudaStream_t st) {
-    const int B = 128;
+    // tiles of 128 tetrahedra and 64 prisms, one thread per element: the shapes the
+    // batch autotuner keeps for these combinations on the 256-mesh workload (a
+    // served launch is not tuned: it is built per launch)
     constexpr size_t kCountersOff = 0, kFixCountOff = 64, kItemsOff = 128;
     uint64_t total = 0;
     for (auto &it : items) total += uint64_t(it.p.n);
@@ -388,7 +429,9 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     if (r != FE_OK) return r;
     std::vector<ClassLaunch> classes;
     std::vector<BatchSeg> segs;
-    if (!make_segs(items, B, segs, classes))
+    int Bc[kCombos], Pc[kCombos];
+    for (int c = 0; c < kCombos; ++c) Bc[c] = c >= 8 ? 64 : 128, Pc[c] = 1;
+    if (!make_segs(items, Bc, Pc, segs, classes))
         return set_error(ctx, FE_ERR_UNSUPPORTED, "2^32 or more tiles of one combination in a batch");
     const size_t items_bytes = (items.size() * sizeof(BatchItemDev) + 15) / 16 * 16;
     const size_t segs_off = kItemsOff + items_bytes;
@@ -416,7 +459,7 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     memcpy(db.h_tab + segs_off, segs.data(), segs.size() * sizeof(BatchSeg));
     cudaError_t e = cudaMemcpyAsync(db.d_tab, db.h_tab, segs_off + segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "cudaMemcpyAsync(batch table)");
-    r = size_classes(ctx, classes, B);
+    r = size_classes(ctx, classes);
     if (r != FE_OK) return r;
     BatchPlan pl;
     pl.d_items = reinterpret_cast<BatchItemDev *>(db.d_tab + kItemsOff);
@@ -426,7 +469,6 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     pl.d_counter = reinterpret_cast<unsigned *>(db.d_tab + kCountersOff);
     pl.scratch = db.scratch;
     pl.scratch.fix_count = d_fix_count;
-    pl.block = B;
     pl.classes = classes;
     r = enqueue_batch(ctx, &pl, st, true);
     // the plan only borrowed the tables
@@ -511,9 +553,9 @@ fe_status fe_batch_set_shape(fe_ctx *ctx, const fe_launch_shape *shape) {
         return FE_OK;
     }
     const int B = shape->elems_per_block, t = shape->threads_per_elem;
-    if ((t != 1 && t != 2) || B < 32 || B % 32 || B * t > 256)
+    if ((t != 1 && t != 2) || B < 32 || B % 32 || B * t > 256 || (shape->persistent != 0 && shape->persistent != 1))
         return set_error(ctx, FE_ERR_INVALID_ARG, "bad batched launch shape");
-    ctx->batch_shape = Shape{B, 1, t};
+    ctx->batch_shape = Shape{B, shape->persistent, t};
     return FE_OK;
 }
 
@@ -541,6 +583,7 @@ fe_status fe_batch_submit(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
     for (auto it = ctx->batch->plans.begin(); it != ctx->batch->plans.end(); ++it) {
         if ((*it)->key == key && (*it)->items_bytes.size() == sizeof(fe_batch_item) * size_t(n_items) &&
             (*it)->pinned_block == ctx->batch_shape.block && (*it)->pinned_tpe == ctx->batch_shape.tpe &&
+            (*it)->pinned_pers == ctx->batch_shape.persistent &&
             memcmp((*it)->items_bytes.data(), items, (*it)->items_bytes.size()) == 0) {
             pl = *it;
             ctx->batch->plans.erase(it);

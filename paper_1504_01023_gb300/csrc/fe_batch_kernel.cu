@@ -52,9 +52,9 @@ struct TileRef {
     int count;
 };
 template <int ID>
-__device__ __forceinline__ TileRef next_tile(const BatchItemDev *items, unsigned n_items, const BatchSeg *segs,
-                                             unsigned n_segs, unsigned n_tiles, unsigned *tile_counter, int B) {
-    TileRef r{atomicAdd(tile_counter, 1u), 0xFFFFFFFFu, 0, 0};
+__device__ __forceinline__ TileRef find_tile(unsigned t, const BatchItemDev *items, unsigned n_items,
+                                             const BatchSeg *segs, unsigned n_segs, unsigned n_tiles, int B) {
+    TileRef r{t, 0xFFFFFFFFu, 0, 0};
     if (r.t < n_tiles && n_segs > 0) {
         unsigned lo = 0, hi = n_segs;
         while (hi - lo > 1) {
@@ -72,13 +72,21 @@ __device__ __forceinline__ TileRef next_tile(const BatchItemDev *items, unsigned
     }
     return r;
 }
+template <int ID>
+__device__ __forceinline__ TileRef next_tile(const BatchItemDev *items, unsigned n_items, const BatchSeg *segs,
+                                             unsigned n_segs, unsigned n_tiles, unsigned *tile_counter, int B) {
+    return find_tile<ID>(atomicAdd(tile_counter, 1u), items, n_items, segs, n_segs, n_tiles, B);
+}
 
-// Persistent kernel of one combination: blocks take the next tile of this
-// combination from its counter until none is left. A batch launches one such
-// kernel per combination present (one register allocation per combination).
-// One lane of warp 1 looks up the following tile while the block loads and
-// computes the current one (double-buffered in shared memory), so the counter
-// and the search stay off the block's critical path.
+// Kernel of one combination. Persistent (tile_counter given): blocks take the
+// next tile of this combination from its counter until none is left; one lane
+// of warp 1 looks up the following tile while the block loads and computes the
+// current one (double-buffered in shared memory), so the counter and the search
+// stay off the block's critical path. Without a counter: block b takes tiles b,
+// b + gridDim.x, ... (a grid of one block per tile), so that the hardware block
+// scheduler overlaps one block's stores with the next block's loads. A batch
+// launches one such kernel per combination present (one register allocation per
+// combination).
 template <int ID>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchItemDev *__restrict__ items, unsigned n_items,
                                                     const BatchSeg *__restrict__ segs, unsigned n_segs, unsigned n_tiles,
@@ -92,9 +100,24 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchItemDev *__restri
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
+    unsigned phase = 0;
+    if (!tile_counter) {
+        for (unsigned t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            if (threadIdx.x == R) s_ref[0] = find_tile<ID>(t, items, n_items, segs, n_segs, n_tiles, B);
+            __syncthreads();
+            const TileRef cur = s_ref[0];
+            if (cur.item == 0xFFFFFFFFu) {
+                if (threadIdx.x == 0) atomicOr(status, ST_BAD_TILE);
+                __syncthreads();
+                continue;
+            }
+            if (!tile_combo<ID>(items + cur.item, cur.first, cur.count, smem, &bar, &phase)) return;
+        }
+        if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        return;
+    }
     if (threadIdx.x == R) s_ref[0] = next_tile<ID>(items, n_items, segs, n_segs, n_tiles, tile_counter, B);
     __syncthreads();
-    unsigned phase = 0;
     for (unsigned i = 0;; ++i) {
         const TileRef cur = s_ref[i & 1u];
         if (cur.t >= n_tiles) break;

@@ -90,12 +90,13 @@ def test_batch_matches_single_calls_and_oracle(ctx, mix, autotune):
         bctx.close()
 
 
-@pytest.mark.parametrize("block,tpe", [(64, 2), (128, 2), (32, 1), (256, 1)])
-def test_batch_pinned_shapes(mix, block, tpe):
-    """Pinned batch shapes, including two threads per prism element: every set
-    against the oracle, flags as in a single call."""
+@pytest.mark.parametrize("block,tpe,pers", [(64, 2, 1), (128, 2, 0), (32, 1, 1), (256, 1, 0), (64, 1, 0)])
+def test_batch_pinned_shapes(mix, block, tpe, pers):
+    """Pinned batch shapes, including two threads per prism element and one block
+    per tile instead of persistent grids: every set against the oracle, flags as in
+    a single call."""
     bctx = api.Context(0)
-    bctx.batch_set_shape(block, tpe)
+    bctx.batch_set_shape(block, tpe, pers)
     outs = [api.alloc_out(et, n, api.FP32_MIXED, api.AOS, "cuda") for (et, kind, quad, cpq, n, _) in MIX]
     items = _items(mix, outs)
     bctx.batch_submit(items)
