@@ -352,7 +352,30 @@ def cpu_baseline(mesh, coefs, target_s=10.0, gpu_out=None, tol=1e-12):
            "cpu": cpu_model()}
     if errors is not None:
         res["gpu_error_vs_oracle"] = errors
+    res["other_workloads"] = oracle_other_workloads(cores)
     return res
+
+
+def oracle_other_workloads(cores):
+    """The oracle on the other single-set workloads, all host cores and one core:
+    the 48,000 Poisson tetrahedra as stated (TET1, d^0 = 1, FP64), and a 200,000-
+    element subsample of the 2M generic prisms (PRISM6, 20 coefficients per point)."""
+    import oracle
+    from paper_1504_01023_gb300 import meshgen
+    out = {}
+    tm = meshgen.tet_cube_mesh(20, jitter=0.2, seed=meshgen.SEED_BASE + 1)
+    pm = meshgen.prism_slab_mesh(1000, None, 0.1, seed=meshgen.SEED_BASE + 3, n_elem=200_000)
+    pc = meshgen.generic_coefs(len(pm), 6, seed=meshgen.SEED_BASE + 3)
+    cases = {"poisson_tet1_48k": (oracle.TET, oracle.POISSON, oracle.Q_TET1, tm, np.ones(len(tm)), False),
+             "generic_prism_per_point_200k": (oracle.PRISM, oracle.GENERIC, oracle.Q_PRISM6, pm, pc, True)}
+    for name, (et, kind, rule, m, c, cpq) in cases.items():
+        rec = {"elements": len(m), "unit": "Melem/s"}
+        for label, nt in (("all_cores", cores), ("one_core", 1)):
+            t = time.perf_counter()
+            oracle.integrate(et, kind, rule, m, c, coef_per_q=cpq, n_threads=nt)
+            rec[label] = len(m) / (time.perf_counter() - t) / 1e6
+        out[name] = rec
+    return out
 
 
 def cpu_model():
