@@ -141,7 +141,7 @@ typedef struct fe_ctx_config {
  *   point (d^0). NC = that count times NQ for FE_COEF_PER_QPOINT (point-major:
  *   scalar j = q*per_point + k), times 1 for FE_COEF_PER_ELEMENT.
  *   SOA: scalar j at coefs[j*coefs_stride + e]; AOS: coefs[e*NC + j].
- * A stride of 0 means n_elem. SOA strides are counted in elements.
+ * A stride of 0 means n_elem. SOA strides are counted in elements, at most 2^40.
  */
 typedef struct fe_elem_args {
     int64_t n_elem;

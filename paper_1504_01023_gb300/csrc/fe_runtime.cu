@@ -672,12 +672,19 @@ fe_status fe_check_args(fe_elem_type type, const fe_elem_args *a, const fe_out *
         if (reinterpret_cast<uintptr_t>(a->conn) & 3) return set_error(nullptr, FE_ERR_INVALID_ARG, "misaligned conn");
     }
     const int64_t n = a->n_elem;
+    // plane strides up to 2^40 elements: every plane offset (at most 120 planes)
+    // stays far inside 64-bit addressing
+    constexpr int64_t kMaxStride = int64_t(1) << 40;
     if (a->coords_layout == FE_LAYOUT_SOA) {
         if ((a->coords_stride != 0 && a->coords_stride < n) || (a->coefs_stride != 0 && a->coefs_stride < n))
             return set_error(nullptr, FE_ERR_INVALID_ARG, "SOA input stride smaller than n_elem");
+        if (a->coords_stride > kMaxStride || a->coefs_stride > kMaxStride)
+            return set_error(nullptr, FE_ERR_INVALID_ARG, "SOA input stride above 2^40");
     }
     if (o->layout == FE_LAYOUT_SOA && o->stride != 0 && o->stride < n)
         return set_error(nullptr, FE_ERR_INVALID_ARG, "SOA output stride smaller than n_elem");
+    if (o->layout == FE_LAYOUT_SOA && o->stride > kMaxStride)
+        return set_error(nullptr, FE_ERR_INVALID_ARG, "SOA output stride above 2^40");
     const unsigned cs = unsigned(csize(a->prec));
     if ((reinterpret_cast<uintptr_t>(a->coords) & 7) || (reinterpret_cast<uintptr_t>(a->coefs) & (cs - 1)) ||
         (reinterpret_cast<uintptr_t>(o->A) & (cs - 1)) || (reinterpret_cast<uintptr_t>(o->b) & (cs - 1)))

@@ -221,3 +221,68 @@ def test_rule_tables_match_the_oracle(lib, quad, elem):
         n = ctypes.c_int()
         arr = (ctypes.c_double * 1)()
         api._check(lib.fe_rule_table(quad, 0 if quad == api.QUAD_TET1 else 1, ctypes.byref(n), arr, None))
+
+
+def test_validation_fuzz(lib):
+    """Host-only fuzzing of the argument validation: valid argument sets with up to
+    three fields replaced by random values (enums in and out of range, negative and
+    huge sizes and strides, null and misaligned pointers, which are never
+    dereferenced) give FE_OK, FE_ERR_INVALID_ARG or FE_ERR_UNSUPPORTED, never a
+    crash; and FE_OK only for arguments that meet the documented rules."""
+    import numpy as np
+    rng = np.random.default_rng(2024)
+    sizes = [-5, -1, 0, 1, 7, 1000, (1 << 31) + 3, (1 << 32) - 1, 1 << 32, 1 << 40]
+    strides = [0, 1, 999, 1000, 1 << 20, (1 << 40), (1 << 40) + 1, 1 << 62, -3]
+    ptrs = [0, 4096, 4097, 4100, 8192, 1 << 40]
+    fields = {
+        "et": lambda: int(rng.integers(-1, 3)), "n_elem": lambda: int(rng.choice(sizes)),
+        "coords": lambda: int(rng.choice(ptrs)), "coefs": lambda: int(rng.choice(ptrs)),
+        "A": lambda: int(rng.choice(ptrs)), "b": lambda: int(rng.choice(ptrs)),
+        "coords_layout": lambda: int(rng.integers(-1, 4)), "coefs_layout": lambda: int(rng.integers(-1, 4)),
+        "layout": lambda: int(rng.integers(-1, 4)), "coords_stride": lambda: int(rng.choice(strides)),
+        "coefs_stride": lambda: int(rng.choice(strides)), "stride": lambda: int(rng.choice(strides)),
+        "kind": lambda: int(rng.integers(-1, 4)), "quad": lambda: int(rng.integers(-1, 4)),
+        "coef_mode": lambda: int(rng.integers(-1, 4)), "prec": lambda: int(rng.integers(-1, 4)),
+        "memory": lambda: int(rng.integers(-1, 3)), "omemory": lambda: int(rng.integers(-1, 3)),
+        "conn": lambda: int(rng.choice(ptrs)), "n_nodes": lambda: int(rng.choice(sizes)),
+        "ordering": lambda: int(rng.integers(-1, 4)), "packed": lambda: int(rng.integers(-1, 3)),
+    }
+    names = list(fields)
+    seen = {0: 0, -1: 0, -6: 0}
+    for _ in range(20000):
+        et = int(rng.integers(0, 2))
+        lay = int(rng.integers(0, 2))
+        v = dict(et=et, n_elem=int(rng.integers(1, 5000)), coords=4096, coefs=8192, A=12288, b=16384,
+                 coords_layout=lay, coefs_layout=lay, layout=int(rng.integers(0, 2)), coords_stride=0,
+                 coefs_stride=0, stride=0, kind=int(rng.integers(0, 2)),
+                 quad=int(rng.integers(0, 2)) if et == 0 else 2, coef_mode=int(rng.integers(0, 2)),
+                 prec=int(rng.integers(0, 3)), memory=0, omemory=0, conn=0, n_nodes=0, ordering=0, packed=0)
+        k = int(rng.integers(0, 4))
+        for f in (rng.choice(names, size=k, replace=False) if k else []):
+            v[f] = fields[f]()
+        a = api.ElemArgs()
+        o = api.Out()
+        a.n_elem, a.coords, a.coefs, o.A, o.b = v["n_elem"], v["coords"], v["coefs"], v["A"], v["b"]
+        a.coords_layout, a.coefs_layout, o.layout = v["coords_layout"], v["coefs_layout"], v["layout"]
+        a.coords_stride, a.coefs_stride, o.stride = v["coords_stride"], v["coefs_stride"], v["stride"]
+        a.kind, a.quad, a.coef_mode, a.prec = v["kind"], v["quad"], v["coef_mode"], v["prec"]
+        a.memory, o.memory, a.conn, a.n_nodes = v["memory"], v["omemory"], v["conn"], v["n_nodes"]
+        a.ordering, o.packed, a.coef_fn = v["ordering"], v["packed"], None
+        st = lib.fe_check_args(v["et"], ctypes.byref(a), ctypes.byref(o))
+        assert st in (0, -1, -6), st
+        seen[st] += 1
+        if st == 0:
+            et = v["et"]
+            assert et in (0, 1) and a.kind in (0, 1) and a.prec in (0, 1, 2) and a.coef_mode in (0, 1)
+            assert a.quad in ((0, 1) if et == 0 else (2,))
+            assert 0 <= a.n_elem < (1 << 32) and a.ordering in (0, 1, 2) and o.packed in (0, 1)
+            assert o.layout in (0, 1) and a.coords_layout in (0, 1, 2) and a.memory in (0, 1) and o.memory in (0, 1)
+            if a.n_elem > 0:
+                assert a.coords and a.coefs and o.A and o.b and a.coords % 8 == 0
+                used = ([a.coords_stride, a.coefs_stride] if a.coords_layout == 0 else []) + \
+                       ([o.stride] if o.layout == 0 else [])
+                for s in used:
+                    assert s == 0 or a.n_elem <= s <= (1 << 40)
+                if a.coords_layout == 2:
+                    assert a.conn and a.conn % 4 == 0 and 0 < a.n_nodes < (1 << 31)
+    assert min(seen.values()) > 100, seen
