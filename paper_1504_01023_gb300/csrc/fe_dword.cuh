@@ -230,6 +230,21 @@ __device__ __forceinline__ DW dw_lin4(DW p1, DW p2, DW p3, DW q) {
     return dw_fast_two_sum(p, c);
 }
 
+// acc += x y, acc held as an unnormalised pair (p, c): p the float sum of the
+// high products, c gathering the TwoSum errors, the products' rounding errors and
+// the cross terms, as the Dot2 accumulation above keeps them across its terms;
+// dw_acc_norm makes the pair a double-word again (after the last term).
+__device__ __forceinline__ void dw_acc(DW &acc, DW x, DW y) {
+    const float q = __fmul_rn(x.h, y.h);
+    const float e = __fmaf_rn(x.h, y.h, -q);
+    const DW s = dw_two_sum(acc.h, q);
+    float c = __fadd_rn(acc.l, __fadd_rn(s.l, e));
+    c = __fmaf_rn(x.h, y.l, c);
+    c = __fmaf_rn(x.l, y.h, c);
+    acc = DW(s.h, c);
+}
+__device__ __forceinline__ DW dw_acc_norm(DW acc) { return dw_two_sum(acc.h, acc.l); }
+
 // a b - c d
 __device__ __forceinline__ DW dw_diff_prod(DW a, DW b, DW c, DW d) {
     const DW x[2] = {a, c}, y[2] = {b, d};

@@ -317,8 +317,10 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             if constexpr (TPE == 1) {
 #pragma unroll
                 for (int l = 0; l < 2; ++l) level_generic(f, l, c, A, b, poor, neg, degenerate);
+                prism_dw_normalise<T>(A, b);
             } else {
                 level_generic(f, part, c, A, b, poor, neg, degenerate);
+                prism_dw_normalise<T>(A, b);
 #pragma unroll
                 for (int k = 0; k < 36; ++k) A[k] = pair_sum(A[k], mask);
             }
