@@ -551,6 +551,14 @@ def run_native(args):
                         hbm={k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "peak_kind",
                                                  "algorithmic_bytes_per_launch", "frac_of_nominal",
                                                  "same_run_copy_gbs")})
+        # the attainable rate: the lower of the HBM bound (peak / bytes per element)
+        # and the pipe bound (peak / instructions per element)
+        ipe = roofline["instructions_per_element"]
+        hbm_bound = peak * 1e9 / bpe / 1e6
+        pipe_bound = roofline["peak"] * 1e12 / ipe / 1e6 if ipe else None
+        att = min(hbm_bound, pipe_bound) if pipe_bound else hbm_bound
+        roofline["attainable"] = {"melem_s": att, "unit": "Melem/s", "hbm_bound_melem_s": hbm_bound,
+                                  "pipe_bound_melem_s": pipe_bound, "frac": melem_k / att}
 
     result = {"metric": METRIC, "value": value, "unit": "Melem/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
