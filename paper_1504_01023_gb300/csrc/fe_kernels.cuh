@@ -375,7 +375,7 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             neg |= is_neg(det);
             const T adet = abs_t(det);
             const T sw = recip_w(adet, T(R::w(0)));          // vol / det^2 (equal weights)
-            const T g11 = sw * dot(a1, a1), g12 = sw * dot(a1, a2), g22 = sw * dot(a2, a2);
+            const T g11 = mul_off(sw, dot(a1, a1)), g12 = mul_off(sw, dot(a1, a2)), g22 = mul_off(sw, dot(a2, a2));
             if (t == 0) {
                 Ll[0] = g11;
                 Ll[1] = g12;
@@ -385,10 +385,10 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
                 Ll[1] += g12;
                 Ll[2] += g22;
             }
-            vl[t][0] = sw * dot(a1, a3);
-            vl[t][1] = sw * dot(a2, a3);
-            c3l[t] = sw * a33;
-            const T vd = (adet * T(R::w(0))) * c(CPQ ? q : 0);
+            vl[t][0] = mul_off(sw, dot(a1, a3));
+            vl[t][1] = mul_off(sw, dot(a2, a3));
+            c3l[t] = mul_off(sw, a33);
+            const T vd = mul_off(mul_off(adet, T(R::w(0))), c(CPQ ? q : 0));
 #pragma unroll
             for (int k = 0; k < 6; ++k) b[k] += vd * (l ? T(R::phi(3 + t, k)) : T(R::phi(t, k)));
         }
@@ -429,7 +429,20 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
         }
     }
 
-    __device__ __forceinline__ static T abs_t(T v) { return v < T(0) ? -v : v; }
+    __device__ __forceinline__ static T abs_t(T v) {
+        if constexpr (PREC == FP64)   // the sign bit cleared (an integer operation)
+            return __longlong_as_double(__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll);
+        else
+            return v < T(0) ? -v : v;
+    }
+    // a b for the products off the critical path: in FP64 in integer instructions
+    // (the same IEEE product, off the double pipe; see TetF64)
+    __device__ __forceinline__ static T mul_off(T a, T b) {
+        if constexpr (PREC == FP64)
+            return i64_dmul(a, b);
+        else
+            return a * b;
+    }
     // w / v for v > 0
     __device__ __forceinline__ static T recip_w(T v, T w) {
         if constexpr (PREC == FP64)
