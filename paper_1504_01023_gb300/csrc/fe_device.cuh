@@ -855,81 +855,9 @@ __device__ __forceinline__ void prism_generic_update(const V3<T> g[6], T vol, co
     }
 }
 
-// The same update with the point's shape values passed in registers (the point
-// loop then needs no unrolling: one copy of the code serves all six points).
-template <class T, class CS>
-__device__ __forceinline__ void prism_generic_update_rt(const V3<T> g[6], T vol, const CS &c, int o, const T ph[6],
-                                                        T A[36], T b[6]) {
-    // one row a of the coefficient matrix at a time: T_as = sum_b vol c_ab Phi_bs,
-    // then A_rs += Phi_ar T_as and b_r += vol d_a Phi_ar (same products as the
-    // full rank-4 update, fewer values live at once)
-    auto row = [&](int a) {
-        const T c0 = vol * c(o + 4 * a), c1 = vol * c(o + 4 * a + 1), c2 = vol * c(o + 4 * a + 2),
-                c3 = vol * c(o + 4 * a + 3);
-        const T da = vol * c(o + 16 + a);
-        T Ta[6];
-#pragma unroll
-        for (int s = 0; s < 6; ++s) Ta[s] = c0 * ph[s] + c1 * g[s].x + c2 * g[s].y + c3 * g[s].z;
-#pragma unroll
-        for (int r = 0; r < 6; ++r) {
-            const T phi = a == 0 ? ph[r] : (a == 1 ? g[r].x : (a == 2 ? g[r].y : g[r].z));
-#pragma unroll
-            for (int s = 0; s < 6; ++s) A[6 * r + s] += phi * Ta[s];
-            b[r] += da * phi;
-        }
-    };
-    if constexpr (std::is_same<T, DW>::value) {
-        // double-word: one copy of the row code (the unrolled rows overflow the
-        // instruction cache); T_as by one compensated dot product each, and A, b
-        // accumulated as unnormalised pairs (dw_acc; prism_dw_normalise after the
-        // last point)
-#pragma unroll 1
-        for (int a = 0; a < 4; ++a) {
-            const DW cr[4] = {vol * c(o + 4 * a), vol * c(o + 4 * a + 1), vol * c(o + 4 * a + 2),
-                              vol * c(o + 4 * a + 3)};
-            const DW da = vol * c(o + 16 + a);
-            DW Ta[6];
-#pragma unroll
-            for (int s = 0; s < 6; ++s) {
-                const DW y[4] = {ph[s], g[s].x, g[s].y, g[s].z};
-                Ta[s] = dw_dot<4>(cr, y);
-            }
-#pragma unroll
-            for (int r = 0; r < 6; ++r) {
-                const DW phi = a == 0 ? ph[r] : (a == 1 ? g[r].x : (a == 2 ? g[r].y : g[r].z));
-#pragma unroll
-                for (int s = 0; s < 6; ++s) dw_acc(A[6 * r + s], phi, Ta[s]);
-                dw_acc(b[r], da, phi);
-            }
-        }
-    } else if constexpr (std::is_same<T, double>::value) {
-        // FP64: the scalings vol c of the coefficients in integer instructions
-        // (off the critical path, the same IEEE products; see TetF64)
-        auto rowd = [&](int a) {
-            const double c0 = i64_dmul(vol, c(o + 4 * a)), c1 = i64_dmul(vol, c(o + 4 * a + 1)),
-                         c2 = i64_dmul(vol, c(o + 4 * a + 2)), c3 = i64_dmul(vol, c(o + 4 * a + 3));
-            const double da = i64_dmul(vol, c(o + 16 + a));
-            double Ta[6];
-#pragma unroll
-            for (int s = 0; s < 6; ++s) Ta[s] = c0 * ph[s] + c1 * g[s].x + c2 * g[s].y + c3 * g[s].z;
-#pragma unroll
-            for (int r = 0; r < 6; ++r) {
-                const double phi = a == 0 ? ph[r] : (a == 1 ? g[r].x : (a == 2 ? g[r].y : g[r].z));
-#pragma unroll
-                for (int s = 0; s < 6; ++s) A[6 * r + s] += phi * Ta[s];
-                b[r] += da * phi;
-            }
-        };
-#pragma unroll
-        for (int a = 0; a < 4; ++a) rowd(a);
-    } else {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) row(a);
-    }
-}
-
-// The double-word accumulators of prism_generic_update_rt made double-words again
-// (no-op for the other types).
+// A^e and b^e of the generic prism, accumulated as unnormalised double-word
+// pairs by its level expansion (level_generic), made double-words again (no-op
+// for the other types).
 template <class T> __device__ __forceinline__ void prism_dw_normalise(T A[36], T b[6]) {
     if constexpr (std::is_same<T, DW>::value) {
 #pragma unroll

@@ -243,6 +243,12 @@ __device__ __forceinline__ void dw_acc(DW &acc, DW x, DW y) {
     c = __fmaf_rn(x.l, y.h, c);
     acc = DW(s.h, c);
 }
+// acc += x for the same unnormalised pair (the TwoSum error and x's low word
+// gathered in the low word).
+__device__ __forceinline__ void dw_acc_add(DW &acc, DW x) {
+    const DW s = dw_two_sum(acc.h, x.h);
+    acc = DW(s.h, __fadd_rn(acc.l, __fadd_rn(s.l, x.l)));
+}
 __device__ __forceinline__ DW dw_acc_norm(DW acc) { return dw_two_sum(acc.h, acc.l); }
 
 // a b - c d

@@ -269,8 +269,9 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
 
     // Q loop on relative coordinates r[0..5] (r[0] = 0). Returns bit1/bit2 flags.
     // Generic coefficients: the three points of a zeta level run in a rolled loop
-    // (shape values computed per point), which keeps the large body in the
-    // instruction cache. Laplace: the points only gather Gram terms of J^{-1}
+    // (which keeps the body in the instruction cache) and gather per-level sums of
+    // the reference-space coefficient matrix; A^e is expanded from them once per
+    // level (level_generic). Laplace: the points only gather Gram terms of J^{-1}
     // (prism_laplace_assemble forms A^e from them once).
     //
     // TPE == 2 (two threads per element): the lane of parity `part` takes the three
@@ -314,12 +315,14 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
         } else {
 #pragma unroll
             for (int k = 0; k < 36; ++k) A[k] = T(0);
+            const T r12 = T(1.0 / 12.0);
+            const V3<T> wm = r12 * ((f.w0 + f.w1) + f.w2);
             if constexpr (TPE == 1) {
 #pragma unroll
-                for (int l = 0; l < 2; ++l) level_generic(f, l, c, A, b, poor, neg, degenerate);
+                for (int l = 0; l < 2; ++l) level_generic(f, wm, l, c, A, b, poor, neg, degenerate);
                 prism_dw_normalise<T>(A, b);
             } else {
-                level_generic(f, part, c, A, b, poor, neg, degenerate);
+                level_generic(f, wm, part, c, A, b, poor, neg, degenerate);
                 prism_dw_normalise<T>(A, b);
 #pragma unroll
                 for (int k = 0; k < 36; ++k) A[k] = pair_sum(A[k], mask);
@@ -394,10 +397,30 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
         }
     }
 
-    // Generic coefficients: the three points of zeta level l in a rolled loop.
+    // Generic coefficients at zeta level l, contracted in reference space (the
+    // same PRISM6 sum as Algorithm 2's per-point update, regrouped). With the
+    // cofactor rows a_i of J (J^{-1} has rows a_i / det) and vol = w |det J|, each
+    // point forms the reference-space coefficient matrix
+    //   Gamma = vol B^T C B,  B = diag(1, J^{-T}):
+    //   Gamma_00 = vol c00, Gamma_0j = w sgn(det) c0. a_j, Gamma_i0 = w sgn(det) a_i . c.0,
+    //   Gamma_ij = (w / |det|) a_i^T C3 a_j  (i, j = 1..3).
+    // The reference derivatives (phi, d/dxi, d/deta, d/dzeta) of shape function
+    // (k, m) (k the triangle vertex, m = 0 bottom, 1 top) are
+    //   psi_(k,m) = z_m u_k + s_m h_k e_3,  u_k = (2 h_k, D_k1, D_k2, 0),
+    // with z_m the level's (1 -+ zeta)/2, s_m = -1 / +1, h_k = lambda_k(t) / 2 and
+    // D = d lambda / d(xi, eta) = ((-1, -1), (1, 0), (0, 1)). A point adds
+    // psi_r^T Gamma psi_s to A_rs; only h_k and Gamma change between the three
+    // points of a level, so the points accumulate the sums
+    //   SF_kk' = sum_t u_k^T Gamma[0..2][0..2] u_k',  SP_kk' = sum_t h_k' u_k . Gamma[0..2][3],
+    //   SQ_kk' = sum_t h_k Gamma[3][0..2] . u_k',      SG_kk' = sum_t h_k h_k' Gamma_33,
+    // and the 6 x 6 expansion runs once per level:
+    //   A_(k,m),(k',m') += z_m z_m' SF + z_m s_m' SP + s_m z_m' SQ + s_m s_m' SG.
+    // Likewise b_(k,m) += z_m BU_k + s_m BR_k with BU_k = sum_t (2 h_k vol d0 +
+    // sum_i D_ki w sgn(det) d. a_i) and BR_k = sum_t h_k w sgn(det) d. a_3.
+    // wm = (w_0 + w_1 + w_2) / 12, so that d x / d zeta at point t is wm + w_t / 4.
     template <class CS>
-    __device__ __forceinline__ static void level_generic(const PrismFrame<T> &f, int l, const CS &c, T A[36], T b[6],
-                                                         bool &poor, bool &neg, bool &degenerate) {
+    __device__ __forceinline__ static void level_generic(const PrismFrame<T> &f, const V3<T> &wm, int l, const CS &c,
+                                                         T A[36], T b[6], bool &poor, bool &neg, bool &degenerate) {
         using R = Rule<Q_PRISM6>;
         const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
         const V3<T> cx = zb * f.ub + zt * f.ut;
@@ -408,27 +431,184 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const V3<float> cxf = hi_f(cx), t1 = 2.0f * hi_f(cy) - cxf;
             fxy = dot(cxf, cxf) + dot(t1, t1) * (1.0f / 3.0f);
         }
+        T SF[9], SP[9], SQ[9], SG[6], S4[4], BU[3], BR[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) SF[k] = SP[k] = SQ[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) SG[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S4[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) BU[k] = BR[k] = T(0);
 #pragma unroll 1
         for (int t = 0; t < 3; ++t) {
-            const int q = 3 * l + t;
-            T ph[6];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const T lam = t == k ? T(2.0 / 3.0) : T(1.0 / 6.0);
-                ph[k] = lam * zb;
-                ph[k + 3] = lam * zt;
-            }
-            V3<T> g[6], cz;
-            const T det = prism_point(f, cx, cy, a3, l, t, g, cz);
+            const int o = CPQ ? 20 * (3 * l + t) : 0;
+            const V3<T> wt = t == 0 ? f.w0 : (t == 1 ? f.w1 : f.w2);
+            const V3<T> cz = {madd(T(0.25), wt.x, wm.x), madd(T(0.25), wt.y, wm.y), madd(T(0.25), wt.z, wm.z)};
+            const V3<T> a1 = cross(cy, cz), a2 = cross(cz, cx);
+            const T det = dot(cx, a1);
             if constexpr (PREC != FP64) poor |= prism_poor(fxy, hi_f(cz), hi_f(det));
             if constexpr (PREC == DWORD) poor |= !dw_det_ok(det.h);
             if constexpr (PREC == FP64) degenerate |= degenerate_det(det);
-            neg |= is_neg(det);
-            const T vol = abs_t(det) * T(R::w(0));
-            prism_generic_update_rt<T>(g, vol, c, CPQ ? 20 * q : 0, ph, A, b);
+            const bool ng = is_neg(det);
+            neg |= ng;
+            const T adet = abs_t(det);
+            const T s2 = recip_w(adet, T(R::w(0)));              // w / |det|
+            const T s1 = ng ? T(-R::w(0)) : T(R::w(0));          // w sgn(det)
+            const T s0 = mul_off(adet, T(R::w(0)));              // vol
+            const V3<T> av[3] = {a1, a2, a3};
+            const V3<T> c0 = {mul_off(s1, c(o + 1)), mul_off(s1, c(o + 2)), mul_off(s1, c(o + 3))};
+            const V3<T> ci0 = {mul_off(s1, c(o + 4)), mul_off(s1, c(o + 8)), mul_off(s1, c(o + 12))};
+            V3<T> C3[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                C3[i] = {mul_off(s2, c(o + 4 * i + 5)), mul_off(s2, c(o + 4 * i + 6)), mul_off(s2, c(o + 4 * i + 7))};
+            T G[4][4];
+            G[0][0] = mul_off(s0, c(o));
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const V3<T> Ca = {dot(C3[0], av[j]), dot(C3[1], av[j]), dot(C3[2], av[j])};
+                G[0][j + 1] = dot(c0, av[j]);
+                G[j + 1][0] = dot(av[j], ci0);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) G[i + 1][j + 1] = dot(av[i], Ca);
+            }
+            // h_k = lambda_k(t) / 2 and 2 h_k
+            T h[3], h2[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                h[k] = t == k ? T(1.0 / 3.0) : T(1.0 / 12.0);
+                h2[k] = t == k ? T(2.0 / 3.0) : T(1.0 / 6.0);
+            }
+            // SF: 4 h_k h_k' G00 + 2 h_k x_k' + 2 h_k' y_k (the D-block of G summed apart in S4)
+            const T xs[3] = {-(G[0][1] + G[0][2]), G[0][1], G[0][2]};
+            const T ys[3] = {-(G[1][0] + G[2][0]), G[1][0], G[2][0]};
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const T e = madd(h2[kk], G[0][0], xs[kk]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    acc(SF[3 * k + kk], h2[k], e);
+                    acc(SF[3 * k + kk], h2[kk], ys[k]);
+                }
+            }
+            acc1(S4[0], G[1][1]);
+            acc1(S4[1], G[1][2]);
+            acc1(S4[2], G[2][1]);
+            acc1(S4[3], G[2][2]);
+            const T p[3] = {madd(h2[0], G[0][3], -(G[1][3] + G[2][3])), madd(h2[1], G[0][3], G[1][3]),
+                            madd(h2[2], G[0][3], G[2][3])};
+            const T qv[3] = {madd(h2[0], G[3][0], -(G[3][1] + G[3][2])), madd(h2[1], G[3][0], G[3][1]),
+                             madd(h2[2], G[3][0], G[3][2])};
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    acc(SP[3 * k + kk], h[kk], p[k]);
+                    acc(SQ[3 * k + kk], h[k], qv[kk]);
+                }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc(SG[k], t == k ? T(1.0 / 9.0) : T(1.0 / 144.0), G[3][3]);
+            acc(SG[3], t == 2 ? T(1.0 / 144.0) : T(1.0 / 36.0), G[3][3]);   // (0, 1)
+            acc(SG[4], t == 1 ? T(1.0 / 144.0) : T(1.0 / 36.0), G[3][3]);   // (0, 2)
+            acc(SG[5], t == 0 ? T(1.0 / 144.0) : T(1.0 / 36.0), G[3][3]);   // (1, 2)
+            // load vector
+            const T d0 = mul_off(s0, c(o + 16));
+            const V3<T> dv = {mul_off(s1, c(o + 17)), mul_off(s1, c(o + 18)), mul_off(s1, c(o + 19))};
+            const T dl1 = dot(dv, a1), dl2 = dot(dv, a2), dl3 = dot(dv, a3);
+            const T dd[3] = {-(dl1 + dl2), dl1, dl2};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                acc(BU[k], h2[k], d0);
+                acc1(BU[k], dd[k]);
+                acc(BR[k], h[k], dl3);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            SF[k] = acc_norm(SF[k]);
+            SP[k] = acc_norm(SP[k]);
+            SQ[k] = acc_norm(SQ[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) SG[k] = acc_norm(SG[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S4[k] = acc_norm(S4[k]);
+        // SF += D S4 D^T
+        SF[4] = SF[4] + S4[0];
+        SF[5] = SF[5] + S4[1];
+        SF[7] = SF[7] + S4[2];
+        SF[8] = SF[8] + S4[3];
+        SF[3] = SF[3] - (S4[0] + S4[1]);
+        SF[6] = SF[6] - (S4[2] + S4[3]);
+        SF[1] = SF[1] - (S4[0] + S4[2]);
+        SF[2] = SF[2] - (S4[1] + S4[3]);
+        SF[0] = SF[0] + ((S4[0] + S4[1]) + (S4[2] + S4[3]));
+        // the level's share of A and b
+        const T zbb = l ? T(R::zb(1) * R::zb(1)) : T(R::zb(0) * R::zb(0));
+        const T ztt = l ? T(R::zt(1) * R::zt(1)) : T(R::zt(0) * R::zt(0));
+        const T zbt = l ? T(R::zb(1) * R::zt(1)) : T(R::zb(0) * R::zt(0));
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const T sf = SF[3 * k + kk], sp = SP[3 * k + kk], sq = SQ[3 * k + kk];
+                const T sg = SG[k == kk ? k : k + kk + 2];
+                T &a00 = A[6 * k + kk], &a01 = A[6 * k + kk + 3], &a10 = A[6 * (k + 3) + kk],
+                  &a11 = A[6 * (k + 3) + kk + 3];
+                acc(a00, zbb, sf);
+                acc(a00, -zb, sp);
+                acc(a00, -zb, sq);
+                acc1(a00, sg);
+                acc(a01, zbt, sf);
+                acc(a01, zb, sp);
+                acc(a01, -zt, sq);
+                acc1(a01, -sg);
+                acc(a10, zbt, sf);
+                acc(a10, -zt, sp);
+                acc(a10, zb, sq);
+                acc1(a10, -sg);
+                acc(a11, ztt, sf);
+                acc(a11, zt, sp);
+                acc(a11, zt, sq);
+                acc1(a11, sg);
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T bu = acc_norm(BU[k]), br = acc_norm(BR[k]);
+            acc(b[k], zb, bu);
+            acc1(b[k], -br);
+            acc(b[k + 3], zt, bu);
+            acc1(b[k + 3], br);
         }
     }
 
+    // a b + c; s += a b and s += a (in double-word s stays an unnormalised pair
+    // until acc_norm); plain fused multiply-adds in the other forms
+    __device__ __forceinline__ static T madd(T a, T b, T c) {
+        if constexpr (PREC == DWORD)
+            return dw_dot_add<1>(&a, &b, c);
+        else
+            return a * b + c;
+    }
+    __device__ __forceinline__ static void acc(T &s, T a, T b) {
+        if constexpr (PREC == DWORD)
+            dw_acc(s, a, b);
+        else
+            s = a * b + s;
+    }
+    __device__ __forceinline__ static void acc1(T &s, T a) {
+        if constexpr (PREC == DWORD)
+            dw_acc_add(s, a);
+        else
+            s = s + a;
+    }
+    __device__ __forceinline__ static T acc_norm(T s) {
+        if constexpr (PREC == DWORD)
+            return dw_acc_norm(s);
+        else
+            return s;
+    }
     __device__ __forceinline__ static T abs_t(T v) {
         if constexpr (PREC == FP64)   // the sign bit cleared (an integer operation)
             return __longlong_as_double(__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll);

@@ -1,8 +1,8 @@
 """Guard bands: output arrays sit inside larger buffers filled with a sentinel
 byte pattern; after each launch the bytes before and after every output (and
 the flags) must be unchanged. Ragged sizes (tiles not full), every element type,
-precision form, input and output layout, packed output and two threads per
-prism element."""
+precision form, input and output layout, packed output, two threads per prism
+element and one row per lane (four threads per tetrahedron, six per prism)."""
 import itertools
 
 import numpy as np
@@ -95,3 +95,28 @@ def test_no_write_outside_outputs_two_threads_per_prism(ctx, prec):
         ctx.sync()
         for raw, nbytes in (ga, gb, gf):
             _check_guards(raw, nbytes)
+
+
+@pytest.mark.parametrize("et,kind", [(api.TET, api.GENERIC), (api.TET, api.POISSON), (api.PRISM, api.GENERIC),
+                                     (api.PRISM, api.POISSON)])
+@pytest.mark.parametrize("prec", [api.FP64, api.FP32_MIXED, api.FP64_DW])
+def test_no_write_outside_outputs_rows_per_lane(ctx, et, kind, prec):
+    """Four threads per tetrahedron and six per prism (one row of A^e each; five
+    groups per warp for prisms, two lanes idle): ragged tiles, persistent and not."""
+    n = 997 if et == api.TET else 611
+    quad = api.QUAD_TET4 if et == api.TET else api.QUAD_PRISM6
+    cpq = 1 if et == api.PRISM else 0
+    mesh, c = make_inputs(et, kind, quad, cpq, n=n, seed=63)
+    X, C, _ = to_device_inputs(et, mesh, c, prec, api.AOS)
+    ga, gb, gf, (A, B, F) = _outputs(et, n, prec, api.AOS, False)
+    kw = dict(kind=kind, quad=quad, coef_mode=api.PER_QPOINT if cpq else api.PER_ELEMENT, prec=prec,
+              layout=api.AOS, out_layout=api.AOS, out=(A, B, F))
+    tpe = 4 if et == api.TET else 6
+    epw = 32 // tpe
+    for block, pers in ((8 * epw, 0), (2 * epw, 1), (4 * epw, 0)):
+        ctx.set_shape(block, pers, et, X, C, tpe=tpe, **kw)
+        ctx.integrate(et, X, C, **kw)
+        ctx.sync()
+        for raw, nbytes in (ga, gb, gf):
+            _check_guards(raw, nbytes)
+        assert torch.isfinite(A).all() and torch.isfinite(B).all()
