@@ -530,19 +530,23 @@ __device__ __forceinline__ void tet_generic_aug(const V3<T> a3[3], T f, T sm, T 
 // cofactors and det J, OM the scalings of the coefficients and of det J, OS the
 // sums of rows and columns; the fused multiply-adds always on the double pipe.
 // Every choice gives the same bits (the same IEEE operations in the same order).
+// An integer multiplication that meets an operand or a product outside the
+// normal range (zero aside) sets `sp`; the caller then redoes the element with
+// the double pipe, as TetF64 with F64<false> throughout.
 // The arithmetic is that of tet_geometry, recip_scaled and tet_generic_aug /
 // tet_poisson_products, written out with explicit operations.
 // ---------------------------------------------------------------------------
 template <class OE, class OX, class OM, class OS> struct TetF64 {
     using O = F64<false>;   // fused multiply-adds
     // a = u x v, component i = u_j v_k - u_k v_j as fma(u_j, v_k, -(u_k v_j))
-    __device__ __forceinline__ static void cross(const double u[3], const double v[3], double w[3]) {
-        w[0] = O::fma(u[1], v[2], -OX::mul(u[2], v[1]));
-        w[1] = O::fma(u[2], v[0], -OX::mul(u[0], v[2]));
-        w[2] = O::fma(u[0], v[1], -OX::mul(u[1], v[0]));
+    __device__ __forceinline__ static void cross(const double u[3], const double v[3], double w[3], bool &sp) {
+        w[0] = O::fma(u[1], v[2], -OX::mul(u[2], v[1], sp));
+        w[1] = O::fma(u[2], v[0], -OX::mul(u[0], v[2], sp));
+        w[2] = O::fma(u[0], v[1], -OX::mul(u[1], v[0], sp));
     }
-    template <class OP = OX> __device__ __forceinline__ static double dot3(const double u[3], const double v[3]) {
-        return O::fma(u[2], v[2], O::fma(u[1], v[1], OP::mul(u[0], v[0])));
+    template <class OP = OX>
+    __device__ __forceinline__ static double dot3(const double u[3], const double v[3], bool &sp) {
+        return O::fma(u[2], v[2], O::fma(u[1], v[1], OP::mul(u[0], v[0], sp)));
     }
     __device__ __forceinline__ static double dot3_add(const double u[3], const double v[3], double z) {
         return O::fma(u[2], v[2], O::fma(u[1], v[1], O::fma(u[0], v[0], z)));
@@ -552,7 +556,7 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
         return O::fma(4.0, q, -OS::add(OS::add(p1, p2), p3));
     }
     // w / v as recip_scaled
-    __device__ __forceinline__ static double recip_w(double v, double w) {
+    __device__ __forceinline__ static double recip_w(double v, double w, bool &sp) {
         const uint32_t hw = static_cast<uint32_t>(__double2hiint(v));
         const uint32_t lw = static_cast<uint32_t>(__double2loint(v));
         const uint32_t ev = (hw >> 20) & 0x7FFu;
@@ -561,43 +565,44 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
         const uint32_t er = (rb >> 23) & 0xFFu;
         const uint32_t yh = ((er + 1919u - ev) << 20) | ((rb & 0x7FFFFFu) >> 3);
         const double y0 = __hiloint2double(static_cast<int>(yh), static_cast<int>(rb << 29));
-        const double wy0 = OM::mul(w, y0);
+        const double wy0 = OM::mul(w, y0, sp);
         const double e = O::fma(-v, y0, 1.0);
         return O::fma(wy0, O::fma(e, e, e), wy0);
     }
     // Edge vectors, cofactor rows a_1..a_3 and det J of the element; false if
     // degenerate (!(|det J| > 1e-300), NaN included).
-    template <class XS> __device__ __forceinline__ static bool geometry(const XS &x, double a[3][3], double &det) {
+    template <class XS>
+    __device__ __forceinline__ static bool geometry(const XS &x, double a[3][3], double &det, bool &sp) {
         double e[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int i = 0; i < 3; ++i) e[k][i] = OE::add(x(3 * (k + 1) + i), -x(i));
-        cross(e[1], e[2], a[0]);
-        cross(e[2], e[0], a[1]);
-        cross(e[0], e[1], a[2]);
-        det = dot3(e[0], a[0]);
+        cross(e[1], e[2], a[0], sp);
+        cross(e[2], e[0], a[1], sp);
+        cross(e[0], e[1], a[2], sp);
+        det = dot3(e[0], a[0], sp);
         return !degenerate_det(det);
     }
     // tet_generic_aug with explicit operations
     template <int QUAD, class CS>
     __device__ __forceinline__ static void generic(const double a[3][3], double det, const CS &c, double A[16],
-                                                   double b[4]) {
+                                                   double b[4], bool &sp) {
         constexpr TetSums S = tet_sums<QUAD>();
         const bool neg = is_neg(det);
         const double V = fabs(det);
-        const double f = recip_w(V, S.W);
+        const double f = recip_w(V, S.W, sp);
         const double sm = neg ? -S.W / 4 : S.W / 4, sW = neg ? -S.W : S.W;
         double M[3][4], M3[4];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) M[i][j] = OM::mul(f, c(4 * (i + 1) + (j + 1)));
-            M[i][3] = OM::mul(sm, c(4 * (i + 1)));
+            for (int j = 0; j < 3; ++j) M[i][j] = OM::mul(f, c(4 * (i + 1) + (j + 1)), sp);
+            M[i][3] = OM::mul(sm, c(4 * (i + 1)), sp);
         }
 #pragma unroll
-        for (int j = 0; j < 3; ++j) M3[j] = OM::mul(sm, c(j + 1));
-        const double mu = OM::mul(OM::mul(V, c(0)), S.M2[0][1]);
+        for (int j = 0; j < 3; ++j) M3[j] = OM::mul(sm, c(j + 1), sp);
+        const double mu = OM::mul(OM::mul(V, c(0), sp), S.M2[0][1], sp);
         M3[3] = mu;
         double P[4][4];
 #pragma unroll
@@ -618,12 +623,12 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
         }
         if constexpr (S.M2[0][0] != S.M2[0][1]) {
             constexpr double ratio = (S.M2[0][0] - S.M2[0][1]) / S.M2[0][1];
-            const double dl = ratio == 1.0 ? mu : OM::mul(mu, ratio);
+            const double dl = ratio == 1.0 ? mu : OM::mul(mu, ratio, sp);
 #pragma unroll
             for (int r = 0; r < 4; ++r) A[5 * r] = OS::add(A[5 * r], dl);
         }
-        const double d[3] = {OM::mul(sW, c(17)), OM::mul(sW, c(18)), OM::mul(sW, c(19))};
-        const double e = OM::mul(OM::mul(V, c(16)), S.W / 4);
+        const double d[3] = {OM::mul(sW, c(17), sp), OM::mul(sW, c(18), sp), OM::mul(sW, c(19), sp)};
+        const double e = OM::mul(OM::mul(V, c(16), sp), S.W / 4, sp);
 #pragma unroll
         for (int r = 1; r < 4; ++r) b[r] = dot3_add(a[r - 1], d, e);
         b[0] = lin4(b[1], b[2], b[3], e);
@@ -632,15 +637,15 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
     // (r, s = 1..3), row and column 0 from the vanishing sums; b as tet_poisson_b.
     template <int QUAD, int CPQ, class CS>
     __device__ __forceinline__ static void poisson(const double a[3][3], double det, const CS &c, double A[16],
-                                                   double b[4]) {
+                                                   double b[4], bool &sp) {
         constexpr TetSums S = tet_sums<QUAD>();
         const double V = fabs(det);
-        const double k = recip_w(V, S.W);
+        const double k = recip_w(V, S.W, sp);
         double G[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int s = r; s < 3; ++s) G[r][s] = G[s][r] = OM::mul(k, dot3<OM>(a[r], a[s]));
+            for (int s = r; s < 3; ++s) G[r][s] = G[s][r] = OM::mul(k, dot3<OM>(a[r], a[s], sp), sp);
         double row0[3];
 #pragma unroll
         for (int s = 0; s < 3; ++s) row0[s] = -OS::add(OS::add(G[0][s], G[1][s]), G[2][s]);
@@ -653,7 +658,7 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
             for (int s = 0; s < 3; ++s) A[4 * (r + 1) + (s + 1)] = G[r][s];
         if constexpr (!CPQ || Rule<QUAD>::NQ == 1) {
             // d^0 per element or a one-point rule: b_r = V d0 m_r, m_r = W / 4
-            const double vd = OM::mul(OM::mul(V, c(0)), S.m[0]);   // m_r = W / 4 for both rules
+            const double vd = OM::mul(OM::mul(V, c(0), sp), S.m[0], sp);   // m_r = W / 4 for both rules
 #pragma unroll
             for (int r = 0; r < 4; ++r) b[r] = vd;
         } else {
@@ -661,12 +666,12 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
             for (int r = 0; r < 4; ++r) b[r] = 0.0;
 #pragma unroll
             for (int q = 0; q < Rule<QUAD>::NQ; ++q) {
-                const double wd = OM::mul(Rule<QUAD>::w(q), c(q));
+                const double wd = OM::mul(Rule<QUAD>::w(q), c(q), sp);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) b[r] = O::fma(wd, Rule<QUAD>::phi(q, r), b[r]);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) b[r] = OM::mul(b[r], V);
+            for (int r = 0; r < 4; ++r) b[r] = OM::mul(b[r], V, sp);
         }
     }
 };

@@ -7,9 +7,11 @@
 // of their double multiplications and additions here instead. These are the
 // same IEEE operations, not approximations: for normal operands and a normal
 // result the value returned is the correctly rounded product or sum, bit for
-// bit what the double-precision instruction returns. Zero, subnormal, infinite
-// and NaN operands, and results that would leave the normal range, go to the
-// double-precision instruction itself, so every input gives the hardware's
+// bit what the double-precision instruction returns; so is the signed zero of a
+// product with a zero operand. Subnormal, infinite and NaN operands, and results
+// that would leave the normal range, go to the double-precision instruction
+// itself (i64_dmul, i64_dadd), or are reported to the caller, which redoes its
+// work on the double pipe (i64_dmul_nz), so every input gives the hardware's
 // result. The fused multiply-adds stay on the double pipe.
 //
 // The algorithms are the textbook ones of IEEE arithmetic on integer
@@ -24,17 +26,12 @@
 
 namespace fe {
 
-__device__ __forceinline__ double i64_dmul(double a, double b) {
-    const unsigned long long ua = static_cast<unsigned long long>(__double_as_longlong(a));
-    const unsigned long long ub = static_cast<unsigned long long>(__double_as_longlong(b));
-    const uint32_t ah = static_cast<uint32_t>(ua >> 32), bh = static_cast<uint32_t>(ub >> 32);
-    const uint32_t al = static_cast<uint32_t>(ua), bl = static_cast<uint32_t>(ub);
-    const uint32_t ea = (ah >> 20) & 0x7FFu, eb = (bh >> 20) & 0x7FFu;
-    // biased exponent of the result before normalisation (one more if the
-    // significands' product reaches 2); normal operands, and a result that stays
-    // normal after normalisation and rounding
-    const int e0 = int(ea) + int(eb) - 1023;
-    if (!((ea - 1u) < 2046u && (eb - 1u) < 2046u && e0 >= 1 && e0 <= 2044)) return __dmul_rn(a, b);
+// Significand product of normal operands whose product stays normal (biased
+// exponent before normalisation e0 in [1, 2044]): the exact 106-bit product,
+// normalised and rounded to nearest even, packed with the exponent and without
+// the sign.
+__device__ __forceinline__ unsigned long long i64_dmul_packed(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                                              int e0) {
     const uint32_t mah = (ah & 0xFFFFFu) | 0x100000u, mbh = (bh & 0xFFFFFu) | 0x100000u;
     // P = (mah 2^32 + al)(mbh 2^32 + bl) = H 2^64 + M 2^32 + L, 2^104 <= P < 2^106
     const unsigned long long t0 = static_cast<unsigned long long>(al) * bl;
@@ -48,8 +45,47 @@ __device__ __forceinline__ double i64_dmul(double a, double b) {
     const uint32_t rbit = s ? static_cast<uint32_t>(Q & 1u) : ((M >> 19) & 1u);
     const uint32_t sticky = (M & (s ? 0xFFFFFu : 0x7FFFFu)) | L;
     m += rbit & ((sticky != 0u) | static_cast<uint32_t>(m & 1u));
-    const unsigned long long r = (static_cast<unsigned long long>(e0 + int(s) - 1) << 52) + m;
-    return __longlong_as_double(static_cast<long long>(r | (static_cast<unsigned long long>((ah ^ bh) & 0x80000000u) << 32)));
+    return (static_cast<unsigned long long>(e0 + int(s) - 1) << 52) + m;
+}
+
+// The product for every input: integer instructions for normal operands with a
+// normal product, the DMUL instruction otherwise.
+__device__ __forceinline__ double i64_dmul(double a, double b) {
+    const unsigned long long ua = static_cast<unsigned long long>(__double_as_longlong(a));
+    const unsigned long long ub = static_cast<unsigned long long>(__double_as_longlong(b));
+    const uint32_t ah = static_cast<uint32_t>(ua >> 32), bh = static_cast<uint32_t>(ub >> 32);
+    const uint32_t ea = (ah >> 20) & 0x7FFu, eb = (bh >> 20) & 0x7FFu;
+    // biased exponent of the result before normalisation (one more if the
+    // significands' product reaches 2)
+    const int e0 = int(ea) + int(eb) - 1023;
+    if (!((ea - 1u) < 2046u && (eb - 1u) < 2046u && e0 >= 1 && e0 <= 2044)) return __dmul_rn(a, b);
+    const unsigned long long r = i64_dmul_packed(ah, static_cast<uint32_t>(ua), bh, static_cast<uint32_t>(ub), e0);
+    const unsigned long long sg = static_cast<unsigned long long>((ah ^ bh) & 0x80000000u) << 32;
+    return __longlong_as_double(static_cast<long long>(r | sg));
+}
+
+// The product for normal or zero operands whose result is normal or zero, bit
+// for bit the DMUL result; any other case (a subnormal, infinite or NaN operand,
+// a result outside the normal range) sets `special` and returns an unspecified
+// value, so that the caller can redo its work on the double pipe. Kernels that
+// call this form take that decision once per element: the DMUL beside every
+// product in i64_dmul is issued (predicated off) on every call and holds the
+// double pipe as long as an executed one.
+__device__ __forceinline__ double i64_dmul_nz(double a, double b, bool &special) {
+    const unsigned long long ua = static_cast<unsigned long long>(__double_as_longlong(a));
+    const unsigned long long ub = static_cast<unsigned long long>(__double_as_longlong(b));
+    const uint32_t ah = static_cast<uint32_t>(ua >> 32), bh = static_cast<uint32_t>(ub >> 32);
+    const uint32_t al = static_cast<uint32_t>(ua), bl = static_cast<uint32_t>(ub);
+    const uint32_t ea = (ah >> 20) & 0x7FFu, eb = (bh >> 20) & 0x7FFu;
+    const int e0 = int(ea) + int(eb) - 1023;
+    const bool na = (ea - 1u) < 2046u, nb = (eb - 1u) < 2046u;
+    const bool za = ((ah & 0x7FFFFFFFu) | al) == 0u, zb = ((bh & 0x7FFFFFFFu) | bl) == 0u;
+    const bool normal = na && nb && e0 >= 1 && e0 <= 2044;
+    const bool zero = (za && (nb || zb)) || (zb && na);
+    special |= !(normal || zero);
+    const unsigned long long sg = static_cast<unsigned long long>((ah ^ bh) & 0x80000000u) << 32;
+    const unsigned long long r = i64_dmul_packed(ah, al, bh, bl, e0);
+    return __longlong_as_double(static_cast<long long>(zero ? sg : (r | sg)));
 }
 
 __device__ __forceinline__ double i64_dadd(double a, double b) {
@@ -87,6 +123,10 @@ __device__ __forceinline__ double i64_dadd(double a, double b) {
 // the same bits.
 template <bool INT> struct F64 {
     __device__ __forceinline__ static double mul(double a, double b) { return INT ? i64_dmul(a, b) : __dmul_rn(a, b); }
+    // the same product with the special cases left to the caller (i64_dmul_nz)
+    __device__ __forceinline__ static double mul(double a, double b, bool &special) {
+        return INT ? i64_dmul_nz(a, b, special) : __dmul_rn(a, b);
+    }
     __device__ __forceinline__ static double add(double a, double b) { return INT ? i64_dadd(a, b) : __dadd_rn(a, b); }
     __device__ __forceinline__ static double sub(double a, double b) { return add(a, -b); }
     __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }

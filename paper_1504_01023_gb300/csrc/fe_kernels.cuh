@@ -77,13 +77,29 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CP
             tet_generic_products<double, QUAD, CPQ>(g, V, c, A, b);
             return is_neg(geo.det) ? 2 : 0;
         } else {
+            // scalings in integer instructions; an element that meets a special
+            // operand or product there is redone on the double pipe (one branch
+            // per element, never taken on ordinary data)
             using TF = TetF64<F64<false>, F64<false>, F64<true>, F64<false>>;
+            using TH = TetF64<F64<false>, F64<false>, F64<false>, F64<false>>;
             double a[3][3], det;
-            if (!TF::geometry(x, a, det)) return zero(A, b);
+            bool sp = false;
+            if (!TF::geometry(x, a, det, sp)) return zero(A, b);
             if constexpr (KIND == POISSON)
-                TF::template poisson<QUAD, CPQ>(a, det, c, A, b);
+                TF::template poisson<QUAD, CPQ>(a, det, c, A, b, sp);
             else
-                TF::template generic<QUAD>(a, det, c, A, b);
+                TF::template generic<QUAD>(a, det, c, A, b, sp);
+            if (sp) {
+                // from the inputs again (the compiler barrier keeps the first pass's
+                // values from being held for this path)
+                asm volatile("" ::: "memory");
+                double a2[3][3], det2;
+                TH::geometry(x, a2, det2, sp);
+                if constexpr (KIND == POISSON)
+                    TH::template poisson<QUAD, CPQ>(a2, det2, c, A, b, sp);
+                else
+                    TH::template generic<QUAD>(a2, det2, c, A, b, sp);
+            }
             return is_neg(det) ? 2 : 0;
         }
     }
@@ -277,9 +293,14 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     // TPE == 2 (two threads per element): the lane of parity `part` takes the three
     // points of zeta level `part` and the pair combines its partial results
     // through shuffles within `mask`; both lanes end with the whole A^e and b^e.
-    template <int TPE = 1, class CS>
+    //
+    // FP64: the products off the critical path run in integer instructions, and
+    // sp is set when one of them meets an operand or a product outside the normal
+    // range (zero aside; with TPE == 2 for both lanes of the pair); the caller then
+    // redoes the element with HW = true (those products on the double pipe).
+    template <int TPE = 1, bool HW = false, class CS>
     __device__ __forceinline__ static uint8_t qloop(const V3<T> r[6], const CS &c, T A[36], T b[6], bool &poor,
-                                                    int part = 0, unsigned mask = 0xFFFFFFFFu) {
+                                                    bool &sp, int part = 0, unsigned mask = 0xFFFFFFFFu) {
         const PrismFrame<T> f = prism_frame(r);
 #pragma unroll
         for (int k = 0; k < 6; ++k) b[k] = T(0);
@@ -290,12 +311,13 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             if constexpr (TPE == 1) {
                 T c3l[2][3];
 #pragma unroll
-                for (int l = 0; l < 2; ++l) level_laplace(f, l, c, L[l], v[l], c3l[l], b, poor, neg, degenerate);
+                for (int l = 0; l < 2; ++l)
+                    level_laplace<HW>(f, l, c, L[l], v[l], c3l[l], b, poor, neg, degenerate, sp);
 #pragma unroll
                 for (int t = 0; t < 3; ++t) c3[t] = c3l[0][t] + c3l[1][t];
             } else {
                 T Lm[3], vm[3][2], c3m[3];
-                level_laplace(f, part, c, Lm, vm, c3m, b, poor, neg, degenerate);
+                level_laplace<HW>(f, part, c, Lm, vm, c3m, b, poor, neg, degenerate, sp);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     const T o = pair_other(Lm[j], mask);
@@ -319,10 +341,10 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const V3<T> wm = r12 * ((f.w0 + f.w1) + f.w2);
             if constexpr (TPE == 1) {
 #pragma unroll
-                for (int l = 0; l < 2; ++l) level_generic(f, wm, l, c, A, b, poor, neg, degenerate);
+                for (int l = 0; l < 2; ++l) level_generic<HW>(f, wm, l, c, A, b, poor, neg, degenerate, sp);
                 prism_dw_normalise<T>(A, b);
             } else {
-                level_generic(f, wm, part, c, A, b, poor, neg, degenerate);
+                level_generic<HW>(f, wm, part, c, A, b, poor, neg, degenerate, sp);
                 prism_dw_normalise<T>(A, b);
 #pragma unroll
                 for (int k = 0; k < 36; ++k) A[k] = pair_sum(A[k], mask);
@@ -332,6 +354,7 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
 #pragma unroll
             for (int k = 0; k < 6; ++k) b[k] = pair_sum(b[k], mask);
             poor = pair_any(poor, mask);
+            if constexpr (PREC == FP64 && !HW) sp = pair_any(sp, mask);
             neg = pair_any(neg, mask);
             degenerate = pair_any(degenerate, mask);
         }
@@ -348,10 +371,11 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     // Laplace: the three points of zeta level l (a constant after unrolling, or a
     // run-time lane parity): per-level sum of (gamma_11, gamma_12, gamma_22), the
     // points' (gamma_13, gamma_23) and gamma_33, and the load vector terms.
-    template <class CS>
+    // HW: the FP64 products on the double pipe (the redo after a special case).
+    template <bool HW = false, class CS>
     __device__ __forceinline__ static void level_laplace(const PrismFrame<T> &f, int l, const CS &c, T Ll[3],
                                                          T vl[3][2], T c3l[3], T b[6], bool &poor, bool &neg,
-                                                         bool &degenerate) {
+                                                         bool &degenerate, bool &sp) {
         using R = Rule<Q_PRISM6>;
         const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
         const V3<T> cx = zb * f.ub + zt * f.ut;
@@ -378,7 +402,8 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             neg |= is_neg(det);
             const T adet = abs_t(det);
             const T sw = recip_w(adet, T(R::w(0)));          // vol / det^2 (equal weights)
-            const T g11 = mul_off(sw, dot(a1, a1)), g12 = mul_off(sw, dot(a1, a2)), g22 = mul_off(sw, dot(a2, a2));
+            const T g11 = mul_off<HW>(sw, dot(a1, a1), sp), g12 = mul_off<HW>(sw, dot(a1, a2), sp),
+                    g22 = mul_off<HW>(sw, dot(a2, a2), sp);
             if (t == 0) {
                 Ll[0] = g11;
                 Ll[1] = g12;
@@ -388,10 +413,10 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
                 Ll[1] += g12;
                 Ll[2] += g22;
             }
-            vl[t][0] = mul_off(sw, dot(a1, a3));
-            vl[t][1] = mul_off(sw, dot(a2, a3));
-            c3l[t] = mul_off(sw, a33);
-            const T vd = mul_off(mul_off(adet, T(R::w(0))), c(CPQ ? q : 0));
+            vl[t][0] = mul_off<HW>(sw, dot(a1, a3), sp);
+            vl[t][1] = mul_off<HW>(sw, dot(a2, a3), sp);
+            c3l[t] = mul_off<HW>(sw, a33, sp);
+            const T vd = mul_off<HW>(mul_off<HW>(adet, T(R::w(0)), sp), c(CPQ ? q : 0), sp);
 #pragma unroll
             for (int k = 0; k < 6; ++k) b[k] += vd * (l ? T(R::phi(3 + t, k)) : T(R::phi(t, k)));
         }
@@ -418,9 +443,11 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     // Likewise b_(k,m) += z_m BU_k + s_m BR_k with BU_k = sum_t (2 h_k vol d0 +
     // sum_i D_ki w sgn(det) d. a_i) and BR_k = sum_t h_k w sgn(det) d. a_3.
     // wm = (w_0 + w_1 + w_2) / 12, so that d x / d zeta at point t is wm + w_t / 4.
-    template <class CS>
+    // HW as for level_laplace.
+    template <bool HW = false, class CS>
     __device__ __forceinline__ static void level_generic(const PrismFrame<T> &f, const V3<T> &wm, int l, const CS &c,
-                                                         T A[36], T b[6], bool &poor, bool &neg, bool &degenerate) {
+                                                         T A[36], T b[6], bool &poor, bool &neg, bool &degenerate,
+                                                         bool &sp) {
         using R = Rule<Q_PRISM6>;
         const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
         const V3<T> cx = zb * f.ub + zt * f.ut;
@@ -455,16 +482,19 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const T adet = abs_t(det);
             const T s2 = recip_w(adet, T(R::w(0)));              // w / |det|
             const T s1 = ng ? T(-R::w(0)) : T(R::w(0));          // w sgn(det)
-            const T s0 = mul_off(adet, T(R::w(0)));              // vol
+            const T s0 = mul_off<HW>(adet, T(R::w(0)), sp);      // vol
             const V3<T> av[3] = {a1, a2, a3};
-            const V3<T> c0 = {mul_off(s1, c(o + 1)), mul_off(s1, c(o + 2)), mul_off(s1, c(o + 3))};
-            const V3<T> ci0 = {mul_off(s1, c(o + 4)), mul_off(s1, c(o + 8)), mul_off(s1, c(o + 12))};
+            const V3<T> c0 = {mul_off<HW>(s1, c(o + 1), sp), mul_off<HW>(s1, c(o + 2), sp),
+                              mul_off<HW>(s1, c(o + 3), sp)};
+            const V3<T> ci0 = {mul_off<HW>(s1, c(o + 4), sp), mul_off<HW>(s1, c(o + 8), sp),
+                               mul_off<HW>(s1, c(o + 12), sp)};
             V3<T> C3[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                C3[i] = {mul_off(s2, c(o + 4 * i + 5)), mul_off(s2, c(o + 4 * i + 6)), mul_off(s2, c(o + 4 * i + 7))};
+                C3[i] = {mul_off<HW>(s2, c(o + 4 * i + 5), sp), mul_off<HW>(s2, c(o + 4 * i + 6), sp),
+                         mul_off<HW>(s2, c(o + 4 * i + 7), sp)};
             T G[4][4];
-            G[0][0] = mul_off(s0, c(o));
+            G[0][0] = mul_off<HW>(s0, c(o), sp);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const V3<T> Ca = {dot(C3[0], av[j]), dot(C3[1], av[j]), dot(C3[2], av[j])};
@@ -513,8 +543,9 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             acc(SG[4], t == 1 ? T(1.0 / 144.0) : T(1.0 / 36.0), G[3][3]);   // (0, 2)
             acc(SG[5], t == 0 ? T(1.0 / 144.0) : T(1.0 / 36.0), G[3][3]);   // (1, 2)
             // load vector
-            const T d0 = mul_off(s0, c(o + 16));
-            const V3<T> dv = {mul_off(s1, c(o + 17)), mul_off(s1, c(o + 18)), mul_off(s1, c(o + 19))};
+            const T d0 = mul_off<HW>(s0, c(o + 16), sp);
+            const V3<T> dv = {mul_off<HW>(s1, c(o + 17), sp), mul_off<HW>(s1, c(o + 18), sp),
+                              mul_off<HW>(s1, c(o + 19), sp)};
             const T dl1 = dot(dv, a1), dl2 = dot(dv, a2), dl3 = dot(dv, a3);
             const T dd[3] = {-(dl1 + dl2), dl1, dl2};
 #pragma unroll
@@ -616,10 +647,18 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             return v < T(0) ? -v : v;
     }
     // a b for the products off the critical path: in FP64 in integer instructions
-    // (the same IEEE product, off the double pipe; see TetF64)
-    __device__ __forceinline__ static T mul_off(T a, T b) {
-        if constexpr (PREC == FP64)
+    // (the same IEEE product, off the double pipe; a special case sets sp, see
+    // TetF64), or on the double pipe with HW. The Laplace kind keeps the
+    // hardware instruction beside each product instead (i64_dmul): with the
+    // element-level redo its kernel spilled and ran 1% slower (measured).
+    template <bool HW>
+    __device__ __forceinline__ static T mul_off(T a, T b, bool &sp) {
+        if constexpr (PREC == FP64 && !HW && KIND == POISSON)
             return i64_dmul(a, b);
+        else if constexpr (PREC == FP64 && !HW)
+            return i64_dmul_nz(a, b, sp);
+        else if constexpr (PREC == FP64)
+            return __dmul_rn(a, b);
         else
             return a * b;
     }
@@ -659,26 +698,44 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
 };
 
 template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, FP64, Q_PRISM6, CPQ> {
-    template <class XS, class CS>
-    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[36], double b[6], bool &poor) {
-        V3<double> r[6];
+    template <class XS> __device__ __forceinline__ static void rel(const XS &x, V3<double> r[6]) {
         const V3<double> x0 = {x(0), x(1), x(2)};
         r[0] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int k = 1; k < 6; ++k) r[k] = V3<double>{x(3 * k), x(3 * k + 1), x(3 * k + 2)} - x0;
-        return PrismMath<KIND, FP64, CPQ>::qloop(r, c, A, b, poor);
+    }
+    // An element whose integer-instruction products met a special case is redone
+    // from its inputs with those products on the double pipe (one branch per
+    // element, never taken on ordinary data; the compiler barrier keeps the first
+    // pass's values from being held for it).
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[36], double b[6], bool &poor) {
+        V3<double> r[6];
+        rel(x, r);
+        bool sp = false;
+        uint8_t fl = PrismMath<KIND, FP64, CPQ>::qloop(r, c, A, b, poor, sp);
+        if (sp) {
+            asm volatile("" ::: "memory");
+            rel(x, r);
+            fl = PrismMath<KIND, FP64, CPQ>::template qloop<1, true>(r, c, A, b, poor, sp);
+        }
+        return fl;
     }
     // Two threads per element: this lane's zeta level; entries 2j + part out.
     template <class XS, class CS>
     __device__ __forceinline__ static uint8_t run_pair(const XS &x, const CS &c, double Ah[18], double bh[3], bool &poor,
                                                        int part, unsigned mask) {
         V3<double> r[6];
-        const V3<double> x0 = {x(0), x(1), x(2)};
-        r[0] = {0.0, 0.0, 0.0};
-#pragma unroll
-        for (int k = 1; k < 6; ++k) r[k] = V3<double>{x(3 * k), x(3 * k + 1), x(3 * k + 2)} - x0;
+        rel(x, r);
         double A[36], b[6];
-        const uint8_t fl = PrismMath<KIND, FP64, CPQ>::template qloop<2>(r, c, A, b, poor, part, mask);
+        bool sp = false;
+        uint8_t fl = PrismMath<KIND, FP64, CPQ>::template qloop<2>(r, c, A, b, poor, sp, part, mask);
+        if (sp) {   // both lanes of the pair: their shuffles within the pair alone
+            asm volatile("" ::: "memory");
+            rel(x, r);
+            const unsigned pm = 3u << ((threadIdx.x & 31u) & ~1u);
+            fl = PrismMath<KIND, FP64, CPQ>::template qloop<2, true>(r, c, A, b, poor, sp, part, pm);
+        }
         pick_half(A, b, Ah, bh, part);
         return fl;
     }
@@ -695,7 +752,8 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> 
 #pragma unroll
         for (int k = 1; k < 6; ++k)
             r[k] = {diff_hilo(h[3 * k], h[0]), diff_hilo(h[3 * k + 1], h[1]), diff_hilo(h[3 * k + 2], h[2])};
-        return PrismMath<KIND, MIXED, CPQ>::qloop(r, c, A, b, poor);
+        bool sp;   // set by the FP64 form only
+        return PrismMath<KIND, MIXED, CPQ>::qloop(r, c, A, b, poor, sp);
     }
     // Two threads per element: this lane's zeta level; entries 2j + part out.
     template <class XS, class CS>
@@ -710,7 +768,8 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> 
         for (int k = 1; k < 6; ++k)
             r[k] = {diff_hilo(h[3 * k], h[0]), diff_hilo(h[3 * k + 1], h[1]), diff_hilo(h[3 * k + 2], h[2])};
         float A[36], b[6];
-        const uint8_t fl = PrismMath<KIND, MIXED, CPQ>::template qloop<2>(r, c, A, b, poor, part, mask);
+        bool sp;   // set by the FP64 form only
+        const uint8_t fl = PrismMath<KIND, MIXED, CPQ>::template qloop<2>(r, c, A, b, poor, sp, part, mask);
         pick_half(A, b, Ah, bh, part);
         return fl;
     }
@@ -768,7 +827,8 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
         for (int k = 1; k < 6; ++k) r[k] = dw_edge_vec(x, k);
         const DwCoef<CS> cd{c};
         DW Ad[36], bd[6];
-        const uint8_t fl = PrismMath<KIND, DWORD, CPQ>::qloop(r, cd, Ad, bd, poor);
+        bool sp;   // set by the FP64 form only
+        const uint8_t fl = PrismMath<KIND, DWORD, CPQ>::qloop(r, cd, Ad, bd, poor, sp);
         poor = poor || !dw_group_ok<36>(Ad) || !dw_group_ok<6>(bd);
 #pragma unroll
         for (int k = 0; k < 36; ++k) A[k] = dw_to_double(Ad[k]);
@@ -787,7 +847,8 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
         for (int k = 1; k < 6; ++k) r[k] = dw_edge_vec(x, k);
         const DwCoef<CS> cd{c};
         DW Ad[36], bd[6];
-        const uint8_t fl = PrismMath<KIND, DWORD, CPQ>::template qloop<2>(r, cd, Ad, bd, poor, part, mask);
+        bool sp;   // set by the FP64 form only
+        const uint8_t fl = PrismMath<KIND, DWORD, CPQ>::template qloop<2>(r, cd, Ad, bd, poor, sp, part, mask);
         poor = poor || !dw_group_ok<36>(Ad) || !dw_group_ok<6>(bd);
 #pragma unroll
         for (int j = 0; j < 18; ++j) Ah[j] = dw_to_double(part ? Ad[2 * j + 1] : Ad[2 * j]);

@@ -26,8 +26,12 @@ def emu_mul(a, b):
     ah, al, bh, bl = ua >> 32, ua & 0xFFFFFFFF, ub >> 32, ub & 0xFFFFFFFF
     ea, eb = (ah >> 20) & 0x7FF, (bh >> 20) & 0x7FF
     e0 = ea + eb - 1023
-    if not (1 <= ea <= 2046 and 1 <= eb <= 2046 and 1 <= e0 <= 2044):
-        return None                                    # the hardware instruction
+    za, zb = (ua & 0x7FFFFFFFFFFFFFFF) == 0, (ub & 0x7FFFFFFFFFFFFFFF) == 0
+    na, nb = 1 <= ea <= 2046, 1 <= eb <= 2046
+    if (za and (nb or zb)) or (zb and na):
+        return dbl(((ah ^ bh) & 0x80000000) << 32)     # a zero operand: the signed zero
+    if not (na and nb and 1 <= e0 <= 2044):
+        return None                                    # left to the hardware instruction
     mah, mbh = (ah & 0xFFFFF) | 0x100000, (bh & 0xFFFFF) | 0x100000
     t0 = al * bl
     t1 = mah * bl + (t0 >> 32)
@@ -111,7 +115,8 @@ def test_mul_random_and_edges():
             y = (1.0 + rng.random()) * 2.0 ** (eb - 1023)
             pairs.append((x, y))
             pairs.append((-x, y))
-    pairs += [(0.0, 1.5), (1.5, -0.0), (1e-310, 3.0), (np.inf, 2.0), (np.nan, 1.0), (1.0, 1.0), (-1.0, 1.0)]
+    pairs += [(0.0, 1.5), (1.5, -0.0), (-0.0, -2.5), (0.0, 0.0), (-0.0, 0.0), (0.0, 1e300), (1e-300, -0.0),
+              (1e-310, 3.0), (0.0, 1e-310), (0.0, np.inf), (np.inf, 2.0), (np.nan, 1.0), (1.0, 1.0), (-1.0, 1.0)]
     assert _check(np.multiply, emu_mul, pairs) > 40000
 
 

@@ -64,6 +64,12 @@ def test_operations_bit_for_bit(lib):
     assert np.array_equal(np.isnan(oi.view(np.float64)), nan)
     diff = np.flatnonzero((oi != oh) & ~nan)
     assert diff.size == 0, [(a[i % m], b[i % m], "mul" if i < m else "add") for i in diff[:5]]
+    # the form that reports special cases (zeros handled in integer instructions)
+    oi, oh = _run(lib, 3, a, b, m, 1)
+    nan = np.isnan(oh.view(np.float64))
+    assert np.array_equal(np.isnan(oi.view(np.float64)), nan)
+    diff = np.flatnonzero((oi != oh) & ~nan)
+    assert diff.size == 0, [(a[i], b[i]) for i in diff[:5]]
 
 
 def _tets(seed):
@@ -91,6 +97,44 @@ def test_tetrahedron_arithmetic_bit_for_bit(lib):
 
 
 def test_selftest_rejects_bad_arguments(lib):
-    assert lib.fe_selftest_f64_int(3, None, None, 1, None, None, None) == -1
+    assert lib.fe_selftest_f64_int(4, None, None, 1, None, None, None) == -1
     assert lib.fe_selftest_f64_int(0, None, None, -1, None, None, None) == -1
     assert lib.fe_selftest_f64_int(0, None, None, 0, None, None, None) == 0
+
+
+@pytest.mark.parametrize("et,kind,quad,cpq,tpe", [
+    (api.TET, api.GENERIC, api.QUAD_TET4, 0, 1), (api.TET, api.POISSON, api.QUAD_TET1, 0, 1),
+    (api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, 1), (api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, 2),
+    (api.PRISM, api.POISSON, api.QUAD_PRISM6, 1, 1), (api.PRISM, api.POISSON, api.QUAD_PRISM6, 1, 2)])
+def test_special_operands_in_the_fp64_kernels(lib, et, kind, quad, cpq, tpe):
+    """Coefficients that send the integer-instruction products of the FP64 kernels
+    to their special cases (a subnormal operand, a product that underflows, signed
+    zeros): those elements are redone on the double pipe, and every element still
+    matches the oracle within the FP64 tolerance."""
+    from helpers import TOL, make_inputs, run_oracle, to_device_inputs
+    mesh, c = make_inputs(et, kind, quad, cpq, n=997 if et == api.TET else 611, seed=71)
+    n = len(mesh)
+    flat = c.reshape(n, -1)
+    specials = [1e-310, -1e-310, 1e-307, -1e-307, 0.0, -0.0]
+    for j, e in enumerate(range(0, n, 5)):
+        flat[e, j % flat.shape[1]] = specials[j % len(specials)]
+    X, C, c_used = to_device_inputs(et, mesh, c, api.FP64, api.AOS)
+    kw = dict(kind=kind, quad=quad, coef_mode=api.PER_QPOINT if cpq else api.PER_ELEMENT, prec=api.FP64,
+              layout=api.AOS, out_layout=api.AOS)
+    with api.Context(0) as ctx:
+        ctx.set_shape(32 * 2 // tpe, 0, et, X, C, tpe=tpe, **kw)
+        A, b, _ = ctx.integrate(et, X, C, **kw)
+        ctx.sync()
+    ns = api.NS[et]
+    An = A.double().cpu().numpy().reshape(n, ns, ns)
+    bn = b.double().cpu().numpy().reshape(n, ns)
+    Ar, br, _ = run_oracle(et, kind, quad, cpq, mesh, c_used)
+    assert np.isfinite(An).all() and np.isfinite(bn).all()
+    # relative per element, with an absolute floor far below the normal range for
+    # the load vectors made of subnormal values alone (a Laplace kind whose d^0 is
+    # one of the specials: its rounding there is coarser than 1e-12 in any order)
+    for G, R in ((An.reshape(n, -1), Ar.reshape(n, -1)), (bn, br)):
+        err = np.linalg.norm(G - R, axis=1)
+        ref = np.linalg.norm(R, axis=1)
+        bad = np.flatnonzero(err > TOL[api.FP64] * ref + 1e-300)
+        assert bad.size == 0, (bad[:5], err[bad[:5]], ref[bad[:5]])
