@@ -1235,12 +1235,20 @@ def bench_serve(api, dev, args):
                            X=X, n=n))
     del pool
     torch.cuda.synchronize(dev)
-    # warm the serving path (first batched launch, pool growth)
-    for m in meshes[:4]:
+    # warm the serving path before the timed windows: every resident mesh, one at a
+    # time and then all at once, twice (first launch of each combination, growth of
+    # the output pool and of the slots' fix-up lists to the working set)
+    for m in meshes:
         tk = ctx.serve_submit(m["id"], m["kind"], m["quad"], m["cm"], m["C"])
         while ctx.serve_poll(tk) is None:
             time.sleep(0.0005)
         ctx.serve_release(tk)
+    for _ in range(2):
+        tks = [ctx.serve_submit(m["id"], m["kind"], m["quad"], m["cm"], m["C"]) for m in meshes]
+        for tk in tks:
+            while ctx.serve_poll(tk) is None:
+                time.sleep(0.0005)
+        ctx.serve_release_many(tks)
     lam, T = 2000.0, args.serve_seconds
     served, arrivals, choice = serve_open_loop(ctx, meshes, lam, T, meshgen.SEED_BASE + 55)
     # arrival-rate sweep: 2000/s x {2, 4, 8, 16}, a shorter window each

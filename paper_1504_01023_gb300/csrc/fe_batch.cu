@@ -425,7 +425,14 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     constexpr size_t kCountersOff = 0, kFixCountOff = 64, kItemsOff = 128;
     uint64_t total = 0;
     for (auto &it : items) total += uint64_t(it.p.n);
-    fe_status r = ensure_scratch(ctx, db.scratch, total);
+    // The fix-up list and the tables grow geometrically (the list from 4M elements):
+    // a growth frees the old buffer, and cudaFree waits for the whole device, so a
+    // serving loop should meet only a few of them, early.
+    uint64_t want = total;
+    if (want > db.scratch.fix_cap)
+        want = std::min<uint64_t>(std::max<uint64_t>({want, 2 * uint64_t(db.scratch.fix_cap), uint64_t(1) << 22}),
+                                  0xFFFFFFFFull);
+    fe_status r = ensure_scratch(ctx, db.scratch, std::max(want, total));
     if (r != FE_OK) return r;
     std::vector<ClassLaunch> classes;
     std::vector<BatchSeg> segs;
@@ -437,11 +444,11 @@ fe_status dyn_batch_launch(fe_ctx *ctx, DynBatch &db, std::vector<BatchItemDev> 
     const size_t segs_off = kItemsOff + items_bytes;
     const size_t need = segs_off + std::max<size_t>(segs.size(), 1) * sizeof(BatchSeg);
     if (need > db.cap_tab) {
+        const size_t cap = std::max({need, 2 * db.cap_tab, size_t(64) << 10});
         if (db.d_tab) cudaFree(db.d_tab);
         if (db.h_tab) cudaFreeHost(db.h_tab);
         db.d_tab = db.h_tab = nullptr;
         db.cap_tab = 0;
-        const size_t cap = std::max(need, size_t(64) << 10);
         r = ctx_malloc(ctx, reinterpret_cast<void **>(&db.d_tab), cap, "cudaMalloc(batch table)");
         if (r == FE_OK) r = cuda_check(ctx, cudaMallocHost(&db.h_tab, cap), "cudaMallocHost(batch table)");
         if (r != FE_OK) return r;
