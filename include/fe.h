@@ -401,8 +401,10 @@ fe_status fe_ctx_inject_fault(fe_ctx *ctx, fe_fault kind, int64_t count, int64_t
      what = 3: x, y operands [n]; out [n]: the products by the form that leaves
                special cases to its caller, completed there by the DMUL
                instruction (the kernels redo such an element on the double pipe).
+     what = 4: as 3 for the sums (the addition that leaves special cases to its
+               caller, completed by the DADD instruction).
    In 1 and 2 the integer-instruction side redoes an element on the double pipe
-   when a multiplication meets a special case, as the kernels do.
+   when a multiplication or an addition meets a special case, as the kernels do.
    Degenerate elements give zeros. FE_ERR_INVALID_ARG for a bad `what`, n < 0 or
    null arrays. */
 fe_status fe_selftest_f64_int(int what, const double *x, const double *y, int64_t n, double *out_int,

@@ -552,8 +552,8 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
         return O::fma(u[2], v[2], O::fma(u[1], v[1], O::fma(u[0], v[0], z)));
     }
     // 4 q - (p1 + p2 + p3)
-    __device__ __forceinline__ static double lin4(double p1, double p2, double p3, double q) {
-        return O::fma(4.0, q, -OS::add(OS::add(p1, p2), p3));
+    __device__ __forceinline__ static double lin4(double p1, double p2, double p3, double q, bool &sp) {
+        return O::fma(4.0, q, -OS::add(OS::add(p1, p2, sp), p3, sp));
     }
     // w / v as recip_scaled
     __device__ __forceinline__ static double recip_w(double v, double w, bool &sp) {
@@ -577,7 +577,7 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) e[k][i] = OE::add(x(3 * (k + 1) + i), -x(i));
+            for (int i = 0; i < 3; ++i) e[k][i] = OE::add(x(3 * (k + 1) + i), -x(i), sp);
         cross(e[1], e[2], a[0], sp);
         cross(e[2], e[0], a[1], sp);
         cross(e[0], e[1], a[2], sp);
@@ -613,25 +613,25 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
                 P[r][k] = dot3_add(a[r - 1], col, M3[k]);
             }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) P[0][k] = lin4(P[1][k], P[2][k], P[3][k], M3[k]);
+        for (int k = 0; k < 4; ++k) P[0][k] = lin4(P[1][k], P[2][k], P[3][k], M3[k], sp);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const double pr[3] = {P[r][0], P[r][1], P[r][2]};
 #pragma unroll
             for (int s = 1; s < 4; ++s) A[4 * r + s] = dot3_add(pr, a[s - 1], P[r][3]);
-            A[4 * r] = lin4(A[4 * r + 1], A[4 * r + 2], A[4 * r + 3], P[r][3]);
+            A[4 * r] = lin4(A[4 * r + 1], A[4 * r + 2], A[4 * r + 3], P[r][3], sp);
         }
         if constexpr (S.M2[0][0] != S.M2[0][1]) {
             constexpr double ratio = (S.M2[0][0] - S.M2[0][1]) / S.M2[0][1];
             const double dl = ratio == 1.0 ? mu : OM::mul(mu, ratio, sp);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) A[5 * r] = OS::add(A[5 * r], dl);
+            for (int r = 0; r < 4; ++r) A[5 * r] = OS::add(A[5 * r], dl, sp);
         }
         const double d[3] = {OM::mul(sW, c(17), sp), OM::mul(sW, c(18), sp), OM::mul(sW, c(19), sp)};
         const double e = OM::mul(OM::mul(V, c(16), sp), S.W / 4, sp);
 #pragma unroll
         for (int r = 1; r < 4; ++r) b[r] = dot3_add(a[r - 1], d, e);
-        b[0] = lin4(b[1], b[2], b[3], e);
+        b[0] = lin4(b[1], b[2], b[3], e, sp);
     }
     // tet_poisson_products with explicit operations: A_rs = W / |det| a_r . a_s
     // (r, s = 1..3), row and column 0 from the vanishing sums; b as tet_poisson_b.
@@ -648,8 +648,8 @@ template <class OE, class OX, class OM, class OS> struct TetF64 {
             for (int s = r; s < 3; ++s) G[r][s] = G[s][r] = OM::mul(k, dot3<OM>(a[r], a[s], sp), sp);
         double row0[3];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) row0[s] = -OS::add(OS::add(G[0][s], G[1][s]), G[2][s]);
-        A[0] = -OS::add(OS::add(row0[0], row0[1]), row0[2]);
+        for (int s = 0; s < 3; ++s) row0[s] = -OS::add(OS::add(G[0][s], G[1][s], sp), G[2][s], sp);
+        A[0] = -OS::add(OS::add(row0[0], row0[1], sp), row0[2], sp);
 #pragma unroll
         for (int s = 0; s < 3; ++s) A[1 + s] = A[4 * (1 + s)] = row0[s];
 #pragma unroll

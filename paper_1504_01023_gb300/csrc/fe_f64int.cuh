@@ -116,6 +116,40 @@ __device__ __forceinline__ double i64_dadd(double a, double b) {
     return __longlong_as_double(static_cast<long long>(r | (x & 0x8000000000000000ull)));
 }
 
+// The sum for normal or zero operands whose result is normal or zero, bit for bit
+// the DADD result (an exact cancellation gives +0, as rounding to nearest does;
+// a zero operand returns the other one, and two zeros the sign rule's zero); any
+// other case (a subnormal, infinite or NaN operand, a result outside the normal
+// range) sets `special` and returns an unspecified value, so that the caller can
+// redo its work on the double pipe, as with i64_dmul_nz.
+__device__ __forceinline__ double i64_dadd_nz(double a, double b, bool &special) {
+    const unsigned long long ua = static_cast<unsigned long long>(__double_as_longlong(a));
+    const unsigned long long ub = static_cast<unsigned long long>(__double_as_longlong(b));
+    const uint32_t ea = static_cast<uint32_t>(ua >> 52) & 0x7FFu, eb = static_cast<uint32_t>(ub >> 52) & 0x7FFu;
+    const bool na = (ea - 1u) < 2046u, nb = (eb - 1u) < 2046u;
+    const bool za = (ua << 1) == 0ull, zb = (ub << 1) == 0ull;
+    const bool swap = (ub & 0x7FFFFFFFFFFFFFFFull) > (ua & 0x7FFFFFFFFFFFFFFFull);
+    const unsigned long long x = swap ? ub : ua, y = swap ? ua : ub;
+    const uint32_t ex = swap ? eb : ea, ey = swap ? ea : eb;
+    const unsigned long long mx = ((x & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+    unsigned long long my = ((y & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+    const uint32_t d = min(ex - ey, 63u);
+    const unsigned long long lost = my & ((1ull << d) - 1ull);
+    my = (my >> d) | static_cast<unsigned long long>(lost != 0ull);
+    unsigned long long S = ((x ^ y) >> 63) ? mx - my : mx + my;
+    const bool zs = S == 0ull;
+    const int lz = __clzll(static_cast<long long>(S));
+    const int e = int(ex) + 1 - lz;
+    S = lz == 0 ? ((S >> 1) | (S & 1ull)) : (S << ((lz - 1) & 63));
+    unsigned long long m = S >> 10;
+    const uint32_t rbit = static_cast<uint32_t>(S >> 9) & 1u;
+    m += rbit & (((S & 0x1FFull) != 0ull) | static_cast<uint32_t>(m & 1u));
+    const unsigned long long r = ((static_cast<unsigned long long>(e - 1) << 52) + m) | (x & 0x8000000000000000ull);
+    special |= !((na || za) && (nb || zb) && (za || zb || zs || (e >= 1 && e <= 2045)));
+    const unsigned long long z = za ? (zb ? (ua & ub) : ub) : (zb ? ua : (zs ? 0ull : r));
+    return __longlong_as_double(static_cast<long long>(z));
+}
+
 // The double operations of a kernel: multiplications and additions either on the
 // double pipe (INT = false) or in integer instructions (INT = true), fused
 // multiply-adds always on the double pipe. Written with the round-to-nearest
@@ -128,6 +162,10 @@ template <bool INT> struct F64 {
         return INT ? i64_dmul_nz(a, b, special) : __dmul_rn(a, b);
     }
     __device__ __forceinline__ static double add(double a, double b) { return INT ? i64_dadd(a, b) : __dadd_rn(a, b); }
+    // the same sum with the special cases left to the caller (i64_dadd_nz)
+    __device__ __forceinline__ static double add(double a, double b, bool &special) {
+        return INT ? i64_dadd_nz(a, b, special) : __dadd_rn(a, b);
+    }
     __device__ __forceinline__ static double sub(double a, double b) { return add(a, -b); }
     __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };

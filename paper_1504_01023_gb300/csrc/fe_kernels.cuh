@@ -50,12 +50,13 @@ template <int ET, int KIND, int PREC, int QUAD, int CPQ> struct ElemMath;
 
 // Tetrahedron, FP64 (Algorithm 3 in double). The Laplace kind and the generic
 // kind with per-element coefficients run the scalings of the coefficients and of
-// det J in integer instructions (TetF64's OM group, the same IEEE results): they
-// are off the critical path and relieve the double pipe. Integer edges, cofactor
-// products or row sums lengthen the chain of dependent operations and measured
-// slower (6M generic tetrahedra: edges 0.89x, sums 0.79x, all 0.70x; scalings
-// 1.05x; Laplace tetrahedra: scalings 1.13x). Per-point coefficients take the
-// general products.
+// det J and the products of the cofactors (TetF64's OM and OX groups) in integer
+// instructions that report special cases (the same IEEE results): they relieve
+// the double pipe (6M generic tetrahedra 3.94 -> 4.04 Gelem/s with the cofactor
+// products, Laplace 9.26 -> 9.65). Integer edges or row sums lengthen the chain
+// of dependent additions and measured slower even in the reporting form (generic:
+// sums 0.83x, edges and sums 0.76x; Laplace 0.84x, 0.71x). Per-point
+// coefficients take the general products.
 template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CPQ> {
     template <class XS, class CS>
     __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, double A[16], double b[4], bool &poor) {
@@ -80,7 +81,7 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, FP64, QUAD, CP
             // scalings in integer instructions; an element that meets a special
             // operand or product there is redone on the double pipe (one branch
             // per element, never taken on ordinary data)
-            using TF = TetF64<F64<false>, F64<false>, F64<true>, F64<false>>;
+            using TF = TetF64<F64<false>, F64<true>, F64<true>, F64<false>>;
             using TH = TetF64<F64<false>, F64<false>, F64<false>, F64<false>>;
             double a[3][3], det;
             bool sp = false;

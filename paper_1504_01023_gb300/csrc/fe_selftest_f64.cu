@@ -32,6 +32,19 @@ __global__ void selftest_mul_nz_kernel(const double *__restrict__ x, const doubl
     }
 }
 
+// The sums of i64_dadd_nz, completed by the DADD instruction where it reports a
+// special case.
+__global__ void selftest_add_nz_kernel(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                                       double *__restrict__ out_int, double *__restrict__ out_hw) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double a = x[i], b = y[i];
+        bool special = false;
+        const double r = i64_dadd_nz(a, b, special);
+        out_int[i] = special ? __dadd_rn(a, b) : r;
+        out_hw[i] = __dadd_rn(a, b);
+    }
+}
+
 // The FP64 tetrahedron arithmetic both ways: KIND 1 generic with TET4 and
 // per-element coefficients (y: 20 per element), KIND 0 Laplace with TET1 (y: d^0
 // per element); out: A^e (16) then b^e (4) per element, zeros for degenerate ones.
@@ -75,7 +88,7 @@ using namespace fe;
 
 extern "C" fe_status fe_selftest_f64_int(int what, const double *x, const double *y, int64_t n, double *out_int,
                                          double *out_hw, void *stream) {
-    if (what < 0 || what > 3 || n < 0 || (n > 0 && (!x || !y || !out_int || !out_hw)))
+    if (what < 0 || what > 4 || n < 0 || (n > 0 && (!x || !y || !out_int || !out_hw)))
         return set_error(nullptr, FE_ERR_INVALID_ARG, "fe_selftest_f64_int: bad arguments");
     if (n == 0) return FE_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -84,6 +97,8 @@ extern "C" fe_status fe_selftest_f64_int(int what, const double *x, const double
         selftest_ops_kernel<<<unsigned(blocks), 256, 0, s>>>(x, y, n, out_int, out_hw);
     else if (what == 3)
         selftest_mul_nz_kernel<<<unsigned(blocks), 256, 0, s>>>(x, y, n, out_int, out_hw);
+    else if (what == 4)
+        selftest_add_nz_kernel<<<unsigned(blocks), 256, 0, s>>>(x, y, n, out_int, out_hw);
     else if (what == 1)
         selftest_tet_kernel<1><<<unsigned(blocks), 256, 0, s>>>(x, y, n, out_int, out_hw);
     else

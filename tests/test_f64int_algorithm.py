@@ -80,6 +80,23 @@ def emu_add(a, b):
     return dbl(r)
 
 
+def emu_add_nz(a, b):
+    """i64_dadd_nz: normal or zero operands with a normal or zero result on the
+    integer path (a zero operand returns the other one, two zeros the AND of
+    their bit patterns); None where the kernel reports a special case."""
+    ua, ub = bits(a), bits(b)
+    ea, eb = (ua >> 52) & 0x7FF, (ub >> 52) & 0x7FF
+    na, nb = 1 <= ea <= 2046, 1 <= eb <= 2046
+    za, zb = ((ua << 1) & M64) == 0, ((ub << 1) & M64) == 0
+    if not ((na or za) and (nb or zb)):
+        return None
+    if za:
+        return dbl(ua & ub) if zb else dbl(ub)
+    if zb:
+        return dbl(ua)
+    return emu_add(a, b)
+
+
 def _check(op, emu, pairs):
     n_fast = 0
     for a, b in pairs:
@@ -148,3 +165,25 @@ def test_add_random_exponent_differences_and_cancellation():
         pairs += [(x, x), (x, -x * 0.75), (x, x * 2.0 ** -3)]
     pairs += [(0.0, 1.0), (-0.0, 0.0), (1e-310, 1.0), (np.inf, 1.0), (np.nan, 2.0), (1.0, -1.0), (-1.0, 1.0)]
     assert _check(np.add, emu_add, pairs) > 50000
+
+
+def test_add_nz_matches_ieee_and_zero_rules():
+    """The reporting form of the integer addition (i64_dadd_nz): the same sums as
+    the fast path where it is taken, zero operands by the sign rule of IEEE
+    round-to-nearest addition, and a report (None) for subnormal, infinite and NaN
+    operands and for results that leave the normal range."""
+    rng = np.random.default_rng(7)
+    pairs = list(zip(_operands(rng, 20000), _operands(rng, 20000)))
+    for _ in range(3000):
+        x = (1.0 + rng.random()) * 2.0 ** rng.integers(-50, 50)
+        pairs.append((x, -x))
+        pairs.append((x, -dbl(bits(x) + int(rng.integers(1, 1 << 20)))))
+    zeros = [(0.0, 0.0), (-0.0, 0.0), (0.0, -0.0), (-0.0, -0.0), (0.0, 1.5), (-0.0, -2.5), (3.0, -0.0),
+             (1e300, 0.0), (-0.0, 1e-300)]
+    pairs += zeros
+    assert _check(np.add, emu_add_nz, pairs) > 20000
+    for a, b in zeros:
+        assert emu_add_nz(a, b) is not None
+    for a, b in [(1e-310, 1.0), (0.0, 1e-310), (np.inf, 1.0), (1.0, np.nan),
+                 (2.0 ** -1022 * 1.5, -2.0 ** -1022), (1.7e308, 1.7e308)]:
+        assert emu_add_nz(a, b) is None

@@ -64,12 +64,13 @@ def test_operations_bit_for_bit(lib):
     assert np.array_equal(np.isnan(oi.view(np.float64)), nan)
     diff = np.flatnonzero((oi != oh) & ~nan)
     assert diff.size == 0, [(a[i % m], b[i % m], "mul" if i < m else "add") for i in diff[:5]]
-    # the form that reports special cases (zeros handled in integer instructions)
-    oi, oh = _run(lib, 3, a, b, m, 1)
-    nan = np.isnan(oh.view(np.float64))
-    assert np.array_equal(np.isnan(oi.view(np.float64)), nan)
-    diff = np.flatnonzero((oi != oh) & ~nan)
-    assert diff.size == 0, [(a[i], b[i]) for i in diff[:5]]
+    # the forms that report special cases (zeros handled in integer instructions)
+    for what in (3, 4):
+        oi, oh = _run(lib, what, a, b, m, 1)
+        nan = np.isnan(oh.view(np.float64))
+        assert np.array_equal(np.isnan(oi.view(np.float64)), nan)
+        diff = np.flatnonzero((oi != oh) & ~nan)
+        assert diff.size == 0, [(what, a[i], b[i]) for i in diff[:5]]
 
 
 def _tets(seed):
@@ -97,7 +98,7 @@ def test_tetrahedron_arithmetic_bit_for_bit(lib):
 
 
 def test_selftest_rejects_bad_arguments(lib):
-    assert lib.fe_selftest_f64_int(4, None, None, 1, None, None, None) == -1
+    assert lib.fe_selftest_f64_int(5, None, None, 1, None, None, None) == -1
     assert lib.fe_selftest_f64_int(0, None, None, -1, None, None, None) == -1
     assert lib.fe_selftest_f64_int(0, None, None, 0, None, None, None) == 0
 

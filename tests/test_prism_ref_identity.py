@@ -46,60 +46,68 @@ def direct(x, C, d):
     return A, b
 
 
-def regrouped(x, C, d):
-    """The kernel's steps: per point the cofactor rows a_i (J^{-1} = rows a_i / det),
-    Gamma from the scaled coefficients, and the per-level sums SF, SP, SQ, SG, BU,
-    BR; per level the expansion into A and b."""
+def level_sums(x, C, d, l):
+    """The kernel's per-level steps: per point the cofactor rows a_i (J^{-1} = rows
+    a_i / det), Gamma from the scaled coefficients, gathered into the per-level sums
+    SF, SP, SQ, SG (3 x 3) and BU, BR (3) of zeta level l."""
     r = x - x[0]
     ub, ut, vb, vt = r[1] - r[0], r[4] - r[3], r[2] - r[0], r[5] - r[3]
     w = [r[3] - r[0], r[4] - r[1], r[5] - r[2]]
     wm = (w[0] + w[1] + w[2]) / 12.0
+    D = np.array(DL)                             # D[k] = (D_k1, D_k2)
+    zb, zt = ZB[l], ZT[l]
+    cx, cy = zb * ub + zt * ut, zb * vb + zt * vt
+    a3 = np.cross(cx, cy)
+    SF, SP, SQ, SG = np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3))
+    S4 = np.zeros((2, 2))
+    BU, BR = np.zeros(3), np.zeros(3)
+    for t in range(3):
+        q = 3 * l + t
+        h = np.array([1 / 3 if t == k else 1 / 12 for k in range(3)])   # lambda_k(t) / 2
+        cz = wm + 0.25 * w[t]
+        a1, a2 = np.cross(cy, cz), np.cross(cz, cx)
+        det = cx @ a1
+        s2, s1, s0 = W / abs(det), np.copysign(W, det), W * abs(det)
+        c = C[q]
+        Ct = np.empty((4, 4))
+        Ct[0, 0] = s0 * c[0, 0]
+        Ct[0, 1:], Ct[1:, 0] = s1 * c[0, 1:], s1 * c[1:, 0]
+        Ct[1:, 1:] = s2 * c[1:, 1:]
+        dt0, dtv = s0 * d[q][0], s1 * d[q][1:]
+        a = [None, a1, a2, a3]
+        G = np.empty((4, 4))
+        G[0, 0] = Ct[0, 0]
+        for j in range(1, 4):
+            Ca = Ct[1:, 1:] @ a[j]
+            G[0, j] = Ct[0, 1:] @ a[j]
+            G[j, 0] = a[j] @ Ct[1:, 0]
+            for i in range(1, 4):
+                G[i, j] = a[i] @ Ca
+        xk = D @ G[0, 1:3]                   # x_k' = sum_j D_k'j Gamma_0j
+        yk = D @ G[1:3, 0]                   # y_k = sum_i D_ki Gamma_i0
+        e = 2 * h * G[0, 0] + xk
+        SF += 2 * np.outer(h, e) + 2 * np.outer(yk, h)
+        S4 += G[1:3, 1:3]
+        p = 2 * h * G[0, 3] + D @ G[1:3, 3]
+        qv = 2 * h * G[3, 0] + D @ G[3, 1:3]
+        SP += np.outer(p, h)
+        SQ += np.outer(h, qv)
+        SG += np.outer(h, h) * G[3, 3]
+        dl = np.array([dtv @ a1, dtv @ a2, dtv @ a3])
+        BU += 2 * h * dt0 + D @ dl[:2]
+        BR += h * dl[2]
+    SF += D @ S4 @ D.T
+    return SF, SP, SQ, SG, BU, BR
+
+
+def regrouped(x, C, d):
+    """One thread per element: per level the sums, then the level's share of the
+    6 x 6 expansion into A and b."""
     A = np.zeros((6, 6))
     b = np.zeros(6)
-    D = np.array(DL)                             # D[k] = (D_k1, D_k2)
     for l in range(2):
         zb, zt = ZB[l], ZT[l]
-        cx, cy = zb * ub + zt * ut, zb * vb + zt * vt
-        a3 = np.cross(cx, cy)
-        SF, SP, SQ, SG = np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3))
-        S4 = np.zeros((2, 2))
-        BU, BR = np.zeros(3), np.zeros(3)
-        for t in range(3):
-            q = 3 * l + t
-            h = np.array([1 / 3 if t == k else 1 / 12 for k in range(3)])   # lambda_k(t) / 2
-            cz = wm + 0.25 * w[t]
-            a1, a2 = np.cross(cy, cz), np.cross(cz, cx)
-            det = cx @ a1
-            s2, s1, s0 = W / abs(det), np.copysign(W, det), W * abs(det)
-            c = C[q]
-            Ct = np.empty((4, 4))
-            Ct[0, 0] = s0 * c[0, 0]
-            Ct[0, 1:], Ct[1:, 0] = s1 * c[0, 1:], s1 * c[1:, 0]
-            Ct[1:, 1:] = s2 * c[1:, 1:]
-            dt0, dtv = s0 * d[q][0], s1 * d[q][1:]
-            a = [None, a1, a2, a3]
-            G = np.empty((4, 4))
-            G[0, 0] = Ct[0, 0]
-            for j in range(1, 4):
-                Ca = Ct[1:, 1:] @ a[j]
-                G[0, j] = Ct[0, 1:] @ a[j]
-                G[j, 0] = a[j] @ Ct[1:, 0]
-                for i in range(1, 4):
-                    G[i, j] = a[i] @ Ca
-            xk = D @ G[0, 1:3]                   # x_k' = sum_j D_k'j Gamma_0j
-            yk = D @ G[1:3, 0]                   # y_k = sum_i D_ki Gamma_i0
-            e = 2 * h * G[0, 0] + xk
-            SF += 2 * np.outer(h, e) + 2 * np.outer(yk, h)
-            S4 += G[1:3, 1:3]
-            p = 2 * h * G[0, 3] + D @ G[1:3, 3]
-            qv = 2 * h * G[3, 0] + D @ G[3, 1:3]
-            SP += np.outer(p, h)
-            SQ += np.outer(h, qv)
-            SG += np.outer(h, h) * G[3, 3]
-            dl = np.array([dtv @ a1, dtv @ a2, dtv @ a3])
-            BU += 2 * h * dt0 + D @ dl[:2]
-            BR += h * dl[2]
-        SF += D @ S4 @ D.T
+        SF, SP, SQ, SG, BU, BR = level_sums(x, C, d, l)
         for k in range(3):
             for kk in range(3):
                 A[k, kk] += zb * (zb * SF[k, kk] - SP[k, kk] - SQ[k, kk]) + SG[k, kk]
@@ -109,6 +117,32 @@ def regrouped(x, C, d):
             b[k] += zb * BU[k] - BR[k]
             b[k + 3] += zt * BU[k] + BR[k]
     return A, b
+
+
+def regrouped_pair(x, C, d):
+    """Two threads per element, one zeta level each: with zb = 1/2 + s c, zt = 1/2 - s c
+    (c = 1/(2 sqrt 3), s = +1 on level 0 and -1 on level 1), so that zb^2 = 1/3 + s c,
+    zt^2 = 1/3 - s c and zb zt = 1/6, each lane forms from its level's sums
+      X = SF/3 + SG - s c (SP + SQ),  Y = s c SF - (SP + SQ)/2,
+      U = SF/6 - SG + s c (SP + SQ),  V = (SP - SQ)/2,
+      Bx = BU/2,  By = s c BU - BR,
+    and the blocks of A are sums over the two levels of
+      A_00 = X + Y,  A_11 = X - Y,  A_01 = U + V,  A_10 = U - V,
+    and b_k = Bx + By, b_(k+3) = Bx - By. Lane 0 keeps X, Y (blocks 00, 11) and the
+    bottom entries of b, lane 1 U, V (blocks 01, 10) and the top ones; each sends
+    the other the two combinations it needs."""
+    c = 0.5 / np.sqrt(3.0)
+    parts = []
+    for l in range(2):
+        sg = 1.0 if l == 0 else -1.0
+        SF, SP, SQ, SG, BU, BR = level_sums(x, C, d, l)
+        Sp, Sm = SP + SQ, SP - SQ
+        parts.append(dict(X=SF / 3 + SG - sg * c * Sp, Y=sg * c * SF - Sp / 2, U=SF / 6 - SG + sg * c * Sp,
+                          V=Sm / 2, Bx=BU / 2, By=sg * c * BU - BR))
+    X, Y, U, V, Bx, By = (parts[0][k] + parts[1][k] for k in ("X", "Y", "U", "V", "Bx", "By"))
+    A = np.zeros((6, 6))
+    A[:3, :3], A[3:, 3:], A[:3, 3:], A[3:, :3] = X + Y, X - Y, U + V, U - V
+    return A, np.concatenate([Bx + By, Bx - By])
 
 
 def _prism(rng, scale=1.0, shift=0.0):
@@ -121,19 +155,21 @@ def _prism(rng, scale=1.0, shift=0.0):
     return scale * x + shift
 
 
+@pytest.mark.parametrize("form", [regrouped, regrouped_pair])
 @pytest.mark.parametrize("seed", range(6))
-def test_regrouped_generic_prism_equals_direct_sum(seed):
+def test_regrouped_generic_prism_equals_direct_sum(seed, form):
     rng = np.random.default_rng(seed)
     x = _prism(rng, scale=rng.uniform(0.01, 10.0), shift=rng.uniform(-50, 50, 3))
     C = rng.uniform(-1, 1, (6, 4, 4))
     d = rng.uniform(-1, 1, (6, 4))
     A0, b0 = direct(x, C, d)
-    A1, b1 = regrouped(x, C, d)
+    A1, b1 = form(x, C, d)
     assert np.linalg.norm(A1 - A0) <= 1e-12 * np.linalg.norm(A0)
     assert np.linalg.norm(b1 - b0) <= 1e-12 * np.linalg.norm(b0)
 
 
-def test_regrouped_inverted_prism():
+@pytest.mark.parametrize("form", [regrouped, regrouped_pair])
+def test_regrouped_inverted_prism(form):
     """Negative det J (top below the base): |det J| in vol, the sign in vol J^{-1}."""
     rng = np.random.default_rng(11)
     x = _prism(rng)
@@ -141,12 +177,13 @@ def test_regrouped_inverted_prism():
     C = rng.uniform(-1, 1, (6, 4, 4))
     d = rng.uniform(-1, 1, (6, 4))
     A0, b0 = direct(x, C, d)
-    A1, b1 = regrouped(x, C, d)
+    A1, b1 = form(x, C, d)
     assert np.linalg.norm(A1 - A0) <= 1e-12 * np.linalg.norm(A0)
     assert np.linalg.norm(b1 - b0) <= 1e-12 * np.linalg.norm(b0)
 
 
-def test_each_coefficient_slot_separately():
+@pytest.mark.parametrize("form", [regrouped, regrouped_pair])
+def test_each_coefficient_slot_separately(form):
     """One coefficient slot at a time (each of c^{00}, c^{0j}, c^{i0}, c^{ij}, d^a), so
     that a dropped or transposed term cannot hide behind the others."""
     rng = np.random.default_rng(5)
@@ -156,10 +193,10 @@ def test_each_coefficient_slot_separately():
             C = np.zeros((6, 4, 4))
             C[:, a, bb] = rng.uniform(0.5, 1.5, 6)
             A0, _ = direct(x, C, np.zeros((6, 4)))
-            A1, _ = regrouped(x, C, np.zeros((6, 4)))
+            A1, _ = form(x, C, np.zeros((6, 4)))
             assert np.linalg.norm(A1 - A0) <= 1e-12 * np.linalg.norm(A0), (a, bb)
         d = np.zeros((6, 4))
         d[:, a] = rng.uniform(0.5, 1.5, 6)
         _, b0 = direct(x, np.zeros((6, 4, 4)), d)
-        _, b1 = regrouped(x, np.zeros((6, 4, 4)), d)
+        _, b1 = form(x, np.zeros((6, 4, 4)), d)
         assert np.linalg.norm(b1 - b0) <= 1e-12 * np.linalg.norm(b0), a
