@@ -861,7 +861,7 @@ __device__ __forceinline__ void prism_generic_update(const V3<T> g[6], T vol, co
 }
 
 // A^e and b^e of the generic prism, accumulated as unnormalised double-word
-// pairs by its level expansion (level_generic), made double-words again (no-op
+// pairs by its level expansion (level_expand), made double-words again (no-op
 // for the other types).
 template <class T> __device__ __forceinline__ void prism_dw_normalise(T A[36], T b[6]) {
     if constexpr (std::is_same<T, DW>::value) {

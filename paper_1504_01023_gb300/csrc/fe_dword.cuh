@@ -121,12 +121,14 @@ __device__ __forceinline__ bool dw_det_ok(float det_h) {
 // their magnitudes is zero or in [2^-80, 2^100], so that the low words of the
 // entries that carry the group's norm are normal floats and what falls below the
 // float range is negligible against the group.
-template <int N> __device__ __forceinline__ bool dw_group_ok(const DW *v) {
+template <int N> __device__ __forceinline__ float dw_abs_sum(const DW *v) {
     float s = 0.0f;
 #pragma unroll
     for (int k = 0; k < N; ++k) s = __fadd_rn(s, fabsf(v[k].h));
-    return s == 0.0f || (s >= 0x1p-80f && s <= 0x1p100f);
+    return s;
 }
+__device__ __forceinline__ bool dw_sum_ok(float s) { return s == 0.0f || (s >= 0x1p-80f && s <= 0x1p100f); }
+template <int N> __device__ __forceinline__ bool dw_group_ok(const DW *v) { return dw_sum_ok(dw_abs_sum<N>(v)); }
 
 // ---------------------------------------------------------------------------
 // double-word -> double: each float becomes its exact double by re-biasing its

@@ -271,13 +271,36 @@ template <int KIND, int QUAD, int CPQ> struct ElemMath<TET, KIND, DWORD, QUAD, C
 
 // Prism (Algorithm 2): T = double, float or double-word arithmetic after the
 // edge vectors.
-// Entries 2j + part of a prism's A^e and b^e (the half that one lane of a pair writes).
-template <class T>
+// The half of a prism's A^e and b^e that lane `part` of a pair writes: entry
+// pair_entry(j, part) of A^e (row-major) in Ah[j], entry pair_b_entry(j, part) of
+// b^e in bh[j]. Laplace: entries 2j + part, picked from the whole A^e and b^e that
+// both lanes hold. Generic: lane 0 the diagonal blocks (bottom-bottom, top-top) of
+// A^e and b_0..2, lane 1 the off-diagonal blocks and b_3..5, as pair_blocks leaves
+// them in A[0..17] and b[0..2].
+template <int KIND> __device__ __forceinline__ int pair_entry(int j, int part) {
+    if constexpr (KIND == GENERIC) {
+        const int blk = j / 9, k = (j % 9) / 3, kk = j % 3;
+        return 6 * (k + 3 * blk) + kk + 3 * (blk ^ part);
+    } else {
+        return 2 * j + part;
+    }
+}
+template <int KIND> __device__ __forceinline__ int pair_b_entry(int j, int part) {
+    return KIND == GENERIC ? 3 * part + j : 2 * j + part;
+}
+template <int KIND, class T>
 __device__ __forceinline__ void pick_half(const T A[36], const T b[6], T Ah[18], T bh[3], int part) {
+    if constexpr (KIND == GENERIC) {
 #pragma unroll
-    for (int j = 0; j < 18; ++j) Ah[j] = part ? A[2 * j + 1] : A[2 * j];
+        for (int j = 0; j < 18; ++j) Ah[j] = A[j];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) bh[j] = part ? b[2 * j + 1] : b[2 * j];
+        for (int j = 0; j < 3; ++j) bh[j] = b[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 18; ++j) Ah[j] = part ? A[2 * j + 1] : A[2 * j];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) bh[j] = part ? b[2 * j + 1] : b[2 * j];
+    }
 }
 
 template <int KIND, int PREC, int CPQ> struct PrismMath {
@@ -287,13 +310,14 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     // Q loop on relative coordinates r[0..5] (r[0] = 0). Returns bit1/bit2 flags.
     // Generic coefficients: the three points of a zeta level run in a rolled loop
     // (which keeps the body in the instruction cache) and gather per-level sums of
-    // the reference-space coefficient matrix; A^e is expanded from them once per
-    // level (level_generic). Laplace: the points only gather Gram terms of J^{-1}
-    // (prism_laplace_assemble forms A^e from them once).
+    // the reference-space coefficient matrix (level_sums); A^e is expanded from
+    // them once per level (level_expand). Laplace: the points only gather Gram
+    // terms of J^{-1} (prism_laplace_assemble forms A^e from them once).
     //
     // TPE == 2 (two threads per element): the lane of parity `part` takes the three
     // points of zeta level `part` and the pair combines its partial results
-    // through shuffles within `mask`; both lanes end with the whole A^e and b^e.
+    // through shuffles within `mask`. Laplace: both lanes end with the whole A^e
+    // and b^e. Generic: each lane ends with its half (pair_blocks).
     //
     // FP64: the products off the critical path run in integer instructions, and
     // sp is set when one of them meets an operand or a product outside the normal
@@ -342,18 +366,23 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             const V3<T> wm = r12 * ((f.w0 + f.w1) + f.w2);
             if constexpr (TPE == 1) {
 #pragma unroll
-                for (int l = 0; l < 2; ++l) level_generic<HW>(f, wm, l, c, A, b, poor, neg, degenerate, sp);
+                for (int l = 0; l < 2; ++l) {
+                    LevelSums S;
+                    level_sums<HW>(f, wm, l, c, S, poor, neg, degenerate, sp);
+                    level_expand(S, l, A, b);
+                }
                 prism_dw_normalise<T>(A, b);
             } else {
-                level_generic<HW>(f, wm, part, c, A, b, poor, neg, degenerate, sp);
-                prism_dw_normalise<T>(A, b);
-#pragma unroll
-                for (int k = 0; k < 36; ++k) A[k] = pair_sum(A[k], mask);
+                LevelSums S;
+                level_sums<HW>(f, wm, part, c, S, poor, neg, degenerate, sp);
+                pair_blocks(S, part, mask, A, b);
             }
         }
         if constexpr (TPE == 2) {
+            if constexpr (KIND == POISSON) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) b[k] = pair_sum(b[k], mask);
+                for (int k = 0; k < 6; ++k) b[k] = pair_sum(b[k], mask);
+            }
             poor = pair_any(poor, mask);
             if constexpr (PREC == FP64 && !HW) sp = pair_any(sp, mask);
             neg = pair_any(neg, mask);
@@ -445,10 +474,13 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
     // sum_i D_ki w sgn(det) d. a_i) and BR_k = sum_t h_k w sgn(det) d. a_3.
     // wm = (w_0 + w_1 + w_2) / 12, so that d x / d zeta at point t is wm + w_t / 4.
     // HW as for level_laplace.
+    struct LevelSums {
+        T SF[9], SP[9], SQ[9], SG[6], BU[3], BR[3];
+    };
     template <bool HW = false, class CS>
-    __device__ __forceinline__ static void level_generic(const PrismFrame<T> &f, const V3<T> &wm, int l, const CS &c,
-                                                         T A[36], T b[6], bool &poor, bool &neg, bool &degenerate,
-                                                         bool &sp) {
+    __device__ __forceinline__ static void level_sums(const PrismFrame<T> &f, const V3<T> &wm, int l, const CS &c,
+                                                      LevelSums &Sl, bool &poor, bool &neg, bool &degenerate,
+                                                      bool &sp) {
         using R = Rule<Q_PRISM6>;
         const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
         const V3<T> cx = zb * f.ub + zt * f.ut;
@@ -576,6 +608,27 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
         SF[1] = SF[1] - (S4[0] + S4[2]);
         SF[2] = SF[2] - (S4[1] + S4[3]);
         SF[0] = SF[0] + ((S4[0] + S4[1]) + (S4[2] + S4[3]));
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            Sl.SF[k] = SF[k];
+            Sl.SP[k] = SP[k];
+            Sl.SQ[k] = SQ[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sl.SG[k] = SG[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Sl.BU[k] = acc_norm(BU[k]);
+            Sl.BR[k] = acc_norm(BR[k]);
+        }
+    }
+
+    // One thread per element: the level's share of A and b, accumulated into them
+    // (unnormalised double-word pairs until prism_dw_normalise).
+    __device__ __forceinline__ static void level_expand(const LevelSums &S, int l, T A[36], T b[6]) {
+        using R = Rule<Q_PRISM6>;
+        const T zb = l ? T(R::zb(1)) : T(R::zb(0)), zt = l ? T(R::zt(1)) : T(R::zt(0));
+        const T *SF = S.SF, *SP = S.SP, *SQ = S.SQ, *SG = S.SG;
         // the level's share of A and b
         const T zbb = l ? T(R::zb(1) * R::zb(1)) : T(R::zb(0) * R::zb(0));
         const T ztt = l ? T(R::zt(1) * R::zt(1)) : T(R::zt(0) * R::zt(0));
@@ -607,11 +660,51 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const T bu = acc_norm(BU[k]), br = acc_norm(BR[k]);
+            const T bu = S.BU[k], br = S.BR[k];
             acc(b[k], zb, bu);
             acc1(b[k], -br);
             acc(b[k + 3], zt, bu);
             acc1(b[k + 3], br);
+        }
+    }
+
+    // Two threads per element, lane `part` holding the sums of zeta level `part`.
+    // With zb = 1/2 + s c and zt = 1/2 - s c on the level (c = 1/(2 sqrt 3), s = +1
+    // on level 0 and -1 on level 1), zb^2 = 1/3 + s c, zt^2 = 1/3 - s c and
+    // zb zt = 1/6, so the level's share of the four 3 x 3 blocks of A^e is
+    //   A_00 = X + Y, A_11 = X - Y, A_01 = U + V, A_10 = U - V,
+    //   X = SF/3 + SG - s c (SP + SQ),  U = SF/2 - X,  Y = s c SF - (SP + SQ)/2,
+    //   V = (SP - SQ)/2,
+    // and of b^e: b_k = Bx + By, b_(k+3) = Bx - By with Bx = BU/2, By = s c BU - BR.
+    // Lane 0 keeps X and Y (blocks 00 and 11) and b_0..2, lane 1 U and V (blocks 01
+    // and 10) and b_3..5; each sends the other the two sums that the other keeps,
+    // so that no lane forms all 36 entries. On return A[j] (j < 18) holds the
+    // lane's entries in the order of pair_entry and b[0..2] its entries of b^e.
+    __device__ __forceinline__ static void pair_blocks(const LevelSums &S, int part, unsigned mask, T A[36],
+                                                       T b[6]) {
+        const T c = T(0.5 * kInvSqrt3);
+        const T sc = part ? -c : c, nsc = part ? c : -c;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const int i = 3 * k + kk;
+                const T sg = S.SG[k == kk ? k : k + kk + 2];
+                const T spq = S.SP[i] + S.SQ[i], smq = S.SP[i] - S.SQ[i];
+                const T X = madd(nsc, spq, madd(T(1.0 / 3.0), S.SF[i], sg));
+                const T U = half(S.SF[i]) - X;
+                const T Y = madd(sc, S.SF[i], -half(spq));
+                const T V = half(smq);
+                const T P = (part ? U : X) + pair_other(part ? X : U, mask);
+                const T Q = (part ? V : Y) + pair_other(part ? Y : V, mask);
+                A[i] = P + Q;
+                A[9 + i] = P - Q;
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T bx = half(S.BU[k]), by = madd(sc, S.BU[k], -S.BR[k]);
+            const T Bx = bx + pair_other(bx, mask), By = by + pair_other(by, mask);
+            b[k] = part ? Bx - By : Bx + By;
         }
     }
 
@@ -622,6 +715,13 @@ template <int KIND, int PREC, int CPQ> struct PrismMath {
             return dw_dot_add<1>(&a, &b, c);
         else
             return a * b + c;
+    }
+    // x / 2 (exact)
+    __device__ __forceinline__ static T half(T x) {
+        if constexpr (PREC == DWORD)
+            return DW(0.5f * x.h, 0.5f * x.l);
+        else
+            return T(0.5) * x;
     }
     __device__ __forceinline__ static void acc(T &s, T a, T b) {
         if constexpr (PREC == DWORD)
@@ -722,7 +822,7 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, FP64, Q_PRISM6, CPQ> {
         }
         return fl;
     }
-    // Two threads per element: this lane's zeta level; entries 2j + part out.
+    // Two threads per element: this lane's zeta level; the lane's half out (pick_half).
     template <class XS, class CS>
     __device__ __forceinline__ static uint8_t run_pair(const XS &x, const CS &c, double Ah[18], double bh[3], bool &poor,
                                                        int part, unsigned mask) {
@@ -737,7 +837,7 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, FP64, Q_PRISM6, CPQ> {
             const unsigned pm = 3u << ((threadIdx.x & 31u) & ~1u);
             fl = PrismMath<KIND, FP64, CPQ>::template qloop<2, true>(r, c, A, b, poor, sp, part, pm);
         }
-        pick_half(A, b, Ah, bh, part);
+        pick_half<KIND>(A, b, Ah, bh, part);
         return fl;
     }
 };
@@ -756,7 +856,7 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> 
         bool sp;   // set by the FP64 form only
         return PrismMath<KIND, MIXED, CPQ>::qloop(r, c, A, b, poor, sp);
     }
-    // Two threads per element: this lane's zeta level; entries 2j + part out.
+    // Two threads per element: this lane's zeta level; the lane's half out (pick_half).
     template <class XS, class CS>
     __device__ __forceinline__ static uint8_t run_pair(const XS &x, const CS &c, float Ah[18], float bh[3], bool &poor,
                                                        int part, unsigned mask) {
@@ -771,7 +871,7 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, MIXED, Q_PRISM6, CPQ> 
         float A[36], b[6];
         bool sp;   // set by the FP64 form only
         const uint8_t fl = PrismMath<KIND, MIXED, CPQ>::template qloop<2>(r, c, A, b, poor, sp, part, mask);
-        pick_half(A, b, Ah, bh, part);
+        pick_half<KIND>(A, b, Ah, bh, part);
         return fl;
     }
     // Flagged element: Jacobian terms in double at every point, narrowed to float.
@@ -837,8 +937,8 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
         for (int k = 0; k < 6; ++k) b[k] = dw_to_double(bd[k]);
         return fl;
     }
-    // Two threads per element: this lane's zeta level; entries 2j + part out
-    // (each lane converts its own half).
+    // Two threads per element: this lane's zeta level; the lane's half out
+    // (pick_half; each lane converts its own half).
     template <class XS, class CS>
     __device__ __forceinline__ static uint8_t run_pair(const XS &x, const CS &c, double Ah[18], double bh[3], bool &poor,
                                                        int part, unsigned mask) {
@@ -850,11 +950,17 @@ template <int KIND, int CPQ> struct ElemMath<PRISM, KIND, DWORD, Q_PRISM6, CPQ> 
         DW Ad[36], bd[6];
         bool sp;   // set by the FP64 form only
         const uint8_t fl = PrismMath<KIND, DWORD, CPQ>::template qloop<2>(r, cd, Ad, bd, poor, sp, part, mask);
-        poor = poor || !dw_group_ok<36>(Ad) || !dw_group_ok<6>(bd);
+        DW Adh[18], bdh[3];
+        pick_half<KIND>(Ad, bd, Adh, bdh, part);
+        // the group tests on the sums over both halves (the same on both lanes); the
+        // shuffles run on every lane of `mask`, whatever the lane's flags
+        const float sa = dw_abs_sum<18>(Adh), sb = dw_abs_sum<3>(bdh);
+        const float ta = __fadd_rn(sa, pair_other(sa, mask)), tb = __fadd_rn(sb, pair_other(sb, mask));
+        poor = poor || !dw_sum_ok(ta) || !dw_sum_ok(tb);
 #pragma unroll
-        for (int j = 0; j < 18; ++j) Ah[j] = dw_to_double(part ? Ad[2 * j + 1] : Ad[2 * j]);
+        for (int j = 0; j < 18; ++j) Ah[j] = dw_to_double(Adh[j]);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) bh[j] = dw_to_double(part ? bd[2 * j + 1] : bd[2 * j]);
+        for (int j = 0; j < 3; ++j) bh[j] = dw_to_double(bdh[j]);
         return fl;
     }
     // Flagged element: the whole element in double.
@@ -1485,7 +1591,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     }
 
     // ---- compute ----
-    CT A[NA], b[NS];   // TPE == 2: this lane's entries 2j + sub in A[j], b[j]; TPE == NS: row sub in A[0..NS), b[0]
+    CT A[NA], b[NS];   // TPE == 2: this lane's half (pair_entry) in A[j], b[j]; TPE == NS: row sub in A[0..NS), b[0]
     bool poor = false;
     bool idx_ok = true;  // INDEXED: every node index of this element is in range
     // lanes that take part in the pairs' exchanges (both lanes of an element)
@@ -1529,9 +1635,9 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     __syncthreads();   // every input read: the output records reuse the same shared memory
     if (TPE == 2 && active) {
 #pragma unroll
-        for (int j = 0; j < NA / TPE; ++j) sA[tid * NAO + TPE * j + sub] = A[j];
+        for (int j = 0; j < NA / TPE; ++j) sA[tid * NAO + pair_entry<KIND>(j, sub)] = A[j];
 #pragma unroll
-        for (int j = 0; j < NS / TPE; ++j) sB[tid * NS + TPE * j + sub] = b[j];
+        for (int j = 0; j < NS / TPE; ++j) sB[tid * NS + pair_b_entry<KIND>(j, sub)] = b[j];
     }
     if (TPE == NS && TPE > 2 && active) {
 #pragma unroll
