@@ -204,13 +204,22 @@ def same_run_copy_gbs(dev, nbytes=2 << 30, reps=10):
 KERNEL_UNITS = ("fe_tet_", "fe_prism_", "fe_idx_", "fe_group_")
 
 
+def code_only(text: str) -> str:
+    """C++ source without its comments and blank lines (the sources carry no
+    comment markers inside string literals), so that editing a comment keeps the
+    hash of the code."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1504_01023_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cuh", ".h")) or (name.endswith(".cu") and name.startswith(KERNEL_UNITS)):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+            with open(os.path.join(csrc, name), encoding="utf-8") as f:
+                h.update((name + code_only(f.read())).encode())
     return h.hexdigest()[:16]
 
 
@@ -475,7 +484,7 @@ def run_native(args):
         wl_name = {"fp64": WORKLOAD, "mixed": MIXED_WORKLOAD}.get(args.form, MESH + ", double-word form")
         if lap:
             wl_name = MESH.split(", TET4")[0] + ", Laplace operator, TET1, d^0 = 1, " + args.form + " form"
-        kernel_name = (f"elem_kernel<TET,{'POISSON' if lap else 'GENERIC'},{PREC_TAG[args.form]},"
+        kernel_name = (f"{'elem_kernel_f64t' if args.form == 'fp64' else 'elem_kernel'}<TET,{'POISSON' if lap else 'GENERIC'},{PREC_TAG[args.form]},"
                        f"{'TET1' if lap else 'TET4'},per-element,AOS,AOS>")
         tag = f"tet_{'poisson_tet1' if lap else 'generic'}_{args.form}_aos"
     else:

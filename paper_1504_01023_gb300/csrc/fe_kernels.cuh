@@ -1701,12 +1701,7 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
 // Main kernel: tiles of blockDim.x elements, grid-stride over tiles.
 // ---------------------------------------------------------------------------
 template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
-// Launch bounds: 512 threads for float and double tetrahedra, 256 otherwise; the
-// double-word Laplace prism is held to two resident 256-thread blocks per SM
-// (128 registers: 2.77 -> 3.15 Gelem/s measured against 144 registers).
-__global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256,
-                                  (ET == PRISM && PREC == DWORD && KIND == POISSON) ? 2 : 0)
-    elem_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
+__device__ __forceinline__ void elem_tiles(const ElemParams &p, const TmaMaps *tm, const CoefFn *fn) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) {
@@ -1724,9 +1719,35 @@ __global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256,
         }
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
-        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase, &tm, &fn)) return;
+        if (!process_tile<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, e0, nb, smem, &bar, phase, tm, fn)) return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+template <int ET, int KIND, int PREC, int QUAD, int CPQ, int INL, int OUTL>
+// Launch bounds: 512 threads for float and double tetrahedra, 256 otherwise; the
+// double-word Laplace prism is held to two resident 256-thread blocks per SM
+// (128 registers: 2.77 -> 3.15 Gelem/s measured against 144 registers).
+__global__ void __launch_bounds__(ET == TET && PREC != DWORD ? 512 : 256,
+                                  (ET == PRISM && PREC == DWORD && KIND == POISSON) ? 2 : 0)
+    elem_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
+    elem_tiles<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>(p, &tm, &fn);
+}
+
+// The same kernel for FP64 tetrahedra with fewer registers per thread. Generic
+// kind 104 (6M tetrahedra 4.10 -> 4.18 Gelem/s against 128 registers; 96 and 80
+// spilled more and measured 4.14 and 4.04): still four warps per SM
+// sub-partition, but the allocation under the bound keeps the double pipe busier
+// (ncu 87.3% -> 89.7%). Laplace kind 80 (6M TET1 9.77 -> 10.58 Gelem/s against
+// 100; 88 and 72 measured 10.29 and 10.52): six warps per sub-partition instead
+// of five to cover the chains of the integer-instruction products. ptxas gets
+// both the block bound (.maxntid 512) and the register bound (.maxnreg); with the
+// register bound alone it allocates differently (the generic element-contiguous
+// kernel spilled 360 bytes instead of 20).
+template <int KIND, int QUAD, int CPQ, int INL, int OUTL>
+__global__ void __launch_bounds__(512) __maxnreg__(KIND == POISSON ? 80 : 104)
+    elem_kernel_f64t(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
+    elem_tiles<TET, KIND, FP64, QUAD, CPQ, INL, OUTL>(p, &tm, &fn);
 }
 
 // ---------------------------------------------------------------------------

@@ -60,3 +60,10 @@ def test_shape_and_context_records_are_json():
     ctx = bench.paper_context()
     json.dumps(ctx)
     assert ctx["melem_s"]["Tesla K20m"]["laplace_tet"] == pytest.approx(1000 / 2.02, abs=0.1)
+
+
+def test_source_hash_ignores_comments_only():
+    src = "template <int K> // bound\n__global__ void k(float *p) {\n    /* body */ p[0] = K; }\n"
+    edited = src.replace("// bound", "// another note").replace("/* body */", "/* the\nbody */")
+    assert bench.code_only(src) == bench.code_only(edited)
+    assert bench.code_only(src) != bench.code_only(src.replace("p[0] = K", "p[0] = 2 * K"))
