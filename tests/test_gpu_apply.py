@@ -188,3 +188,36 @@ def test_apply_rejects_element_contiguous_geometry(ctx):
     v = torch.zeros(100, dtype=torch.float32, device="cuda")
     st = api.load().fe_apply_tet(ctx.h, __import__("ctypes").byref(a), v.data_ptr(), v.data_ptr(), None, None, None)
     assert st == -6
+
+
+def _fan_mesh(layers=30, ring=12):
+    """Stacked fans of tetrahedra around the z axis: layer L has apex (0, 0, L),
+    top (0, 0, L + 1) and a ring of `ring` nodes at height L + 1/2; its elements
+    are (apex, ring_i, ring_i+1, top). Every element of a layer holds the apex in
+    slot 0 and the top in slot 3, the top is the next layer's apex (slot 0), and
+    each ring node sits in slot 1 of one element and slot 2 of its neighbour."""
+    th = 2 * np.pi * np.arange(ring) / ring
+    nodes = [(0.0, 0.0, float(L)) for L in range(layers + 1)]
+    conn = []
+    for L in range(layers):
+        base = len(nodes)
+        nodes += [(np.cos(t), np.sin(t), L + 0.5) for t in th]
+        for i in range(ring):
+            conn.append((L, base + i, base + (i + 1) % ring, L + 1))
+    return np.asarray(nodes, dtype=np.float64), np.asarray(conn, dtype=np.int32)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_apply_nodes_shared_across_a_warp(ctx, prec):
+    """Many lanes of a warp add to the same node, from the same slot and from
+    different slots; the sums are those of the oracle's element matrices."""
+    nodes, conn = _fan_mesh()
+    _, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh=nodes[conn], seed=41)
+    x, y0, f0 = _vectors(len(nodes), prec, 42)
+    y, f, fl, cu = _apply(ctx, api.TET, api.GENERIC, api.QUAD_TET4, 0, prec, nodes, conn, c, x, y0, f0)
+    Ao, bo, fo = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, nodes[conn], cu)
+    assert ((fl & 6) == fo).all()
+    yr, fr, sy, my, sf, mf = _reference(Ao, bo, conn, x.astype(np.float64), y0.astype(np.float64),
+                                        f0.astype(np.float64), np.arange(len(conn)))
+    _check(y, yr, sy, my, prec)
+    _check(f, fr, sf, mf, prec)
