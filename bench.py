@@ -1268,6 +1268,7 @@ def bench_serve(api, dev, args):
                                                "p99_ms", "sustained_melem_s", "offered_melem_s")})
     # capacity: closed loops with 48 and 96 requests outstanding
     saturated = [serve_saturated(api, ctx, meshes, max(1.0, args.serve_seconds / 2), d) for d in (48, 96)]
+    upload = serve_upload_inclusive(api, ctx, meshes, dev, meshgen.SEED_BASE + 56)
     ctx.close()
 
     # plain one-request-at-a-time FP64 path on the same arrivals (first 0.25 s)
@@ -1310,7 +1311,49 @@ def bench_serve(api, dev, args):
     torch.cuda.empty_cache()
     return {"workload": "Poisson arrivals 2000/s (seeded) on 64 resident meshes, sizes log-uniform [1e4, 4e6], "
                         "50/50 tetrahedra/prisms and Poisson/generic, mixed precision, 120 GB budget, 4 stream slots",
-            "served": served, "arrival_sweep": sweep, "saturated": saturated, "plain_fp64": plain}
+            "served": served, "arrival_sweep": sweep, "saturated": saturated, "upload_inclusive": upload,
+            "plain_fp64": plain}
+
+
+def serve_upload_inclusive(api, ctx, meshes, dev, seed, n_meshes=16, passes=3):
+    """Latency with the upload included: requests on meshes that are not resident.
+    For each request, one after another: register its geometry from pinned host
+    memory (fe_mesh_register copies it to the device), copy its coefficients from
+    pinned host memory, submit, wait for the completion, then release the request
+    and the mesh. Latency = wall clock from the start of the upload to the
+    completion; `upload_ms` is the part before the submission. A seeded draw of
+    `n_meshes` of the pool's meshes, `passes` times each."""
+    import torch
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(len(meshes), size=n_meshes, replace=False)
+    host = {int(j): (meshes[j]["X"].cpu().pin_memory(), meshes[j]["C"].cpu().pin_memory()) for j in pick}
+    stream = torch.cuda.current_stream(dev)
+    lat, up, elems = [], [], 0
+    order = [int(j) for _ in range(passes) for j in rng.permutation(pick)]
+    for i, j in enumerate(order):
+        m, (Xh, Ch) = meshes[j], host[j]
+        t0 = time.perf_counter()
+        mid = ctx.mesh_register(m["et"], Xh, api.AOS)
+        Cd = Ch.to(dev, non_blocking=True)
+        stream.synchronize()
+        t1 = time.perf_counter()
+        tk = ctx.serve_submit(mid, m["kind"], m["quad"], m["cm"], Cd)
+        while ctx.serve_poll(tk) is None:
+            time.sleep(0.0001)
+        t2 = time.perf_counter()
+        ctx.serve_release(tk)
+        ctx.mesh_release(mid)
+        del Cd
+        if i >= n_meshes // 2:          # the first requests warm the register path
+            lat.append((t2 - t0) * 1e3)
+            up.append((t1 - t0) * 1e3)
+            elems += m["n"]
+    lat, up = np.array(lat), np.array(up)
+    return {"path": "fe_mesh_register from pinned host memory + coefficient copy + fe_serve_submit, one request "
+                    "at a time, mesh released after each", "requests": int(len(lat)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "upload_p50_ms": float(np.percentile(up, 50)), "upload_p99_ms": float(np.percentile(up, 99)),
+            "mean_elements": elems / max(len(lat), 1), "sustained_melem_s": elems / (lat.sum() * 1e-3) / 1e6}
 
 
 def serve_open_loop(ctx, meshes, lam, T, seed):
