@@ -201,7 +201,7 @@ def same_run_copy_gbs(dev, nbytes=2 << 30, reps=10):
 # The sources that determine the element kernels' code: every header, and the
 # translation units that instantiate the single-set kernels (host runtime, batch,
 # serving, study and self-test units are left out).
-KERNEL_UNITS = ("fe_tet_", "fe_prism_", "fe_idx_", "fe_group_")
+KERNEL_UNITS = ("fe_tet_", "fe_prism_", "fe_idx_", "fe_group_", "fe_entry_")
 
 
 def code_only(text: str) -> str:
@@ -1075,7 +1075,7 @@ def tpe_study(ctx, dev, api, mesh, coefs, args):
     nt, npr = min(2_000_000, len(mesh)), 1_000_000
     pm, pc = prism_workload(0, args.n_slab)
     cases = {"generic tetrahedra, TET4, per-element coefficients, 2,000,000 elements":
-                 (api.TET, mesh[:nt], coefs[:nt], api.QUAD_TET4, api.PER_ELEMENT, (1, 4)),
+                 (api.TET, mesh[:nt], coefs[:nt], api.QUAD_TET4, api.PER_ELEMENT, (1, 4, 16)),
              "generic prisms, PRISM6, per-point coefficients, 1,000,000 elements":
                  (api.PRISM, pm[:npr], pc[:npr], api.QUAD_PRISM6, api.PER_QPOINT, (1, 2, 6))}
     res = {"unit": "Melem/s", "note": "best shape per threads-per-element value; main-kernel time from profiling "

@@ -427,7 +427,10 @@ fe_status fe_ctx_kernel_time(fe_ctx *ctx, double *ms, int64_t *launches, int res
      4 per tetrahedron: one row of A^e and one entry of b^e per thread, the
        Jacobian terms formed once per element and shared by shuffles;
      6 per prism: thread q forms the Jacobian terms at point q, passes them to the
-       group by shuffles and owns row q of A^e and entry q of b^e.
+       group by shuffles and owns row q of A^e and entry q of b^e;
+     16 per tetrahedron (the entry per work-item of the entry-outer orderings,
+       Algorithm 7): thread 4 r + s delivers entry (r, s) of A^e (and b^e_r when
+       s = 0), the Jacobian terms formed once per element and shared by shuffles.
    Writes the tuning cache if set. */
 fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args, const fe_out *out,
                   void *stream);
@@ -446,7 +449,7 @@ fe_status fe_get_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *args,
 /* Launch shape with the threads per element made explicit. */
 typedef struct fe_launch_shape {
     int elems_per_block;           /* elements per tile (one block per tile) */
-    int threads_per_elem;          /* 1; 2 or 6 (prisms), 4 (tetrahedra), as described at fe_tune */
+    int threads_per_elem;          /* 1; 2 or 6 (prisms), 4 or 16 (tetrahedra), as described at fe_tune */
     int persistent;                /* 0 or 1 */
 } fe_launch_shape;
 /* As fe_get_shape / fe_set_shape. Set: a warp holds 32 / threads_per_elem

@@ -83,6 +83,8 @@ const void *kernel_prism_dw(int kind, int cpq, int inl, int outl);
 const void *kernel_prism_pair(int kind, int prec, int cpq);
 // One group of NS lanes per element (4 for tetrahedra, 6 for prisms), one row each.
 const void *kernel_group_tet(int kind, int prec, int quad, int cpq);
+// Sixteen threads per tetrahedron (one entry of A^e each): entry_kernel.
+const void *kernel_entry_tet(int kind, int prec, int quad, int cpq);
 const void *kernel_group_prism(int kind, int prec, int cpq);
 
 // Fix-up kernels (flagged elements of the mixed and double-word forms, redone

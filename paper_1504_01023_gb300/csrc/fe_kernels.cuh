@@ -1010,12 +1010,13 @@ template <class T> __device__ __forceinline__ T sel3(int r, T v0, T v1, T v2) { 
 // Double-word results of a row: the group's windows (as dw_group_ok over the whole
 // A^e and b^e, from the sums of the rows' magnitudes), then conversion.
 template <int N>
-__device__ __forceinline__ bool dw_rows_out(const DW *A, DW b, double *Ar, double &br, unsigned mask, int base) {
+__device__ __forceinline__ bool dw_rows_out(const DW *A, DW b, double *Ar, double &br, unsigned mask, int base,
+                                            int lanes = N) {
     float sa = 0.0f;
 #pragma unroll
     for (int k = 0; k < N; ++k) sa = __fadd_rn(sa, fabsf(A[k].h));
-    sa = grp_sum(sa, mask, base, N);
-    const float sb = grp_sum(fabsf(b.h), mask, base, N);
+    sa = grp_sum(sa, mask, base, lanes);
+    const float sb = grp_sum(fabsf(b.h), mask, base, lanes);
 #pragma unroll
     for (int k = 0; k < N; ++k) Ar[k] = dw_to_double(A[k]);
     br = dw_to_double(b);
@@ -1173,6 +1174,66 @@ template <int KIND, int PREC, int QUAD, int CPQ> struct TetRows {
             }
             b = V * (dot(db, gr) + er);
         }
+    }
+};
+
+// Sixteen threads per tetrahedron (the entry-per-work-item mapping of the
+// paper's entry-outer orderings, Sec. 3.3, Algorithm 7): lane sub = 4 r + s of the
+// group (lanes base .. base + 15) delivers entry (r, s) of A^e, and lanes with
+// s == 0 also b^e_r. Lanes 1..3 form edge k and cofactor row a_k (det J on lane
+// 1) as TetRows does, shared by shuffles; every lane then forms row r of the
+// QSS products (TetRows::products, so the four lanes of a row repeat it, as each
+// entry's loop does in Algorithm 7) and keeps entry s.
+template <int KIND, int PREC, int QUAD, int CPQ> struct TetEntries {
+    using TR = TetRows<KIND, PREC, QUAD, CPQ>;
+    using T = typename TR::T;
+    using CT = typename TR::CT;
+
+    template <class XS, class CS>
+    __device__ __forceinline__ static uint8_t run(const XS &x, const CS &c, CT &Ars, CT &br, bool &poor, int sub,
+                                                  unsigned mask, int base) {
+        const int r = sub >> 2, s = sub & 3;
+        const int k = (sub >= 1 && sub <= 3) ? sub : 1;
+        const V3<T> ek = form_edge<PREC>(x, k);
+        V3<T> e[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) e[j] = grp_get(ek, mask, base + 1 + j);
+        const V3<T> u = sel3(k % 3, e[0], e[1], e[2]), v = sel3((k + 1) % 3, e[0], e[1], e[2]);
+        const V3<T> ak = cross(u, v);
+        const T det_k = dot(e[0], ak);
+        V3<T> a[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) a[j] = grp_get(ak, mask, base + 1 + j);
+        const T det = grp_get(det_k, mask, base + 1);
+        const bool neg = is_neg(det);
+        poor = false;
+        if constexpr (PREC != FP64) poor = tet_poor(hi_f(e[0]), hi_f(e[1]), hi_f(e[2]), hi_f(det));
+        if constexpr (PREC == DWORD) poor = poor || !dw_det_ok(det.h);
+        if constexpr (PREC == FP64) {
+            if (degenerate_det(det)) {
+                Ars = 0.0;
+                br = 0.0;
+                return 4;
+            }
+        }
+        T Arow[4], b;
+        if constexpr (PREC == DWORD) {
+            const DwCoef<CS> cd{c};
+            TR::products(a, det, neg, cd, r, Arow, b);
+            // the windows of the double-word form on the group's sums of magnitudes
+            const DW ars = sel4(s, Arow[0], Arow[1], Arow[2], Arow[3]);
+            const DW bs = s == 0 ? b : DW(0.0f, 0.0f);
+            double A1[1], b1;
+            const bool ok = dw_rows_out<1>(&ars, bs, A1, b1, mask, base, 16);
+            Ars = A1[0];
+            br = b1;
+            poor = !ok || poor;
+        } else {
+            TR::products(a, det, neg, c, r, Arow, b);
+            Ars = sel4(s, Arow[0], Arow[1], Arow[2], Arow[3]);
+            br = b;
+        }
+        return neg ? 2 : 0;
     }
 };
 
@@ -1520,8 +1581,9 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
     using SM = BlockSmem<ET, KIND, PREC, QUAD, CPQ, INL, OUTL>;
     constexpr int NAO = SM::NAO;
     constexpr int NS = CF::NS, NX = CF::NX, NA = CF::NA, NC = CF::NC;
-    static_assert(TPE == 1 || (INL == AOS && OUTL == AOS && CPQ < 2 && (TPE == NS || (TPE == 2 && ET == PRISM))),
-                  "several threads per element: element-contiguous, coefficient arrays; 2 (prisms) or NS");
+    static_assert(TPE == 1 || (INL == AOS && OUTL == AOS && CPQ < 2 &&
+                               (TPE == NS || (TPE == 2 && ET == PRISM) || (TPE == 16 && ET == TET))),
+                  "several threads per element: element-contiguous, coefficient arrays; 2 (prisms), NS or 16 (tets)");
     constexpr int EPW = 32 / TPE;            // elements (groups) per warp
     const int lane = threadIdx.x & 31;
     const int B = (blockDim.x >> 5) * EPW;   // elements per tile
@@ -1617,6 +1679,8 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
                 fl = run_elem<ET, KIND, PREC, QUAD, CPQ>(xs, cs, fn, A, b, poor);
             else if constexpr (TPE == 2)
                 fl = ElemMath<ET, KIND, PREC, QUAD, CPQ>::run_pair(xs, cs, A, b, poor, sub, pmask);
+            else if constexpr (ET == TET && TPE == 16)
+                fl = TetEntries<KIND, PREC, QUAD, CPQ>::run(xs, cs, A[0], b[0], poor, sub, pmask, lane - sub);
             else if constexpr (ET == TET)
                 fl = TetRows<KIND, PREC, QUAD, CPQ>::run(xs, cs, A, b[0], poor, sub, pmask, lane - sub);
             else
@@ -1643,6 +1707,10 @@ __device__ __forceinline__ bool process_tile(const ElemParams &p, int64_t e0, in
 #pragma unroll
         for (int j = 0; j < NS; ++j) sA[tid * NAO + NS * sub + j] = A[j];
         sB[tid * NS + sub] = b[0];
+    }
+    if (TPE == 16 && active) {
+        sA[tid * NAO + sub] = A[0];
+        if ((sub & 3) == 0) sB[tid * NS + (sub >> 2)] = b[0];
     }
     if (TPE == 1 && active) {
         // entry k_out of the written A^e: (r, s) row-major, or its upper triangle
@@ -1807,6 +1875,35 @@ __global__ void __launch_bounds__(256)
         const int64_t e0 = tile * B;
         const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
         if (!process_tile<ET, KIND, PREC, QUAD, CPQ, AOS, AOS, TPE>(p, e0, nb, smem, &bar, phase, &tm, &fn)) return;
+    }
+    if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Sixteen lanes per tetrahedron (TetEntries), element-contiguous input and
+// output: tiles of (blockDim.x / 32) x 2 elements, grid-stride over tiles.
+// ---------------------------------------------------------------------------
+template <int KIND, int PREC, int QUAD, int CPQ>
+__global__ void __launch_bounds__(256)
+    entry_kernel(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    const int B = (blockDim.x >> 5) * 2;
+    const int64_t ntiles = (p.n + B - 1) / B;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (p.skip_mod > 0 && tile % p.skip_mod == 0) {   // injected fault: no load, no store
+            if (threadIdx.x == 0) atomicOr(p.status, ST_SKIPPED_TILES);
+            continue;
+        }
+        const int64_t e0 = tile * B;
+        const int nb = static_cast<int>(p.n - e0 < B ? p.n - e0 : B);
+        if (!process_tile<TET, KIND, PREC, QUAD, CPQ, AOS, AOS, 16>(p, e0, nb, smem, &bar, phase, &tm, &fn)) return;
     }
     if (threadIdx.x < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }

@@ -104,11 +104,13 @@ static bool group_ok(fe_elem_type type, const fe_elem_args *a, int outl) {
     return a->coords_layout == FE_LAYOUT_AOS && outl == AOS && !a->ordering && cpq_of(a) < 2 && (type == FE_TET || type == FE_PRISM);
 }
 
-// Threads per element a key may use: 1; 2 (prisms) and NS (4 for tetrahedra, 6 for
-// prisms) with element-contiguous inputs and outputs, coefficient arrays, QSS.
+// Threads per element a key may use: 1; 2 (prisms), NS (4 for tetrahedra, 6 for
+// prisms) and 16 (tetrahedra) with element-contiguous inputs and outputs,
+// coefficient arrays, QSS.
 static bool tpe_ok(fe_elem_type type, const fe_elem_args *a, int outl, int tpe) {
     if (tpe == 1) return true;
     if (tpe == 2) return pair_ok(type, a, outl);
+    if (tpe == 16) return type == FE_TET && group_ok(type, a, outl);
     return tpe == ns_of(type) && group_ok(type, a, outl);
 }
 
@@ -117,6 +119,7 @@ static const void *main_kernel(fe_elem_type type, const fe_elem_args *a, int out
     if (tpe == 2) return pair_ok(type, a, outl) ? kernel_prism_pair(a->kind, a->prec, cpq) : nullptr;
     if (tpe > 2) {
         if (!tpe_ok(type, a, outl, tpe)) return nullptr;
+        if (tpe == 16) return kernel_entry_tet(a->kind, a->prec, a->quad, cpq);
         return type == FE_TET ? kernel_group_tet(a->kind, a->prec, a->quad, cpq) : kernel_group_prism(a->kind, a->prec, cpq);
     }
     if (tpe != 1) return nullptr;
@@ -604,7 +607,7 @@ static void load_tuning_cache(fe_ctx *ctx) {
         int block = 0, pers = 0, tpe = 1;
         if (!(ls >> dev >> key >> block >> pers)) continue;
         if (!(ls >> tpe)) tpe = 1;
-        if (dev == ctx->device_name && block > 0 && (tpe == 1 || tpe == 2 || tpe == 4 || tpe == 6) &&
+        if (dev == ctx->device_name && block > 0 && (tpe == 1 || tpe == 2 || tpe == 4 || tpe == 6 || tpe == 16) &&
             shape_threads(block, tpe))
             ctx->shapes[key] = Shape{block, pers, tpe};
     }
@@ -956,13 +959,13 @@ fe_status fe_set_launch_shape(fe_ctx *ctx, fe_elem_type type, const fe_elem_args
     fe_status st = fe_check_args(type, args, out);
     if (st != FE_OK) return st;
     const int B = shape->elems_per_block, t = shape->threads_per_elem;
-    const int threads = (t == 1 || t == 2 || t == 4 || t == 6) ? shape_threads(B, t) : 0;
+    const int threads = (t == 1 || t == 2 || t == 4 || t == 6 || t == 16) ? shape_threads(B, t) : 0;
     if (!threads || threads > (t == 1 ? max_block(type, args->prec) : 256) ||
         (shape->persistent != 0 && shape->persistent != 1))
         return set_error(ctx, FE_ERR_INVALID_ARG, "bad launch shape");
     if (!tpe_ok(type, args, out_mode(out), t))
-        return set_error(ctx, FE_ERR_UNSUPPORTED, "several threads per element: 2 for prisms, 4 for tetrahedra, 6 for "
-                                                  "prisms, with element-contiguous coordinates and outputs, "
+        return set_error(ctx, FE_ERR_UNSUPPORTED, "several threads per element: 2 for prisms, 4 or 16 for tetrahedra, "
+                                                  "6 for prisms, with element-contiguous coordinates and outputs, "
                                                   "coefficient arrays and the QSS order only");
     if (smem_bytes(type, args, out_mode(out), B) + kStaticSmem > ctx->max_smem_optin)
         return set_error(ctx, FE_ERR_UNSUPPORTED, "shared memory of this launch shape too large");
@@ -1003,10 +1006,10 @@ fe_status fe_tune(fe_ctx *ctx, fe_elem_type type, const fe_elem_args *a, const f
     float best = 1e30f;
     Shape best_shape = default_shape(type);
     // candidates: elements per tile x grid kind, and with element-contiguous data
-    // also several threads per element (2 or 6 per prism, 4 per tetrahedron):
-    // blocks of 64 up to the kernel's limit of threads
+    // also several threads per element (2 or 6 per prism, 4 or 16 per
+    // tetrahedron): blocks of 64 up to the kernel's limit of threads
     std::vector<Shape> cands;
-    for (int tpe : {1, 2, 4, 6}) {
+    for (int tpe : {1, 2, 4, 6, 16}) {
         if (!tpe_ok(type, a, out_mode(o), tpe)) continue;
         const int lim = tpe == 1 ? max_block(type, a->prec) : 256, epw = 32 / tpe;
         for (int warps = 2; warps * 32 <= lim; warps *= 2)

@@ -1,9 +1,10 @@
-"""Several threads per element, one row each (4 per tetrahedron, 6 per prism;
-the intra-element parallelism of Sec. 3.3 with the QSS loop order kept): every
+"""Several threads per element, one row each (4 per tetrahedron, 6 per prism) or
+one entry each (16 per tetrahedron; the intra-element parallelism of Sec. 3.3
+with the QSS loop order kept): every
 kind, precision form, rule and coefficient mode against the FP64 oracle on
 ragged tiles, persistent and not; the same flags as one thread per element;
 slivers and inverted elements through the fix-up; the launch-shape rules; the
-autotuner's choice among one, two, four and six threads per element."""
+autotuner's choice among one, two, four, six and sixteen threads per element."""
 import itertools
 
 import numpy as np
@@ -44,15 +45,14 @@ def _run(ctx, et, mesh, c, kind, quad, cpq, prec, block, tpe, persistent=0):
     return A.double().cpu().numpy(), b.double().cpu().numpy(), f.cpu().numpy(), c.astype(cdt).astype(np.float64)
 
 
-CASES = [(api.TET, q) for q in (api.QUAD_TET1, api.QUAD_TET4)] + [(api.PRISM, api.QUAD_PRISM6)]
+CASES = [(api.TET, q, t) for q in (api.QUAD_TET1, api.QUAD_TET4) for t in (4, 16)] + [(api.PRISM, api.QUAD_PRISM6, 6)]
 
 
-@pytest.mark.parametrize("et,quad", CASES)
+@pytest.mark.parametrize("et,quad,tpe", CASES)
 @pytest.mark.parametrize("kind,cpq,prec", list(itertools.product([api.POISSON, api.GENERIC], [0, 1], PRECS)))
-def test_rows_per_lane_match_oracle(ctx, et, quad, kind, cpq, prec):
+def test_rows_per_lane_match_oracle(ctx, et, quad, tpe, kind, cpq, prec):
     n = 1234 if et == api.TET else 777                 # ragged last tile
     mesh, c = make_inputs(et, kind, quad, cpq, n=n, seed=71 + kind + 2 * cpq)
-    tpe = NS_OF[et]
     epw = 32 // tpe
     for block, pers in ((8 * epw, 0), (2 * epw, 1)):
         An, bn, fn, cu = _run(ctx, et, mesh, c, kind, quad, cpq, prec, block, tpe, pers)
@@ -76,16 +76,17 @@ def test_rows_per_lane_slivers_and_inverted(ctx, prec):
     inv = np.arange(5, len(mesh), 97)
     mesh[inv] = mesh[inv][:, [0, 2, 1, 3]]
     _, c = make_inputs(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh=mesh, seed=75)
-    An, bn, fn, cu = _run(ctx, api.TET, mesh, c, api.GENERIC, api.QUAD_TET4, 0, prec, 64, 4)
-    Ao, bo, fo = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh, cu)
-    ea, eb = max_errors(An, bn, Ao, bo)
-    assert ea <= TOL[prec] and eb <= TOL[prec], (ea, eb)
-    assert np.array_equal(fn & 6, fo)
-    if prec != api.FP64:
-        q = oracle.quality(oracle.TET, mesh, n_threads=8)
-        clear = np.abs(q - 0.1) > 1e-3 * 0.1
-        assert np.array_equal((fn & 1).astype(bool)[clear], q[clear] < 0.1)
-        assert (fn & 1).sum() >= 0.5 * len(sl)
+    for tpe, block in ((4, 64), (16, 16)):
+        An, bn, fn, cu = _run(ctx, api.TET, mesh, c, api.GENERIC, api.QUAD_TET4, 0, prec, block, tpe)
+        Ao, bo, fo = run_oracle(api.TET, api.GENERIC, api.QUAD_TET4, 0, mesh, cu)
+        ea, eb = max_errors(An, bn, Ao, bo)
+        assert ea <= TOL[prec] and eb <= TOL[prec], (tpe, ea, eb)
+        assert np.array_equal(fn & 6, fo)
+        if prec != api.FP64:
+            q = oracle.quality(oracle.TET, mesh, n_threads=8)
+            clear = np.abs(q - 0.1) > 1e-3 * 0.1
+            assert np.array_equal((fn & 1).astype(bool)[clear], q[clear] < 0.1)
+            assert (fn & 1).sum() >= 0.5 * len(sl)
     # prisms: flattened and inverted ones
     pm, pc = make_inputs(api.PRISM, api.GENERIC, api.QUAD_PRISM6, 1, n=1500, seed=76)
     pm = pm.copy()
@@ -115,20 +116,20 @@ def test_rows_per_lane_shape_rules(ctx):
     kw = dict(kind=api.GENERIC, coef_mode=api.PER_ELEMENT, prec=api.FP32_MIXED)
     # the wrong group size for the type, or plane-major outputs: unsupported
     for (X, C, et, quad), tpe, block, outl in ((T, 6, 10, api.AOS), (P, 4, 16, api.AOS), (T, 4, 16, api.SOA),
-                                               (P, 6, 10, api.SOA)):
+                                               (P, 6, 10, api.SOA), (P, 16, 4, api.AOS), (T, 16, 4, api.SOA)):
         with pytest.raises(api.FeError) as e:
             ctx.set_shape(block, 0, et, X, C, quad=quad, layout=api.AOS, out_layout=outl, tpe=tpe, **kw)
         assert e.value.status == -6, (et, tpe, outl)
     # not whole warps of groups, or more than 256 threads
-    for (X, C, et, quad), tpe, block in ((T, 4, 12, ), (T, 4, 72), (P, 6, 12), (P, 6, 45)):
+    for (X, C, et, quad), tpe, block in ((T, 4, 12, ), (T, 4, 72), (P, 6, 12), (P, 6, 45), (T, 16, 3), (T, 16, 18)):
         with pytest.raises(api.FeError) as e:
             ctx.set_shape(block, 0, et, X, C, quad=quad, layout=api.AOS, out_layout=api.AOS, tpe=tpe, **kw)
         assert e.value.status == -1, (et, tpe, block)
 
 
 def test_tuner_considers_rows_per_lane(ctx):
-    """The autotuner's candidates include four threads per tetrahedron and two and
-    six per prism; whatever it keeps gives oracle-accurate results."""
+    """The autotuner's candidates include four and sixteen threads per tetrahedron
+    and two and six per prism; whatever it keeps gives oracle-accurate results."""
     for et, quad, cpq in ((api.TET, api.QUAD_TET4, 0), (api.PRISM, api.QUAD_PRISM6, 1)):
         mesh, c = make_inputs(et, api.GENERIC, quad, cpq, n=20000 if et == api.TET else 8000, seed=80)
         for prec in PRECS:
@@ -138,7 +139,7 @@ def test_tuner_considers_rows_per_lane(ctx):
             kw = dict(kind=api.GENERIC, quad=quad, coef_mode=api.PER_QPOINT if cpq else api.PER_ELEMENT, prec=prec,
                       layout=api.AOS, out_layout=api.AOS)
             block, pers, tpe = ctx.tune(et, X, C, **kw)
-            assert tpe in ((1, 4) if et == api.TET else (1, 2, 6)) and pers in (0, 1)
+            assert tpe in ((1, 4, 16) if et == api.TET else (1, 2, 6)) and pers in (0, 1)
             A, b, f = ctx.integrate(et, X, C, **kw)
             ctx.sync()
             Ao, bo, _ = run_oracle(et, api.GENERIC, quad, cpq, mesh, c.astype(cdt).astype(np.float64))
