@@ -72,10 +72,24 @@ def test_generic_tets_6M_mixed_sampled(ctx):
 
 
 def test_generic_tets_6M_fp64_sampled(ctx):
+    """The benchmark's step: the default shape, the autotuner's choice (as the
+    benchmark times it) and the two tile sizes the tuner picks between."""
     mesh = meshgen.tet_cube_mesh(100, 0.2, seed=meshgen.SEED_BASE + 2)
     c = meshgen.generic_coefs(len(mesh), 1, seed=meshgen.SEED_BASE + 2)
     A, b, f, cu = _run_aos(ctx, api.TET, mesh, c, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP64, tune=False)
     _check_sample(api.TET, A, b, f, mesh, cu, api.GENERIC, oracle.Q_TET4, 0, TOL[api.FP64], 2)
+    A, b, f, cu = _run_aos(ctx, api.TET, mesh, c, api.GENERIC, api.QUAD_TET4, api.PER_ELEMENT, api.FP64, tune=True)
+    _check_sample(api.TET, A, b, f, mesh, cu, api.GENERIC, oracle.Q_TET4, 0, TOL[api.FP64], 3)
+    n = len(mesh)
+    X = torch.from_numpy(np.ascontiguousarray(mesh)).cuda()
+    C = torch.from_numpy(np.ascontiguousarray(c.reshape(n, -1))).cuda()
+    kw = dict(kind=api.GENERIC, quad=api.QUAD_TET4, coef_mode=api.PER_ELEMENT, prec=api.FP64, layout=api.AOS,
+              out_layout=api.AOS)
+    for block, seed in ((64, 4), (128, 5)):
+        ctx.set_shape(block, 0, api.TET, X, C, **kw)
+        A, b, f = ctx.integrate(api.TET, X, C, **kw)
+        ctx.sync()
+        _check_sample(api.TET, A, b, f, mesh, cu, api.GENERIC, oracle.Q_TET4, 0, TOL[api.FP64], seed)
 
 
 def test_generic_prisms_2M_mixed_sampled(ctx):
