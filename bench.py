@@ -484,7 +484,8 @@ def run_native(args):
         wl_name = {"fp64": WORKLOAD, "mixed": MIXED_WORKLOAD}.get(args.form, MESH + ", double-word form")
         if lap:
             wl_name = MESH.split(", TET4")[0] + ", Laplace operator, TET1, d^0 = 1, " + args.form + " form"
-        kernel_name = (f"{'elem_kernel_f64t' if args.form == 'fp64' else 'elem_kernel'}<TET,{'POISSON' if lap else 'GENERIC'},{PREC_TAG[args.form]},"
+        kname = {"fp64": "elem_kernel_f64t", "dw": "elem_kernel_dwt"}.get(args.form, "elem_kernel")
+        kernel_name = (f"{kname}<TET,{'POISSON' if lap else 'GENERIC'},{PREC_TAG[args.form]},"
                        f"{'TET1' if lap else 'TET4'},per-element,AOS,AOS>")
         tag = f"tet_{'poisson_tet1' if lap else 'generic'}_{args.form}_aos"
     else:

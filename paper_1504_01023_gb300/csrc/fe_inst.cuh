@@ -10,6 +10,10 @@
 #define FE_F64T_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                  \
     if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
         return reinterpret_cast<const void *>(&fe::elem_kernel_f64t<KD, QUAD, CP, IL, OL>);
+// Double-word tetrahedra: the register-capped variant of the main kernel for
+// per-element coefficients (dw_tet_kernel).
+#define FE_DWT_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                   \
+    if (kind == KD && cpq == CP && inl == IL && outl == OL) return fe::dw_tet_kernel<KD, QUAD, CP, IL, OL>();
 #define FE_FIX_CASE(ET, PREC, QUAD, KD, CP, IL, OL)                                   \
     if (kind == KD && cpq == CP && inl == IL && outl == OL)                          \
         return reinterpret_cast<const void *>(&fe::fixup_kernel<ET, KD, PREC, QUAD, CP, IL, OL>);

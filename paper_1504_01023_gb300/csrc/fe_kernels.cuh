@@ -1818,6 +1818,25 @@ __global__ void __launch_bounds__(512) __maxnreg__(KIND == POISSON ? 80 : 104)
     elem_tiles<TET, KIND, FP64, QUAD, CPQ, INL, OUTL>(p, &tm, &fn);
 }
 
+// The same kernel for double-word tetrahedra with per-element coefficients and
+// fewer registers per thread: generic kind 72 (6M tetrahedra 7.83 -> 8.46 Gelem/s
+// against 88 registers; 80 and 64 measured 8.28 and 7.62), Laplace kind 48 (6M
+// TET1 16.99 -> 19.44 Gelem/s against 60; 56 and 40 measured 18.37 and 17.28):
+// more resident warps cover the chains of dependent double-word operations. Both
+// bounds reach ptxas as for elem_kernel_f64t. Per-point coefficients keep
+// elem_kernel (at 72 registers the generic kind spilled 3.5 KB).
+template <int KIND, int QUAD, int CPQ, int INL, int OUTL>
+__global__ void __launch_bounds__(256) __maxnreg__(KIND == POISSON ? 48 : 72)
+    elem_kernel_dwt(const ElemParams p, const __grid_constant__ TmaMaps tm, const __grid_constant__ CoefFn fn) {
+    elem_tiles<TET, KIND, DWORD, QUAD, CPQ, INL, OUTL>(p, &tm, &fn);
+}
+template <int KIND, int QUAD, int CPQ, int INL, int OUTL> const void *dw_tet_kernel() {
+    if constexpr (CPQ == 0)
+        return reinterpret_cast<const void *>(&elem_kernel_dwt<KIND, QUAD, CPQ, INL, OUTL>);
+    else
+        return reinterpret_cast<const void *>(&elem_kernel<TET, KIND, DWORD, QUAD, CPQ, INL, OUTL>);
+}
+
 // ---------------------------------------------------------------------------
 // Prisms with two threads per element (element-contiguous input and output):
 // tiles of blockDim.x / 2 elements, grid-stride over tiles.

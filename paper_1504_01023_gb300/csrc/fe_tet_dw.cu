@@ -9,7 +9,7 @@ const void *kernel_fixup_tet_dw4(int kind, int cpq, int inl, int outl);
 const void *kernel_tet_dw(int kind, int quad, int cpq, int inl, int outl) {
     if (inl == INDEXED) return kernel_tet_dw_idx(kind, quad, cpq, outl);
     if (quad == Q_TET4) return kernel_tet_dw4(kind, cpq, inl, outl);
-    if (quad == Q_TET1) { FE_ALL16(FE_ELEM_CASE, TET, DWORD, Q_TET1) FE_PK8(FE_ELEM_CASE, TET, DWORD, Q_TET1) FE_FN2(FE_ELEM_CASE, 0, TET, DWORD, Q_TET1) FE_FN2(FE_ELEM_CASE, 1, TET, DWORD, Q_TET1) }
+    if (quad == Q_TET1) { FE_ALL16(FE_DWT_CASE, TET, DWORD, Q_TET1) FE_PK8(FE_DWT_CASE, TET, DWORD, Q_TET1) FE_FN2(FE_ELEM_CASE, 0, TET, DWORD, Q_TET1) FE_FN2(FE_ELEM_CASE, 1, TET, DWORD, Q_TET1) }
     return nullptr;
 }
 const void *kernel_fixup_tet_dw(int kind, int quad, int cpq, int inl, int outl) {
